@@ -1,0 +1,244 @@
+/*
+ * mln.h -- C-ABI of the GB300 (sm_103a) Maxwell-Liouville-von Neumann solver.
+ *
+ * The library advances the one-dimensional Maxwell-Liouville-von Neumann
+ * (MLN) equations of Riesch & Jirauschek (arXiv:1710.09799):
+ *   - Maxwell's curl equations for E_z and H_y with the polarisation current
+ *     dP/dt as source (Sec. 2, Eq. 1), on the staggered FDTD grid of Fig. 1;
+ *   - the Liouville-von Neumann equation of every medium cell in the adjoint
+ *     (SU(N), pseudospin) representation, d/dt d = (M + U E_z) d + d_eq
+ *     (Sec. 3, Eq. 14), advanced by the symmetric Strang splitting of
+ *     Sec. 4.1 (Eq. 23) with the interaction exponential exp(U E_z dt) done by
+ *     the diagonalisation method of Sec. 4.2 (Eq. 25) in its real form
+ *     (the matrix T of Eq. 26): per cell only scalar sin/cos and small dense
+ *     products;
+ *   - dP/dt = N_a/2 v^T (M d + d_eq) (Sec. 3, Eq. 17).
+ * One time step: H^{n+1/2} from E^n; d^{n-1/2} -> d^{n+1/2} with E^n;
+ * dP/dt^{n+1/2}; E^{n+1} from H^{n+1/2} and dP/dt^{n+1/2}; then the source.
+ *
+ * Conventions for every call:
+ *   - All entry points return an mln_status; no exception crosses the ABI.
+ *     The context keeps a message with details (mln_last_error).
+ *   - Complex matrices are arrays of interleaved (re, im) doubles, row-major.
+ *     A superoperator is an (N*N) x (N*N) complex matrix acting on the
+ *     row-major vectorisation vec(X)[j*N + k] = X[j][k].
+ *   - Units are SI: J, C*m, 1/s, V/m, A/m, m, s.
+ *   - Device buffers passed to mln_create are owned by the caller and must
+ *     outlive the context. The context owns a second copy of the state (the
+ *     steps alternate between the two), a few hundred bytes of flags and the
+ *     output conversion tables; mln_destroy frees them.
+ *   - Work is queued on the CUDA stream given at creation. Calls that return
+ *     data to the host synchronise that stream.
+ */
+#ifndef MLN_H
+#define MLN_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum mln_status {
+    MLN_OK = 0,
+    MLN_EINVAL = 1,        /* invalid argument or parameter set */
+    MLN_ENOMEM = 2,        /* host or device allocation failed */
+    MLN_ECUDA = 3,         /* a CUDA runtime call failed */
+    MLN_ENUMERIC = 4,      /* host set-up failed a numerical check */
+    MLN_ETIMEOUT = 5,      /* a bounded device wait gave up */
+    MLN_EUNSUPPORTED = 6,  /* valid but not built (e.g. N outside the compiled range) */
+    MLN_ENONFINITE = 7     /* the device saw a non-finite field value */
+} mln_status;
+
+enum { MLN_BC_PERIODIC = 0, MLN_BC_OPEN = 1 };
+enum { MLN_SRC_NONE = 0, MLN_SRC_HARD = 1, MLN_SRC_SOFT = 2 };
+enum { MLN_FP64 = 0, MLN_FP32 = 1 };
+/* MLN_FORM_STRANG applies Eq. 23 literally: A0, T^T, plane rotations, T, A0.
+ * MLN_FORM_ROTATED keeps each cell's vector in the eigenbasis of U between
+ * steps (p = T^T (A0 d + b)), so that a step is rotate, dP/dt, p <- C p + c'
+ * with C = T^T A0^2 T: the same arithmetic result, reassociated. */
+enum { MLN_FORM_STRANG = 0, MLN_FORM_ROTATED = 1 };
+
+#define MLN_MIN_N 2
+#define MLN_MAX_N 6
+
+/*
+ * Problem description. Every pointer is read during mln_create only.
+ *   N             number of levels, MLN_MIN_N..MLN_MAX_N; adjoint dimension D = N*N-1.
+ *   precision     MLN_FP64 or MLN_FP32: type of the device state, fields and
+ *                 propagator arithmetic. Set-up is always FP64.
+ *   form          MLN_FORM_STRANG or MLN_FORM_ROTATED.
+ *   H0            N x N complex Hermitian, J (Eq. 2, H = H0 - mu E_z).
+ *   mu            N x N complex Hermitian dipole operator, C m.
+ *   G             (N*N) x (N*N) complex relaxation superoperator, 1/s; it must
+ *                 preserve trace and Hermiticity (Eq. 2). NULL: no relaxation.
+ *   rho0          N x N complex initial density matrix of every medium cell:
+ *                 Hermitian, unit trace, positive semidefinite.
+ *   N_a           density of quantum systems, m^-3 (Eq. 3).
+ *   n_cells       number of E_z cells (>= 4).
+ *   medium_begin, medium_end  the medium occupies cells [begin, end).
+ *   dx, dt        grid spacing (m) and time step (s); c dt / dx <= 1.
+ *   eps_r, mu_r, sigma  relative permittivity and permeability (> 0) and
+ *                 conductivity (>= 0, S/m) of the whole grid (Eq. 1).
+ *   boundary      MLN_BC_PERIODIC: ring. MLN_BC_OPEN: E_z at cell 0 changes
+ *                 only through a hard source at cell 0, the right end uses the
+ *                 first-order Mur absorbing condition; the medium must end at
+ *                 least one cell before the last cell.
+ *   source_kind, source_cell  MLN_SRC_HARD replaces, MLN_SRC_SOFT adds the
+ *                 sample to E_z at source_cell after the E_z update; sample k
+ *                 of an mln_step call belongs to the step producing E^{n+1},
+ *                 n = the context's step count at the call + k.
+ *   block_steps   steps fused into one kernel launch (temporal blocking);
+ *                 0 picks a default. 1..64.
+ *   tile_cells    cells written by one thread block; 0 picks a default.
+ */
+typedef struct mln_params {
+    int32_t N;
+    int32_t precision;
+    int32_t form;
+    int32_t boundary;
+    int32_t source_kind;
+    int32_t block_steps;
+    int32_t tile_cells;
+    int32_t reserved0;
+    const double *H0;
+    const double *mu;
+    const double *G;
+    const double *rho0;
+    double N_a;
+    int64_t n_cells;
+    int64_t medium_begin;
+    int64_t medium_end;
+    int64_t source_cell;
+    double dx;
+    double dt;
+    double eps_r;
+    double mu_r;
+    double sigma;
+} mln_params;
+
+typedef struct mln_ctx mln_ctx;
+
+/*
+ * Sizes of the caller-owned device buffers for a parameter set:
+ *   state_bytes  the per-cell state of the medium, structure of arrays:
+ *                element j of medium cell m (cell medium_begin + m) is at
+ *                index j * stride + m, j < D, stride = n_medium rounded up to
+ *                a multiple of 64; real type = precision.
+ *   field_bytes  one of E_z or H_y: n_cells reals (H_y[i] sits at i + 1/2).
+ * Returns MLN_EINVAL for an invalid parameter set (same checks as mln_create).
+ */
+mln_status mln_query_buffers(const mln_params *p, size_t *state_bytes, size_t *field_bytes);
+
+/*
+ * Validate p, compute the FP64 set-up of Secs. 3-4 (generators, M, U, d_eq,
+ * v, A0 = exp(M dt/2) with its affine offset, the real eigenbasis T and
+ * rotation rates of U, polarisation coefficients), allocate the context's
+ * alternate state, and queue on `stream` (a cudaStream_t; NULL = legacy
+ * default stream) the initial medium state built from rho0 into d_state.
+ * Ez and Hy are used as they are: the caller fills them with E^0 and
+ * H^{-1/2} (zeros, noise, ...). d_state, Ez and Hy are device pointers with
+ * the sizes of mln_query_buffers, 16-byte aligned.
+ * Errors: MLN_EINVAL (bad parameters: N range, Hermiticity to 1e-12
+ * relative, rho0 trace/positivity, G trace/Hermiticity preservation, ranges,
+ * dt, Courant number), MLN_ENUMERIC (eigen-decomposition residual above
+ * 1e-12), MLN_EUNSUPPORTED, MLN_ENOMEM, MLN_ECUDA. On error *out is NULL.
+ */
+mln_status mln_create(const mln_params *p, void *d_state, void *Ez, void *Hy, void *stream,
+                      mln_ctx **out);
+
+/*
+ * Queue n_steps time steps (>= 0) on the context's stream. src is NULL (no
+ * source) or a device array of n_steps doubles (see source_kind). When the
+ * call returns, the queued work leaves the current state in the caller's
+ * buffers. Device-side problems (non-finite E_z) are reported by the next
+ * mln_sync or read call.
+ */
+mln_status mln_step(mln_ctx *ctx, int64_t n_steps, const double *src);
+
+/* Wait for the queued work; report device-side problems (MLN_ENONFINITE). */
+mln_status mln_sync(mln_ctx *ctx);
+
+/* Number of time steps taken so far. */
+int64_t mln_step_count(const mln_ctx *ctx);
+
+/* Number of fused-step kernel launches queued so far, and the launch shape
+ * in use: steps fused per launch and cells written per thread block. */
+int64_t mln_launch_count(const mln_ctx *ctx);
+mln_status mln_launch_shape(const mln_ctx *ctx, int32_t *block_steps, int32_t *tile_cells,
+                            int32_t *threads_per_block);
+
+/*
+ * Copy E_z^n and H_y^{n-1/2} (n = step count) to host arrays of n_cells
+ * doubles each (either may be NULL). Synchronises.
+ */
+mln_status mln_get_fields(mln_ctx *ctx, double *Ez_host, double *Hy_host);
+
+/*
+ * Density matrices rho^{n-1/2} of medium cells [cell0, cell0 + count) (grid
+ * cell indices) into rho_host, count * N * N complex, converted on the device
+ * by rho = I/N + 1/2 sum_j d_j s_j (Eq. 6). Synchronises.
+ */
+mln_status mln_get_rho(mln_ctx *ctx, int64_t cell0, int64_t count, double *rho_host);
+
+/* Populations rho_ll of medium cells [cell0, cell0 + count): count * N doubles. */
+mln_status mln_get_populations(mln_ctx *ctx, int64_t cell0, int64_t count, double *pop_host);
+
+/*
+ * Checkpoint / resume in a precision- and form-independent layout:
+ * d_host holds n_medium * D doubles, cell-major (d of medium cell m at
+ * m * D .. m * D + D - 1, adjoint vector of Eq. 6), Ez_host and Hy_host
+ * n_cells doubles each. Either call may take NULL for parts it should skip.
+ * save synchronises; load queues the host-to-device copies on the stream and
+ * returns after they are complete.
+ */
+mln_status mln_save_state(mln_ctx *ctx, double *d_host, double *Ez_host, double *Hy_host);
+mln_status mln_load_state(mln_ctx *ctx, const double *d_host, const double *Ez_host,
+                          const double *Hy_host);
+
+/* Free the context (NULL-safe). Caller buffers are not touched. */
+void mln_destroy(mln_ctx *ctx);
+
+const char *mln_status_string(mln_status s);
+/* Last error message of a context (empty string if none; "" for NULL). */
+const char *mln_last_error(const mln_ctx *ctx);
+/* Last error message of a failed mln_create or mln_setup_host on this thread. */
+const char *mln_create_error(void);
+
+/*
+ * Host-only inspection of the FP64 set-up (no GPU needed). Arrays are
+ * row-major doubles with the sizes given; the caller provides capacity for
+ * D_max = MLN_MAX_N^2 - 1.
+ *   M, U, A0, T, C: D x D;  d_eq, v, b, w, d0: D;  theta: q = N(N-1)/2
+ *   rotation rates (rad s^-1 per V/m: the plane k of T turns by
+ *   theta_k E dt in a step); c: scalar; gen: D x N x N complex generators
+ *   (2 * D * N * N doubles, Sec. 3 ordering u_jk, v_jk, w_l).
+ */
+typedef struct mln_setup {
+    int32_t N, D, q, reserved;
+    double M[(MLN_MAX_N * MLN_MAX_N - 1) * (MLN_MAX_N * MLN_MAX_N - 1)];
+    double U[(MLN_MAX_N * MLN_MAX_N - 1) * (MLN_MAX_N * MLN_MAX_N - 1)];
+    double A0[(MLN_MAX_N * MLN_MAX_N - 1) * (MLN_MAX_N * MLN_MAX_N - 1)];
+    double T[(MLN_MAX_N * MLN_MAX_N - 1) * (MLN_MAX_N * MLN_MAX_N - 1)];
+    double C[(MLN_MAX_N * MLN_MAX_N - 1) * (MLN_MAX_N * MLN_MAX_N - 1)];
+    double d_eq[MLN_MAX_N * MLN_MAX_N - 1];
+    double v[MLN_MAX_N * MLN_MAX_N - 1];
+    double b[MLN_MAX_N * MLN_MAX_N - 1];
+    double w[MLN_MAX_N * MLN_MAX_N - 1];
+    double d0[MLN_MAX_N * MLN_MAX_N - 1];
+    double theta[MLN_MAX_N * (MLN_MAX_N - 1) / 2];
+    double c;
+    double gen[2 * (MLN_MAX_N * MLN_MAX_N - 1) * MLN_MAX_N * MLN_MAX_N];
+} mln_setup;
+
+mln_status mln_setup_host(const mln_params *p, mln_setup *out);
+
+/* Library version string. */
+const char *mln_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MLN_H */

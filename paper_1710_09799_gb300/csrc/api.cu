@@ -1,0 +1,536 @@
+// C-ABI of the MLN solver: context life cycle, step loop and state I/O.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "dispatch.cuh"
+#include "mln.h"
+#include "setup.h"
+
+struct mln_ctx {
+    mln_params p{};
+    mln::Setup s;
+    int D = 0;
+    int64_t n_med = 0, stride = 0;
+    size_t rsz = 8;                 // bytes per device real
+    size_t state_bytes = 0, field_bytes = 0;
+    void *st[2] = {nullptr, nullptr};  // [0] caller's buffer, [1] context-owned alternate
+    void *E[2] = {nullptr, nullptr};
+    void *H[2] = {nullptr, nullptr};
+    cudaStream_t stream = nullptr;
+    unsigned int *flags = nullptr;
+    std::vector<unsigned char> consts;
+    int K = 16, tile = 0, threads = 0;
+    int64_t steps = 0, launches = 0;
+    // output tables (FP64, device): rows x D matrix followed by rows offsets
+    double *tab_rho = nullptr, *tab_pop = nullptr, *tab_d = nullptr, *tab_in = nullptr;
+    void *scratch = nullptr;
+    size_t scratch_bytes = 0;
+    std::string err;
+};
+
+namespace {
+
+thread_local std::string g_create_err;
+
+const char *kVersion = "mln-gb300 0.1 (sm_103a)";
+
+#define MLN_CK(ctx, call)                                                       \
+    do {                                                                        \
+        cudaError_t e_ = (call);                                                \
+        if (e_ != cudaSuccess) {                                                \
+            (ctx)->err = std::string(#call) + ": " + cudaGetErrorString(e_);    \
+            return MLN_ECUDA;                                                   \
+        }                                                                       \
+    } while (0)
+
+// out[c * rows + r] = tab[rows * D + r] + sum_k tab[r * D + k] * state[k * stride + m0 + c]
+template <typename R>
+__global__ void state_to_rows(const R *__restrict__ state, int64_t stride, int64_t m0, int64_t count, int D,
+                              int rows, const double *__restrict__ tab, double *__restrict__ out) {
+    int64_t c = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+    if (c >= count) return;
+    for (int r = 0; r < rows; ++r) {
+        double acc = tab[rows * D + r];
+        for (int k = 0; k < D; ++k) acc += tab[r * D + k] * static_cast<double>(state[k * stride + m0 + c]);
+        out[c * rows + r] = acc;
+    }
+}
+
+// state[k * stride + c] = tab[D * D + k] + sum_j tab[k * D + j] * in[c * D + j]
+template <typename R>
+__global__ void rows_to_state(const double *__restrict__ in, int64_t count, int D, const double *__restrict__ tab,
+                              R *__restrict__ state, int64_t stride) {
+    int64_t c = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+    if (c >= count) return;
+    for (int k = 0; k < D; ++k) {
+        double acc = tab[D * D + k];
+        for (int j = 0; j < D; ++j) acc += tab[k * D + j] * in[c * D + j];
+        state[k * stride + c] = static_cast<R>(acc);
+    }
+}
+
+// Every medium cell starts from the same state vector v (D doubles).
+template <typename R>
+__global__ void fill_state(R *__restrict__ state, int64_t stride, int64_t count, int D, const double *__restrict__ v) {
+    int64_t c = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+    if (c >= count) return;
+    for (int k = 0; k < D; ++k) state[k * stride + c] = static_cast<R>(v[k]);
+}
+
+__global__ void f32_to_f64(const float *__restrict__ in, double *__restrict__ out, int64_t n) {
+    int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+    if (i < n) out[i] = in[i];
+}
+
+__global__ void f64_to_f32(const double *__restrict__ in, float *__restrict__ out, int64_t n) {
+    int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+    if (i < n) out[i] = static_cast<float>(in[i]);
+}
+
+inline unsigned grid_for(int64_t n, int bs) { return static_cast<unsigned>((n + bs - 1) / bs); }
+
+mln_status ensure_scratch(mln_ctx *c, size_t bytes) {
+    if (c->scratch_bytes >= bytes) return MLN_OK;
+    if (c->scratch) cudaFree(c->scratch);
+    c->scratch = nullptr;
+    c->scratch_bytes = 0;
+    MLN_CK(c, cudaMalloc(&c->scratch, bytes));
+    c->scratch_bytes = bytes;
+    return MLN_OK;
+}
+
+// Upload a rows x D table and its offsets (row-major, offsets after the matrix).
+mln_status upload_table(mln_ctx *c, double **dst, const std::vector<double> &mat, const std::vector<double> &off) {
+    std::vector<double> buf(mat);
+    buf.insert(buf.end(), off.begin(), off.end());
+    MLN_CK(c, cudaMalloc(dst, buf.size() * sizeof(double)));
+    MLN_CK(c, cudaMemcpy(*dst, buf.data(), buf.size() * sizeof(double), cudaMemcpyHostToDevice));
+    return MLN_OK;
+}
+
+void pick_launch_shape(mln_ctx *c) {
+    int dev = 0, sms = 152;
+    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    c->K = c->p.block_steps > 0 ? c->p.block_steps : 16;
+    const int64_t n = c->p.n_cells;
+    int tile = c->p.tile_cells;
+    if (tile <= 0) {
+        // one tile per SM (or per SM multiple) while a block stays <= kMaxThreads threads
+        int64_t ntiles = sms;
+        tile = static_cast<int>((n + ntiles - 1) / ntiles);
+        while (tile + 2 * c->K > mln::kMaxThreads) {
+            ntiles += sms;
+            tile = static_cast<int>((n + ntiles - 1) / ntiles);
+        }
+        tile = std::max(tile, 1);
+    }
+    if (tile > n) tile = static_cast<int>(n);
+    if (tile + 2 * c->K > mln::kMaxThreads) tile = mln::kMaxThreads - 2 * c->K;
+    c->tile = tile;
+    c->threads = (tile + 2 * c->K + 31) / 32 * 32;
+}
+
+template <typename R>
+mln_status run_steps(mln_ctx *c, int64_t n_steps, const double *src) {
+    const int64_t ntiles = (c->p.n_cells + c->tile - 1) / c->tile;
+    const double eps = mln::kEps0 * c->p.eps_r, mu = mln::kMu0 * c->p.mu_r;
+    const double sg = c->p.sigma * c->p.dt / (2.0 * eps);
+    const double cv = 1.0 / std::sqrt(eps * mu);
+    mln::BlockArgs<R> a{};
+    a.flags = c->flags;
+    a.n_cells = c->p.n_cells;
+    a.mb = c->p.medium_begin;
+    a.me = c->p.medium_end;
+    a.stride = c->stride;
+    a.source_cell = c->p.source_cell;
+    a.halo = c->K;
+    a.tile = c->tile;
+    a.boundary = c->p.boundary;
+    a.source_kind = c->p.source_kind;
+    a.ch = static_cast<R>(c->p.dt / (mu * c->p.dx));
+    a.ca = static_cast<R>((1.0 - sg) / (1.0 + sg));
+    a.cb = static_cast<R>((c->p.dt / eps) / (1.0 + sg));
+    a.inv_dx = static_cast<R>(1.0 / c->p.dx);
+    a.kappa = static_cast<R>((cv * c->p.dt - c->p.dx) / (cv * c->p.dt + c->p.dx));
+    const size_t smem = 2 * static_cast<size_t>(c->threads) * sizeof(R);
+    int cur = 0;
+    for (int64_t done = 0; done < n_steps;) {
+        int ns = static_cast<int>(std::min<int64_t>(c->K, n_steps - done));
+        a.E_in = static_cast<const R *>(c->E[cur]);
+        a.H_in = static_cast<const R *>(c->H[cur]);
+        a.s_in = static_cast<const R *>(c->st[cur]);
+        a.E_out = static_cast<R *>(c->E[cur ^ 1]);
+        a.H_out = static_cast<R *>(c->H[cur ^ 1]);
+        a.s_out = static_cast<R *>(c->st[cur ^ 1]);
+        a.src = (src && c->p.source_kind != MLN_SRC_NONE) ? src + done : nullptr;
+        a.nsteps = ns;
+        cudaError_t e = mln::launch_block(c->p.N, c->p.form, a, c->consts, dim3(static_cast<unsigned>(ntiles)),
+                                          dim3(c->threads), smem, c->stream);
+        if (e != cudaSuccess) {
+            c->err = std::string("step kernel launch: ") + cudaGetErrorString(e);
+            return MLN_ECUDA;
+        }
+        ++c->launches;
+        cur ^= 1;
+        done += ns;
+    }
+    if (cur == 1) {
+        MLN_CK(c, cudaMemcpyAsync(c->st[0], c->st[1], c->state_bytes, cudaMemcpyDeviceToDevice, c->stream));
+        MLN_CK(c, cudaMemcpyAsync(c->E[0], c->E[1], c->field_bytes, cudaMemcpyDeviceToDevice, c->stream));
+        MLN_CK(c, cudaMemcpyAsync(c->H[0], c->H[1], c->field_bytes, cudaMemcpyDeviceToDevice, c->stream));
+    }
+    return MLN_OK;
+}
+
+// Rows of the output table for medium cells [m0, m0 + count) into host memory.
+mln_status read_rows(mln_ctx *c, int64_t m0, int64_t count, const double *tab, int rows, double *host) {
+    if (count == 0) return MLN_OK;
+    mln_status st = ensure_scratch(c, static_cast<size_t>(count) * rows * sizeof(double));
+    if (st != MLN_OK) return st;
+    double *out = static_cast<double *>(c->scratch);
+    if (c->p.precision == MLN_FP64)
+        state_to_rows<double><<<grid_for(count, 128), 128, 0, c->stream>>>(
+            static_cast<const double *>(c->st[0]), c->stride, m0, count, c->D, rows, tab, out);
+    else
+        state_to_rows<float><<<grid_for(count, 128), 128, 0, c->stream>>>(
+            static_cast<const float *>(c->st[0]), c->stride, m0, count, c->D, rows, tab, out);
+    MLN_CK(c, cudaGetLastError());
+    MLN_CK(c, cudaMemcpyAsync(host, out, static_cast<size_t>(count) * rows * sizeof(double), cudaMemcpyDeviceToHost,
+                              c->stream));
+    MLN_CK(c, cudaStreamSynchronize(c->stream));
+    return MLN_OK;
+}
+
+mln_status read_field(mln_ctx *c, const void *dev, double *host) {
+    const int64_t n = c->p.n_cells;
+    if (c->p.precision == MLN_FP64) {
+        MLN_CK(c, cudaMemcpyAsync(host, dev, n * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    } else {
+        mln_status st = ensure_scratch(c, n * sizeof(double));
+        if (st != MLN_OK) return st;
+        f32_to_f64<<<grid_for(n, 256), 256, 0, c->stream>>>(static_cast<const float *>(dev),
+                                                               static_cast<double *>(c->scratch), n);
+        MLN_CK(c, cudaGetLastError());
+        MLN_CK(c, cudaMemcpyAsync(host, c->scratch, n * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    }
+    MLN_CK(c, cudaStreamSynchronize(c->stream));
+    return MLN_OK;
+}
+
+mln_status write_field(mln_ctx *c, void *dev, const double *host) {
+    const int64_t n = c->p.n_cells;
+    if (c->p.precision == MLN_FP64) {
+        MLN_CK(c, cudaMemcpyAsync(dev, host, n * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    } else {
+        mln_status st = ensure_scratch(c, n * sizeof(double));
+        if (st != MLN_OK) return st;
+        MLN_CK(c, cudaMemcpyAsync(c->scratch, host, n * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+        f64_to_f32<<<grid_for(n, 256), 256, 0, c->stream>>>(static_cast<const double *>(c->scratch),
+                                                               static_cast<float *>(dev), n);
+        MLN_CK(c, cudaGetLastError());
+    }
+    MLN_CK(c, cudaStreamSynchronize(c->stream));
+    return MLN_OK;
+}
+
+mln_status check_cells(mln_ctx *c, int64_t cell0, int64_t count, int64_t *m0) {
+    if (count < 0 || cell0 < c->p.medium_begin || cell0 + count > c->p.medium_end) {
+        c->err = "cell range outside the medium";
+        return MLN_EINVAL;
+    }
+    *m0 = cell0 - c->p.medium_begin;
+    return MLN_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *mln_version(void) { return kVersion; }
+
+const char *mln_status_string(mln_status s) {
+    switch (s) {
+    case MLN_OK: return "ok";
+    case MLN_EINVAL: return "invalid argument";
+    case MLN_ENOMEM: return "out of memory";
+    case MLN_ECUDA: return "CUDA error";
+    case MLN_ENUMERIC: return "numerical set-up check failed";
+    case MLN_ETIMEOUT: return "device wait timed out";
+    case MLN_EUNSUPPORTED: return "unsupported configuration";
+    case MLN_ENONFINITE: return "non-finite field value";
+    }
+    return "unknown status";
+}
+
+const char *mln_last_error(const mln_ctx *ctx) { return ctx ? ctx->err.c_str() : ""; }
+
+const char *mln_create_error(void) { return g_create_err.c_str(); }
+
+mln_status mln_query_buffers(const mln_params *p, size_t *state_bytes, size_t *field_bytes) {
+    if (!p) return MLN_EINVAL;
+    std::string err;
+    mln_status st = mln::validate(*p, err);
+    if (st != MLN_OK) {
+        g_create_err = err;
+        return st;
+    }
+    size_t r = p->precision == MLN_FP64 ? 8 : 4;
+    const int64_t D = p->N * p->N - 1;
+    if (state_bytes) *state_bytes = static_cast<size_t>(D * mln::state_stride(*p)) * r;
+    if (field_bytes) *field_bytes = static_cast<size_t>(p->n_cells) * r;
+    return MLN_OK;
+}
+
+mln_status mln_setup_host(const mln_params *p, mln_setup *out) {
+    if (!p || !out) return MLN_EINVAL;
+    std::string err;
+    mln_status st = mln::validate(*p, err);
+    mln::Setup s;
+    if (st == MLN_OK) st = mln::build_setup(*p, s, err);
+    if (st != MLN_OK) {
+        g_create_err = err;
+        return st;
+    }
+    std::memset(out, 0, sizeof(*out));
+    out->N = s.N;
+    out->D = s.D;
+    out->q = s.q;
+    const int D = s.D;
+    for (int i = 0; i < D * D; ++i) {
+        out->M[i] = s.M[i];
+        out->U[i] = s.U[i];
+        out->A0[i] = s.A0[i];
+        out->T[i] = s.T[i];
+        out->C[i] = s.C[i];
+    }
+    for (int i = 0; i < D; ++i) {
+        out->d_eq[i] = s.d_eq[i];
+        out->v[i] = s.v[i];
+        out->b[i] = s.b[i];
+        out->w[i] = s.w[i];
+        out->d0[i] = s.d0[i];
+    }
+    for (int i = 0; i < s.q; ++i) out->theta[i] = s.theta[i];
+    out->c = s.c;
+    for (size_t i = 0; i < s.gen.size(); ++i) {
+        out->gen[2 * i] = s.gen[i].real();
+        out->gen[2 * i + 1] = s.gen[i].imag();
+    }
+    return MLN_OK;
+}
+
+void mln_destroy(mln_ctx *c) {
+    if (!c) return;
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    cudaFree(c->st[1]);
+    cudaFree(c->E[1]);
+    cudaFree(c->H[1]);
+    cudaFree(c->flags);
+    cudaFree(c->tab_rho);
+    cudaFree(c->tab_pop);
+    cudaFree(c->tab_d);
+    cudaFree(c->tab_in);
+    cudaFree(c->scratch);
+    delete c;
+}
+
+mln_status mln_create(const mln_params *p, void *d_state, void *Ez, void *Hy, void *stream, mln_ctx **out) {
+    if (out) *out = nullptr;
+    if (!p || !out || !d_state || !Ez || !Hy) {
+        g_create_err = "null argument";
+        return MLN_EINVAL;
+    }
+    std::string err;
+    mln_status st = mln::validate(*p, err);
+    if (st != MLN_OK) {
+        g_create_err = err;
+        return st;
+    }
+    mln_ctx *c = new (std::nothrow) mln_ctx();
+    if (!c) return MLN_ENOMEM;
+    c->p = *p;
+    c->p.H0 = c->p.mu = c->p.G = c->p.rho0 = nullptr;
+    st = mln::build_setup(*p, c->s, err);
+    if (st != MLN_OK) {
+        g_create_err = err;
+        delete c;
+        return st;
+    }
+    c->D = c->s.D;
+    c->n_med = p->medium_end - p->medium_begin;
+    c->stride = mln::state_stride(*p);
+    c->rsz = p->precision == MLN_FP64 ? 8 : 4;
+    c->state_bytes = static_cast<size_t>(c->D) * c->stride * c->rsz;
+    c->field_bytes = static_cast<size_t>(p->n_cells) * c->rsz;
+    c->st[0] = d_state;
+    c->E[0] = Ez;
+    c->H[0] = Hy;
+    c->stream = static_cast<cudaStream_t>(stream);
+    bool ok = p->precision == MLN_FP64 ? mln::pack_consts(c->s, p->form, p->dt, 0.0, c->consts)
+                                       : mln::pack_consts(c->s, p->form, p->dt, 0.0f, c->consts);
+    auto fail = [&](mln_status s_) {
+        g_create_err = c->err.empty() ? err : c->err;
+        mln_destroy(c);
+        return s_;
+    };
+    if (!ok) {
+        c->err = "no kernel for this N";
+        return fail(MLN_EUNSUPPORTED);
+    }
+    pick_launch_shape(c);
+    if (cudaMalloc(&c->st[1], std::max<size_t>(c->state_bytes, 16)) != cudaSuccess ||
+        cudaMalloc(&c->E[1], c->field_bytes) != cudaSuccess || cudaMalloc(&c->H[1], c->field_bytes) != cudaSuccess ||
+        cudaMalloc(&c->flags, 256) != cudaSuccess) {
+        cudaGetLastError();
+        c->err = "device allocation failed";
+        return fail(MLN_ENOMEM);
+    }
+    if (cudaMemsetAsync(c->flags, 0, 256, c->stream) != cudaSuccess) {
+        c->err = "flag reset failed";
+        return fail(MLN_ECUDA);
+    }
+    // output tables: rho = rho_c + Z (sd0 + Sd s), populations, d = sd0 + Sd s
+    const int D = c->D, n = p->N, nn = n * n;
+    std::vector<double> zr((size_t)2 * nn * D, 0.0), zo(2 * nn, 0.0);
+    for (int r = 0; r < 2 * nn; ++r) {
+        double o = c->s.rho_c[r];
+        for (int j = 0; j < D; ++j) o += c->s.Z[r * D + j] * c->s.sd0[j];
+        zo[r] = o;
+        for (int k = 0; k < D; ++k) {
+            double acc = 0;
+            for (int j = 0; j < D; ++j) acc += c->s.Z[r * D + j] * c->s.Sd[j * D + k];
+            zr[(size_t)r * D + k] = acc;
+        }
+    }
+    std::vector<double> pr((size_t)n * D), po(n);
+    for (int l = 0; l < n; ++l) {
+        int r = 2 * (l * n + l);
+        po[l] = zo[r];
+        for (int k = 0; k < D; ++k) pr[(size_t)l * D + k] = zr[(size_t)r * D + k];
+    }
+    if ((st = upload_table(c, &c->tab_rho, zr, zo)) != MLN_OK) return fail(st);
+    if ((st = upload_table(c, &c->tab_pop, pr, po)) != MLN_OK) return fail(st);
+    if ((st = upload_table(c, &c->tab_d, c->s.Sd, c->s.sd0)) != MLN_OK) return fail(st);
+    if ((st = upload_table(c, &c->tab_in, c->s.Sp, c->s.sp0)) != MLN_OK) return fail(st);
+    // initial medium state from rho0: state = sp0 + Sp d0
+    if (c->n_med > 0) {
+        std::vector<double> v0(D);
+        for (int k = 0; k < D; ++k) {
+            double acc = c->s.sp0[k];
+            for (int j = 0; j < D; ++j) acc += c->s.Sp[k * D + j] * c->s.d0[j];
+            v0[k] = acc;
+        }
+        if ((st = ensure_scratch(c, D * sizeof(double))) != MLN_OK) return fail(st);
+        if (cudaMemcpy(c->scratch, v0.data(), D * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess) {
+            c->err = "upload of the initial state failed";
+            return fail(MLN_ECUDA);
+        }
+        if (p->precision == MLN_FP64)
+            fill_state<double><<<grid_for(c->n_med, 256), 256, 0, c->stream>>>(
+                static_cast<double *>(c->st[0]), c->stride, c->n_med, D, static_cast<double *>(c->scratch));
+        else
+            fill_state<float><<<grid_for(c->n_med, 256), 256, 0, c->stream>>>(
+                static_cast<float *>(c->st[0]), c->stride, c->n_med, D, static_cast<double *>(c->scratch));
+        if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(c->stream) != cudaSuccess) {
+            c->err = "initial state kernel failed";
+            return fail(MLN_ECUDA);
+        }
+    }
+    *out = c;
+    return MLN_OK;
+}
+
+mln_status mln_step(mln_ctx *c, int64_t n_steps, const double *src) {
+    if (!c || n_steps < 0) return MLN_EINVAL;
+    if (n_steps == 0) return MLN_OK;
+    mln_status st = c->p.precision == MLN_FP64 ? run_steps<double>(c, n_steps, src) : run_steps<float>(c, n_steps, src);
+    if (st == MLN_OK) c->steps += n_steps;
+    return st;
+}
+
+mln_status mln_sync(mln_ctx *c) {
+    if (!c) return MLN_EINVAL;
+    MLN_CK(c, cudaStreamSynchronize(c->stream));
+    unsigned int f = 0;
+    MLN_CK(c, cudaMemcpy(&f, c->flags, sizeof(f), cudaMemcpyDeviceToHost));
+    if (f & 1u) {
+        c->err = "non-finite E_z on the device";
+        MLN_CK(c, cudaMemset(c->flags, 0, sizeof(unsigned int)));
+        return MLN_ENONFINITE;
+    }
+    return MLN_OK;
+}
+
+int64_t mln_step_count(const mln_ctx *c) { return c ? c->steps : -1; }
+
+int64_t mln_launch_count(const mln_ctx *c) { return c ? c->launches : -1; }
+
+mln_status mln_launch_shape(const mln_ctx *c, int32_t *block_steps, int32_t *tile_cells, int32_t *threads) {
+    if (!c) return MLN_EINVAL;
+    if (block_steps) *block_steps = c->K;
+    if (tile_cells) *tile_cells = c->tile;
+    if (threads) *threads = c->threads;
+    return MLN_OK;
+}
+
+mln_status mln_get_fields(mln_ctx *c, double *Ez_host, double *Hy_host) {
+    if (!c) return MLN_EINVAL;
+    mln_status st = MLN_OK;
+    if (Ez_host && (st = read_field(c, c->E[0], Ez_host)) != MLN_OK) return st;
+    if (Hy_host && (st = read_field(c, c->H[0], Hy_host)) != MLN_OK) return st;
+    return MLN_OK;
+}
+
+mln_status mln_get_rho(mln_ctx *c, int64_t cell0, int64_t count, double *rho_host) {
+    if (!c || (!rho_host && count > 0)) return MLN_EINVAL;
+    int64_t m0;
+    mln_status st = check_cells(c, cell0, count, &m0);
+    if (st != MLN_OK) return st;
+    return read_rows(c, m0, count, c->tab_rho, 2 * c->p.N * c->p.N, rho_host);
+}
+
+mln_status mln_get_populations(mln_ctx *c, int64_t cell0, int64_t count, double *pop_host) {
+    if (!c || (!pop_host && count > 0)) return MLN_EINVAL;
+    int64_t m0;
+    mln_status st = check_cells(c, cell0, count, &m0);
+    if (st != MLN_OK) return st;
+    return read_rows(c, m0, count, c->tab_pop, c->p.N, pop_host);
+}
+
+mln_status mln_save_state(mln_ctx *c, double *d_host, double *Ez_host, double *Hy_host) {
+    if (!c) return MLN_EINVAL;
+    mln_status st;
+    if (d_host && (st = read_rows(c, 0, c->n_med, c->tab_d, c->D, d_host)) != MLN_OK) return st;
+    return mln_get_fields(c, Ez_host, Hy_host);
+}
+
+mln_status mln_load_state(mln_ctx *c, const double *d_host, const double *Ez_host, const double *Hy_host) {
+    if (!c) return MLN_EINVAL;
+    mln_status st;
+    if (d_host && c->n_med > 0) {
+        size_t bytes = static_cast<size_t>(c->n_med) * c->D * sizeof(double);
+        if ((st = ensure_scratch(c, bytes)) != MLN_OK) return st;
+        MLN_CK(c, cudaMemcpyAsync(c->scratch, d_host, bytes, cudaMemcpyHostToDevice, c->stream));
+        if (c->p.precision == MLN_FP64)
+            rows_to_state<double><<<grid_for(c->n_med, 128), 128, 0, c->stream>>>(
+                static_cast<const double *>(c->scratch), c->n_med, c->D, c->tab_in, static_cast<double *>(c->st[0]),
+                c->stride);
+        else
+            rows_to_state<float><<<grid_for(c->n_med, 128), 128, 0, c->stream>>>(
+                static_cast<const double *>(c->scratch), c->n_med, c->D, c->tab_in, static_cast<float *>(c->st[0]),
+                c->stride);
+        MLN_CK(c, cudaGetLastError());
+        MLN_CK(c, cudaStreamSynchronize(c->stream));
+    }
+    if (Ez_host && (st = write_field(c, c->E[0], Ez_host)) != MLN_OK) return st;
+    if (Hy_host && (st = write_field(c, c->H[0], Hy_host)) != MLN_OK) return st;
+    return MLN_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,105 @@
+// Packing of the per-context constants and launch of the fused step kernel
+// for one precision (internal; included by kernels_fp64.cu / kernels_fp32.cu).
+#pragma once
+
+#include <cstring>
+#include <vector>
+
+#include "kernels.cuh"
+#include "setup.h"
+
+namespace mln {
+
+template <int N, typename R>
+void pack_strang(const Setup &s, double dt, std::vector<unsigned char> &out) {
+    constexpr int D = Dims<N>::D, Q = Dims<N>::Q;
+    StrangConsts<N, R> k;
+    std::memset(&k, 0, sizeof(k));
+    for (int i = 0; i < D * D; ++i) {
+        k.A0[i] = static_cast<R>(s.A0[i]);
+        k.T[i] = static_cast<R>(s.T[i]);
+    }
+    for (int i = 0; i < D; ++i) {
+        k.b[i] = static_cast<R>(s.b[i]);
+        k.w[i] = static_cast<R>(s.w[i]);
+    }
+    for (int i = 0; i < Q; ++i) k.theta_dt[i] = static_cast<R>(s.theta[i] * dt);
+    k.c = static_cast<R>(s.c);
+    out.resize(sizeof(k));
+    std::memcpy(out.data(), &k, sizeof(k));
+}
+
+template <int N, typename R>
+void pack_rot(const Setup &s, double dt, std::vector<unsigned char> &out) {
+    constexpr int D = Dims<N>::D, Q = Dims<N>::Q;
+    RotConsts<N, R> k;
+    std::memset(&k, 0, sizeof(k));
+    for (int i = 0; i < D * D; ++i) k.C[i] = static_cast<R>(s.C[i]);
+    for (int i = 0; i < D; ++i) {
+        k.cp[i] = static_cast<R>(s.cp[i]);
+        k.wr[i] = static_cast<R>(s.wr[i]);
+    }
+    for (int i = 0; i < Q; ++i) k.theta_dt[i] = static_cast<R>(s.theta[i] * dt);
+    k.cr = static_cast<R>(s.cr);
+    out.resize(sizeof(k));
+    std::memcpy(out.data(), &k, sizeof(k));
+}
+
+template <typename R>
+bool pack_consts_t(const Setup &s, int form, double dt, std::vector<unsigned char> &out) {
+    switch (s.N) {
+#define MLN_PACK_CASE(NN)                                        \
+    case NN:                                                     \
+        if (form == MLN_FORM_STRANG) pack_strang<NN, R>(s, dt, out); \
+        else pack_rot<NN, R>(s, dt, out);                        \
+        return true;
+        MLN_PACK_CASE(2)
+        MLN_PACK_CASE(3)
+        MLN_PACK_CASE(4)
+        MLN_PACK_CASE(5)
+        MLN_PACK_CASE(6)
+#undef MLN_PACK_CASE
+    default:
+        return false;
+    }
+}
+
+template <int N, typename R, typename K>
+cudaError_t launch_one(const BlockArgs<R> &a, const std::vector<unsigned char> &consts, dim3 grid,
+                       dim3 block, size_t smem, cudaStream_t st) {
+    K k;
+    if (consts.size() != sizeof(K)) return cudaErrorInvalidValue;
+    std::memcpy(&k, consts.data(), sizeof(K));
+    mln_block_kernel<N, R, K><<<grid, block, smem, st>>>(a, k);
+    return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_block_t(int N, int form, const BlockArgs<R> &a, const std::vector<unsigned char> &consts,
+                           dim3 grid, dim3 block, size_t smem, cudaStream_t st) {
+    switch (N) {
+#define MLN_LAUNCH_CASE(NN)                                                                     \
+    case NN:                                                                                    \
+        if (form == MLN_FORM_STRANG)                                                            \
+            return launch_one<NN, R, StrangConsts<NN, R>>(a, consts, grid, block, smem, st);    \
+        return launch_one<NN, R, RotConsts<NN, R>>(a, consts, grid, block, smem, st);
+        MLN_LAUNCH_CASE(2)
+        MLN_LAUNCH_CASE(3)
+        MLN_LAUNCH_CASE(4)
+        MLN_LAUNCH_CASE(5)
+        MLN_LAUNCH_CASE(6)
+#undef MLN_LAUNCH_CASE
+    default:
+        return cudaErrorInvalidValue;
+    }
+}
+
+// Entry points defined once per precision.
+bool pack_consts(const Setup &s, int form, double dt, double tag, std::vector<unsigned char> &out);
+bool pack_consts(const Setup &s, int form, double dt, float tag, std::vector<unsigned char> &out);
+cudaError_t launch_block(int N, int form, const BlockArgs<double> &a, const std::vector<unsigned char> &consts,
+                         dim3 grid, dim3 block, size_t smem, cudaStream_t st);
+cudaError_t launch_block(int N, int form, const BlockArgs<float> &a, const std::vector<unsigned char> &consts,
+                         dim3 grid, dim3 block, size_t smem, cudaStream_t st);
+
+}  // namespace mln

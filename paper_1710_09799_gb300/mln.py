@@ -1,0 +1,327 @@
+"""ctypes binding of the C-ABI in include/mln.h.
+
+The functions below carry the C names and only marshal arguments: every step
+of the solver runs in libmln.so (host FP64 set-up and sm_103a kernels).
+PyTorch provides the device buffers and the CUDA stream. If the library is
+missing or does not load, every entry point raises; there is no fallback.
+
+`Solver` is a convenience wrapper that allocates the caller-owned buffers as
+torch tensors and keeps them alive with the context.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libmln.so")
+
+MLN_OK, MLN_EINVAL, MLN_ENOMEM, MLN_ECUDA, MLN_ENUMERIC, MLN_ETIMEOUT, MLN_EUNSUPPORTED, MLN_ENONFINITE = range(8)
+MLN_BC_PERIODIC, MLN_BC_OPEN = 0, 1
+MLN_SRC_NONE, MLN_SRC_HARD, MLN_SRC_SOFT = 0, 1, 2
+MLN_FP64, MLN_FP32 = 0, 1
+MLN_FORM_STRANG, MLN_FORM_ROTATED = 0, 1
+MLN_MIN_N, MLN_MAX_N = 2, 6
+_DMAX = MLN_MAX_N * MLN_MAX_N - 1
+
+BOUNDARY = {"periodic": MLN_BC_PERIODIC, "open": MLN_BC_OPEN}
+SOURCE = {"none": MLN_SRC_NONE, "hard": MLN_SRC_HARD, "soft": MLN_SRC_SOFT}
+PRECISION = {"fp64": MLN_FP64, "fp32": MLN_FP32}
+FORM = {"strang": MLN_FORM_STRANG, "rotated": MLN_FORM_ROTATED}
+
+_dp = C.POINTER(C.c_double)
+
+
+class mln_params(C.Structure):
+    _fields_ = [
+        ("N", C.c_int32), ("precision", C.c_int32), ("form", C.c_int32), ("boundary", C.c_int32),
+        ("source_kind", C.c_int32), ("block_steps", C.c_int32), ("tile_cells", C.c_int32),
+        ("reserved0", C.c_int32),
+        ("H0", _dp), ("mu", _dp), ("G", _dp), ("rho0", _dp),
+        ("N_a", C.c_double),
+        ("n_cells", C.c_int64), ("medium_begin", C.c_int64), ("medium_end", C.c_int64),
+        ("source_cell", C.c_int64),
+        ("dx", C.c_double), ("dt", C.c_double), ("eps_r", C.c_double), ("mu_r", C.c_double),
+        ("sigma", C.c_double),
+    ]
+
+
+class mln_setup(C.Structure):
+    _fields_ = [
+        ("N", C.c_int32), ("D", C.c_int32), ("q", C.c_int32), ("reserved", C.c_int32),
+        ("M", C.c_double * (_DMAX * _DMAX)), ("U", C.c_double * (_DMAX * _DMAX)),
+        ("A0", C.c_double * (_DMAX * _DMAX)), ("T", C.c_double * (_DMAX * _DMAX)),
+        ("C", C.c_double * (_DMAX * _DMAX)),
+        ("d_eq", C.c_double * _DMAX), ("v", C.c_double * _DMAX), ("b", C.c_double * _DMAX),
+        ("w", C.c_double * _DMAX), ("d0", C.c_double * _DMAX),
+        ("theta", C.c_double * (MLN_MAX_N * (MLN_MAX_N - 1) // 2)),
+        ("c", C.c_double),
+        ("gen", C.c_double * (2 * _DMAX * MLN_MAX_N * MLN_MAX_N)),
+    ]
+
+
+# Every exported symbol of include/mln.h with (restype, argtypes).
+_P = C.POINTER(mln_params)
+_SIGS = {
+    "mln_query_buffers": (C.c_int, [_P, C.POINTER(C.c_size_t), C.POINTER(C.c_size_t)]),
+    "mln_create": (C.c_int, [_P, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(C.c_void_p)]),
+    "mln_step": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p]),
+    "mln_sync": (C.c_int, [C.c_void_p]),
+    "mln_step_count": (C.c_int64, [C.c_void_p]),
+    "mln_launch_count": (C.c_int64, [C.c_void_p]),
+    "mln_launch_shape": (C.c_int, [C.c_void_p, C.POINTER(C.c_int32), C.POINTER(C.c_int32),
+                                   C.POINTER(C.c_int32)]),
+    "mln_get_fields": (C.c_int, [C.c_void_p, _dp, _dp]),
+    "mln_get_rho": (C.c_int, [C.c_void_p, C.c_int64, C.c_int64, _dp]),
+    "mln_get_populations": (C.c_int, [C.c_void_p, C.c_int64, C.c_int64, _dp]),
+    "mln_save_state": (C.c_int, [C.c_void_p, _dp, _dp, _dp]),
+    "mln_load_state": (C.c_int, [C.c_void_p, _dp, _dp, _dp]),
+    "mln_destroy": (None, [C.c_void_p]),
+    "mln_status_string": (C.c_char_p, [C.c_int]),
+    "mln_last_error": (C.c_char_p, [C.c_void_p]),
+    "mln_create_error": (C.c_char_p, []),
+    "mln_setup_host": (C.c_int, [_P, C.POINTER(mln_setup)]),
+    "mln_version": (C.c_char_p, []),
+}
+
+_lib = None
+_lock = threading.Lock()
+
+
+def lib():
+    """Load libmln.so (raises if it was not built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(f"libmln.so not built ({LIB_PATH}); run the package build first")
+            l = C.CDLL(LIB_PATH)
+            for name, (res, args) in _SIGS.items():
+                f = getattr(l, name)
+                f.restype = res
+                f.argtypes = args
+            _lib = l
+    return _lib
+
+
+class MLNError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{status_string(status)}: {msg}")
+        self.status = status
+
+
+def status_string(s: int) -> str:
+    return lib().mln_status_string(s).decode()
+
+
+def _check(status: int, ctx=None):
+    if status != MLN_OK:
+        if ctx is not None:
+            msg = lib().mln_last_error(ctx).decode()
+        else:
+            msg = lib().mln_create_error().decode()
+        raise MLNError(status, msg)
+
+
+def _cplx(a) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(a, dtype=np.complex128)).view(np.float64).copy()
+
+
+def _ptr(a: np.ndarray | None):
+    if a is None:
+        return None
+    assert a.dtype == np.float64 and a.flags.c_contiguous
+    return a.ctypes.data_as(_dp)
+
+
+class Params:
+    """An mln_params with its host arrays kept alive."""
+
+    def __init__(self, *, N, H0, mu, rho0, N_a, n_cells, medium_begin, medium_end, dx, dt,
+                 G=None, eps_r=1.0, mu_r=1.0, sigma=0.0, boundary="periodic", source_kind="none",
+                 source_cell=0, precision="fp64", form="strang", block_steps=0, tile_cells=0):
+        self._H0, self._mu, self._rho0 = _cplx(H0), _cplx(mu), _cplx(rho0)
+        self._G = None if G is None else _cplx(G)
+        self.s = mln_params(
+            N=N, precision=PRECISION.get(precision, precision), form=FORM.get(form, form),
+            boundary=BOUNDARY.get(boundary, boundary), source_kind=SOURCE.get(source_kind, source_kind),
+            block_steps=block_steps, tile_cells=tile_cells, reserved0=0,
+            H0=_ptr(self._H0), mu=_ptr(self._mu), G=_ptr(self._G), rho0=_ptr(self._rho0),
+            N_a=N_a, n_cells=n_cells, medium_begin=medium_begin, medium_end=medium_end,
+            source_cell=source_cell, dx=dx, dt=dt, eps_r=eps_r, mu_r=mu_r, sigma=sigma)
+
+    @property
+    def D(self):
+        return self.s.N * self.s.N - 1
+
+
+# ------------------------------------------------------------------ C names
+
+def mln_query_buffers(params: Params):
+    sb, fb = C.c_size_t(), C.c_size_t()
+    _check(lib().mln_query_buffers(C.byref(params.s), C.byref(sb), C.byref(fb)))
+    return sb.value, fb.value
+
+
+def mln_create(params: Params, d_state_ptr: int, ez_ptr: int, hy_ptr: int, stream_ptr: int):
+    out = C.c_void_p()
+    _check(lib().mln_create(C.byref(params.s), C.c_void_p(d_state_ptr), C.c_void_p(ez_ptr),
+                            C.c_void_p(hy_ptr), C.c_void_p(stream_ptr), C.byref(out)))
+    return out
+
+
+def mln_step(ctx, n_steps: int, src_ptr: int | None = None):
+    _check(lib().mln_step(ctx, n_steps, None if src_ptr is None else C.c_void_p(src_ptr)), ctx)
+
+
+def mln_sync(ctx):
+    _check(lib().mln_sync(ctx), ctx)
+
+
+def mln_step_count(ctx) -> int:
+    return lib().mln_step_count(ctx)
+
+
+def mln_launch_count(ctx) -> int:
+    return lib().mln_launch_count(ctx)
+
+
+def mln_launch_shape(ctx):
+    k, t, th = C.c_int32(), C.c_int32(), C.c_int32()
+    _check(lib().mln_launch_shape(ctx, C.byref(k), C.byref(t), C.byref(th)), ctx)
+    return k.value, t.value, th.value
+
+
+def mln_get_fields(ctx, n_cells: int):
+    E, H = np.zeros(n_cells), np.zeros(n_cells)
+    _check(lib().mln_get_fields(ctx, _ptr(E), _ptr(H)), ctx)
+    return E, H
+
+
+def mln_get_rho(ctx, N: int, cell0: int, count: int) -> np.ndarray:
+    out = np.zeros(2 * count * N * N)
+    _check(lib().mln_get_rho(ctx, cell0, count, _ptr(out)), ctx)
+    return out.view(np.complex128).reshape(count, N, N)
+
+
+def mln_get_populations(ctx, N: int, cell0: int, count: int) -> np.ndarray:
+    out = np.zeros(count * N)
+    _check(lib().mln_get_populations(ctx, cell0, count, _ptr(out)), ctx)
+    return out.reshape(count, N)
+
+
+def mln_save_state(ctx, n_medium: int, D: int, n_cells: int):
+    d, E, H = np.zeros(n_medium * D), np.zeros(n_cells), np.zeros(n_cells)
+    _check(lib().mln_save_state(ctx, _ptr(d), _ptr(E), _ptr(H)), ctx)
+    return d.reshape(n_medium, D), E, H
+
+
+def mln_load_state(ctx, d=None, E=None, H=None):
+    arr = [None if x is None else np.ascontiguousarray(x, dtype=np.float64).reshape(-1) for x in (d, E, H)]
+    _check(lib().mln_load_state(ctx, *[_ptr(a) for a in arr]), ctx)
+
+
+def mln_destroy(ctx):
+    if ctx:
+        lib().mln_destroy(ctx)
+
+
+def mln_setup_host(params: Params) -> dict:
+    out = mln_setup()
+    _check(lib().mln_setup_host(C.byref(params.s), C.byref(out)))
+    N, D, q = out.N, out.D, out.q
+    m = lambda a: np.array(a[:D * D]).reshape(D, D)
+    v = lambda a: np.array(a[:D])
+    gen = np.array(out.gen[:2 * D * N * N]).view(np.complex128).reshape(D, N, N)
+    return dict(N=N, D=D, q=q, M=m(out.M), U=m(out.U), A0=m(out.A0), T=m(out.T), C=m(out.C),
+                d_eq=v(out.d_eq), v=v(out.v), b=v(out.b), w=v(out.w), d0=v(out.d0),
+                theta=np.array(out.theta[:q]), c=out.c, gen=gen)
+
+
+def mln_version() -> str:
+    return lib().mln_version().decode()
+
+
+# ------------------------------------------------------------------ wrapper
+
+class Solver:
+    """Owns the torch device buffers of one context (E_z, H_y, medium state)."""
+
+    def __init__(self, params: Params, E0=None, H0=None, device="cuda", stream=None):
+        import torch
+        self.params = params
+        self.N, self.D = params.s.N, params.D
+        self.n_cells = params.s.n_cells
+        self.n_medium = params.s.medium_end - params.s.medium_begin
+        self.dtype = torch.float64 if params.s.precision == MLN_FP64 else torch.float32
+        sb, fb = mln_query_buffers(params)
+        esz = 8 if self.dtype == torch.float64 else 4
+        self.stride = sb // (esz * self.D) if self.D else 0
+        dev = torch.device(device)
+        self.state = torch.zeros(max(sb // esz, 1), dtype=self.dtype, device=dev)
+        self.E = torch.zeros(self.n_cells, dtype=self.dtype, device=dev)
+        self.H = torch.zeros(self.n_cells, dtype=self.dtype, device=dev)
+        if E0 is not None:
+            self.E.copy_(torch.as_tensor(np.asarray(E0), dtype=self.dtype))
+        if H0 is not None:
+            self.H.copy_(torch.as_tensor(np.asarray(H0), dtype=self.dtype))
+        self.stream = stream if stream is not None else torch.cuda.current_stream(dev)
+        self.ctx = mln_create(params, self.state.data_ptr(), self.E.data_ptr(), self.H.data_ptr(),
+                              self.stream.cuda_stream)
+
+    def step(self, n_steps: int, src=None):
+        """src: None or a float64 CUDA tensor of n_steps samples."""
+        ptr = None
+        if src is not None:
+            assert src.dtype.is_floating_point and src.element_size() == 8 and src.is_cuda
+            assert src.numel() >= n_steps
+            ptr = src.data_ptr()
+        mln_step(self.ctx, n_steps, ptr)
+
+    def sync(self):
+        mln_sync(self.ctx)
+
+    @property
+    def steps(self) -> int:
+        return mln_step_count(self.ctx)
+
+    @property
+    def launches(self) -> int:
+        return mln_launch_count(self.ctx)
+
+    @property
+    def launch_shape(self):
+        return mln_launch_shape(self.ctx)
+
+    def fields(self):
+        return mln_get_fields(self.ctx, self.n_cells)
+
+    def rho(self, cell0=None, count=None):
+        cell0 = self.params.s.medium_begin if cell0 is None else cell0
+        count = self.n_medium if count is None else count
+        return mln_get_rho(self.ctx, self.N, cell0, count)
+
+    def populations(self, cell0=None, count=None):
+        cell0 = self.params.s.medium_begin if cell0 is None else cell0
+        count = self.n_medium if count is None else count
+        return mln_get_populations(self.ctx, self.N, cell0, count)
+
+    def save(self):
+        return mln_save_state(self.ctx, self.n_medium, self.D, self.n_cells)
+
+    def load(self, d=None, E=None, H=None):
+        mln_load_state(self.ctx, d, E, H)
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            mln_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
