@@ -38,12 +38,17 @@ METRIC = "cell-updates/sec on 1 GB300 (FP32/batched vs plain FP64 at stated err)
 UNIT = "cell-updates/s"
 WORKLOAD = "three-level QCL-like medium, periodic ring, 65536 cells x 100000 steps"
 
-# Algorithmic flops (FMA = 2) per medium cell-update, adjoint dimension D, q planes,
-# excluding the q sin/cos evaluations; and per grid cell for the two FDTD updates.
-def cell_flops(form: str, D: int, q: int) -> int:
+# Algorithmic flops (FMA = 2, add/mul = 1) per medium cell-update for adjoint
+# dimension D, q rotation planes and N levels, counted from the kernels'
+# arithmetic: each D x D product 2 D^2, each identity + increment D adds,
+# the rotation increments 6 flops per plane, the N - 1 evaluations of
+# (sin, cos - 1) by their series 28 flops each, 12 flops per plane derived by
+# angle subtraction, the dP/dt dot 2 D. FDTD: 9 flops per grid cell.
+def cell_flops(form: str, D: int, q: int, N: int) -> int:
+    rot = 6 * q + 28 * (N - 1) + 12 * (q - (N - 1))
     if form == "strang":
-        return 8 * D * D + 7 * q          # A0, T^T, T, A0 products + rotations
-    return 2 * D * D + 2 * D + 7 * q      # rotations, dP/dt dot, C p + c'
+        return 4 * 2 * D * D + 3 * D + rot + 2 * D      # Dl, T^T, T, Dl products
+    return 3 * 2 * D * D + 2 * D + rot + 2 * D          # T^T, T, C1 products
 
 
 FDTD_FLOPS = 9
@@ -288,7 +293,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="mine", choices=["mine", "reference"])
     ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32"])
-    ap.add_argument("--form", default="rotated", choices=["strang", "rotated"])
+    ap.add_argument("--form", default="merged", choices=["strang", "merged"])
     ap.add_argument("--seg", type=int, default=1000, help="time steps per benchmark step")
     ap.add_argument("--block-steps", type=int, default=20)
     ap.add_argument("--tile", type=int, default=0)
@@ -318,14 +323,15 @@ def main():
     # roofline of the fused step kernel (the only kernel in the timed region)
     launches = main_run["launches"]
     per_launch_s = main_run["ms_local"] / 1e3 / max(launches, 1)
-    flops_per_step = p.n_medium * cell_flops(args.form, D, q) + p.n_cells * FDTD_FLOPS
+    flops_per_step = p.n_medium * cell_flops(args.form, D, q, p.N) + p.n_cells * FDTD_FLOPS
     achieved = flops_per_step * (args.seg * args.steps / max(launches, 1)) / per_launch_s / 1e12
     peak = alu_peak_tflops(args.precision)
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "kernel": "mln_block_kernel",
                 "frac": achieved / peak, "traffic": None,
                 "peak_source": f"derived: {SMS} SMs x {FP64_FLOP_PER_CLK_SM if args.precision == 'fp64' else FP32_FLOP_PER_CLK_SM} "
                                f"flop/clk x {SM_MAX_MHZ:.0f} MHz",
-                "flops_per_cell_update": cell_flops(args.form, D, q), "sincos_per_cell_update": q}
+                "flops_per_cell_update": cell_flops(args.form, D, q, p.N)}
     clk = main_run["clocks"] or {}
     if clk.get("sm_mhz"):
         roofline["frac_at_measured_clock"] = achieved / alu_peak_tflops(args.precision, clk["sm_mhz"])
@@ -349,7 +355,7 @@ def main():
 
     if not args.quick and rank == 0:
         variants = {}
-        for prec, form in (("fp64", "strang"), ("fp32", "rotated"), ("fp32", "strang")):
+        for prec, form in (("fp64", "strang"), ("fp32", "merged"), ("fp32", "strang")):
             if (prec, form) == (args.precision, args.form):
                 continue
             r = time_device(p, prec, form, args.seg, 10, 2, args.block_steps, args.tile, 1)

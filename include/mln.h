@@ -54,11 +54,16 @@ typedef enum mln_status {
 enum { MLN_BC_PERIODIC = 0, MLN_BC_OPEN = 1 };
 enum { MLN_SRC_NONE = 0, MLN_SRC_HARD = 1, MLN_SRC_SOFT = 2 };
 enum { MLN_FP64 = 0, MLN_FP32 = 1 };
-/* MLN_FORM_STRANG applies Eq. 23 literally: A0, T^T, plane rotations, T, A0.
- * MLN_FORM_ROTATED keeps each cell's vector in the eigenbasis of U between
- * steps (p = T^T (A0 d + b)), so that a step is rotate, dP/dt, p <- C p + c'
- * with C = T^T A0^2 T: the same arithmetic result, reassociated. */
-enum { MLN_FORM_STRANG = 0, MLN_FORM_ROTATED = 1 };
+/* MLN_FORM_STRANG applies the three updates of Eq. 23 as written: half a
+ * step of exp(M dt/2), the interaction exp(U E dt) through the eigenbasis T,
+ * half a step of exp(M dt/2).
+ * MLN_FORM_MERGED fuses the second half-step of one step with the first
+ * half-step of the next into one affine map (A0^2, A0 b + b); the state is
+ * then the vector after the first half-step. Same result up to rounding,
+ * three D x D products per step instead of four.
+ * Both apply each propagator as identity + increment, which keeps the
+ * rounding of the small coherences at their own scale. */
+enum { MLN_FORM_STRANG = 0, MLN_FORM_MERGED = 1 };
 
 #define MLN_MIN_N 2
 #define MLN_MAX_N 6
@@ -68,7 +73,7 @@ enum { MLN_FORM_STRANG = 0, MLN_FORM_ROTATED = 1 };
  *   N             number of levels, MLN_MIN_N..MLN_MAX_N; adjoint dimension D = N*N-1.
  *   precision     MLN_FP64 or MLN_FP32: type of the device state, fields and
  *                 propagator arithmetic. Set-up is always FP64.
- *   form          MLN_FORM_STRANG or MLN_FORM_ROTATED.
+ *   form          MLN_FORM_STRANG or MLN_FORM_MERGED.
  *   H0            N x N complex Hermitian, J (Eq. 2, H = H0 - mu E_z).
  *   mu            N x N complex Hermitian dipole operator, C m.
  *   G             (N*N) x (N*N) complex relaxation superoperator, 1/s; it must
@@ -210,9 +215,9 @@ const char *mln_create_error(void);
  * Host-only inspection of the FP64 set-up (no GPU needed). Arrays are
  * row-major doubles with the sizes given; the caller provides capacity for
  * D_max = MLN_MAX_N^2 - 1.
- *   M, U, A0, T, C: D x D;  d_eq, v, b, w, d0: D;  theta: q = N(N-1)/2
- *   rotation rates (rad s^-1 per V/m: the plane k of T turns by
- *   theta_k E dt in a step); c: scalar; gen: D x N x N complex generators
+ *   M, U, A0, T, C1 (= A0^2 - I): D x D;  d_eq, v, b, w, d0: D;
+ *   theta: q = N(N-1)/2 rotation rates (rad s^-1 per V/m: plane k of T turns
+ *   by theta_k E dt in a step); c: scalar; gen: D x N x N complex generators
  *   (2 * D * N * N doubles, Sec. 3 ordering u_jk, v_jk, w_l).
  */
 typedef struct mln_setup {
@@ -221,7 +226,7 @@ typedef struct mln_setup {
     double U[(MLN_MAX_N * MLN_MAX_N - 1) * (MLN_MAX_N * MLN_MAX_N - 1)];
     double A0[(MLN_MAX_N * MLN_MAX_N - 1) * (MLN_MAX_N * MLN_MAX_N - 1)];
     double T[(MLN_MAX_N * MLN_MAX_N - 1) * (MLN_MAX_N * MLN_MAX_N - 1)];
-    double C[(MLN_MAX_N * MLN_MAX_N - 1) * (MLN_MAX_N * MLN_MAX_N - 1)];
+    double C1[(MLN_MAX_N * MLN_MAX_N - 1) * (MLN_MAX_N * MLN_MAX_N - 1)];
     double d_eq[MLN_MAX_N * MLN_MAX_N - 1];
     double v[MLN_MAX_N * MLN_MAX_N - 1];
     double b[MLN_MAX_N * MLN_MAX_N - 1];
@@ -233,6 +238,14 @@ typedef struct mln_setup {
 } mln_setup;
 
 mln_status mln_setup_host(const mln_params *p, mln_setup *out);
+
+/*
+ * Diagnostic: evaluate on the device, for n angles x (host array), the pair
+ * (sin x, cos x - 1) exactly as the step kernels of the given precision do,
+ * into host arrays s and c1. Synchronous; uses the legacy default stream and
+ * allocates temporary device memory.
+ */
+mln_status mln_rotation_terms(int32_t precision, const double *x, int64_t n, double *s, double *c1);
 
 /* Library version string. */
 const char *mln_version(void);

@@ -38,7 +38,7 @@ namespace {
 
 thread_local std::string g_create_err;
 
-const char *kVersion = "mln-gb300 0.1 (sm_103a)";
+const char *kVersion = "mln-gb300 0.2 (sm_103a)";
 
 #define MLN_CK(ctx, call)                                                       \
     do {                                                                        \
@@ -254,6 +254,25 @@ extern "C" {
 
 const char *mln_version(void) { return kVersion; }
 
+mln_status mln_rotation_terms(int32_t precision, const double *x, int64_t n, double *s, double *c1) {
+    if ((n > 0 && (!x || !s || !c1)) || n < 0 || (precision != MLN_FP64 && precision != MLN_FP32)) return MLN_EINVAL;
+    if (n == 0) return MLN_OK;
+    double *dx = nullptr;
+    size_t bytes = static_cast<size_t>(n) * sizeof(double);
+    if (cudaMalloc(&dx, 3 * bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return MLN_ENOMEM;
+    }
+    mln_status st = MLN_OK;
+    if (cudaMemcpy(dx, x, bytes, cudaMemcpyHostToDevice) != cudaSuccess ||
+        mln::launch_sin_cosm1(precision, dx, n, dx + n, dx + 2 * n, nullptr) != cudaSuccess ||
+        cudaMemcpy(s, dx + n, bytes, cudaMemcpyDeviceToHost) != cudaSuccess ||
+        cudaMemcpy(c1, dx + 2 * n, bytes, cudaMemcpyDeviceToHost) != cudaSuccess)
+        st = MLN_ECUDA;
+    cudaFree(dx);
+    return st;
+}
+
 const char *mln_status_string(mln_status s) {
     switch (s) {
     case MLN_OK: return "ok";
@@ -307,7 +326,7 @@ mln_status mln_setup_host(const mln_params *p, mln_setup *out) {
         out->U[i] = s.U[i];
         out->A0[i] = s.A0[i];
         out->T[i] = s.T[i];
-        out->C[i] = s.C[i];
+        out->C1[i] = s.C1[i];
     }
     for (int i = 0; i < D; ++i) {
         out->d_eq[i] = s.d_eq[i];

@@ -12,35 +12,39 @@ namespace mln {
 
 template <int N, typename R>
 void pack_strang(const Setup &s, double dt, std::vector<unsigned char> &out) {
-    constexpr int D = Dims<N>::D, Q = Dims<N>::Q;
+    constexpr int D = Dims<N>::D;
     StrangConsts<N, R> k;
     std::memset(&k, 0, sizeof(k));
-    for (int i = 0; i < D * D; ++i) {
-        k.A0[i] = static_cast<R>(s.A0[i]);
-        k.T[i] = static_cast<R>(s.T[i]);
-    }
+    for (int i = 0; i < D; ++i)
+        for (int j = 0; j < D; ++j) {
+            k.Dl[i * D + j] = static_cast<R>(s.A0[i * D + j] - (i == j ? 1.0 : 0.0));
+            k.T[i * D + j] = static_cast<R>(s.T[i * D + j]);
+        }
     for (int i = 0; i < D; ++i) {
         k.b[i] = static_cast<R>(s.b[i]);
         k.w[i] = static_cast<R>(s.w[i]);
     }
-    for (int i = 0; i < Q; ++i) k.theta_dt[i] = static_cast<R>(s.theta[i] * dt);
+    for (int a = 0; a < N - 1; ++a) k.psi_dt[a] = static_cast<R>(s.psi[a] * dt);
     k.c = static_cast<R>(s.c);
     out.resize(sizeof(k));
     std::memcpy(out.data(), &k, sizeof(k));
 }
 
 template <int N, typename R>
-void pack_rot(const Setup &s, double dt, std::vector<unsigned char> &out) {
-    constexpr int D = Dims<N>::D, Q = Dims<N>::Q;
-    RotConsts<N, R> k;
+void pack_merged(const Setup &s, double dt, std::vector<unsigned char> &out) {
+    constexpr int D = Dims<N>::D;
+    MergedConsts<N, R> k;
     std::memset(&k, 0, sizeof(k));
-    for (int i = 0; i < D * D; ++i) k.C[i] = static_cast<R>(s.C[i]);
-    for (int i = 0; i < D; ++i) {
-        k.cp[i] = static_cast<R>(s.cp[i]);
-        k.wr[i] = static_cast<R>(s.wr[i]);
+    for (int i = 0; i < D * D; ++i) {
+        k.C1[i] = static_cast<R>(s.C1[i]);
+        k.T[i] = static_cast<R>(s.T[i]);
     }
-    for (int i = 0; i < Q; ++i) k.theta_dt[i] = static_cast<R>(s.theta[i] * dt);
-    k.cr = static_cast<R>(s.cr);
+    for (int i = 0; i < D; ++i) {
+        k.b2[i] = static_cast<R>(s.b2[i]);
+        k.wm[i] = static_cast<R>(s.wm[i]);
+    }
+    for (int a = 0; a < N - 1; ++a) k.psi_dt[a] = static_cast<R>(s.psi[a] * dt);
+    k.cm = static_cast<R>(s.cm);
     out.resize(sizeof(k));
     std::memcpy(out.data(), &k, sizeof(k));
 }
@@ -51,7 +55,7 @@ bool pack_consts_t(const Setup &s, int form, double dt, std::vector<unsigned cha
 #define MLN_PACK_CASE(NN)                                        \
     case NN:                                                     \
         if (form == MLN_FORM_STRANG) pack_strang<NN, R>(s, dt, out); \
-        else pack_rot<NN, R>(s, dt, out);                        \
+        else pack_merged<NN, R>(s, dt, out);                        \
         return true;
         MLN_PACK_CASE(2)
         MLN_PACK_CASE(3)
@@ -82,7 +86,7 @@ cudaError_t launch_block_t(int N, int form, const BlockArgs<R> &a, const std::ve
     case NN:                                                                                    \
         if (form == MLN_FORM_STRANG)                                                            \
             return launch_one<NN, R, StrangConsts<NN, R>>(a, consts, grid, block, smem, st);    \
-        return launch_one<NN, R, RotConsts<NN, R>>(a, consts, grid, block, smem, st);
+        return launch_one<NN, R, MergedConsts<NN, R>>(a, consts, grid, block, smem, st);
         MLN_LAUNCH_CASE(2)
         MLN_LAUNCH_CASE(3)
         MLN_LAUNCH_CASE(4)
@@ -101,5 +105,6 @@ cudaError_t launch_block(int N, int form, const BlockArgs<double> &a, const std:
                          dim3 grid, dim3 block, size_t smem, cudaStream_t st);
 cudaError_t launch_block(int N, int form, const BlockArgs<float> &a, const std::vector<unsigned char> &consts,
                          dim3 grid, dim3 block, size_t smem, cudaStream_t st);
+cudaError_t launch_sin_cosm1(int precision, const double *x, int64_t n, double *s, double *c1, cudaStream_t st);
 
 }  // namespace mln

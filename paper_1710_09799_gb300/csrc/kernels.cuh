@@ -28,28 +28,41 @@ struct Dims {
     static constexpr int Q = N * (N - 1) / 2; // rotation planes of U
 };
 
-// Constants of the literal Strang form (Eq. 23 with the diagonalisation of Eq. 25):
-// d' = A0 d + b; z = T^T d'; z rotated plane by plane by theta_dt[k] * E;
-// d'' = T z; d_new = A0 d'' + b; dP/dt = w . d_new + c.
+// Every propagator is applied as identity + increment: a cell's adjoint vector
+// holds O(1) population components next to small coherences, and a product
+// with a near-identity matrix would otherwise round the coherences at the
+// scale of the populations in every step.
+//
+// Literal form (Eq. 23 with the diagonalisation of Eqs. 25-26), per step:
+//   d'  = d  + (Dl d  + b)            Dl = A0 - I, A0 = exp(M dt/2)     (23a)
+//   z   = T^T d'                      coordinates in the eigenbasis of U
+//   d'' = d' + T (R(E) - I) z         R: plane rotations by theta_k E dt (23b, 25)
+//   d   = d'' + (Dl d'' + b)                                             (23c)
+//   dP/dt = w . d + c                                                    (Eq. 17)
 template <int N, typename R>
 struct StrangConsts {
-    R A0[Dims<N>::D * Dims<N>::D];
+    R Dl[Dims<N>::D * Dims<N>::D];
     R T[Dims<N>::D * Dims<N>::D];
     R b[Dims<N>::D];
     R w[Dims<N>::D];
-    R theta_dt[Dims<N>::Q];
+    R psi_dt[N - 1];
     R c;
 };
 
-// Constants of the rotated form: state p = T^T (A0 d + b);
-// z = R(E) p; dP/dt = wr . z + cr; p_new = C z + cp.
+// Merged form: the second half-step of step n and the first of step n+1 are
+// one affine map A0^2 y + (A0 b + b). The state is y = d' (after the first
+// half-step); per step:
+//   z = T^T y;  y'' = y + T (R(E) - I) z;
+//   dP/dt = wm . y'' + cm              wm = A0^T w, cm = w . b + c  (= w . (A0 y'' + b) + c)
+//   y = y'' + (C1 y'' + b2)            C1 = A0^2 - I, b2 = A0 b + b
 template <int N, typename R>
-struct RotConsts {
-    R C[Dims<N>::D * Dims<N>::D];
-    R cp[Dims<N>::D];
-    R wr[Dims<N>::D];
-    R theta_dt[Dims<N>::Q];
-    R cr;
+struct MergedConsts {
+    R C1[Dims<N>::D * Dims<N>::D];
+    R T[Dims<N>::D * Dims<N>::D];
+    R b2[Dims<N>::D];
+    R wm[Dims<N>::D];
+    R psi_dt[N - 1];
+    R cm;
 };
 
 template <typename R>
@@ -70,44 +83,126 @@ struct BlockArgs {
 __device__ __forceinline__ void sincos_r(double x, double *s, double *c) { sincos(x, s, c); }
 __device__ __forceinline__ void sincos_r(float x, float *s, float *c) { sincosf(x, s, c); }
 
-// Turn plane k = (z[2k], z[2k+1]) by phi_k = theta_dt[k] * e:
+// Truncated Taylor series of sin x and cos x - 1 for |x| <= 1/8. With terms
+// up to x^11 (sin) and x^12 (cos - 1) the Lagrange remainder is below
+// 2^-36/13! ~ 2e-21 relative in FP64; FP32 keeps terms up to x^7 / x^8
+// (remainder below 2^-24/9! ~ 2e-13).
+template <typename R>
+struct SmallAngle;
+template <>
+struct SmallAngle<double> {
+    static constexpr double kMax = 0.125;
+    __device__ __forceinline__ static void eval(double x, double &s, double &c1) {
+        const double x2 = x * x;
+        double ps = -1.0 / 39916800.0;                 // -1/11!
+        ps = fma(ps, x2, 1.0 / 362880.0);              //  1/9!
+        ps = fma(ps, x2, -1.0 / 5040.0);               // -1/7!
+        ps = fma(ps, x2, 1.0 / 120.0);                 //  1/5!
+        ps = fma(ps, x2, -1.0 / 6.0);                  // -1/3!
+        s = fma(x * x2, ps, x);
+        double pc = 1.0 / 479001600.0;                 //  1/12!
+        pc = fma(pc, x2, -1.0 / 3628800.0);            // -1/10!
+        pc = fma(pc, x2, 1.0 / 40320.0);               //  1/8!
+        pc = fma(pc, x2, -1.0 / 720.0);                // -1/6!
+        pc = fma(pc, x2, 1.0 / 24.0);                  //  1/4!
+        pc = fma(pc, x2, -0.5);                        // -1/2!
+        c1 = x2 * pc;
+    }
+};
+template <>
+struct SmallAngle<float> {
+    static constexpr float kMax = 0.125f;
+    __device__ __forceinline__ static void eval(float x, float &s, float &c1) {
+        const float x2 = x * x;
+        float ps = -1.0f / 5040.0f;
+        ps = fmaf(ps, x2, 1.0f / 120.0f);
+        ps = fmaf(ps, x2, -1.0f / 6.0f);
+        s = fmaf(x * x2, ps, x);
+        float pc = 1.0f / 40320.0f;
+        pc = fmaf(pc, x2, -1.0f / 720.0f);
+        pc = fmaf(pc, x2, 1.0f / 24.0f);
+        pc = fmaf(pc, x2, -0.5f);
+        c1 = x2 * pc;
+    }
+};
+
+// (sin x, cos x - 1) without cancellation: the series for small |x|, else
+// sin x = 2 sin(x/2) cos(x/2) and cos x - 1 = -2 sin^2(x/2) from the library.
+template <typename R>
+__device__ __forceinline__ void sin_cosm1(R x, R &s, R &c1) {
+    if (fabs(x) <= SmallAngle<R>::kMax) {
+        SmallAngle<R>::eval(x, s, c1);
+    } else {
+        R sh, ch;
+        sincos_r(x * R(0.5), &sh, &ch);
+        s = R(2) * sh * ch;
+        c1 = R(-2) * sh * sh;
+    }
+}
+
+// z <- (R(E) - I) z for the q planes of T. Plane (a, b), a < b, in row-major
+// pair order turns by phi_ab = (m_a - m_b) E dt / hbar (m: eigenvalues of mu):
 // (x, y) -> (x cos phi + y sin phi, -x sin phi + y cos phi), the flow of the
-// block [[0, theta], [-theta, 0]] of T^T U T over E dt.
+// block [[0, theta], [-theta, 0]] of T^T U T over E dt. Only the N-1 angles
+// psi_a = (m_a - m_{N-1}) E dt / hbar are evaluated; phi_ab = psi_a - psi_b
+// follows by the subtraction formulas written for (sin, cos - 1):
+//   sin(p - r)     = s_p - s_r + s_p c1_r - c1_p s_r
+//   cos(p - r) - 1 = c1_p + c1_r + c1_p c1_r + s_p s_r
 template <int N, typename R>
-__device__ __forceinline__ void rotate_planes(R (&z)[Dims<N>::D], const R *theta_dt, R e) {
+__device__ __forceinline__ void rotation_increment(R (&z)[Dims<N>::D], const R *psi_dt, R e) {
+    R sp[N], cp[N];
 #pragma unroll
-    for (int k = 0; k < Dims<N>::Q; ++k) {
-        R sn, cs;
-        sincos_r(theta_dt[k] * e, &sn, &cs);
-        R x = z[2 * k], y = z[2 * k + 1];
-        z[2 * k] = fma(cs, x, sn * y);
-        z[2 * k + 1] = fma(cs, y, -(sn * x));
+    for (int a = 0; a < N - 1; ++a) sin_cosm1(psi_dt[a] * e, sp[a], cp[a]);
+    sp[N - 1] = R(0);
+    cp[N - 1] = R(0);
+    int k = 0;
+#pragma unroll
+    for (int a = 0; a < N; ++a) {
+#pragma unroll
+        for (int b = a + 1; b < N; ++b) {
+            R s, c1;
+            if (b == N - 1) {
+                s = sp[a];
+                c1 = cp[a];
+            } else {
+                s = (sp[a] - sp[b]) + fma(sp[a], cp[b], -(cp[a] * sp[b]));
+                c1 = (cp[a] + cp[b]) + fma(cp[a], cp[b], sp[a] * sp[b]);
+            }
+            const R x = z[2 * k], y = z[2 * k + 1];
+            z[2 * k] = fma(c1, x, s * y);
+            z[2 * k + 1] = fma(c1, y, -(s * x));
+            ++k;
+        }
     }
+#pragma unroll
+    for (int i = 2 * Dims<N>::Q; i < Dims<N>::D; ++i) z[i] = R(0);  // null space of U: no change
 }
 
-// y = A x (+ b) with A row-major D x D held in the constant bank.
+// y = x + (A x + b) with A row-major D x D held in the constant bank.
 template <int D, typename R>
-__device__ __forceinline__ void matvec(R (&y)[D], const R *A, const R (&x)[D]) {
-#pragma unroll
-    for (int i = 0; i < D; ++i) {
-        R acc = A[i * D] * x[0];
-#pragma unroll
-        for (int j = 1; j < D; ++j) acc = fma(A[i * D + j], x[j], acc);
-        y[i] = acc;
-    }
-}
-
-template <int D, typename R>
-__device__ __forceinline__ void matvec_bias(R (&y)[D], const R *A, const R (&x)[D], const R *b) {
+__device__ __forceinline__ void affine_inc(R (&y)[D], const R *A, const R (&x)[D], const R *b) {
 #pragma unroll
     for (int i = 0; i < D; ++i) {
         R acc = b[i];
 #pragma unroll
         for (int j = 0; j < D; ++j) acc = fma(A[i * D + j], x[j], acc);
-        y[i] = acc;
+        y[i] = x[i] + acc;
     }
 }
 
+// y += A x
+template <int D, typename R>
+__device__ __forceinline__ void matvec_acc(R (&y)[D], const R *A, const R (&x)[D]) {
+#pragma unroll
+    for (int i = 0; i < D; ++i) {
+        R acc = A[i * D] * x[0];
+#pragma unroll
+        for (int j = 1; j < D; ++j) acc = fma(A[i * D + j], x[j], acc);
+        y[i] = y[i] + acc;
+    }
+}
+
+// y = A^T x
 template <int D, typename R>
 __device__ __forceinline__ void matTvec(R (&y)[D], const R *A, const R (&x)[D]) {
 #pragma unroll
@@ -127,37 +222,49 @@ __device__ __forceinline__ R dot_bias(const R *w, const R (&x)[D], R c) {
     return acc;
 }
 
-// One Liouville step of one cell; returns dP/dt^{n+1/2}.
-// Only two D-vectors are live at a time (s and y) to keep register pressure low.
+// One Liouville step of one cell; returns dP/dt^{n+1/2}. Two D-vectors live.
 template <int N, typename R>
 __device__ __forceinline__ R cell_step(R (&s)[Dims<N>::D], R e, const StrangConsts<N, R> &k) {
     constexpr int D = Dims<N>::D;
     R y[D];
-    matvec_bias<D>(y, k.A0, s, k.b);   // d' = A0 d + b           (Eq. 23a)
-    matTvec<D>(s, k.T, y);             // into the eigenbasis of U
-    rotate_planes<N>(s, k.theta_dt, e); // exp(Lambda E dt), real form (Eqs. 23b, 25)
-    matvec<D>(y, k.T, s);              // d'' = T z
-    matvec_bias<D>(s, k.A0, y, k.b);   // d = A0 d'' + b          (Eq. 23c)
-    return dot_bias<D>(k.w, s, k.c);   // dP/dt = w . d + c       (Eq. 17)
+    affine_inc<D>(y, k.Dl, s, k.b);        // d' = A0 d + b
+    matTvec<D>(s, k.T, y);                 // z = T^T d'
+    rotation_increment<N>(s, k.psi_dt, e); // (R - I) z
+    matvec_acc<D>(y, k.T, s);              // d'' = d' + T (R - I) z
+    affine_inc<D>(s, k.Dl, y, k.b);        // d = A0 d'' + b
+    return dot_bias<D>(k.w, s, k.c);
 }
 
 template <int N, typename R>
-__device__ __forceinline__ R cell_step(R (&s)[Dims<N>::D], R e, const RotConsts<N, R> &k) {
+__device__ __forceinline__ R cell_step(R (&s)[Dims<N>::D], R e, const MergedConsts<N, R> &k) {
     constexpr int D = Dims<N>::D;
     R z[D];
+    matTvec<D>(z, k.T, s);                 // z = T^T y
+    rotation_increment<N>(z, k.psi_dt, e);
+    matvec_acc<D>(s, k.T, z);              // y'' = y + T (R - I) z
+    const R dpdt = dot_bias<D>(k.wm, s, k.cm);
+    affine_inc<D>(z, k.C1, s, k.b2);       // y = A0^2 y'' + A0 b + b
 #pragma unroll
-    for (int i = 0; i < D; ++i) z[i] = s[i];
-    rotate_planes<N>(z, k.theta_dt, e);
-    R dpdt = dot_bias<D>(k.wr, z, k.cr);
-    matvec_bias<D>(s, k.C, z, k.cp);
+    for (int i = 0; i < D; ++i) s[i] = z[i];
     return dpdt;
+}
+
+// Evaluates (sin x, cos x - 1) as the step kernels do (diagnostic entry point).
+template <typename R>
+__global__ void sin_cosm1_kernel(const double *x, int64_t n, double *s, double *c1) {
+    int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+    if (i >= n) return;
+    R sv, cv;
+    sin_cosm1(static_cast<R>(x[i]), sv, cv);
+    s[i] = sv;
+    c1[i] = cv;
 }
 
 // Blocks have at most kMaxThreads threads, which leaves up to 128 registers per thread.
 constexpr int kMaxThreads = 512;
 
 template <int N, typename R, typename K>
-__global__ void __launch_bounds__(kMaxThreads) mln_block_kernel(const __grid_constant__ BlockArgs<R> a,
+__global__ void __launch_bounds__(kMaxThreads, 1) mln_block_kernel(const __grid_constant__ BlockArgs<R> a,
                                                          const __grid_constant__ K k) {
     constexpr int D = Dims<N>::D;
     extern __shared__ __align__(16) unsigned char smem_raw[];

@@ -12,4 +12,12 @@ cudaError_t launch_block(int N, int form, const BlockArgs<double> &a, const std:
     return launch_block_t<double>(N, form, a, consts, grid, block, smem, st);
 }
 
+cudaError_t launch_sin_cosm1(int precision, const double *x, int64_t n, double *s, double *c1, cudaStream_t st) {
+    const unsigned grid = static_cast<unsigned>((n + 255) / 256);
+    if (n <= 0) return cudaSuccess;
+    if (precision == MLN_FP64) sin_cosm1_kernel<double><<<grid, 256, 0, st>>>(x, n, s, c1);
+    else sin_cosm1_kernel<float><<<grid, 256, 0, st>>>(x, n, s, c1);
+    return cudaGetLastError();
+}
+
 }  // namespace mln

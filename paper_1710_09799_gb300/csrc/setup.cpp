@@ -246,8 +246,8 @@ mln_status validate(const mln_params &p, std::string &err) {
         err = "precision must be MLN_FP64 or MLN_FP32";
         return MLN_EINVAL;
     }
-    if (p.form != MLN_FORM_STRANG && p.form != MLN_FORM_ROTATED) {
-        err = "form must be MLN_FORM_STRANG or MLN_FORM_ROTATED";
+    if (p.form != MLN_FORM_STRANG && p.form != MLN_FORM_MERGED) {
+        err = "form must be MLN_FORM_STRANG or MLN_FORM_MERGED";
         return MLN_EINVAL;
     }
     if (p.boundary != MLN_BC_PERIODIC && p.boundary != MLN_BC_OPEN) {
@@ -450,6 +450,8 @@ mln_status build_setup(const mln_params &p, Setup &s, std::string &err) {
     CMat Wh = cadj(Wm, n);
     s.T.assign((size_t)D * D, 0.0);
     s.theta.assign(q, 0.0);
+    s.psi.assign(n - 1, 0.0);
+    for (int a = 0; a < n - 1; ++a) s.psi[a] = (mev[a] - mev[n - 1]) / kHbar;
     auto put_col = [&](int col, const CMat &X) {
         for (int j = 0; j < D; ++j) s.T[j * D + col] = 0.5 * trace_of_product(X, g[j], n).real();
     };
@@ -501,18 +503,17 @@ mln_status build_setup(const mln_params &p, Setup &s, std::string &err) {
         s.c = 0.5 * p.N_a * acc;
     }
 
-    // Rotated form. With p = T^T (A0 d + b) before the rotation of a step:
-    // d^{n+1/2} = A0 T R p + b, p_next = T^T (A0 d^{n+1/2} + b) = C R p + cp,
-    // C = T^T A0^2 T, cp = T^T (A0 b + b); dP/dt = (T^T A0^T w) . (R p) + (w . b + c).
+    // Merged form (state y = d' = A0 d + b after the first half-step of Eq. 23a):
+    // y'' = exp(U E dt) y; dP/dt = w . (A0 y'' + b) + c = (A0^T w) . y'' + (w . b + c);
+    // the next state is A0 (A0 y'' + b) + b = y'' + (A0^2 - I) y'' + (A0 b + b).
     RMat A0sq = rmul(s.A0, s.A0, D);
-    s.C = rmul(Tt, rmul(A0sq, s.T, D), D);
-    std::vector<double> A0b = rmatvec(s.A0, s.b, D);
-    for (int i = 0; i < D; ++i) A0b[i] += s.b[i];
-    s.cp = rmatvec(Tt, A0b, D);
-    RMat A0t = rtrans(s.A0, D);
-    s.wr = rmatvec(Tt, rmatvec(A0t, s.w, D), D);
-    s.cr = s.c;
-    for (int i = 0; i < D; ++i) s.cr += s.w[i] * s.b[i];
+    s.C1 = A0sq;
+    for (int i = 0; i < D; ++i) s.C1[i * D + i] -= 1.0;
+    s.b2 = rmatvec(s.A0, s.b, D);
+    for (int i = 0; i < D; ++i) s.b2[i] += s.b[i];
+    s.wm = rmatvec(rtrans(s.A0, D), s.w, D);
+    s.cm = s.c;
+    for (int i = 0; i < D; ++i) s.cm += s.w[i] * s.b[i];
 
     // State <-> adjoint vector maps.
     s.Sd.assign((size_t)D * D, 0.0);
@@ -522,11 +523,11 @@ mln_status build_setup(const mln_params &p, Setup &s, std::string &err) {
     if (p.form == MLN_FORM_STRANG) {
         for (int i = 0; i < D; ++i) s.Sd[i * D + i] = s.Sp[i * D + i] = 1.0;
     } else {
-        // d = A0^-1 (T p - b) = A0inv T p + binv;  p = T^T A0 d + T^T b
-        s.Sd = rmul(s.A0inv, s.T, D);
+        // d = A0^-1 (y - b) = A0inv y + binv;  y = A0 d + b
+        s.Sd = s.A0inv;
         s.sd0 = s.binv;
-        s.Sp = rmul(Tt, s.A0, D);
-        s.sp0 = rmatvec(Tt, s.b, D);
+        s.Sp = s.A0;
+        s.sp0 = s.b;
     }
 
     // rho = I/N + 1/2 sum_j d_j s_j (Eq. 6) as rho_c + Z d over interleaved re/im.

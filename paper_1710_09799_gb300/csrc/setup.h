@@ -22,13 +22,14 @@ struct Setup {
     std::vector<double> d_eq, v;          // D (Eqs. 12, 15)
     std::vector<double> A0, b;            // exp(M dt/2) and its affine offset (Eq. 23)
     std::vector<double> A0inv, binv;      // exp(-M dt/2) of the same affine flow
-    std::vector<double> T, theta;         // real eigenbasis of U (Eq. 26), rotation rates
+    std::vector<double> T, theta;         // real eigenbasis of U (Eq. 26), plane rotation rates
+    std::vector<double> psi;              // (m_a - m_{N-1})/hbar, a < N-1: base rates of the planes
     std::vector<double> w;                // N_a/2 M^T v  (Eq. 17)
     double c = 0;                         // N_a/2 v^T d_eq
     std::vector<double> d0;               // adjoint vector of rho0 (Eq. 6)
-    // rotated form: p = T^T (A0 d + b); step p <- C R(E) p + cp, dP/dt = wr . R(E) p + cr
-    std::vector<double> C, cp, wr;
-    double cr = 0;
+    // merged form: state y = A0 d + b; C1 = A0^2 - I, b2 = A0 b + b, wm = A0^T w, cm = w . b + c
+    std::vector<double> C1, b2, wm;
+    double cm = 0;
     // device state -> adjoint vector d = sd0 + Sd state, and back state = sp0 + Sp d
     std::vector<double> Sd, sd0, Sp, sp0;
     // rho (2 N^2 reals, interleaved re/im) = rho_c + Z d   (Eq. 6)

@@ -23,14 +23,14 @@ MLN_OK, MLN_EINVAL, MLN_ENOMEM, MLN_ECUDA, MLN_ENUMERIC, MLN_ETIMEOUT, MLN_EUNSU
 MLN_BC_PERIODIC, MLN_BC_OPEN = 0, 1
 MLN_SRC_NONE, MLN_SRC_HARD, MLN_SRC_SOFT = 0, 1, 2
 MLN_FP64, MLN_FP32 = 0, 1
-MLN_FORM_STRANG, MLN_FORM_ROTATED = 0, 1
+MLN_FORM_STRANG, MLN_FORM_MERGED = 0, 1
 MLN_MIN_N, MLN_MAX_N = 2, 6
 _DMAX = MLN_MAX_N * MLN_MAX_N - 1
 
 BOUNDARY = {"periodic": MLN_BC_PERIODIC, "open": MLN_BC_OPEN}
 SOURCE = {"none": MLN_SRC_NONE, "hard": MLN_SRC_HARD, "soft": MLN_SRC_SOFT}
 PRECISION = {"fp64": MLN_FP64, "fp32": MLN_FP32}
-FORM = {"strang": MLN_FORM_STRANG, "rotated": MLN_FORM_ROTATED}
+FORM = {"strang": MLN_FORM_STRANG, "merged": MLN_FORM_MERGED}
 
 _dp = C.POINTER(C.c_double)
 
@@ -54,7 +54,7 @@ class mln_setup(C.Structure):
         ("N", C.c_int32), ("D", C.c_int32), ("q", C.c_int32), ("reserved", C.c_int32),
         ("M", C.c_double * (_DMAX * _DMAX)), ("U", C.c_double * (_DMAX * _DMAX)),
         ("A0", C.c_double * (_DMAX * _DMAX)), ("T", C.c_double * (_DMAX * _DMAX)),
-        ("C", C.c_double * (_DMAX * _DMAX)),
+        ("C1", C.c_double * (_DMAX * _DMAX)),
         ("d_eq", C.c_double * _DMAX), ("v", C.c_double * _DMAX), ("b", C.c_double * _DMAX),
         ("w", C.c_double * _DMAX), ("d0", C.c_double * _DMAX),
         ("theta", C.c_double * (MLN_MAX_N * (MLN_MAX_N - 1) // 2)),
@@ -85,6 +85,7 @@ _SIGS = {
     "mln_create_error": (C.c_char_p, []),
     "mln_setup_host": (C.c_int, [_P, C.POINTER(mln_setup)]),
     "mln_version": (C.c_char_p, []),
+    "mln_rotation_terms": (C.c_int, [C.c_int32, _dp, C.c_int64, _dp, _dp]),
 }
 
 _lib = None
@@ -236,9 +237,16 @@ def mln_setup_host(params: Params) -> dict:
     m = lambda a: np.array(a[:D * D]).reshape(D, D)
     v = lambda a: np.array(a[:D])
     gen = np.array(out.gen[:2 * D * N * N]).view(np.complex128).reshape(D, N, N)
-    return dict(N=N, D=D, q=q, M=m(out.M), U=m(out.U), A0=m(out.A0), T=m(out.T), C=m(out.C),
+    return dict(N=N, D=D, q=q, M=m(out.M), U=m(out.U), A0=m(out.A0), T=m(out.T), C1=m(out.C1),
                 d_eq=v(out.d_eq), v=v(out.v), b=v(out.b), w=v(out.w), d0=v(out.d0),
                 theta=np.array(out.theta[:q]), c=out.c, gen=gen)
+
+
+def mln_rotation_terms(precision: str, x):
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    s, c1 = np.zeros_like(x), np.zeros_like(x)
+    _check(lib().mln_rotation_terms(PRECISION.get(precision, precision), _ptr(x), len(x), _ptr(s), _ptr(c1)))
+    return s, c1
 
 
 def mln_version() -> str:

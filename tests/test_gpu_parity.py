@@ -40,7 +40,7 @@ def pops(rho):
     return np.einsum("cii->ci", rho).real
 
 
-@pytest.mark.parametrize("form", ["strang", "rotated"])
+@pytest.mark.parametrize("form", ["strang", "merged"])
 def test_two_level_sit_full_fp64(orc, form):
     """The two-level workload at full size: 2000 cells, medium [500, 1500),
     sech pulse of area 2 pi, hard source + Mur, 20000 steps."""
@@ -54,7 +54,7 @@ def test_two_level_sit_full_fp64(orc, form):
     assert pops(ref.rho)[:, 1].max() > 1e-3  # the pulse reached and excited the medium
 
 
-@pytest.mark.parametrize("form", ["strang", "rotated"])
+@pytest.mark.parametrize("form", ["strang", "merged"])
 def test_three_level_ring_small_fp64(orc, form):
     """Three-level ring, 4096 cells (several tiles, ragged last tile), 1500 steps."""
     p = W.three_level_ring(n_cells=4096, n_steps=1500)
@@ -66,7 +66,7 @@ def test_three_level_ring_small_fp64(orc, form):
     assert np.abs(rho - ref.rho).max() < FP64_POP
 
 
-@pytest.mark.parametrize("form", ["strang", "rotated"])
+@pytest.mark.parametrize("form", ["strang", "merged"])
 def test_six_level_small_fp64(orc, form):
     """Six-level manifold (D = 35), 700 cells (medium up to the cell before the
     Mur cell), Gaussian source, 400 steps."""
@@ -89,7 +89,7 @@ def test_other_N_fp64(orc, N):
                   medium_end=650, boundary="periodic", n_steps=300,
                   E_init=rng.normal(0, 1e8, size=777))
     ref = oracle_ref(orc, p, p.n_steps)
-    for form in ("strang", "rotated"):
+    for form in ("strang", "merged"):
         E, H, rho, _ = gpu_run(p, p.n_steps, "fp64", form)
         assert rel_inf(E, ref.E) < FP64_E
         assert np.abs(rho - ref.rho).max() < FP64_POP
@@ -100,7 +100,7 @@ def test_three_level_ring_full_size_sampled(orc):
     sampled across tiles are recomputed by the oracle from their light cones."""
     p = W.three_level_ring()
     steps = 200
-    for form in ("strang", "rotated"):
+    for form in ("strang", "merged"):
         E, H, rho, s = gpu_run(p, steps, "fp64", form)
         for c in (0, 431, 432, 30000, 65535):
             e, h, r = orc.run_window(p, c, steps)
@@ -114,7 +114,7 @@ def test_fp32_error_bounds(orc):
     p = W.three_level_ring(n_cells=4096, n_steps=2000)
     ref = oracle_ref(orc, p, p.n_steps)
     k = p.n_steps / 1000
-    for form in ("strang", "rotated"):
+    for form in ("strang", "merged"):
         E, H, rho, _ = gpu_run(p, p.n_steps, "fp32", form)
         e_err = rel_inf(E, ref.E)
         p_err = np.abs(pops(rho) - pops(ref.rho)).max()
@@ -127,7 +127,7 @@ def test_fp32_two_level(orc):
     p = W.two_level_sit(n_steps=6000)
     ref = oracle_ref(orc, p, p.n_steps)
     k = p.n_steps / 1000
-    for form in ("strang", "rotated"):
+    for form in ("strang", "merged"):
         E, H, rho, _ = gpu_run(p, p.n_steps, "fp32", form)
         e_err = rel_inf(E, ref.E)
         p_err = np.abs(pops(rho) - pops(ref.rho)).max()
@@ -151,8 +151,8 @@ def test_launch_shape_does_not_change_results(shape):
 
 def test_step_splitting_is_exact():
     p = W.two_level_sit(n_steps=900)
-    E0, H0, r0, _ = gpu_run(p, 900, "fp64", "rotated")
-    E1, H1, r1, _ = gpu_run(p, 900, "fp64", "rotated", chunks=[1, 16, 17, 300, 566])
+    E0, H0, r0, _ = gpu_run(p, 900, "fp64", "merged")
+    E1, H1, r1, _ = gpu_run(p, 900, "fp64", "merged", chunks=[1, 16, 17, 300, 566])
     assert np.array_equal(E0, E1) and np.array_equal(r0, r1)
 
 
@@ -177,7 +177,7 @@ def test_edge_cases(orc, case):
     else:
         p = W.two_level_sit(n_cells=300, medium=(100, 200), n_steps=500).with_(eps_r=2.25, mu_r=1.1)
     ref = oracle_ref(orc, p, p.n_steps)
-    for form in ("strang", "rotated"):
+    for form in ("strang", "merged"):
         E, H, rho, _ = gpu_run(p, p.n_steps, "fp64", form, block_steps=7)
         assert rel_inf(E, ref.E) < FP64_E, case
         if p.n_medium:
@@ -187,7 +187,7 @@ def test_edge_cases(orc, case):
 def test_zero_steps_and_state_round_trip(orc):
     p = W.three_level_ring(n_cells=500, n_steps=100)
     for prec in ("fp64", "fp32"):
-        for form in ("strang", "rotated"):
+        for form in ("strang", "merged"):
             s = make_solver(p, prec, form)
             s.step(0)
             s.sync()
@@ -210,7 +210,7 @@ def test_resume_matches_uninterrupted_run(orc):
     oracle's 800-step run (the checkpoint is the precision-independent d)."""
     p = W.three_level_ring(n_cells=2048, n_steps=800)
     ref = oracle_ref(orc, p, 800)
-    _, _, _, s = gpu_run(p, 400, "fp64", "rotated")
+    _, _, _, s = gpu_run(p, 400, "fp64", "merged")
     d, E, H = s.save()
     s2 = make_solver(p, "fp64", "strang")
     s2.load(d, E, H)
@@ -224,7 +224,7 @@ def test_resume_matches_uninterrupted_run(orc):
 def test_nonfinite_field_is_reported():
     from paper_1710_09799_gb300 import mln
     p = W.three_level_ring(n_cells=256, n_steps=10)
-    s = make_solver(p, "fp64", "rotated")
+    s = make_solver(p, "fp64", "merged")
     E = p.e_init().copy()
     E[100] = np.nan
     s.load(E=E)
@@ -239,9 +239,33 @@ def test_nonfinite_field_is_reported():
 
 def test_populations_and_rho_agree():
     p = W.three_level_ring(n_cells=300, n_steps=50)
-    _, _, rho, s = gpu_run(p, 50, "fp64", "rotated")
+    _, _, rho, s = gpu_run(p, 50, "fp64", "merged")
     pp = s.populations()
     assert np.abs(pp - pops(rho)).max() < 1e-15
     sub = s.rho(10, 5)
     assert np.array_equal(sub, rho[10:15])
     assert np.abs(np.einsum("cii->c", rho) - 1).max() < 1e-14
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_rotation_terms_against_exact(precision):
+    """(sin x, cos x - 1) as the kernels evaluate them (series for |x| <= 1/8,
+    half-angle library sincos above) against 50-digit values, within a few
+    units in the last place of the kernel's precision."""
+    import mpmath
+    from paper_1710_09799_gb300 import mln
+    rng = np.random.default_rng(0)
+    x = np.concatenate([rng.uniform(-0.125, 0.125, 3000), rng.uniform(-3, 3, 2000),
+                        10.0 ** rng.uniform(-12, -1, 1000) * rng.choice([-1, 1], 1000),
+                        [0.0, 0.125, -0.125, 0.12500001, 1e-300, 50.0]])
+    if precision == "fp32":
+        x = x.astype(np.float32).astype(np.float64)
+    s, c1 = mln.mln_rotation_terms(precision, x)
+    eps = np.finfo(np.float64 if precision == "fp64" else np.float32).eps
+    with mpmath.workdps(50):
+        ref_s = np.array([float(mpmath.sin(mpmath.mpf(v))) for v in x])
+        ref_c = np.array([float(-2 * mpmath.sin(mpmath.mpf(v) / 2) ** 2) for v in x])
+    tol_s = 6 * eps * np.maximum(np.abs(ref_s), np.finfo(float).tiny)
+    tol_c = 6 * eps * np.maximum(np.abs(ref_c), np.finfo(float).tiny)
+    assert np.all(np.abs(s - ref_s) <= tol_s), np.max(np.abs(s - ref_s) / np.maximum(np.abs(ref_s), 1e-300))
+    assert np.all(np.abs(c1 - ref_c) <= tol_c), np.max(np.abs(c1 - ref_c) / np.maximum(np.abs(ref_c), 1e-300))

@@ -174,11 +174,11 @@ def test_polarisation_coefficients_match_oracle(lib, orc, N):
         assert abs(got - ref) < 1e-12 * abs(ref)
 
 
-def test_rotated_form_constants(lib):
-    """C = T^T A0^2 T (the merged half-steps of the rotated form)."""
+def test_merged_form_constants(lib):
+    """C1 = A0^2 - I: the two half-steps of Eq. 23 that meet between steps."""
     p = random_problem(3, 50)
     s = mln.mln_setup_host(params_of(p))
-    assert np.abs(s["C"] - s["T"].T @ s["A0"] @ s["A0"] @ s["T"]).max() < 1e-14
+    assert np.abs(s["C1"] - (s["A0"] @ s["A0"] - np.eye(s["D"]))).max() < 1e-15
 
 
 def _status_of(fn):
