@@ -225,16 +225,17 @@ def test_nonfinite_field_is_reported():
     from paper_1710_09799_gb300 import mln
     p = W.three_level_ring(n_cells=256, n_steps=10)
     s = make_solver(p, "fp64", "merged")
-    E = p.e_init().copy()
+    d0, E0, H0 = s.save()
+    E = E0.copy()
     E[100] = np.nan
     s.load(E=E)
     s.step(10)
     with pytest.raises(mln.MLNError) as ei:
         s.sync()
     assert ei.value.status == mln.MLN_ENONFINITE
-    s.load(E=p.e_init())  # the context stays usable
+    s.load(d0, E0, H0)  # the NaN reached the medium too; reload everything
     s.step(5)
-    s.sync()
+    s.sync()  # the context stays usable and the flag was cleared
 
 
 def test_populations_and_rho_agree():
