@@ -156,20 +156,20 @@ def max_over_ranks(ws, x: float) -> float:
     return float(t.item())
 
 
-def make_params(p, precision, form, block_steps=0, tile_cells=0):
+def make_params(p, precision, form, block_steps=0, tile_cells=0, kernel="auto"):
     from paper_1710_09799_gb300 import mln
     return mln.Params(N=p.N, H0=p.H0, mu=p.mu, G=p.G, rho0=p.rho0, N_a=p.N_a, n_cells=p.n_cells,
                       medium_begin=p.medium_begin, medium_end=p.medium_end, dx=p.dx, dt=p.dt,
                       boundary=p.boundary, precision=precision, form=form, block_steps=block_steps,
-                      tile_cells=tile_cells)
+                      tile_cells=tile_cells, kernel=kernel)
 
 
 def time_device(p, precision, form, seg, steps, warmup, block_steps, tile_cells, ws, flush=True,
-                sampler=None):
+                sampler=None, kernel="auto"):
     """Device-timed run: returns dict with total ms (max over ranks), launches, shape."""
     import torch
     from paper_1710_09799_gb300 import mln
-    s = mln.Solver(make_params(p, precision, form, block_steps, tile_cells), E0=p.e_init())
+    s = mln.Solver(make_params(p, precision, form, block_steps, tile_cells, kernel), E0=p.e_init())
     stream = s.stream
     for _ in range(warmup):
         s.step(seg)
@@ -297,6 +297,7 @@ def main():
     ap.add_argument("--seg", type=int, default=1000, help="time steps per benchmark step")
     ap.add_argument("--block-steps", type=int, default=20)
     ap.add_argument("--tile", type=int, default=0)
+    ap.add_argument("--kernel", default="auto", choices=["auto", "register", "sparse"])
     ap.add_argument("--quick", action="store_true", help="skip variants, e2e and the CPU baseline")
     args = ap.parse_args()
     if args.impl == "reference":
@@ -315,7 +316,7 @@ def main():
     smi_index = int(vis.split(",")[local]) if vis and vis.split(",")[local].isdigit() else local
     sampler = ClockSampler(smi_index)
     main_run = time_device(p, args.precision, args.form, args.seg, args.steps, args.warmup, args.block_steps,
-                           args.tile, ws, sampler=sampler)
+                           args.tile, ws, sampler=sampler, kernel=args.kernel)
     total_s = main_run["ms"] / 1e3
     cell_updates = p.n_cells * args.seg * args.steps
     value = ws * cell_updates / total_s
@@ -343,7 +344,7 @@ def main():
         "data": "synthetic (seeded: levels, dipoles, rates, noise E^0)",
         "config": {"workload": WORKLOAD, "n_cells": p.n_cells, "levels": p.N,
                    "time_steps_per_step": args.seg, "time_steps_total": args.seg * args.steps,
-                   "form": args.form, "precision": args.precision,
+                   "form": args.form, "precision": args.precision, "kernel": args.kernel,
                    "block_steps": main_run["shape"][0], "tile_cells": main_run["shape"][1],
                    "threads_per_block": main_run["shape"][2],
                    "l2": "flushed between steps (256 MiB write); state 5.2 MB stays on chip within a step",
@@ -355,12 +356,13 @@ def main():
 
     if not args.quick and rank == 0:
         variants = {}
-        for prec, form in (("fp64", "strang"), ("fp32", "merged"), ("fp32", "strang")):
-            if (prec, form) == (args.precision, args.form):
+        for prec, form, kern in (("fp64", "merged", "register"), ("fp64", "strang", "auto"),
+                                 ("fp32", "merged", "auto"), ("fp32", "strang", "auto")):
+            if (prec, form, kern) == (args.precision, args.form, args.kernel):
                 continue
-            r = time_device(p, prec, form, args.seg, 10, 2, args.block_steps, args.tile, 1)
-            variants[f"{prec}_{form}"] = {"value": p.n_cells * args.seg * 10 / (r["ms"] / 1e3), "unit": UNIT,
-                                          "ms_per_step": r["ms"] / 10}
+            r = time_device(p, prec, form, args.seg, 10, 2, args.block_steps, args.tile, 1, kernel=kern)
+            variants[f"{prec}_{form}_{kern}"] = {"value": p.n_cells * args.seg * 10 / (r["ms"] / 1e3), "unit": UNIT,
+                                                 "ms_per_step": r["ms"] / 10}
         line["variants"] = variants
         line["e2e"] = time_e2e(p, args.precision, args.form, args.seg, min(10, args.steps))
         if ws == 1:

@@ -64,6 +64,14 @@ enum { MLN_FP64 = 0, MLN_FP32 = 1 };
  * Both apply each propagator as identity + increment, which keeps the
  * rounding of the small coherences at their own scale. */
 enum { MLN_FORM_STRANG = 0, MLN_FORM_MERGED = 1 };
+/* Cell model of the step kernel. MLN_KERNEL_REGISTER keeps each cell's
+ * vector in registers and multiplies by the full D x D constant matrices.
+ * MLN_KERNEL_SPARSE (FP64, merged form only) keeps the vectors in shared
+ * memory and multiplies only by the entries of the constant matrices that
+ * are not exactly zero; the sums run in the same order, so both give the
+ * same result. MLN_KERNEL_AUTO picks SPARSE for FP64 merged, REGISTER
+ * otherwise. */
+enum { MLN_KERNEL_AUTO = 0, MLN_KERNEL_REGISTER = 1, MLN_KERNEL_SPARSE = 2 };
 
 #define MLN_MIN_N 2
 #define MLN_MAX_N 6
@@ -97,6 +105,7 @@ enum { MLN_FORM_STRANG = 0, MLN_FORM_MERGED = 1 };
  *   block_steps   steps fused into one kernel launch (temporal blocking);
  *                 0 picks a default. 1..64.
  *   tile_cells    cells written by one thread block; 0 picks a default.
+ *   kernel        MLN_KERNEL_AUTO, MLN_KERNEL_REGISTER or MLN_KERNEL_SPARSE.
  */
 typedef struct mln_params {
     int32_t N;
@@ -106,7 +115,7 @@ typedef struct mln_params {
     int32_t source_kind;
     int32_t block_steps;
     int32_t tile_cells;
-    int32_t reserved0;
+    int32_t kernel;
     const double *H0;
     const double *mu;
     const double *G;

@@ -25,8 +25,11 @@ struct mln_ctx {
     cudaStream_t stream = nullptr;
     unsigned int *flags = nullptr;
     std::vector<unsigned char> consts;
-    int K = 16, tile = 0, threads = 0;
+    int K = 16, tile = 0, threads = 0, max_threads = mln::kMaxThreads;
     int64_t steps = 0, launches = 0;
+    bool sparse = false;               // shared-memory sparse cell model (FP64 merged)
+    void *prog = nullptr;              // its program: rowptr | cols | vals
+    int nnz = 0, nrowptr = 0;
     // output tables (FP64, device): rows x D matrix followed by rows offsets
     double *tab_rho = nullptr, *tab_pop = nullptr, *tab_d = nullptr, *tab_in = nullptr;
     void *scratch = nullptr;
@@ -117,23 +120,45 @@ mln_status upload_table(mln_ctx *c, double **dst, const std::vector<double> &mat
 void pick_launch_shape(mln_ctx *c) {
     int dev = 0, sms = 152;
     if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int maxt = c->max_threads;
     c->K = c->p.block_steps > 0 ? c->p.block_steps : 16;
+    if (2 * c->K > maxt - 32) c->K = (maxt - 32) / 2;
     const int64_t n = c->p.n_cells;
     int tile = c->p.tile_cells;
     if (tile <= 0) {
-        // one tile per SM (or per SM multiple) while a block stays <= kMaxThreads threads
+        // one tile per SM (or per SM multiple) while a block stays <= maxt threads
         int64_t ntiles = sms;
         tile = static_cast<int>((n + ntiles - 1) / ntiles);
-        while (tile + 2 * c->K > mln::kMaxThreads) {
+        while (tile + 2 * c->K > maxt) {
             ntiles += sms;
             tile = static_cast<int>((n + ntiles - 1) / ntiles);
         }
         tile = std::max(tile, 1);
     }
     if (tile > n) tile = static_cast<int>(n);
-    if (tile + 2 * c->K > mln::kMaxThreads) tile = mln::kMaxThreads - 2 * c->K;
+    if (tile + 2 * c->K > maxt) tile = maxt - 2 * c->K;
     c->tile = tile;
     c->threads = (tile + 2 * c->K + 31) / 32 * 32;
+}
+
+cudaError_t launch(mln_ctx *c, const mln::BlockArgs<double> &a, dim3 g, dim3 b, size_t smem) {
+    if (c->sparse) return mln::launch_block_sparse(c->p.N, a, c->consts, g, b, smem, c->stream);
+    return mln::launch_block(c->p.N, c->p.form, a, c->consts, g, b, smem, c->stream);
+}
+
+cudaError_t launch(mln_ctx *c, const mln::BlockArgs<float> &a, dim3 g, dim3 b, size_t smem) {
+    return mln::launch_block(c->p.N, c->p.form, a, c->consts, g, b, smem, c->stream);
+}
+
+// Largest block (multiple of 32, <= kMaxThreads) whose shared memory fits.
+int sparse_max_threads(mln_ctx *c) {
+    const size_t limit = 227 * 1024 - 1024;
+    int best = 0;
+    for (int t = 32; t <= mln::kMaxThreads; t += 32) {
+        size_t bytes = 2 * static_cast<size_t>(t) * sizeof(double) + mln::sparse_smem_bytes(c->p.N, t, c->nnz, c->nrowptr);
+        if (bytes <= limit) best = t;
+    }
+    return best;
 }
 
 template <typename R>
@@ -158,7 +183,8 @@ mln_status run_steps(mln_ctx *c, int64_t n_steps, const double *src) {
     a.cb = static_cast<R>((c->p.dt / eps) / (1.0 + sg));
     a.inv_dx = static_cast<R>(1.0 / c->p.dx);
     a.kappa = static_cast<R>((cv * c->p.dt - c->p.dx) / (cv * c->p.dt + c->p.dx));
-    const size_t smem = 2 * static_cast<size_t>(c->threads) * sizeof(R);
+    size_t smem = 2 * static_cast<size_t>(c->threads) * sizeof(R);
+    if (c->sparse) smem += mln::sparse_smem_bytes(c->p.N, c->threads, c->nnz, c->nrowptr);
     int cur = 0;
     for (int64_t done = 0; done < n_steps;) {
         int ns = static_cast<int>(std::min<int64_t>(c->K, n_steps - done));
@@ -170,8 +196,7 @@ mln_status run_steps(mln_ctx *c, int64_t n_steps, const double *src) {
         a.s_out = static_cast<R *>(c->st[cur ^ 1]);
         a.src = (src && c->p.source_kind != MLN_SRC_NONE) ? src + done : nullptr;
         a.nsteps = ns;
-        cudaError_t e = mln::launch_block(c->p.N, c->p.form, a, c->consts, dim3(static_cast<unsigned>(ntiles)),
-                                          dim3(c->threads), smem, c->stream);
+        cudaError_t e = launch(c, a, dim3(static_cast<unsigned>(ntiles)), dim3(c->threads), smem);
         if (e != cudaSuccess) {
             c->err = std::string("step kernel launch: ") + cudaGetErrorString(e);
             return MLN_ECUDA;
@@ -356,6 +381,7 @@ void mln_destroy(mln_ctx *c) {
     cudaFree(c->tab_d);
     cudaFree(c->tab_in);
     cudaFree(c->scratch);
+    cudaFree(c->prog);
     delete c;
 }
 
@@ -391,13 +417,46 @@ mln_status mln_create(const mln_params *p, void *d_state, void *Ez, void *Hy, vo
     c->E[0] = Ez;
     c->H[0] = Hy;
     c->stream = static_cast<cudaStream_t>(stream);
-    bool ok = p->precision == MLN_FP64 ? mln::pack_consts(c->s, p->form, p->dt, 0.0, c->consts)
-                                       : mln::pack_consts(c->s, p->form, p->dt, 0.0f, c->consts);
+    c->sparse = p->kernel == MLN_KERNEL_SPARSE ||
+                (p->kernel == MLN_KERNEL_AUTO && p->precision == MLN_FP64 && p->form == MLN_FORM_MERGED);
     auto fail = [&](mln_status s_) {
         g_create_err = c->err.empty() ? err : c->err;
         mln_destroy(c);
         return s_;
     };
+    bool ok;
+    if (c->sparse) {
+        std::vector<int32_t> rowptr, cols;
+        std::vector<double> vals;
+        mln::build_sparse_program(c->s, rowptr, cols, vals);
+        c->nnz = static_cast<int>(vals.size());
+        c->nrowptr = static_cast<int>(rowptr.size());
+        size_t b_rp = rowptr.size() * 4, b_cols = cols.size() * 4;
+        size_t off_vals = (b_rp + b_cols + 15) / 16 * 16;
+        size_t bytes = off_vals + vals.size() * 8 + 16;
+        std::vector<unsigned char> host(bytes, 0);
+        std::memcpy(host.data(), rowptr.data(), b_rp);
+        std::memcpy(host.data() + b_rp, cols.data(), b_cols);
+        std::memcpy(host.data() + off_vals, vals.data(), vals.size() * 8);
+        if (cudaMalloc(&c->prog, bytes) != cudaSuccess ||
+            cudaMemcpy(c->prog, host.data(), bytes, cudaMemcpyHostToDevice) != cudaSuccess) {
+            cudaGetLastError();
+            c->err = "upload of the sparse program failed";
+            return fail(MLN_ENOMEM);
+        }
+        unsigned char *base = static_cast<unsigned char *>(c->prog);
+        ok = mln::pack_sparse_consts(c->s, p->dt, reinterpret_cast<const int32_t *>(base),
+                                     reinterpret_cast<const int32_t *>(base + b_rp),
+                                     reinterpret_cast<const double *>(base + off_vals), c->nnz, c->nrowptr, c->consts);
+        c->max_threads = sparse_max_threads(c);
+        if (c->max_threads < 64) {
+            c->err = "sparse program does not fit in shared memory";
+            return fail(MLN_EUNSUPPORTED);
+        }
+    } else {
+        ok = p->precision == MLN_FP64 ? mln::pack_consts(c->s, p->form, p->dt, 0.0, c->consts)
+                                      : mln::pack_consts(c->s, p->form, p->dt, 0.0f, c->consts);
+    }
     if (!ok) {
         c->err = "no kernel for this N";
         return fail(MLN_EUNSUPPORTED);

@@ -74,7 +74,69 @@ cudaError_t launch_one(const BlockArgs<R> &a, const std::vector<unsigned char> &
     K k;
     if (consts.size() != sizeof(K)) return cudaErrorInvalidValue;
     std::memcpy(&k, consts.data(), sizeof(K));
-    mln_block_kernel<N, R, K><<<grid, block, smem, st>>>(a, k);
+    mln_block_kernel<N, R, RegisterCell<N, R, K>><<<grid, block, smem, st>>>(a, k);
+    return cudaGetLastError();
+}
+
+// The sparse program of the merged FP64 step (see SparseConsts): entries of
+// T^T on the plane rows, T on the plane columns, A0^2 - I and A0^T w whose
+// FP64 value is not exactly zero.
+inline void build_sparse_program(const Setup &s, std::vector<int32_t> &rowptr, std::vector<int32_t> &cols,
+                                 std::vector<double> &vals) {
+    const int D = s.D, P = 2 * s.q;
+    rowptr.clear();
+    cols.clear();
+    vals.clear();
+    auto put = [&](int c, double v) {
+        if (v != 0.0) {
+            cols.push_back(c);
+            vals.push_back(v);
+        }
+    };
+    for (int r = 0; r < P; ++r) {  // z_r = sum_i T[i][r] y_i
+        rowptr.push_back(static_cast<int32_t>(vals.size()));
+        for (int i = 0; i < D; ++i) put(i, s.T[i * D + r]);
+    }
+    rowptr.push_back(static_cast<int32_t>(vals.size()));
+    for (int r = 0; r < D; ++r) {  // y_r += sum_k T[r][k] z_k
+        for (int k = 0; k < P; ++k) put(k, s.T[r * D + k]);
+        rowptr.push_back(static_cast<int32_t>(vals.size()));
+    }
+    for (int r = 0; r < D; ++r) {  // (C1 y)_r
+        for (int j = 0; j < D; ++j) put(j, s.C1[r * D + j]);
+        rowptr.push_back(static_cast<int32_t>(vals.size()));
+    }
+    for (int i = 0; i < D; ++i) put(i, s.wm[i]);  // wm . y
+    rowptr.push_back(static_cast<int32_t>(vals.size()));
+}
+
+template <int N>
+void pack_sparse(const Setup &s, double dt, const int32_t *rowptr, const int32_t *cols, const double *vals,
+                 int nnz, int nrowptr, std::vector<unsigned char> &out) {
+    SparseConsts<N> k;
+    std::memset(&k, 0, sizeof(k));
+    for (int i = 0; i < Dims<N>::D; ++i) k.b2[i] = s.b2[i];
+    for (int a = 0; a < N - 1; ++a) k.psi_dt[a] = s.psi[a] * dt;
+    k.cm = s.cm;
+    k.rowptr = rowptr;
+    k.cols = cols;
+    k.vals = vals;
+    k.nnz = nnz;
+    k.nrowptr = nrowptr;
+    out.resize(sizeof(k));
+    std::memcpy(out.data(), &k, sizeof(k));
+}
+
+template <int N>
+cudaError_t launch_sparse_one(const BlockArgs<double> &a, const std::vector<unsigned char> &consts, dim3 grid,
+                              dim3 block, size_t smem, cudaStream_t st) {
+    SparseConsts<N> k;
+    if (consts.size() != sizeof(k)) return cudaErrorInvalidValue;
+    std::memcpy(&k, consts.data(), sizeof(k));
+    auto kern = mln_block_kernel<N, double, SharedSparseCell<N>>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+    if (e != cudaSuccess) return e;
+    kern<<<grid, block, smem, st>>>(a, k);
     return cudaGetLastError();
 }
 
@@ -106,5 +168,10 @@ cudaError_t launch_block(int N, int form, const BlockArgs<double> &a, const std:
 cudaError_t launch_block(int N, int form, const BlockArgs<float> &a, const std::vector<unsigned char> &consts,
                          dim3 grid, dim3 block, size_t smem, cudaStream_t st);
 cudaError_t launch_sin_cosm1(int precision, const double *x, int64_t n, double *s, double *c1, cudaStream_t st);
+bool pack_sparse_consts(const Setup &s, double dt, const int32_t *rowptr, const int32_t *cols, const double *vals,
+                        int nnz, int nrowptr, std::vector<unsigned char> &out);
+cudaError_t launch_block_sparse(int N, const BlockArgs<double> &a, const std::vector<unsigned char> &consts,
+                                dim3 grid, dim3 block, size_t smem, cudaStream_t st);
+size_t sparse_smem_bytes(int N, int threads, int nnz, int nrowptr);
 
 }  // namespace mln

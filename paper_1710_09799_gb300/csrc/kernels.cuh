@@ -83,30 +83,47 @@ struct BlockArgs {
 __device__ __forceinline__ void sincos_r(double x, double *s, double *c) { sincos(x, s, c); }
 __device__ __forceinline__ void sincos_r(float x, float *s, float *c) { sincosf(x, s, c); }
 
-// Truncated Taylor series of sin x and cos x - 1 for |x| <= 1/8. With terms
-// up to x^11 (sin) and x^12 (cos - 1) the Lagrange remainder is below
-// 2^-36/13! ~ 2e-21 relative in FP64; FP32 keeps terms up to x^7 / x^8
-// (remainder below 2^-24/9! ~ 2e-13).
+// Truncated Taylor series of sin x and cos x - 1 for |x| <= 1/8, bounded by
+// the Lagrange remainder: FP64 up to x^11 / x^12 (remainder below
+// 2^-36/13! ~ 2e-21 relative), fewer terms for smaller |x|; FP32 up to
+// x^7 / x^8 (remainder below 2^-24/9! ~ 2e-13).
 template <typename R>
 struct SmallAngle;
 template <>
 struct SmallAngle<double> {
     static constexpr double kMax = 0.125;
+    // Three tiers by |x|: the number of terms is the fewest that keeps the
+    // remainder below 1e-20 relative (|x| <= 2^-16: to x^3 / x^4;
+    // |x| <= 2^-6: to x^7 / x^8; |x| <= 1/8: to x^11 / x^12).
     __device__ __forceinline__ static void eval(double x, double &s, double &c1) {
         const double x2 = x * x;
-        double ps = -1.0 / 39916800.0;                 // -1/11!
-        ps = fma(ps, x2, 1.0 / 362880.0);              //  1/9!
-        ps = fma(ps, x2, -1.0 / 5040.0);               // -1/7!
-        ps = fma(ps, x2, 1.0 / 120.0);                 //  1/5!
-        ps = fma(ps, x2, -1.0 / 6.0);                  // -1/3!
-        s = fma(x * x2, ps, x);
-        double pc = 1.0 / 479001600.0;                 //  1/12!
-        pc = fma(pc, x2, -1.0 / 3628800.0);            // -1/10!
-        pc = fma(pc, x2, 1.0 / 40320.0);               //  1/8!
-        pc = fma(pc, x2, -1.0 / 720.0);                // -1/6!
-        pc = fma(pc, x2, 1.0 / 24.0);                  //  1/4!
-        pc = fma(pc, x2, -0.5);                        // -1/2!
-        c1 = x2 * pc;
+        const double ax = fabs(x);
+        if (ax <= 0x1p-16) {
+            s = fma(x * x2, -1.0 / 6.0, x);
+            c1 = x2 * fma(x2, 1.0 / 24.0, -0.5);
+        } else if (ax <= 0x1p-6) {
+            double ps = fma(x2, -1.0 / 5040.0, 1.0 / 120.0);
+            ps = fma(ps, x2, -1.0 / 6.0);
+            s = fma(x * x2, ps, x);
+            double pc = fma(x2, 1.0 / 40320.0, -1.0 / 720.0);
+            pc = fma(pc, x2, 1.0 / 24.0);
+            pc = fma(pc, x2, -0.5);
+            c1 = x2 * pc;
+        } else {
+            double ps = -1.0 / 39916800.0;                 // -1/11!
+            ps = fma(ps, x2, 1.0 / 362880.0);              //  1/9!
+            ps = fma(ps, x2, -1.0 / 5040.0);               // -1/7!
+            ps = fma(ps, x2, 1.0 / 120.0);                 //  1/5!
+            ps = fma(ps, x2, -1.0 / 6.0);                  // -1/3!
+            s = fma(x * x2, ps, x);
+            double pc = 1.0 / 479001600.0;                 //  1/12!
+            pc = fma(pc, x2, -1.0 / 3628800.0);            // -1/10!
+            pc = fma(pc, x2, 1.0 / 40320.0);               //  1/8!
+            pc = fma(pc, x2, -1.0 / 720.0);                // -1/6!
+            pc = fma(pc, x2, 1.0 / 24.0);                  //  1/4!
+            pc = fma(pc, x2, -0.5);                        // -1/2!
+            c1 = x2 * pc;
+        }
     }
 };
 template <>
@@ -263,10 +280,127 @@ __global__ void sin_cosm1_kernel(const double *x, int64_t n, double *s, double *
 // Blocks have at most kMaxThreads threads, which leaves up to 128 registers per thread.
 constexpr int kMaxThreads = 512;
 
+// Cell model with the medium state in registers and dense D x D products
+// whose constants are kernel-parameter (constant-bank) operands.
 template <int N, typename R, typename K>
-__global__ void __launch_bounds__(kMaxThreads, 1) mln_block_kernel(const __grid_constant__ BlockArgs<R> a,
-                                                         const __grid_constant__ K k) {
-    constexpr int D = Dims<N>::D;
+struct RegisterCell {
+    static constexpr int D = Dims<N>::D;
+    using Consts = K;
+    R s[D];
+    __device__ __forceinline__ void setup(unsigned char *, const K &) {}
+    __device__ __forceinline__ void load(const R *src, int64_t stride, int64_t m) {
+#pragma unroll
+        for (int i = 0; i < D; ++i) s[i] = src[i * stride + m];
+    }
+    __device__ __forceinline__ void store(R *dst, int64_t stride, int64_t m) const {
+#pragma unroll
+        for (int i = 0; i < D; ++i) dst[i * stride + m] = s[i];
+    }
+    __device__ __forceinline__ R step(R e, const K &k) { return cell_step<N>(s, e, k); }
+    __device__ __forceinline__ void end_step() {}
+};
+
+// Sparse program of the merged FP64 step: the non-zero entries of T^T
+// (restricted to the 2q plane rows), T (restricted to the plane columns),
+// A0^2 - I and A0^T w, row by row in ascending column order (the order of
+// the dense products, so both give the same sums). Built once per context.
+template <int N>
+struct SparseConsts {
+    double b2[Dims<N>::D];
+    double psi_dt[N - 1];
+    double cm;
+    const int32_t *rowptr;  // global entry index where each row starts: Tt (2q + 1), T (D + 1), C1 (D + 1), wm (2)
+    const int32_t *cols;    // column of each entry
+    const double *vals;     // value of each entry
+    int32_t nnz;            // entries in all four products
+    int32_t nrowptr;        // length of rowptr
+};
+
+// Cell model with the medium state in shared memory (one column per thread)
+// and products that walk the sparse program, also held in shared memory. On
+// GB300 an FP64 FMA costs 16 issue slots' worth of FP64-pipe time per warp,
+// so the extra shared-memory loads and loop control are free and only the
+// non-zero entries cost time.
+template <int N>
+struct SharedSparseCell {
+    static constexpr int D = Dims<N>::D, Q = Dims<N>::Q;
+    using Consts = SparseConsts<N>;
+    double *yc, *yn, *z;       // this thread's column: element i at [i * nt]
+    const double *vals;
+    const int32_t *offs, *rp;  // offs[e] = cols[e] * nt
+    int nt;
+
+    // Shared-memory bytes besides the E/H arrays.
+    __host__ __device__ static size_t smem_bytes(int threads, int nnz, int nrowptr) {
+        return static_cast<size_t>(threads) * (2 * D + 2 * Q) * sizeof(double) + static_cast<size_t>(nnz) * 12 +
+               static_cast<size_t>(nrowptr) * 4;
+    }
+
+    // Block-cooperative: lay out the state columns and copy the program.
+    __device__ __forceinline__ void setup(unsigned char *extra, const Consts &k) {
+        nt = blockDim.x;
+        const int t = threadIdx.x;
+        double *base = reinterpret_cast<double *>(extra);
+        yc = base + t;
+        yn = base + D * nt + t;
+        z = base + 2 * D * nt + t;
+        double *v = base + (2 * D + 2 * Q) * nt;
+        int32_t *o = reinterpret_cast<int32_t *>(v + k.nnz);
+        int32_t *r = o + k.nnz;
+        for (int e = t; e < k.nnz; e += nt) {
+            v[e] = k.vals[e];
+            o[e] = k.cols[e] * nt;
+        }
+        for (int e = t; e < k.nrowptr; e += nt) r[e] = k.rowptr[e];
+        vals = v;
+        offs = o;
+        rp = r;
+    }
+    __device__ __forceinline__ void load(const double *src, int64_t stride, int64_t m) {
+        for (int i = 0; i < D; ++i) yc[i * nt] = src[i * stride + m];
+    }
+    __device__ __forceinline__ void store(double *dst, int64_t stride, int64_t m) const {
+        for (int i = 0; i < D; ++i) dst[i * stride + m] = yc[i * nt];
+    }
+    // sum over the entries of row r of a product with input column x
+    __device__ __forceinline__ double row(int r, const double *x, double acc) const {
+        const int e1 = rp[r + 1];
+#pragma unroll 1
+        for (int e = rp[r]; e < e1; ++e) acc = fma(vals[e], x[offs[e]], acc);
+        return acc;
+    }
+    __device__ __forceinline__ double step(double e, const Consts &k) {
+        constexpr int rT = 2 * Q + 1, rC = rT + D + 1, rW = rC + D + 1;
+        // z = T^T y on the plane rows
+#pragma unroll 1
+        for (int r = 0; r < 2 * Q; ++r) z[r * nt] = row(r, yc, 0.0);
+        // (R(E) - I) z
+        double zz[D];
+#pragma unroll
+        for (int i = 0; i < 2 * Q; ++i) zz[i] = z[i * nt];
+        rotation_increment<N>(zz, k.psi_dt, e);
+#pragma unroll
+        for (int i = 0; i < 2 * Q; ++i) z[i * nt] = zz[i];
+        // y'' = y + T (R - I) z
+#pragma unroll 1
+        for (int r = 0; r < D; ++r) yc[r * nt] = yc[r * nt] + row(rT + r, z, 0.0);
+        const double dpdt = row(rW, yc, k.cm);
+        // y = y'' + (C1 y'' + b2)
+#pragma unroll 1
+        for (int r = 0; r < D; ++r) yn[r * nt] = yc[r * nt] + row(rC + r, yc, k.b2[r]);
+        return dpdt;
+    }
+    // every thread of the block swaps, medium or not, so the columns stay aligned
+    __device__ __forceinline__ void end_step() {
+        double *t = yc;
+        yc = yn;
+        yn = t;
+    }
+};
+
+template <int N, typename R, typename Cell>
+__global__ void __launch_bounds__(kMaxThreads, 1)
+    mln_block_kernel(const __grid_constant__ BlockArgs<R> a, const __grid_constant__ typename Cell::Consts k) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     R *sE = reinterpret_cast<R *>(smem_raw);
     R *sH = sE + blockDim.x;
@@ -289,13 +423,13 @@ __global__ void __launch_bounds__(kMaxThreads, 1) mln_block_kernel(const __grid_
     const bool medium = loaded && gm >= a.mb && gm < a.me;
     const int64_t m = gm - a.mb;
 
+    Cell cell;
+    cell.setup(reinterpret_cast<unsigned char *>(sH + blockDim.x), k);
     R e = loaded ? a.E_in[gm] : R(0);
     R h = loaded ? a.H_in[gm] : R(0);
     sE[j] = e;
     sH[j] = h;
-    R s[D];
-#pragma unroll
-    for (int i = 0; i < D; ++i) s[i] = medium ? a.s_in[i * a.stride + m] : R(0);
+    if (medium) cell.load(a.s_in, a.stride, m);
 
     // H_{i+1/2} exists for every cell of a ring and for cells 0..n-2 of an open grid;
     // it needs E of the next loaded cell.
@@ -314,7 +448,8 @@ __global__ void __launch_bounds__(kMaxThreads, 1) mln_block_kernel(const __grid_
         }
         __syncthreads();
         R dpdt = R(0);
-        if (medium) dpdt = cell_step<N>(s, e, k);
+        if (medium) dpdt = cell.step(e, k);
+        cell.end_step();
         R en = e;
         if (e_upd) en = fma(a.ca, e, a.cb * fma(h - sH[j - 1], a.inv_dx, -dpdt));
         R e_mur = R(0);
@@ -341,10 +476,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1) mln_block_kernel(const __grid_
     if (interior) {
         a.E_out[gm] = e;
         a.H_out[gm] = h;
-        if (medium) {
-#pragma unroll
-            for (int i = 0; i < D; ++i) a.s_out[i * a.stride + m] = s[i];
-        }
+        if (medium) cell.store(a.s_out, a.stride, m);
         if (!isfinite(e)) atomicOr(a.flags, 1u);
     }
 }

@@ -289,6 +289,14 @@ mln_status validate(const mln_params &p, std::string &err) {
         err = "block_steps must be in [0, 64]";
         return MLN_EINVAL;
     }
+    if (p.kernel < MLN_KERNEL_AUTO || p.kernel > MLN_KERNEL_SPARSE) {
+        err = "kernel must be MLN_KERNEL_AUTO, MLN_KERNEL_REGISTER or MLN_KERNEL_SPARSE";
+        return MLN_EINVAL;
+    }
+    if (p.kernel == MLN_KERNEL_SPARSE && (p.precision != MLN_FP64 || p.form != MLN_FORM_MERGED)) {
+        err = "MLN_KERNEL_SPARSE needs MLN_FP64 and MLN_FORM_MERGED";
+        return MLN_EINVAL;
+    }
     if (p.tile_cells < 0) {
         err = "tile_cells must be >= 0";
         return MLN_EINVAL;

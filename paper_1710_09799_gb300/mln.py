@@ -24,6 +24,7 @@ MLN_BC_PERIODIC, MLN_BC_OPEN = 0, 1
 MLN_SRC_NONE, MLN_SRC_HARD, MLN_SRC_SOFT = 0, 1, 2
 MLN_FP64, MLN_FP32 = 0, 1
 MLN_FORM_STRANG, MLN_FORM_MERGED = 0, 1
+MLN_KERNEL_AUTO, MLN_KERNEL_REGISTER, MLN_KERNEL_SPARSE = 0, 1, 2
 MLN_MIN_N, MLN_MAX_N = 2, 6
 _DMAX = MLN_MAX_N * MLN_MAX_N - 1
 
@@ -31,6 +32,7 @@ BOUNDARY = {"periodic": MLN_BC_PERIODIC, "open": MLN_BC_OPEN}
 SOURCE = {"none": MLN_SRC_NONE, "hard": MLN_SRC_HARD, "soft": MLN_SRC_SOFT}
 PRECISION = {"fp64": MLN_FP64, "fp32": MLN_FP32}
 FORM = {"strang": MLN_FORM_STRANG, "merged": MLN_FORM_MERGED}
+KERNEL = {"auto": MLN_KERNEL_AUTO, "register": MLN_KERNEL_REGISTER, "sparse": MLN_KERNEL_SPARSE}
 
 _dp = C.POINTER(C.c_double)
 
@@ -39,7 +41,7 @@ class mln_params(C.Structure):
     _fields_ = [
         ("N", C.c_int32), ("precision", C.c_int32), ("form", C.c_int32), ("boundary", C.c_int32),
         ("source_kind", C.c_int32), ("block_steps", C.c_int32), ("tile_cells", C.c_int32),
-        ("reserved0", C.c_int32),
+        ("kernel", C.c_int32),
         ("H0", _dp), ("mu", _dp), ("G", _dp), ("rho0", _dp),
         ("N_a", C.c_double),
         ("n_cells", C.c_int64), ("medium_begin", C.c_int64), ("medium_end", C.c_int64),
@@ -143,13 +145,14 @@ class Params:
 
     def __init__(self, *, N, H0, mu, rho0, N_a, n_cells, medium_begin, medium_end, dx, dt,
                  G=None, eps_r=1.0, mu_r=1.0, sigma=0.0, boundary="periodic", source_kind="none",
-                 source_cell=0, precision="fp64", form="strang", block_steps=0, tile_cells=0):
+                 source_cell=0, precision="fp64", form="strang", block_steps=0, tile_cells=0,
+                 kernel="auto"):
         self._H0, self._mu, self._rho0 = _cplx(H0), _cplx(mu), _cplx(rho0)
         self._G = None if G is None else _cplx(G)
         self.s = mln_params(
             N=N, precision=PRECISION.get(precision, precision), form=FORM.get(form, form),
             boundary=BOUNDARY.get(boundary, boundary), source_kind=SOURCE.get(source_kind, source_kind),
-            block_steps=block_steps, tile_cells=tile_cells, reserved0=0,
+            block_steps=block_steps, tile_cells=tile_cells, kernel=KERNEL.get(kernel, kernel),
             H0=_ptr(self._H0), mu=_ptr(self._mu), G=_ptr(self._G), rho0=_ptr(self._rho0),
             N_a=N_a, n_cells=n_cells, medium_begin=medium_begin, medium_end=medium_end,
             source_cell=source_cell, dx=dx, dt=dt, eps_r=eps_r, mu_r=mu_r, sigma=sigma)

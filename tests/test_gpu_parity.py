@@ -270,3 +270,19 @@ def test_rotation_terms_against_exact(precision):
     tol_c = 6 * eps * np.maximum(np.abs(ref_c), np.finfo(float).tiny)
     assert np.all(np.abs(s - ref_s) <= tol_s), np.max(np.abs(s - ref_s) / np.maximum(np.abs(ref_s), 1e-300))
     assert np.all(np.abs(c1 - ref_c) <= tol_c), np.max(np.abs(c1 - ref_c) / np.maximum(np.abs(ref_c), 1e-300))
+
+
+@pytest.mark.parametrize("N", [2, 3, 6])
+def test_sparse_and_register_models_agree_bitwise(N):
+    """The shared-memory sparse cell model skips the exact zeros of the
+    constant matrices but sums the other terms in the dense order: FP64 merged
+    results are bit-identical to the register model's."""
+    if N == 2:
+        p = W.two_level_sit(n_cells=700, medium=(100, 600), n_steps=400)
+    elif N == 3:
+        p = W.three_level_ring(n_cells=3000, n_steps=300)
+    else:
+        p = W.six_level_pulse(n_cells=600, n_steps=200, t0=15e-15, fwhm=10e-15).with_(medium_end=599)
+    E0, H0, r0, _ = gpu_run(p, p.n_steps, "fp64", "merged", kernel="register")
+    E1, H1, r1, _ = gpu_run(p, p.n_steps, "fp64", "merged", kernel="sparse")
+    assert np.array_equal(E0, E1) and np.array_equal(H0, H1) and np.array_equal(r0, r1)
