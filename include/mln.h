@@ -217,7 +217,8 @@ void mln_destroy(mln_ctx *ctx);
 const char *mln_status_string(mln_status s);
 /* Last error message of a context (empty string if none; "" for NULL). */
 const char *mln_last_error(const mln_ctx *ctx);
-/* Last error message of a failed mln_create or mln_setup_host on this thread. */
+/* Last error message of a failed mln_create, mln_setup_host or
+ * mln_query_buffers on this thread. */
 const char *mln_create_error(void);
 
 /*

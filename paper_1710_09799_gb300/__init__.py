@@ -11,5 +11,5 @@ __all__ = ["mln", "Params", "Solver", "MLNError", "build"]
 
 
 def build(force: bool = False) -> str:
-    from .build import build as _build
+    from ._nvcc_build import build as _build
     return _build(force=force)

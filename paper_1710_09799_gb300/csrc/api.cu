@@ -39,7 +39,7 @@ struct mln_ctx {
 
 namespace {
 
-thread_local std::string g_create_err;
+thread_local std::string g_create_err_store;
 
 const char *kVersion = "mln-gb300 0.2 (sm_103a)";
 
@@ -275,6 +275,10 @@ mln_status check_cells(mln_ctx *c, int64_t cell0, int64_t count, int64_t *m0) {
 
 }  // namespace
 
+namespace mln {
+std::string &create_error() { return g_create_err_store; }
+}  // namespace mln
+
 extern "C" {
 
 const char *mln_version(void) { return kVersion; }
@@ -314,14 +318,14 @@ const char *mln_status_string(mln_status s) {
 
 const char *mln_last_error(const mln_ctx *ctx) { return ctx ? ctx->err.c_str() : ""; }
 
-const char *mln_create_error(void) { return g_create_err.c_str(); }
+const char *mln_create_error(void) { return mln::create_error().c_str(); }
 
 mln_status mln_query_buffers(const mln_params *p, size_t *state_bytes, size_t *field_bytes) {
     if (!p) return MLN_EINVAL;
     std::string err;
     mln_status st = mln::validate(*p, err);
     if (st != MLN_OK) {
-        g_create_err = err;
+        mln::create_error() = err;
         return st;
     }
     size_t r = p->precision == MLN_FP64 ? 8 : 4;
@@ -338,7 +342,7 @@ mln_status mln_setup_host(const mln_params *p, mln_setup *out) {
     mln::Setup s;
     if (st == MLN_OK) st = mln::build_setup(*p, s, err);
     if (st != MLN_OK) {
-        g_create_err = err;
+        mln::create_error() = err;
         return st;
     }
     std::memset(out, 0, sizeof(*out));
@@ -388,13 +392,13 @@ void mln_destroy(mln_ctx *c) {
 mln_status mln_create(const mln_params *p, void *d_state, void *Ez, void *Hy, void *stream, mln_ctx **out) {
     if (out) *out = nullptr;
     if (!p || !out || !d_state || !Ez || !Hy) {
-        g_create_err = "null argument";
+        mln::create_error() = "null argument";
         return MLN_EINVAL;
     }
     std::string err;
     mln_status st = mln::validate(*p, err);
     if (st != MLN_OK) {
-        g_create_err = err;
+        mln::create_error() = err;
         return st;
     }
     mln_ctx *c = new (std::nothrow) mln_ctx();
@@ -403,7 +407,7 @@ mln_status mln_create(const mln_params *p, void *d_state, void *Ez, void *Hy, vo
     c->p.H0 = c->p.mu = c->p.G = c->p.rho0 = nullptr;
     st = mln::build_setup(*p, c->s, err);
     if (st != MLN_OK) {
-        g_create_err = err;
+        mln::create_error() = err;
         delete c;
         return st;
     }
@@ -420,7 +424,7 @@ mln_status mln_create(const mln_params *p, void *d_state, void *Ez, void *Hy, vo
     c->sparse = p->kernel == MLN_KERNEL_SPARSE ||
                 (p->kernel == MLN_KERNEL_AUTO && p->precision == MLN_FP64 && p->form == MLN_FORM_MERGED);
     auto fail = [&](mln_status s_) {
-        g_create_err = c->err.empty() ? err : c->err;
+        mln::create_error() = c->err.empty() ? err : c->err;
         mln_destroy(c);
         return s_;
     };
@@ -431,6 +435,18 @@ mln_status mln_create(const mln_params *p, void *d_state, void *Ez, void *Hy, vo
         mln::build_sparse_program(c->s, rowptr, cols, vals);
         c->nnz = static_cast<int>(vals.size());
         c->nrowptr = static_cast<int>(rowptr.size());
+        // the kernel indexes rows by this layout: check it before anything reaches the device
+        const int P = 2 * c->s.q, D = c->s.D;
+        bool layout_ok = c->nrowptr == P + 2 * D + 2 && rowptr.front() == 0 && rowptr.back() == c->nnz;
+        for (size_t r = 0; layout_ok && r + 1 < rowptr.size(); ++r) {
+            const int lim = (static_cast<int>(r) >= P && static_cast<int>(r) < P + D) ? P : D;
+            layout_ok = rowptr[r] <= rowptr[r + 1];
+            for (int e = rowptr[r]; layout_ok && e < rowptr[r + 1]; ++e) layout_ok = cols[e] >= 0 && cols[e] < lim;
+        }
+        if (!layout_ok) {
+            c->err = "sparse program layout check failed";
+            return fail(MLN_ENUMERIC);
+        }
         size_t b_rp = rowptr.size() * 4, b_cols = cols.size() * 4;
         size_t off_vals = (b_rp + b_cols + 15) / 16 * 16;
         size_t bytes = off_vals + vals.size() * 8 + 16;

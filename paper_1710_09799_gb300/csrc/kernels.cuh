@@ -309,7 +309,8 @@ struct SparseConsts {
     double b2[Dims<N>::D];
     double psi_dt[N - 1];
     double cm;
-    const int32_t *rowptr;  // global entry index where each row starts: Tt (2q + 1), T (D + 1), C1 (D + 1), wm (2)
+    const int32_t *rowptr;  // entry index where each row starts, then the end of the last row:
+                            // T^T rows 0..2q-1, T rows 2q.., C1 rows 2q+D.., wm row 2q+2D; 2q + 2D + 2 entries
     const int32_t *cols;    // column of each entry
     const double *vals;     // value of each entry
     int32_t nnz;            // entries in all four products
@@ -370,7 +371,9 @@ struct SharedSparseCell {
         return acc;
     }
     __device__ __forceinline__ double step(double e, const Consts &k) {
-        constexpr int rT = 2 * Q + 1, rC = rT + D + 1, rW = rC + D + 1;
+        // row bases in rowptr: T^T rows [0, 2q), T rows [2q, 2q + D), C1 rows
+        // [2q + D, 2q + 2D), the wm row 2q + 2D; rowptr has 2q + 2D + 2 entries
+        constexpr int rT = 2 * Q, rC = 2 * Q + D, rW = 2 * Q + 2 * D;
         // z = T^T y on the plane rows
 #pragma unroll 1
         for (int r = 0; r < 2 * Q; ++r) z[r * nt] = row(r, yc, 0.0);

@@ -46,4 +46,8 @@ mln_status build_setup(const mln_params &p, Setup &s, std::string &err);
 // Stride (in elements) of one adjoint component in the device state.
 int64_t state_stride(const mln_params &p);
 
+// Message of the last failed context-free call on this thread (mln_create,
+// mln_setup_host, mln_query_buffers).
+std::string &create_error();
+
 }  // namespace mln
