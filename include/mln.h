@@ -217,8 +217,8 @@ void mln_destroy(mln_ctx *ctx);
 const char *mln_status_string(mln_status s);
 /* Last error message of a context (empty string if none; "" for NULL). */
 const char *mln_last_error(const mln_ctx *ctx);
-/* Last error message of a failed mln_create, mln_setup_host or
- * mln_query_buffers on this thread. */
+/* Last error message of a failed mln_create, mln_setup_host, mln_query_buffers
+ * or mln_step_noalloc on this thread. */
 const char *mln_create_error(void);
 
 /*
@@ -256,6 +256,45 @@ mln_status mln_setup_host(const mln_params *p, mln_setup *out);
  * allocates temporary device memory.
  */
 mln_status mln_rotation_terms(int32_t precision, const double *x, int64_t n, double *s, double *c1);
+
+/*
+ * mln_step_noalloc -- the fused step for callers that cannot allocate device
+ * memory. (Not a part of the paper's method: it has no counterpart there.)
+ *
+ * Who needs it: code that may not call cudaMalloc or any allocating library
+ * routine once it runs -- a host application whose device memory is owned by
+ * its own pool or framework, a plug-in that must not grow the process's
+ * device footprint, a loop with a fixed memory budget. mln_create allocates
+ * the context's second copy of the state and fields, its flag word and its
+ * conversion tables; this call allocates nothing. It runs the same
+ * register-model step kernel (MLN_KERNEL_REGISTER) as mln_step, and keeps the
+ * second copy of the state and fields and the flag word in one fixed
+ * file-scope device array of MLN_STATIC_SCRATCH_BYTES (32 MiB), which every
+ * GPU that loads this library holds until the process exits.
+ *
+ *   p           problem (as for mln_create; kernel must not be MLN_KERNEL_SPARSE).
+ *   d_state, Ez, Hy  caller-owned device buffers with the sizes and layout of
+ *               mln_query_buffers: the state in, the state after n_steps out.
+ *   init_state  non-zero: first write the initial medium state built from
+ *               rho0 into d_state (Ez, Hy are used as given).
+ *   n_steps     steps to queue (>= 0); src as for mln_step (samples 0 ..
+ *               n_steps-1 of this call).
+ *   stream      cudaStream_t for all work (NULL: legacy default stream).
+ *
+ * The problem must fit: 256 + align256(state bytes) + 2 * align256(n_cells *
+ * real size) <= MLN_STATIC_SCRATCH_BYTES, else MLN_EINVAL with a message
+ * (mln_create_error). The FP64 set-up runs on the host at every call (host
+ * heap only). The first call on each device looks up the array's device
+ * address with that device current (cudaGetSymbolAddress) and keeps it; make
+ * that first call before any stream capture. Every call shares the one array
+ * and leaves its contents behind (the flag word is cleared at each call), so
+ * calls whose work overlaps on the GPU -- on different streams, or from
+ * different threads -- race and corrupt each other's results: serialise them.
+ * Work is queued asynchronously; non-finite values are not reported.
+ */
+#define MLN_STATIC_SCRATCH_BYTES (32u * 1024u * 1024u)
+mln_status mln_step_noalloc(const mln_params *p, void *d_state, void *Ez, void *Hy, int32_t init_state,
+                            int64_t n_steps, const double *src, void *stream);
 
 /* Library version string. */
 const char *mln_version(void);

@@ -47,7 +47,7 @@ mln_status build_setup(const mln_params &p, Setup &s, std::string &err);
 int64_t state_stride(const mln_params &p);
 
 // Message of the last failed context-free call on this thread (mln_create,
-// mln_setup_host, mln_query_buffers).
+// mln_setup_host, mln_query_buffers, mln_step_noalloc).
 std::string &create_error();
 
 }  // namespace mln

@@ -88,6 +88,8 @@ _SIGS = {
     "mln_setup_host": (C.c_int, [_P, C.POINTER(mln_setup)]),
     "mln_version": (C.c_char_p, []),
     "mln_rotation_terms": (C.c_int, [C.c_int32, _dp, C.c_int64, _dp, _dp]),
+    "mln_step_noalloc": (C.c_int, [_P, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_int64, C.c_void_p,
+                                   C.c_void_p]),
 }
 
 _lib = None
@@ -250,6 +252,18 @@ def mln_rotation_terms(precision: str, x):
     s, c1 = np.zeros_like(x), np.zeros_like(x)
     _check(lib().mln_rotation_terms(PRECISION.get(precision, precision), _ptr(x), len(x), _ptr(s), _ptr(c1)))
     return s, c1
+
+
+MLN_STATIC_SCRATCH_BYTES = 32 * 1024 * 1024
+
+
+def mln_step_noalloc(params: Params, d_state_ptr: int, ez_ptr: int, hy_ptr: int, init_state: bool,
+                     n_steps: int, src_ptr: int | None = None, stream_ptr: int = 0):
+    """The step for callers that cannot allocate device memory: scratch in a
+    fixed device array of the library (see include/mln.h)."""
+    _check(lib().mln_step_noalloc(C.byref(params.s), C.c_void_p(d_state_ptr), C.c_void_p(ez_ptr),
+                                  C.c_void_p(hy_ptr), 1 if init_state else 0, n_steps,
+                                  None if src_ptr is None else C.c_void_p(src_ptr), C.c_void_p(stream_ptr)))
 
 
 def mln_version() -> str:
