@@ -36,22 +36,13 @@ import workloads as W  # noqa: E402
 
 METRIC = "cell-updates/sec on 1 GB300 (FP32/batched vs plain FP64 at stated err); % roofline"
 UNIT = "cell-updates/s"
-WORKLOAD = "three-level QCL-like medium, periodic ring, 65536 cells x 100000 steps"
+WORKLOADS = {
+    "three_level_ring": "three-level QCL-like medium, periodic ring, 65536 cells x 100000 steps",
+    "six_level_pulse": "six-level manifold (D = 35), Gaussian pulse, hard source + Mur, 1048576 cells x 10000 steps",
+    "two_level_sit": "two-level SIT, sech pulse of area 2 pi, 2000 cells x 20000 steps",
+}
+WORKLOAD = WORKLOADS["three_level_ring"]
 
-# Algorithmic flops (FMA = 2, add/mul = 1) per medium cell-update for adjoint
-# dimension D, q rotation planes and N levels, counted from the kernels'
-# arithmetic: each D x D product 2 D^2, each identity + increment D adds,
-# the rotation increments 6 flops per plane, the N - 1 evaluations of
-# (sin, cos - 1) by their series 28 flops each, 12 flops per plane derived by
-# angle subtraction, the dP/dt dot 2 D. FDTD: 9 flops per grid cell.
-def cell_flops(form: str, D: int, q: int, N: int) -> int:
-    rot = 6 * q + 28 * (N - 1) + 12 * (q - (N - 1))
-    if form == "strang":
-        return 4 * 2 * D * D + 3 * D + rot + 2 * D      # Dl, T^T, T, Dl products
-    return 3 * 2 * D * D + 2 * D + rot + 2 * D          # T^T, T, C1 products
-
-
-FDTD_FLOPS = 9
 
 # FP64 and FP32 pipe peaks from unit counts and the maximum SM clock (GB300:
 # 152 SMs, 2070 MHz; FP64 1.25 TFLOP/s nominal = 2 DFMA/clk/SM; FP32 128 FFMA/clk/SM).
@@ -171,8 +162,13 @@ def time_device(p, precision, form, seg, steps, warmup, block_steps, tile_cells,
     from paper_1710_09799_gb300 import mln
     s = mln.Solver(make_params(p, precision, form, block_steps, tile_cells, kernel), E0=p.e_init())
     stream = s.stream
-    for _ in range(warmup):
-        s.step(seg)
+    # source samples of every step of the run, resident on the device
+    total = (warmup + steps) * seg
+    samples = p.source_samples(0, total)
+    src = None if samples is None else torch.as_tensor(samples, dtype=torch.float64, device="cuda")
+    seg_src = lambda k: None if src is None else src[k * seg:(k + 1) * seg]
+    for w in range(warmup):
+        s.step(seg, seg_src(w))
     s.sync()
     flush_buf = torch.empty(256 << 20, dtype=torch.uint8, device="cuda") if flush else None
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
@@ -187,7 +183,7 @@ def time_device(p, precision, form, seg, steps, warmup, block_steps, tile_cells,
             if flush_buf is not None:
                 flush_buf.fill_(i & 0xFF)
             evs[i][0].record(stream)
-            s.step(seg)
+            s.step(seg, seg_src(warmup + i))
             evs[i][1].record(stream)
     torch.cuda.synchronize()
     t_wall = time.perf_counter() - t_wall
@@ -198,8 +194,9 @@ def time_device(p, precision, form, seg, steps, warmup, block_steps, tile_cells,
     ms = sum(a.elapsed_time(b) for a, b in evs)
     ms_max = max_over_ranks(ws, ms)
     shape = s.launch_shape
+    work = s.work_per_step
     s.close()
-    return dict(ms=ms_max, ms_local=ms, wall_s=t_wall, launches=launches, shape=shape, clocks=clocks)
+    return dict(ms=ms_max, ms_local=ms, wall_s=t_wall, launches=launches, shape=shape, clocks=clocks, work=work)
 
 
 def time_e2e(p, precision, form, seg, steps):
@@ -295,9 +292,10 @@ def main():
     ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32"])
     ap.add_argument("--form", default="merged", choices=["strang", "merged"])
     ap.add_argument("--seg", type=int, default=1000, help="time steps per benchmark step")
-    ap.add_argument("--block-steps", type=int, default=20)
+    ap.add_argument("--block-steps", type=int, default=10)
     ap.add_argument("--tile", type=int, default=0)
     ap.add_argument("--kernel", default="auto", choices=["auto", "register", "sparse"])
+    ap.add_argument("--workload", default="three_level_ring", choices=sorted(WORKLOADS))
     ap.add_argument("--quick", action="store_true", help="skip variants, e2e and the CPU baseline")
     args = ap.parse_args()
     if args.impl == "reference":
@@ -309,7 +307,7 @@ def main():
     from paper_1710_09799_gb300 import build, mln
     if rank == 0 or ws > 1:
         build()
-    p = W.three_level_ring()
+    p = W.config(args.workload)
     D, q = p.D, p.N * (p.N - 1) // 2
 
     vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
@@ -324,7 +322,8 @@ def main():
     # roofline of the fused step kernel (the only kernel in the timed region)
     launches = main_run["launches"]
     per_launch_s = main_run["ms_local"] / 1e3 / max(launches, 1)
-    flops_per_step = p.n_medium * cell_flops(args.form, D, q, p.N) + p.n_cells * FDTD_FLOPS
+    f_med, f_cell, _, _ = main_run["work"]
+    flops_per_step = p.n_medium * f_med + p.n_cells * f_cell
     achieved = flops_per_step * (args.seg * args.steps / max(launches, 1)) / per_launch_s / 1e12
     peak = alu_peak_tflops(args.precision)
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
@@ -332,7 +331,8 @@ def main():
                 "frac": achieved / peak, "traffic": None,
                 "peak_source": f"derived: {SMS} SMs x {FP64_FLOP_PER_CLK_SM if args.precision == 'fp64' else FP32_FLOP_PER_CLK_SM} "
                                f"flop/clk x {SM_MAX_MHZ:.0f} MHz",
-                "flops_per_cell_update": cell_flops(args.form, D, q, p.N)}
+                "flops_per_medium_cell_update": f_med, "flops_per_grid_cell": f_cell,
+                "counted": "non-zero entries of the set-up matrices only (mln_work_per_step)"}
     clk = main_run["clocks"] or {}
     if clk.get("sm_mhz"):
         roofline["frac_at_measured_clock"] = achieved / alu_peak_tflops(args.precision, clk["sm_mhz"])
@@ -342,7 +342,7 @@ def main():
         "warmup": args.warmup, "ms_per_step": main_run["ms"] / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32",
         "data": "synthetic (seeded: levels, dipoles, rates, noise E^0)",
-        "config": {"workload": WORKLOAD, "n_cells": p.n_cells, "levels": p.N,
+        "config": {"workload": WORKLOADS[args.workload], "n_cells": p.n_cells, "levels": p.N,
                    "time_steps_per_step": args.seg, "time_steps_total": args.seg * args.steps,
                    "form": args.form, "precision": args.precision, "kernel": args.kernel,
                    "block_steps": main_run["shape"][0], "tile_cells": main_run["shape"][1],
@@ -354,7 +354,7 @@ def main():
         "clocks": clk,
     }
 
-    if not args.quick and rank == 0:
+    if not args.quick and rank == 0 and args.workload == "three_level_ring":
         variants = {}
         for prec, form, kern in (("fp64", "merged", "register"), ("fp64", "strang", "auto"),
                                  ("fp32", "merged", "auto"), ("fp32", "strang", "auto")):

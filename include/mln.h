@@ -184,6 +184,20 @@ mln_status mln_launch_shape(const mln_ctx *ctx, int32_t *block_steps, int32_t *t
                             int32_t *threads_per_block);
 
 /*
+ * Algorithmic work of one time step, for roofline accounting (not a
+ * measurement): flops_medium = flops (FMA = 2, other operations 1) of one
+ * medium cell-update, counting only the entries of the constant matrices that
+ * are not exactly zero and only the rotation-plane columns of T (the work the
+ * method needs for this problem, whatever the cell model executes), with the
+ * shortest series for (sin, cos - 1); flops_cell = flops of the FDTD updates
+ * of one grid cell (9); bytes_medium / bytes_cell = device-memory bytes one
+ * launch reads and writes per medium / vacuum cell (state and fields, once
+ * each way). Any output pointer may be NULL.
+ */
+mln_status mln_work_per_step(const mln_ctx *ctx, double *flops_medium, double *flops_cell, double *bytes_medium,
+                             double *bytes_cell);
+
+/*
  * Copy E_z^n and H_y^{n-1/2} (n = step count) to host arrays of n_cells
  * doubles each (either may be NULL). Synchronises.
  */

@@ -565,6 +565,32 @@ int64_t mln_step_count(const mln_ctx *c) { return c ? c->steps : -1; }
 
 int64_t mln_launch_count(const mln_ctx *c) { return c ? c->launches : -1; }
 
+mln_status mln_work_per_step(const mln_ctx *c, double *flops_medium, double *flops_cell, double *bytes_medium,
+                             double *bytes_cell) {
+    if (!c) return MLN_EINVAL;
+    const mln::Setup &s = c->s;
+    const int D = s.D, q = s.q, N = s.N, P = 2 * q;
+    auto nz = [](const std::vector<double> &v, int rows, int cols, int ld, double diag) {
+        double n = 0;
+        for (int i = 0; i < rows; ++i)
+            for (int j = 0; j < cols; ++j) n += (v[i * ld + j] - (i == j ? diag : 0.0)) != 0.0;
+        return n;
+    };
+    const double nT = nz(s.T, D, P, D, 0.0);          // T on the plane columns (= T^T on the plane rows)
+    const double rot = 6.0 * q + 12.0 * (q - (N - 1)) + 8.0 * (N - 1);
+    double f;
+    if (c->p.form == MLN_FORM_MERGED) {
+        f = 4 * nT + 2 * nz(s.C1, D, D, D, 0.0) + 2 * D + 2 * nz(s.wm, 1, D, D, 0.0) + rot;
+    } else {
+        f = 4 * nz(s.A0, D, D, D, 1.0) + 4 * nT + 3 * D + 2 * nz(s.w, 1, D, D, 0.0) + rot;
+    }
+    if (flops_medium) *flops_medium = f;
+    if (flops_cell) *flops_cell = 9.0;
+    if (bytes_medium) *bytes_medium = 2.0 * (2 + D) * c->rsz;
+    if (bytes_cell) *bytes_cell = 2.0 * 2 * c->rsz;
+    return MLN_OK;
+}
+
 mln_status mln_launch_shape(const mln_ctx *c, int32_t *block_steps, int32_t *tile_cells, int32_t *threads) {
     if (!c) return MLN_EINVAL;
     if (block_steps) *block_steps = c->K;

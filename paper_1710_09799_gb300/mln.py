@@ -76,6 +76,7 @@ _SIGS = {
     "mln_launch_count": (C.c_int64, [C.c_void_p]),
     "mln_launch_shape": (C.c_int, [C.c_void_p, C.POINTER(C.c_int32), C.POINTER(C.c_int32),
                                    C.POINTER(C.c_int32)]),
+    "mln_work_per_step": (C.c_int, [C.c_void_p, _dp, _dp, _dp, _dp]),
     "mln_get_fields": (C.c_int, [C.c_void_p, _dp, _dp]),
     "mln_get_rho": (C.c_int, [C.c_void_p, C.c_int64, C.c_int64, _dp]),
     "mln_get_populations": (C.c_int, [C.c_void_p, C.c_int64, C.c_int64, _dp]),
@@ -201,6 +202,14 @@ def mln_launch_shape(ctx):
     return k.value, t.value, th.value
 
 
+def mln_work_per_step(ctx):
+    """(flops per medium cell-update, flops per grid cell, bytes per medium cell
+    per launch, bytes per vacuum cell per launch)."""
+    out = [C.c_double() for _ in range(4)]
+    _check(lib().mln_work_per_step(ctx, *[C.byref(o) for o in out]), ctx)
+    return tuple(o.value for o in out)
+
+
 def mln_get_fields(ctx, n_cells: int):
     E, H = np.zeros(n_cells), np.zeros(n_cells)
     _check(lib().mln_get_fields(ctx, _ptr(E), _ptr(H)), ctx)
@@ -320,6 +329,10 @@ class Solver:
     @property
     def launch_shape(self):
         return mln_launch_shape(self.ctx)
+
+    @property
+    def work_per_step(self):
+        return mln_work_per_step(self.ctx)
 
     def fields(self):
         return mln_get_fields(self.ctx, self.n_cells)

@@ -286,3 +286,20 @@ def test_sparse_and_register_models_agree_bitwise(N):
     E0, H0, r0, _ = gpu_run(p, p.n_steps, "fp64", "merged", kernel="register")
     E1, H1, r1, _ = gpu_run(p, p.n_steps, "fp64", "merged", kernel="sparse")
     assert np.array_equal(E0, E1) and np.array_equal(H0, H1) and np.array_equal(r0, r1)
+
+
+def test_six_level_fp32_error_4096_cells(orc):
+    """The six-level workload (D = 35) in FP32 with FP64 set-up against the FP64
+    oracle on a separate 4096-cell run with the same parameters (a subgrid of
+    the 1048576-cell run is not self-contained: its light cone is too wide)."""
+    p = W.six_level_pulse(n_cells=4096, n_steps=1000)
+    p = p.with_(medium_end=4095)
+    ref = oracle_ref(orc, p, p.n_steps)
+    k = p.n_steps / 1000
+    for form in ("merged",):
+        E, H, rho, _ = gpu_run(p, p.n_steps, "fp32", form)
+        e_err = rel_inf(E, ref.E)
+        p_err = np.abs(pops(rho) - pops(ref.rho)).max()
+        print(f"fp32 six-level {form}: E rel {e_err:.3e}  pop abs {p_err:.3e}")
+        assert e_err < FP32_E_PER_KSTEP * k
+        assert p_err < FP32_POP_PER_KSTEP * k
