@@ -184,6 +184,16 @@ mln_status mln_launch_shape(const mln_ctx *ctx, int32_t *block_steps, int32_t *t
                             int32_t *threads_per_block);
 
 /*
+ * Autotuner: time candidate launch shapes (steps fused per launch K and cells
+ * per thread block) on this context and keep the fastest. Each candidate is
+ * timed by repeating one launch that reads the caller's buffers and writes
+ * the context's alternate copy, so the state is not changed. trials: timed
+ * launches per candidate (>= 1). The chosen K and tile are returned (either
+ * pointer may be NULL) and used by later mln_step calls. Synchronises.
+ */
+mln_status mln_autotune(mln_ctx *ctx, int32_t trials, int32_t *block_steps, int32_t *tile_cells);
+
+/*
  * Algorithmic work of one time step, for roofline accounting (not a
  * measurement): flops_medium = flops (FMA = 2, other operations 1) of one
  * medium cell-update, counting only the entries of the constant matrices that

@@ -162,6 +162,103 @@ int sparse_max_threads(mln_ctx *c) {
 }
 
 template <typename R>
+mln::BlockArgs<R> base_args(mln_ctx *c) {
+    const double eps = mln::kEps0 * c->p.eps_r, mu = mln::kMu0 * c->p.mu_r;
+    const double sg = c->p.sigma * c->p.dt / (2.0 * eps);
+    const double cv = 1.0 / std::sqrt(eps * mu);
+    mln::BlockArgs<R> a{};
+    a.flags = c->flags;
+    a.n_cells = c->p.n_cells;
+    a.mb = c->p.medium_begin;
+    a.me = c->p.medium_end;
+    a.stride = c->stride;
+    a.source_cell = c->p.source_cell;
+    a.halo = c->K;
+    a.tile = c->tile;
+    a.boundary = c->p.boundary;
+    a.source_kind = c->p.source_kind;
+    a.ch = static_cast<R>(c->p.dt / (mu * c->p.dx));
+    a.ca = static_cast<R>((1.0 - sg) / (1.0 + sg));
+    a.cb = static_cast<R>((c->p.dt / eps) / (1.0 + sg));
+    a.inv_dx = static_cast<R>(1.0 / c->p.dx);
+    a.kappa = static_cast<R>((cv * c->p.dt - c->p.dx) / (cv * c->p.dt + c->p.dx));
+    return a;
+}
+
+template <typename R>
+size_t smem_for(mln_ctx *c, int threads) {
+    size_t smem = 2 * static_cast<size_t>(threads) * sizeof(R);
+    if (c->sparse) smem += mln::sparse_smem_bytes(c->p.N, threads, c->nnz, c->nrowptr);
+    return smem;
+}
+
+// Time candidate (K, tile) shapes; each candidate repeats one launch reading
+// buffer set 0 and writing set 1, which leaves the caller's state untouched.
+template <typename R>
+mln_status autotune_t(mln_ctx *c, int trials) {
+    int dev = 0, sms = 152;
+    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int64_t n = c->p.n_cells;
+    const int maxt = c->max_threads;
+    const int Ks[] = {2, 4, 6, 8, 10, 12, 16, 20, 24, 32, 40, 48, 64};
+    cudaEvent_t e0, e1;
+    MLN_CK(c, cudaEventCreate(&e0));
+    MLN_CK(c, cudaEventCreate(&e1));
+    double best = 1e300;
+    int bestK = c->K, bestTile = c->tile;
+    for (int K : Ks) {
+        if (2 * K > maxt - 32) continue;
+        std::vector<int> tiles;
+        for (int m = 1; m <= 8; m *= 2) {
+            int64_t nt = static_cast<int64_t>(m) * sms;
+            int tile = static_cast<int>((n + nt - 1) / nt);
+            if (tile + 2 * K <= maxt && tile >= 1) tiles.push_back(tile);
+        }
+        int whole = maxt - 2 * K;  // as few blocks as possible
+        if (whole >= 1) tiles.push_back(static_cast<int>(std::min<int64_t>(whole, n)));
+        std::sort(tiles.begin(), tiles.end());
+        tiles.erase(std::unique(tiles.begin(), tiles.end()), tiles.end());
+        for (int tile : tiles) {
+            c->K = K;
+            c->tile = tile;
+            c->threads = (tile + 2 * K + 31) / 32 * 32;
+            mln::BlockArgs<R> a = base_args<R>(c);
+            a.E_in = static_cast<const R *>(c->E[0]);
+            a.H_in = static_cast<const R *>(c->H[0]);
+            a.s_in = static_cast<const R *>(c->st[0]);
+            a.E_out = static_cast<R *>(c->E[1]);
+            a.H_out = static_cast<R *>(c->H[1]);
+            a.s_out = static_cast<R *>(c->st[1]);
+            a.src = nullptr;
+            a.nsteps = K;
+            const dim3 g(static_cast<unsigned>((n + tile - 1) / tile)), b(c->threads);
+            const size_t smem = smem_for<R>(c, c->threads);
+            if (launch(c, a, g, b, smem) != cudaSuccess) continue;
+            MLN_CK(c, cudaEventRecord(e0, c->stream));
+            for (int t = 0; t < trials; ++t) MLN_CK(c, launch(c, a, g, b, smem));
+            MLN_CK(c, cudaEventRecord(e1, c->stream));
+            MLN_CK(c, cudaEventSynchronize(e1));
+            float ms = 0;
+            MLN_CK(c, cudaEventElapsedTime(&ms, e0, e1));
+            double per_step = ms / (static_cast<double>(trials) * K);
+            if (per_step < best) {
+                best = per_step;
+                bestK = K;
+                bestTile = tile;
+            }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    c->K = bestK;
+    c->tile = bestTile;
+    c->threads = (bestTile + 2 * bestK + 31) / 32 * 32;
+    MLN_CK(c, cudaMemsetAsync(c->flags, 0, sizeof(unsigned int), c->stream));
+    MLN_CK(c, cudaStreamSynchronize(c->stream));
+    return MLN_OK;
+}
+
+template <typename R>
 mln_status run_steps(mln_ctx *c, int64_t n_steps, const double *src) {
     const int64_t ntiles = (c->p.n_cells + c->tile - 1) / c->tile;
     const double eps = mln::kEps0 * c->p.eps_r, mu = mln::kMu0 * c->p.mu_r;
@@ -183,8 +280,7 @@ mln_status run_steps(mln_ctx *c, int64_t n_steps, const double *src) {
     a.cb = static_cast<R>((c->p.dt / eps) / (1.0 + sg));
     a.inv_dx = static_cast<R>(1.0 / c->p.dx);
     a.kappa = static_cast<R>((cv * c->p.dt - c->p.dx) / (cv * c->p.dt + c->p.dx));
-    size_t smem = 2 * static_cast<size_t>(c->threads) * sizeof(R);
-    if (c->sparse) smem += mln::sparse_smem_bytes(c->p.N, c->threads, c->nnz, c->nrowptr);
+    const size_t smem = smem_for<R>(c, c->threads);
     int cur = 0;
     for (int64_t done = 0; done < n_steps;) {
         int ns = static_cast<int>(std::min<int64_t>(c->K, n_steps - done));
@@ -564,6 +660,15 @@ mln_status mln_sync(mln_ctx *c) {
 int64_t mln_step_count(const mln_ctx *c) { return c ? c->steps : -1; }
 
 int64_t mln_launch_count(const mln_ctx *c) { return c ? c->launches : -1; }
+
+mln_status mln_autotune(mln_ctx *c, int32_t trials, int32_t *block_steps, int32_t *tile_cells) {
+    if (!c || trials < 1) return MLN_EINVAL;
+    MLN_CK(c, cudaStreamSynchronize(c->stream));
+    mln_status st = c->p.precision == MLN_FP64 ? autotune_t<double>(c, trials) : autotune_t<float>(c, trials);
+    if (block_steps) *block_steps = c->K;
+    if (tile_cells) *tile_cells = c->tile;
+    return st;
+}
 
 mln_status mln_work_per_step(const mln_ctx *c, double *flops_medium, double *flops_cell, double *bytes_medium,
                              double *bytes_cell) {

@@ -77,6 +77,7 @@ _SIGS = {
     "mln_launch_shape": (C.c_int, [C.c_void_p, C.POINTER(C.c_int32), C.POINTER(C.c_int32),
                                    C.POINTER(C.c_int32)]),
     "mln_work_per_step": (C.c_int, [C.c_void_p, _dp, _dp, _dp, _dp]),
+    "mln_autotune": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
     "mln_get_fields": (C.c_int, [C.c_void_p, _dp, _dp]),
     "mln_get_rho": (C.c_int, [C.c_void_p, C.c_int64, C.c_int64, _dp]),
     "mln_get_populations": (C.c_int, [C.c_void_p, C.c_int64, C.c_int64, _dp]),
@@ -200,6 +201,13 @@ def mln_launch_shape(ctx):
     k, t, th = C.c_int32(), C.c_int32(), C.c_int32()
     _check(lib().mln_launch_shape(ctx, C.byref(k), C.byref(t), C.byref(th)), ctx)
     return k.value, t.value, th.value
+
+
+def mln_autotune(ctx, trials: int = 3):
+    """Pick the fastest (block_steps, tile_cells) for this context; returns them."""
+    k, t = C.c_int32(), C.c_int32()
+    _check(lib().mln_autotune(ctx, trials, C.byref(k), C.byref(t)), ctx)
+    return k.value, t.value
 
 
 def mln_work_per_step(ctx):
@@ -329,6 +337,9 @@ class Solver:
     @property
     def launch_shape(self):
         return mln_launch_shape(self.ctx)
+
+    def autotune(self, trials: int = 3):
+        return mln_autotune(self.ctx, trials)
 
     @property
     def work_per_step(self):

@@ -149,6 +149,22 @@ def test_launch_shape_does_not_change_results(shape):
     assert np.array_equal(E0, E1) and np.array_equal(H0, H1) and np.array_equal(r0, r1)
 
 
+@pytest.mark.parametrize("precision,form", [("fp64", "merged"), ("fp32", "merged"), ("fp64", "strang")])
+def test_autotune_changes_no_state_and_no_result(precision, form):
+    """The autotuner times candidate shapes without touching the state, and
+    the shape it picks gives the same bits as the default shape."""
+    p = W.three_level_ring(n_cells=5000, n_steps=120)
+    E0, H0, r0, _ = gpu_run(p, p.n_steps, precision, form)
+    s = make_solver(p, precision, form)
+    K, tile = s.autotune(2)
+    assert 1 <= K <= 64 and tile >= 1
+    assert s.launch_shape[:2] == (K, tile)
+    s.step(p.n_steps)
+    s.sync()
+    E1, H1 = s.fields()
+    assert np.array_equal(E0, E1) and np.array_equal(H0, H1) and np.array_equal(r0, s.rho())
+
+
 def test_step_splitting_is_exact():
     p = W.two_level_sit(n_steps=900)
     E0, H0, r0, _ = gpu_run(p, 900, "fp64", "merged")
@@ -282,7 +298,7 @@ def test_sparse_and_register_models_agree_bitwise(N):
     elif N == 3:
         p = W.three_level_ring(n_cells=3000, n_steps=300)
     else:
-        p = W.six_level_pulse(n_cells=600, n_steps=200, t0=15e-15, fwhm=10e-15).with_(medium_end=599)
+        p = W.six_level_pulse(n_cells=600, n_steps=200, t0=15e-15, fwhm=10e-15)
     E0, H0, r0, _ = gpu_run(p, p.n_steps, "fp64", "merged", kernel="register")
     E1, H1, r1, _ = gpu_run(p, p.n_steps, "fp64", "merged", kernel="sparse")
     assert np.array_equal(E0, E1) and np.array_equal(H0, H1) and np.array_equal(r0, r1)
@@ -293,7 +309,6 @@ def test_six_level_fp32_error_4096_cells(orc):
     oracle on a separate 4096-cell run with the same parameters (a subgrid of
     the 1048576-cell run is not self-contained: its light cone is too wide)."""
     p = W.six_level_pulse(n_cells=4096, n_steps=1000)
-    p = p.with_(medium_end=4095)
     ref = oracle_ref(orc, p, p.n_steps)
     k = p.n_steps / 1000
     for form in ("merged",):

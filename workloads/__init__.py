@@ -262,7 +262,8 @@ def six_level_pulse(n_cells: int = 1048576, n_steps: int = 10000, seed: int = 0,
     magnitudes ~ U[1, 5] nm*e and uniform phases; pure dephasing
     gamma_jk = gamma_kj ~ U[1, 10] /ps; rho0 = ground state of H0; hard source at
     cell 0 (Gaussian envelope, FWHM fwhm, centre t0, carrier at the mean
-    transition frequency of H0), first-order Mur at the right end."""
+    transition frequency of H0), first-order Mur at the right end. Every cell but
+    the last (the Mur cell, vacuum) is medium."""
     rng = np.random.default_rng(seed)
     N = 6
     X = rng.normal(size=(N, N)) + 1j * rng.normal(size=(N, N))
@@ -288,7 +289,7 @@ def six_level_pulse(n_cells: int = 1048576, n_steps: int = 10000, seed: int = 0,
     diffs = [abs(ev[a] - ev[b]) for a in range(N) for b in range(a + 1, N)]
     omega = float(np.mean(diffs)) / HBAR
     p = Problem(name="six_level_pulse", N=N, H0=H0, mu=mu, G=G, rho0=rho0, N_a=N_a,
-                n_cells=n_cells, medium_begin=0, medium_end=n_cells,
+                n_cells=n_cells, medium_begin=0, medium_end=n_cells - 1,
                 boundary=BC_OPEN, source_kind=SRC_HARD, source_cell=0, n_steps=n_steps)
     p.meta.update(seed=seed, source_fn=gauss_pulse(amplitude, fwhm, t0, omega, p.dt),
                   omega=omega)
