@@ -40,6 +40,7 @@ WORKLOADS = {
     "three_level_ring": "three-level QCL-like medium, periodic ring, 65536 cells x 100000 steps",
     "six_level_pulse": "six-level manifold (D = 35), Gaussian pulse, hard source + Mur, 1048576 cells x 10000 steps",
     "two_level_sit": "two-level SIT, sech pulse of area 2 pi, 2000 cells x 20000 steps",
+    "batched": "256 independent devices, N in {2,3,4}, 1k-64k cells (log-uniform), 20000 steps, one graph per call",
 }
 WORKLOAD = WORKLOADS["three_level_ring"]
 
@@ -201,6 +202,50 @@ def time_device(p, precision, form, seg, steps, warmup, block_steps, tile_cells,
     return dict(ms=ms_max, ms_local=ms, wall_s=t_wall, launches=launches, shape=shape, clocks=clocks, work=work)
 
 
+def time_batch(precision, seg, steps, warmup, sampler=None):
+    """Batched workload: every bench step advances all devices by seg steps (one
+    graph launch); returns the same fields as time_device."""
+    import torch
+    from paper_1710_09799_gb300 import mln
+    total = (warmup + steps) * seg
+    devs = W.batched_devices(n_steps=total)
+    pars = [make_params(d, precision, "merged", kernel="register") for d in devs]
+    srcs = [d.source_samples(0, total) for d in devs]
+    b = mln.Batch(pars, [d.e_init() for d in devs], srcs, total)
+    shape = b.autotune(3)
+    for _ in range(warmup):
+        b.step(seg)
+    b.sync()
+    flush_buf = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    stream = b.stream
+    l0 = b.shape[3]
+    torch.cuda.synchronize()
+    if sampler:
+        sampler.start()
+    with torch.cuda.stream(stream):
+        for i in range(steps):
+            flush_buf.fill_(i & 0xFF)
+            evs[i][0].record(stream)
+            b.step(seg)
+            evs[i][1].record(stream)
+    torch.cuda.synchronize()
+    clocks = sampler.stop() if sampler else None
+    b.sync()
+    ms = sum(a.elapsed_time(c) for a, c in evs)
+    launches = b.shape[3] - l0
+    cells = sum(d.n_cells for d in devs)
+    # algorithmic work per step of every device
+    flops = 0.0
+    for i, d in enumerate(devs):
+        f_med, f_cell, _, _ = mln.mln_work_per_step(mln.mln_batch_context(b.b, i))
+        flops += d.n_medium * f_med + d.n_cells * f_cell
+    items = b.shape[2]
+    b.close()
+    return dict(ms=ms, ms_local=ms, launches=launches, shape=(shape[0], shape[1], items), clocks=clocks,
+                cells=cells, flops_per_step=flops, devices=len(devs))
+
+
 def time_e2e(p, precision, form, seg, steps):
     """End to end through the C-ABI with host buffers: each step loads the state
     from pinned host memory, advances seg time steps and reads E_z, H_y back."""
@@ -286,6 +331,32 @@ def run_reference(args):
     return 0
 
 
+def run_batched(args, ws, rank, local):
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
+    smi_index = int(vis.split(",")[local]) if vis and vis.split(",")[local].isdigit() else local
+    prec = args.precision
+    r = time_batch(prec, args.seg, args.steps, args.warmup, ClockSampler(smi_index))
+    total_s = max_over_ranks(ws, r["ms"]) / 1e3
+    value = ws * r["cells"] * args.seg * args.steps / total_s
+    per_launch_s = r["ms"] / 1e3 / max(r["launches"], 1)
+    achieved = r["flops_per_step"] * (args.seg * args.steps / max(r["launches"], 1)) / per_launch_s / 1e12
+    peak = alu_peak_tflops(prec)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": r["ms"] / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if prec == "fp64" else "f32", "data": "synthetic (seeded devices)",
+        "config": {"workload": WORKLOADS["batched"], "devices": r["devices"], "cells": r["cells"],
+                   "time_steps_per_step": args.seg, "block_steps": r["shape"][0], "tile_cells": r["shape"][1],
+                   "work_items_per_launch": r["shape"][2], "l2": "flushed between steps (256 MiB write)"},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                     "traffic": None, "kernel": "mln_batch_kernel"},
+        "gpu_launches": r["launches"], "clocks": r["clocks"],
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -310,6 +381,8 @@ def main():
     from paper_1710_09799_gb300 import build, mln
     if rank == 0 or ws > 1:
         build()
+    if args.workload == "batched":
+        return run_batched(args, ws, rank, local)
     p = W.config(args.workload)
     D, q = p.D, p.N * (p.N - 1) // 2
 

@@ -235,6 +235,45 @@ mln_status mln_save_state(mln_ctx *ctx, double *d_host, double *Ez_host, double 
 mln_status mln_load_state(mln_ctx *ctx, const double *d_host, const double *Ez_host,
                           const double *Hy_host);
 
+/*
+ * Batches: many independent grids advanced together. Every launch covers
+ * every tile of every grid (one work list, tiles of the costliest grids
+ * first), so small and large grids of different N share the GPU; the
+ * launches of one mln_batch_step call are captured into a CUDA graph and
+ * replayed as one graph launch.
+ *
+ * mln_batch_create: count grids, params[i] as for mln_create with one common
+ * precision, form MLN_FORM_MERGED, N <= 4 and kernel AUTO or REGISTER;
+ * d_state[i], Ez[i], Hy[i] caller-owned device buffers as for mln_create;
+ * src NULL or count device pointers to src_len source samples per grid
+ * (sample k applies to the batch's step k; NULL entries for grids without a
+ * source); stream as for mln_create. Each grid gets an internal context
+ * (alternate buffers, tables). Errors as mln_create, message in
+ * mln_create_error().
+ * mln_batch_autotune: choose steps per launch and tile size (same for every
+ * grid) by timing candidates that read the caller's buffers and write the
+ * contexts' own, so the state is not changed. Synchronises.
+ * mln_batch_step: queue n_steps steps of every grid (async, one graph launch).
+ * mln_batch_sync: wait; report the first grid's device-side problem.
+ * mln_batch_context: the internal context of grid i, for reading results
+ * (mln_get_fields, mln_get_rho, mln_save_state, ...); owned by the batch:
+ * do not step or destroy it.
+ * mln_batch_shape: steps per launch, tile, work items per launch, launches.
+ * mln_batch_error: message of the last failed call on the batch.
+ */
+typedef struct mln_batch mln_batch;
+mln_status mln_batch_create(int32_t count, const mln_params *params, void *const *d_state, void *const *Ez,
+                            void *const *Hy, const double *const *src, int64_t src_len, void *stream,
+                            mln_batch **out);
+mln_status mln_batch_autotune(mln_batch *b, int32_t trials, int32_t *block_steps, int32_t *tile_cells);
+mln_status mln_batch_step(mln_batch *b, int64_t n_steps);
+mln_status mln_batch_sync(mln_batch *b);
+mln_ctx *mln_batch_context(mln_batch *b, int32_t i);
+mln_status mln_batch_shape(const mln_batch *b, int32_t *block_steps, int32_t *tile_cells, int64_t *items,
+                           int64_t *launches);
+const char *mln_batch_error(const mln_batch *b);
+void mln_batch_destroy(mln_batch *b);
+
 /* Free the context (NULL-safe). Caller buffers are not touched. */
 void mln_destroy(mln_ctx *ctx);
 

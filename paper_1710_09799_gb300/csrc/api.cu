@@ -8,34 +8,10 @@
 #include <string>
 #include <vector>
 
+#include "ctx.h"
 #include "dispatch.cuh"
 #include "mln.h"
 #include "setup.h"
-
-struct mln_ctx {
-    mln_params p{};
-    mln::Setup s;
-    int D = 0;
-    int64_t n_med = 0, stride = 0;
-    size_t rsz = 8;                 // bytes per device real
-    size_t state_bytes = 0, field_bytes = 0;
-    void *st[2] = {nullptr, nullptr};  // [0] caller's buffer, [1] context-owned alternate
-    void *E[2] = {nullptr, nullptr};
-    void *H[2] = {nullptr, nullptr};
-    cudaStream_t stream = nullptr;
-    unsigned int *flags = nullptr;
-    std::vector<unsigned char> consts;
-    int K = 16, tile = 0, threads = 0, max_threads = mln::kMaxThreads;
-    int64_t steps = 0, launches = 0;
-    bool sparse = false;               // shared-memory sparse cell model (FP64 merged)
-    void *prog = nullptr;              // its program: rowptr | cols | vals
-    int nnz = 0, nrowptr = 0;
-    // output tables (FP64, device): rows x D matrix followed by rows offsets
-    double *tab_rho = nullptr, *tab_pop = nullptr, *tab_d = nullptr, *tab_in = nullptr;
-    void *scratch = nullptr;
-    size_t scratch_bytes = 0;
-    std::string err;
-};
 
 namespace {
 
@@ -162,30 +138,6 @@ int sparse_max_threads(mln_ctx *c) {
 }
 
 template <typename R>
-mln::BlockArgs<R> base_args(mln_ctx *c) {
-    const double eps = mln::kEps0 * c->p.eps_r, mu = mln::kMu0 * c->p.mu_r;
-    const double sg = c->p.sigma * c->p.dt / (2.0 * eps);
-    const double cv = 1.0 / std::sqrt(eps * mu);
-    mln::BlockArgs<R> a{};
-    a.flags = c->flags;
-    a.n_cells = c->p.n_cells;
-    a.mb = c->p.medium_begin;
-    a.me = c->p.medium_end;
-    a.stride = c->stride;
-    a.source_cell = c->p.source_cell;
-    a.halo = c->K;
-    a.tile = c->tile;
-    a.boundary = c->p.boundary;
-    a.source_kind = c->p.source_kind;
-    a.ch = static_cast<R>(c->p.dt / (mu * c->p.dx));
-    a.ca = static_cast<R>((1.0 - sg) / (1.0 + sg));
-    a.cb = static_cast<R>((c->p.dt / eps) / (1.0 + sg));
-    a.inv_dx = static_cast<R>(1.0 / c->p.dx);
-    a.kappa = static_cast<R>((cv * c->p.dt - c->p.dx) / (cv * c->p.dt + c->p.dx));
-    return a;
-}
-
-template <typename R>
 size_t smem_for(mln_ctx *c, int threads) {
     size_t smem = 2 * static_cast<size_t>(threads) * sizeof(R);
     if (c->sparse) smem += mln::sparse_smem_bytes(c->p.N, threads, c->nnz, c->nrowptr);
@@ -222,7 +174,7 @@ mln_status autotune_t(mln_ctx *c, int trials) {
             c->K = K;
             c->tile = tile;
             c->threads = (tile + 2 * K + 31) / 32 * 32;
-            mln::BlockArgs<R> a = base_args<R>(c);
+            mln::BlockArgs<R> a = mln::base_args<R>(c);
             a.E_in = static_cast<const R *>(c->E[0]);
             a.H_in = static_cast<const R *>(c->H[0]);
             a.s_in = static_cast<const R *>(c->st[0]);
@@ -261,25 +213,7 @@ mln_status autotune_t(mln_ctx *c, int trials) {
 template <typename R>
 mln_status run_steps(mln_ctx *c, int64_t n_steps, const double *src) {
     const int64_t ntiles = (c->p.n_cells + c->tile - 1) / c->tile;
-    const double eps = mln::kEps0 * c->p.eps_r, mu = mln::kMu0 * c->p.mu_r;
-    const double sg = c->p.sigma * c->p.dt / (2.0 * eps);
-    const double cv = 1.0 / std::sqrt(eps * mu);
-    mln::BlockArgs<R> a{};
-    a.flags = c->flags;
-    a.n_cells = c->p.n_cells;
-    a.mb = c->p.medium_begin;
-    a.me = c->p.medium_end;
-    a.stride = c->stride;
-    a.source_cell = c->p.source_cell;
-    a.halo = c->K;
-    a.tile = c->tile;
-    a.boundary = c->p.boundary;
-    a.source_kind = c->p.source_kind;
-    a.ch = static_cast<R>(c->p.dt / (mu * c->p.dx));
-    a.ca = static_cast<R>((1.0 - sg) / (1.0 + sg));
-    a.cb = static_cast<R>((c->p.dt / eps) / (1.0 + sg));
-    a.inv_dx = static_cast<R>(1.0 / c->p.dx);
-    a.kappa = static_cast<R>((cv * c->p.dt - c->p.dx) / (cv * c->p.dt + c->p.dx));
+    mln::BlockArgs<R> a = mln::base_args<R>(c);
     const size_t smem = smem_for<R>(c, c->threads);
     int cur = 0;
     for (int64_t done = 0; done < n_steps;) {

@@ -281,7 +281,8 @@ __global__ void sin_cosm1_kernel(const double *x, int64_t n, double *s, double *
 constexpr int kMaxThreads = 512;
 
 // Cell model with the medium state in registers and dense D x D products
-// whose constants are kernel-parameter (constant-bank) operands.
+// whose constants are kernel-parameter (constant-bank) operands (or, in the
+// batched kernel, a structure in shared memory).
 template <int N, typename R, typename K>
 struct RegisterCell {
     static constexpr int D = Dims<N>::D;
@@ -401,16 +402,17 @@ struct SharedSparseCell {
     }
 };
 
+// One thread block advances tile `tile_index` of one grid by a.nsteps steps.
+// smem: 2 * blockDim.x reals for E and H, then the cell model's extra space.
 template <int N, typename R, typename Cell>
-__global__ void __launch_bounds__(kMaxThreads, 1)
-    mln_block_kernel(const __grid_constant__ BlockArgs<R> a, const __grid_constant__ typename Cell::Consts k) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    R *sE = reinterpret_cast<R *>(smem_raw);
+__device__ __forceinline__ void block_body(const BlockArgs<R> &a, const typename Cell::Consts &k, int64_t tile_index,
+                                           unsigned char *smem) {
+    R *sE = reinterpret_cast<R *>(smem);
     R *sH = sE + blockDim.x;
 
     const int j = threadIdx.x;
     const int64_t n = a.n_cells;
-    const int64_t t0 = static_cast<int64_t>(blockIdx.x) * a.tile;
+    const int64_t t0 = tile_index * a.tile;
     const int64_t t1 = min(t0 + a.tile, n);
     const int L = static_cast<int>(t1 - t0) + 2 * a.halo;
     const bool periodic = a.boundary == 0;
@@ -482,6 +484,13 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
         if (medium) cell.store(a.s_out, a.stride, m);
         if (!isfinite(e)) atomicOr(a.flags, 1u);
     }
+}
+
+template <int N, typename R, typename Cell>
+__global__ void __launch_bounds__(kMaxThreads, 1)
+    mln_block_kernel(const __grid_constant__ BlockArgs<R> a, const __grid_constant__ typename Cell::Consts k) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    block_body<N, R, Cell>(a, k, static_cast<int64_t>(blockIdx.x), smem_raw);
 }
 
 }  // namespace mln

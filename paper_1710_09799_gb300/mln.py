@@ -89,6 +89,17 @@ _SIGS = {
     "mln_create_error": (C.c_char_p, []),
     "mln_setup_host": (C.c_int, [_P, C.POINTER(mln_setup)]),
     "mln_version": (C.c_char_p, []),
+    "mln_batch_create": (C.c_int, [C.c_int32, _P, C.POINTER(C.c_void_p), C.POINTER(C.c_void_p),
+                                   C.POINTER(C.c_void_p), C.POINTER(C.c_void_p), C.c_int64, C.c_void_p,
+                                   C.POINTER(C.c_void_p)]),
+    "mln_batch_autotune": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
+    "mln_batch_step": (C.c_int, [C.c_void_p, C.c_int64]),
+    "mln_batch_sync": (C.c_int, [C.c_void_p]),
+    "mln_batch_context": (C.c_void_p, [C.c_void_p, C.c_int32]),
+    "mln_batch_shape": (C.c_int, [C.c_void_p, C.POINTER(C.c_int32), C.POINTER(C.c_int32),
+                                  C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
+    "mln_batch_error": (C.c_char_p, [C.c_void_p]),
+    "mln_batch_destroy": (None, [C.c_void_p]),
     "mln_rotation_terms": (C.c_int, [C.c_int32, _dp, C.c_int64, _dp, _dp]),
     "mln_step_noalloc": (C.c_int, [_P, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_int64, C.c_void_p,
                                    C.c_void_p]),
@@ -368,6 +379,114 @@ class Solver:
         if getattr(self, "ctx", None):
             mln_destroy(self.ctx)
             self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ------------------------------------------------------------------ batches
+
+def _bcheck(status: int, b):
+    if status != MLN_OK:
+        raise MLNError(status, lib().mln_batch_error(b).decode())
+
+
+def mln_batch_create(params: list, d_states: list, ezs: list, hys: list, srcs: list | None, src_len: int,
+                     stream_ptr: int):
+    n = len(params)
+    arr = (mln_params * n)(*[p.s for p in params])
+    vp = lambda xs: (C.c_void_p * n)(*[C.c_void_p(x) for x in xs])
+    src_arr = None if srcs is None else vp([0 if x is None else x for x in srcs])
+    out = C.c_void_p()
+    _check(lib().mln_batch_create(n, arr, vp(d_states), vp(ezs), vp(hys), src_arr, src_len,
+                                  C.c_void_p(stream_ptr), C.byref(out)))
+    return out
+
+
+def mln_batch_autotune(b, trials: int = 3):
+    k, t = C.c_int32(), C.c_int32()
+    _bcheck(lib().mln_batch_autotune(b, trials, C.byref(k), C.byref(t)), b)
+    return k.value, t.value
+
+
+def mln_batch_step(b, n_steps: int):
+    _bcheck(lib().mln_batch_step(b, n_steps), b)
+
+
+def mln_batch_sync(b):
+    _bcheck(lib().mln_batch_sync(b), b)
+
+
+def mln_batch_context(b, i: int):
+    return C.c_void_p(lib().mln_batch_context(b, i))
+
+
+def mln_batch_shape(b):
+    k, t, it, la = C.c_int32(), C.c_int32(), C.c_int64(), C.c_int64()
+    _bcheck(lib().mln_batch_shape(b, C.byref(k), C.byref(t), C.byref(it), C.byref(la)), b)
+    return k.value, t.value, it.value, la.value
+
+
+def mln_batch_destroy(b):
+    if b:
+        lib().mln_batch_destroy(b)
+
+
+class Batch:
+    """Torch-owned buffers and an mln_batch for a list of Params (with E0 arrays
+    and optional source sample arrays covering src_len steps)."""
+
+    def __init__(self, params: list, E0s: list, srcs: list | None = None, src_len: int = 0, device="cuda"):
+        import torch
+        self.params = params
+        self.tensors = []
+        states, ezs, hys = [], [], []
+        self.dtype = torch.float64 if params[0].s.precision == MLN_FP64 else torch.float32
+        esz = 8 if self.dtype == torch.float64 else 4
+        for par, E0 in zip(params, E0s):
+            sb, fb = mln_query_buffers(par)
+            st = torch.zeros(max(sb // esz, 1), dtype=self.dtype, device=device)
+            E = torch.as_tensor(np.asarray(E0), dtype=self.dtype, device=device).clone()
+            H = torch.zeros(par.s.n_cells, dtype=self.dtype, device=device)
+            self.tensors.append((st, E, H))
+            states.append(st.data_ptr()); ezs.append(E.data_ptr()); hys.append(H.data_ptr())
+        self.src_tensors = None
+        src_ptrs = None
+        if srcs is not None and src_len > 0:
+            self.src_tensors = [None if s is None else torch.as_tensor(np.asarray(s[:src_len]), dtype=torch.float64,
+                                                                           device=device) for s in srcs]
+            src_ptrs = [None if t is None else t.data_ptr() for t in self.src_tensors]
+        self.stream = torch.cuda.current_stream()
+        self.b = mln_batch_create(params, states, ezs, hys, src_ptrs, src_len if src_ptrs else 0,
+                                  self.stream.cuda_stream)
+
+    def autotune(self, trials: int = 3):
+        return mln_batch_autotune(self.b, trials)
+
+    def step(self, n_steps: int):
+        mln_batch_step(self.b, n_steps)
+
+    def sync(self):
+        mln_batch_sync(self.b)
+
+    @property
+    def shape(self):
+        return mln_batch_shape(self.b)
+
+    def fields(self, i: int):
+        return mln_get_fields(mln_batch_context(self.b, i), self.params[i].s.n_cells)
+
+    def rho(self, i: int):
+        p = self.params[i].s
+        return mln_get_rho(mln_batch_context(self.b, i), p.N, p.medium_begin, p.medium_end - p.medium_begin)
+
+    def close(self):
+        if getattr(self, "b", None):
+            mln_batch_destroy(self.b)
+            self.b = None
 
     def __del__(self):
         try:

@@ -296,6 +296,56 @@ def six_level_pulse(n_cells: int = 1048576, n_steps: int = 10000, seed: int = 0,
     return p
 
 
+def multi_level_ring(N: int, n_cells: int, n_steps: int, seed: int, N_a: float = 1e24,
+                     noise: float = 1e3) -> Problem:
+    """N-level ring like the three-level workload: H0 = diag(e_l), e_l ~ U[0, 50]
+    meV; real symmetric dipoles U[1, 5] nm*e on every pair; one downward
+    Lindblad rate U[0.5, 5] /ps per pair in the energy order; seeded random
+    diagonal rho0; E^0 ~ N(0, noise^2)."""
+    rng = np.random.default_rng(seed)
+    lev = rng.uniform(0.0, 50.0, size=N) * MEV
+    mu = np.zeros((N, N), dtype=np.complex128)
+    for j in range(N):
+        for k in range(j + 1, N):
+            mu[j, k] = mu[k, j] = rng.uniform(1.0, 5.0) * NM_E
+    order = np.argsort(lev)
+    rates = {}
+    for ia in range(N):
+        for ib in range(ia + 1, N):
+            rates[(int(order[ib]), int(order[ia]))] = rng.uniform(0.5, 5.0) * 1e12
+    pops = rng.uniform(0.1, 1.0, size=N)
+    rho0 = np.diag(pops / pops.sum()).astype(np.complex128)
+    p = Problem(name=f"{N}_level_ring", N=N, H0=np.diag(lev).astype(np.complex128), mu=mu,
+                G=lindblad_superop(N, rates), rho0=rho0, N_a=N_a, n_cells=n_cells, medium_begin=0,
+                medium_end=n_cells, boundary=BC_PERIODIC, n_steps=n_steps,
+                E_init=rng.normal(0.0, noise, size=n_cells))
+    p.meta.update(seed=seed, rates=rates)
+    return p
+
+
+def batched_devices(count: int = 256, n_steps: int = 20000, seed: int = 0, min_cells: int = 1024,
+                    max_cells: int = 65536) -> list[Problem]:
+    """Independent devices for the batched workload: N ~ uniform{2, 3, 4}, length
+    floor(exp(U[ln min_cells, ln max_cells])) cells. N = 2 devices are two-level
+    SIT grids (sech pulse, hard source + Mur, medium = the middle half); N = 3
+    and N = 4 devices are rings with noise E^0 (parameters drawn per device)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(count):
+        N = int(rng.integers(2, 5))
+        L = int(np.exp(rng.uniform(np.log(min_cells), np.log(max_cells))))
+        sub = int(rng.integers(0, 2**31 - 1))
+        if N == 2:
+            p = two_level_sit(n_cells=L, medium=(L // 4, 3 * L // 4), n_steps=n_steps)
+        elif N == 3:
+            p = three_level_ring(n_cells=L, n_steps=n_steps, seed=sub)
+        else:
+            p = multi_level_ring(4, n_cells=L, n_steps=n_steps, seed=sub)
+        p.name = f"device{i}_{p.name}"
+        out.append(p)
+    return out
+
+
 def config(name: str, **kw) -> Problem:
     """The named workload at its full size (keyword overrides allowed)."""
     table = {
