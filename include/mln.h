@@ -63,7 +63,11 @@ enum { MLN_FP64 = 0, MLN_FP32 = 1 };
  * three D x D products per step instead of four.
  * Both apply each propagator as identity + increment, which keeps the
  * rounding of the small coherences at their own scale. */
-enum { MLN_FORM_STRANG = 0, MLN_FORM_MERGED = 1 };
+/* MLN_FORM_RODRIGUES (N <= 4) is the literal Strang form with the interaction
+ * exponential evaluated by the generalised Rodrigues formula of Eq. 27,
+ * I + sum_k sin(a_k) S_k + (1 - cos a_k) S_k^2, with the rank-2 matrices
+ * S_k = T Theta_k T^T (and S_k^2) stored in full: the paper's "rodr" method. */
+enum { MLN_FORM_STRANG = 0, MLN_FORM_MERGED = 1, MLN_FORM_RODRIGUES = 2 };
 /* Cell model of the step kernel. MLN_KERNEL_REGISTER keeps each cell's
  * vector in registers and multiplies by the full D x D constant matrices.
  * MLN_KERNEL_SPARSE (FP64, merged form only) keeps the vectors in shared
@@ -81,7 +85,7 @@ enum { MLN_KERNEL_AUTO = 0, MLN_KERNEL_REGISTER = 1, MLN_KERNEL_SPARSE = 2 };
  *   N             number of levels, MLN_MIN_N..MLN_MAX_N; adjoint dimension D = N*N-1.
  *   precision     MLN_FP64 or MLN_FP32: type of the device state, fields and
  *                 propagator arithmetic. Set-up is always FP64.
- *   form          MLN_FORM_STRANG or MLN_FORM_MERGED.
+ *   form          MLN_FORM_STRANG, MLN_FORM_MERGED or MLN_FORM_RODRIGUES (N <= 4).
  *   H0            N x N complex Hermitian, J (Eq. 2, H = H0 - mu E_z).
  *   mu            N x N complex Hermitian dipole operator, C m.
  *   G             (N*N) x (N*N) complex relaxation superoperator, 1/s; it must
@@ -253,7 +257,9 @@ mln_status mln_load_state(mln_ctx *ctx, const double *d_host, const double *Ez_h
  * mln_batch_autotune: choose steps per launch and tile size (same for every
  * grid) by timing candidates that read the caller's buffers and write the
  * contexts' own, so the state is not changed. Synchronises.
- * mln_batch_step: queue n_steps steps of every grid (async, one graph launch).
+ * mln_batch_step: queue n_steps steps of every grid (async, one graph launch
+ * on the batch's own stream, ordered after the work already queued on the
+ * creation stream, which in turn waits for the graph).
  * mln_batch_sync: wait; report the first grid's device-side problem.
  * mln_batch_context: the internal context of grid i, for reading results
  * (mln_get_fields, mln_get_rho, mln_save_state, ...); owned by the batch:

@@ -620,6 +620,10 @@ mln_status mln_work_per_step(const mln_ctx *c, double *flops_medium, double *flo
     double f;
     if (c->p.form == MLN_FORM_MERGED) {
         f = 4 * nT + 2 * nz(s.C1, D, D, D, 0.0) + 2 * D + 2 * nz(s.wm, 1, D, D, 0.0) + rot;
+    } else if (c->p.form == MLN_FORM_RODRIGUES) {
+        // per plane: S_k d' and S_k^2 d' (dense, 2 D^2 each) and the two scaled adds (4 D)
+        f = 4 * nz(s.A0, D, D, D, 1.0) + 3 * D + 2 * nz(s.w, 1, D, D, 0.0) + q * (4.0 * D * D + 4.0 * D) +
+            (rot - 6.0 * q);
     } else {
         f = 4 * nz(s.A0, D, D, D, 1.0) + 4 * nT + 3 * D + 2 * nz(s.w, 1, D, D, 0.0) + rot;
     }

@@ -96,7 +96,9 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
 struct mln_batch {
     std::vector<mln_ctx *> ctx;
     int precision = MLN_FP32;
-    cudaStream_t stream = nullptr;
+    cudaStream_t user = nullptr;     // the caller's stream (may be the legacy default stream)
+    cudaStream_t stream = nullptr;   // the batch's own stream: graphs are captured and replayed here
+    cudaEvent_t ev_in = nullptr, ev_out = nullptr;
     int K = 16, tile = 256, threads = 288;
     int64_t steps = 0, src_len = 0, launches = 0;
     std::vector<const double *> src;
@@ -268,6 +270,9 @@ void mln_batch_destroy(mln_batch *b) {
     if (!b) return;
     if (b->stream) cudaStreamSynchronize(b->stream);
     drop_graphs(b);
+    if (b->ev_in) cudaEventDestroy(b->ev_in);
+    if (b->ev_out) cudaEventDestroy(b->ev_out);
+    if (b->stream) cudaStreamDestroy(b->stream);
     cudaFree(b->d_grids);
     cudaFree(b->d_items);
     cudaFree(b->d_consts);
@@ -299,8 +304,16 @@ mln_status mln_batch_create(int32_t count, const mln_params *params, void *const
     mln_batch *b = new (std::nothrow) mln_batch();
     if (!b) return MLN_ENOMEM;
     b->precision = params[0].precision;
-    b->stream = static_cast<cudaStream_t>(stream);
+    b->user = static_cast<cudaStream_t>(stream);
     b->src_len = src_len;
+    if (cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&b->ev_in, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&b->ev_out, cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        mln::create_error() = "creating the batch stream failed";
+        mln_batch_destroy(b);
+        return MLN_ECUDA;
+    }
     for (int32_t i = 0; i < count; ++i) {
         mln_params p = params[i];
         p.kernel = MLN_KERNEL_REGISTER;
@@ -329,6 +342,7 @@ mln_status mln_batch_create(int32_t count, const mln_params *params, void *const
 
 mln_status mln_batch_autotune(mln_batch *b, int32_t trials, int32_t *block_steps, int32_t *tile_cells) {
     if (!b || trials < 1) return MLN_EINVAL;
+    MLN_BCK(b, cudaStreamSynchronize(b->user));
     MLN_BCK(b, cudaStreamSynchronize(b->stream));
     drop_graphs(b);
     mln_status st = b->precision == MLN_FP64 ? autotune_batch<double>(b, trials) : autotune_batch<float>(b, trials);
@@ -371,7 +385,12 @@ mln_status mln_batch_step(mln_batch *b, int64_t n_steps) {
         MLN_BCK(b, ie);
         b->graphs[key] = exec;
     }
+    // order the batch's stream after the caller's work, and the caller's after the graph
+    MLN_BCK(b, cudaEventRecord(b->ev_in, b->user));
+    MLN_BCK(b, cudaStreamWaitEvent(b->stream, b->ev_in, 0));
     MLN_BCK(b, cudaGraphLaunch(exec, b->stream));
+    MLN_BCK(b, cudaEventRecord(b->ev_out, b->stream));
+    MLN_BCK(b, cudaStreamWaitEvent(b->user, b->ev_out, 0));
     const int64_t per = (n_steps + b->K - 1) / b->K;
     b->launches += per;
     b->steps += n_steps;
@@ -385,6 +404,7 @@ mln_status mln_batch_step(mln_batch *b, int64_t n_steps) {
 mln_status mln_batch_sync(mln_batch *b) {
     if (!b) return MLN_EINVAL;
     MLN_BCK(b, cudaStreamSynchronize(b->stream));
+    MLN_BCK(b, cudaStreamSynchronize(b->user));
     for (size_t i = 0; i < b->ctx.size(); ++i) {
         mln_status st = mln_sync(b->ctx[i]);
         if (st != MLN_OK) {

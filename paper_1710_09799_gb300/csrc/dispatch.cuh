@@ -49,8 +49,50 @@ void pack_merged(const Setup &s, double dt, std::vector<unsigned char> &out) {
     std::memcpy(out.data(), &k, sizeof(k));
 }
 
+// S_k = T Theta_k T^T (Theta_k: -1 at (2k, 2k+1), +1 at (2k+1, 2k)) and S_k^2, in FP64.
+template <int N, typename R>
+void pack_rodrigues(const Setup &s, double dt, std::vector<unsigned char> &out) {
+    constexpr int D = Dims<N>::D, Q = Dims<N>::Q;
+    RodriguesConsts<N, R> k;
+    std::memset(&k, 0, sizeof(k));
+    for (int i = 0; i < D; ++i)
+        for (int j = 0; j < D; ++j) k.Dl[i * D + j] = static_cast<R>(s.A0[i * D + j] - (i == j ? 1.0 : 0.0));
+    std::vector<double> S(D * D), S2(D * D);
+    for (int p = 0; p < Q; ++p) {
+        for (int i = 0; i < D; ++i)
+            for (int j = 0; j < D; ++j)
+                S[i * D + j] = -s.T[i * D + 2 * p] * s.T[j * D + 2 * p + 1] + s.T[i * D + 2 * p + 1] * s.T[j * D + 2 * p];
+        for (int i = 0; i < D; ++i)
+            for (int j = 0; j < D; ++j) {
+                double acc = 0;
+                for (int l = 0; l < D; ++l) acc += S[i * D + l] * S[l * D + j];
+                S2[i * D + j] = acc;
+            }
+        for (int i = 0; i < D * D; ++i) {
+            k.S[p * D * D + i] = static_cast<R>(S[i]);
+            k.S2[p * D * D + i] = static_cast<R>(S2[i]);
+        }
+    }
+    for (int i = 0; i < D; ++i) {
+        k.b[i] = static_cast<R>(s.b[i]);
+        k.w[i] = static_cast<R>(s.w[i]);
+    }
+    for (int a = 0; a < N - 1; ++a) k.psi_dt[a] = static_cast<R>(s.psi[a] * dt);
+    k.c = static_cast<R>(s.c);
+    out.resize(sizeof(k));
+    std::memcpy(out.data(), &k, sizeof(k));
+}
+
 template <typename R>
 bool pack_consts_t(const Setup &s, int form, double dt, std::vector<unsigned char> &out) {
+    if (form == MLN_FORM_RODRIGUES) {
+        switch (s.N) {
+        case 2: pack_rodrigues<2, R>(s, dt, out); return true;
+        case 3: pack_rodrigues<3, R>(s, dt, out); return true;
+        case 4: pack_rodrigues<4, R>(s, dt, out); return true;
+        default: return false;
+        }
+    }
     switch (s.N) {
 #define MLN_PACK_CASE(NN)                                        \
     case NN:                                                     \
@@ -143,6 +185,14 @@ cudaError_t launch_sparse_one(const BlockArgs<double> &a, const std::vector<unsi
 template <typename R>
 cudaError_t launch_block_t(int N, int form, const BlockArgs<R> &a, const std::vector<unsigned char> &consts,
                            dim3 grid, dim3 block, size_t smem, cudaStream_t st) {
+    if (form == MLN_FORM_RODRIGUES) {
+        switch (N) {
+        case 2: return launch_one<2, R, RodriguesConsts<2, R>>(a, consts, grid, block, smem, st);
+        case 3: return launch_one<3, R, RodriguesConsts<3, R>>(a, consts, grid, block, smem, st);
+        case 4: return launch_one<4, R, RodriguesConsts<4, R>>(a, consts, grid, block, smem, st);
+        default: return cudaErrorInvalidValue;
+        }
+    }
     switch (N) {
 #define MLN_LAUNCH_CASE(NN)                                                                     \
     case NN:                                                                                    \

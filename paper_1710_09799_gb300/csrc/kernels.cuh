@@ -157,16 +157,15 @@ __device__ __forceinline__ void sin_cosm1(R x, R &s, R &c1) {
     }
 }
 
-// z <- (R(E) - I) z for the q planes of T. Plane (a, b), a < b, in row-major
-// pair order turns by phi_ab = (m_a - m_b) E dt / hbar (m: eigenvalues of mu):
-// (x, y) -> (x cos phi + y sin phi, -x sin phi + y cos phi), the flow of the
-// block [[0, theta], [-theta, 0]] of T^T U T over E dt. Only the N-1 angles
-// psi_a = (m_a - m_{N-1}) E dt / hbar are evaluated; phi_ab = psi_a - psi_b
-// follows by the subtraction formulas written for (sin, cos - 1):
+// (sin phi_k, cos phi_k - 1) for the q planes of T. Plane (a, b), a < b, in
+// row-major pair order turns by phi_ab = (m_a - m_b) E dt / hbar (m: the
+// eigenvalues of mu). Only the N-1 angles psi_a = (m_a - m_{N-1}) E dt / hbar
+// are evaluated; phi_ab = psi_a - psi_b follows by the subtraction formulas
+// written for (sin, cos - 1):
 //   sin(p - r)     = s_p - s_r + s_p c1_r - c1_p s_r
 //   cos(p - r) - 1 = c1_p + c1_r + c1_p c1_r + s_p s_r
 template <int N, typename R>
-__device__ __forceinline__ void rotation_increment(R (&z)[Dims<N>::D], const R *psi_dt, R e) {
+__device__ __forceinline__ void plane_terms(const R *psi_dt, R e, R (&s)[Dims<N>::Q], R (&c1)[Dims<N>::Q]) {
     R sp[N], cp[N];
 #pragma unroll
     for (int a = 0; a < N - 1; ++a) sin_cosm1(psi_dt[a] * e, sp[a], cp[a]);
@@ -177,22 +176,34 @@ __device__ __forceinline__ void rotation_increment(R (&z)[Dims<N>::D], const R *
     for (int a = 0; a < N; ++a) {
 #pragma unroll
         for (int b = a + 1; b < N; ++b) {
-            R s, c1;
             if (b == N - 1) {
-                s = sp[a];
-                c1 = cp[a];
+                s[k] = sp[a];
+                c1[k] = cp[a];
             } else {
-                s = (sp[a] - sp[b]) + fma(sp[a], cp[b], -(cp[a] * sp[b]));
-                c1 = (cp[a] + cp[b]) + fma(cp[a], cp[b], sp[a] * sp[b]);
+                s[k] = (sp[a] - sp[b]) + fma(sp[a], cp[b], -(cp[a] * sp[b]));
+                c1[k] = (cp[a] + cp[b]) + fma(cp[a], cp[b], sp[a] * sp[b]);
             }
-            const R x = z[2 * k], y = z[2 * k + 1];
-            z[2 * k] = fma(c1, x, s * y);
-            z[2 * k + 1] = fma(c1, y, -(s * x));
             ++k;
         }
     }
+}
+
+// z <- (R(E) - I) z for the q planes of T: plane k turns (x, y) to
+// (x cos phi + y sin phi, -x sin phi + y cos phi), the flow of the block
+// [[0, theta], [-theta, 0]] of T^T U T over E dt; the null space of U (the
+// last N - 1 coordinates) does not change.
+template <int N, typename R>
+__device__ __forceinline__ void rotation_increment(R (&z)[Dims<N>::D], const R *psi_dt, R e) {
+    R s[Dims<N>::Q], c1[Dims<N>::Q];
+    plane_terms<N>(psi_dt, e, s, c1);
 #pragma unroll
-    for (int i = 2 * Dims<N>::Q; i < Dims<N>::D; ++i) z[i] = R(0);  // null space of U: no change
+    for (int k = 0; k < Dims<N>::Q; ++k) {
+        const R x = z[2 * k], y = z[2 * k + 1];
+        z[2 * k] = fma(c1[k], x, s[k] * y);
+        z[2 * k + 1] = fma(c1[k], y, -(s[k] * x));
+    }
+#pragma unroll
+    for (int i = 2 * Dims<N>::Q; i < Dims<N>::D; ++i) z[i] = R(0);
 }
 
 // y = x + (A x + b) with A row-major D x D held in the constant bank.
@@ -239,6 +250,22 @@ __device__ __forceinline__ R dot_bias(const R *w, const R (&x)[D], R c) {
     return acc;
 }
 
+// Generalised Rodrigues form (Eq. 27) of the interaction step, for N <= 4:
+// exp(U E dt) = I + sum_k sin(a_k) S_k + (1 - cos a_k) S_k^2 with
+// S_k = T Theta_k T^T and, in the orientation of this T, a_k = -phi_k, so
+//   d'' = d' + sum_k (-sin(phi_k) S_k d' - (cos(phi_k) - 1) S_k^2 d').
+// The rest of the step is the literal Strang form.
+template <int N, typename R>
+struct RodriguesConsts {
+    R Dl[Dims<N>::D * Dims<N>::D];
+    R S[Dims<N>::Q * Dims<N>::D * Dims<N>::D];
+    R S2[Dims<N>::Q * Dims<N>::D * Dims<N>::D];
+    R b[Dims<N>::D];
+    R w[Dims<N>::D];
+    R psi_dt[N - 1];
+    R c;
+};
+
 // One Liouville step of one cell; returns dP/dt^{n+1/2}. Two D-vectors live.
 template <int N, typename R>
 __device__ __forceinline__ R cell_step(R (&s)[Dims<N>::D], R e, const StrangConsts<N, R> &k) {
@@ -264,6 +291,35 @@ __device__ __forceinline__ R cell_step(R (&s)[Dims<N>::D], R e, const MergedCons
 #pragma unroll
     for (int i = 0; i < D; ++i) s[i] = z[i];
     return dpdt;
+}
+
+template <int N, typename R>
+__device__ __forceinline__ R cell_step(R (&s)[Dims<N>::D], R e, const RodriguesConsts<N, R> &k) {
+    constexpr int D = Dims<N>::D, Q = Dims<N>::Q;
+    R y[D];
+    affine_inc<D>(y, k.Dl, s, k.b);  // d' = A0 d + b
+    R sn[Q], c1[Q];
+    plane_terms<N>(k.psi_dt, e, sn, c1);
+#pragma unroll
+    for (int i = 0; i < D; ++i) s[i] = R(0);  // accumulates the increment
+#pragma unroll
+    for (int p = 0; p < Q; ++p) {
+        const R *Sp = k.S + p * D * D, *S2p = k.S2 + p * D * D;
+#pragma unroll
+        for (int i = 0; i < D; ++i) {
+            R u = Sp[i * D] * y[0], v = S2p[i * D] * y[0];
+#pragma unroll
+            for (int j = 1; j < D; ++j) {
+                u = fma(Sp[i * D + j], y[j], u);
+                v = fma(S2p[i * D + j], y[j], v);
+            }
+            s[i] = fma(-sn[p], u, fma(-c1[p], v, s[i]));
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < D; ++i) y[i] = y[i] + s[i];  // d''
+    affine_inc<D>(s, k.Dl, y, k.b);                  // d = A0 d'' + b
+    return dot_bias<D>(k.w, s, k.c);
 }
 
 // Evaluates (sin x, cos x - 1) as the step kernels do (diagnostic entry point).

@@ -246,9 +246,13 @@ mln_status validate(const mln_params &p, std::string &err) {
         err = "precision must be MLN_FP64 or MLN_FP32";
         return MLN_EINVAL;
     }
-    if (p.form != MLN_FORM_STRANG && p.form != MLN_FORM_MERGED) {
-        err = "form must be MLN_FORM_STRANG or MLN_FORM_MERGED";
+    if (p.form != MLN_FORM_STRANG && p.form != MLN_FORM_MERGED && p.form != MLN_FORM_RODRIGUES) {
+        err = "form must be MLN_FORM_STRANG, MLN_FORM_MERGED or MLN_FORM_RODRIGUES";
         return MLN_EINVAL;
+    }
+    if (p.form == MLN_FORM_RODRIGUES && p.N > 4) {
+        err = "MLN_FORM_RODRIGUES is built for N <= 4";
+        return MLN_EUNSUPPORTED;
     }
     if (p.boundary != MLN_BC_PERIODIC && p.boundary != MLN_BC_OPEN) {
         err = "boundary must be MLN_BC_PERIODIC or MLN_BC_OPEN";
@@ -528,7 +532,7 @@ mln_status build_setup(const mln_params &p, Setup &s, std::string &err) {
     s.sd0.assign(D, 0.0);
     s.Sp.assign((size_t)D * D, 0.0);
     s.sp0.assign(D, 0.0);
-    if (p.form == MLN_FORM_STRANG) {
+    if (p.form != MLN_FORM_MERGED) {
         for (int i = 0; i < D; ++i) s.Sd[i * D + i] = s.Sp[i * D + i] = 1.0;
     } else {
         // d = A0^-1 (y - b) = A0inv y + binv;  y = A0 d + b

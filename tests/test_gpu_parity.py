@@ -40,7 +40,7 @@ def pops(rho):
     return np.einsum("cii->ci", rho).real
 
 
-@pytest.mark.parametrize("form", ["strang", "merged"])
+@pytest.mark.parametrize("form", ["strang", "merged", "rodrigues"])
 def test_two_level_sit_full_fp64(orc, form):
     """The two-level workload at full size: 2000 cells, medium [500, 1500),
     sech pulse of area 2 pi, hard source + Mur, 20000 steps."""
@@ -54,7 +54,7 @@ def test_two_level_sit_full_fp64(orc, form):
     assert pops(ref.rho)[:, 1].max() > 1e-3  # the pulse reached and excited the medium
 
 
-@pytest.mark.parametrize("form", ["strang", "merged"])
+@pytest.mark.parametrize("form", ["strang", "merged", "rodrigues"])
 def test_three_level_ring_small_fp64(orc, form):
     """Three-level ring, 4096 cells (several tiles, ragged last tile), 1500 steps."""
     p = W.three_level_ring(n_cells=4096, n_steps=1500)
@@ -89,7 +89,7 @@ def test_other_N_fp64(orc, N):
                   medium_end=650, boundary="periodic", n_steps=300,
                   E_init=rng.normal(0, 1e8, size=777))
     ref = oracle_ref(orc, p, p.n_steps)
-    for form in ("strang", "merged"):
+    for form in ("strang", "merged") + (("rodrigues",) if N <= 4 else ()):
         E, H, rho, _ = gpu_run(p, p.n_steps, "fp64", form)
         assert rel_inf(E, ref.E) < FP64_E
         assert np.abs(rho - ref.rho).max() < FP64_POP
@@ -114,7 +114,7 @@ def test_fp32_error_bounds(orc):
     p = W.three_level_ring(n_cells=4096, n_steps=2000)
     ref = oracle_ref(orc, p, p.n_steps)
     k = p.n_steps / 1000
-    for form in ("strang", "merged"):
+    for form in ("strang", "merged", "rodrigues"):
         E, H, rho, _ = gpu_run(p, p.n_steps, "fp32", form)
         e_err = rel_inf(E, ref.E)
         p_err = np.abs(pops(rho) - pops(ref.rho)).max()
