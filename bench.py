@@ -41,6 +41,8 @@ WORKLOADS = {
     "six_level_pulse": "six-level manifold (D = 35), Gaussian pulse, hard source + Mur, 1048576 cells x 10000 steps",
     "two_level_sit": "two-level SIT, sech pulse of area 2 pi, 2000 cells x 20000 steps",
     "batched": "256 independent devices, N in {2,3,4}, 1k-64k cells (log-uniform), 20000 steps, one graph per call",
+    "adjoint": "gradient of the probe energy: three-level ring, 8192 cells x 5000 steps, soft source (512 samples), "
+               "checkpoints every 256 steps",
 }
 WORKLOAD = WORKLOADS["three_level_ring"]
 
@@ -139,11 +141,13 @@ def barrier(ws):
 
 
 def max_over_ranks(ws, x: float) -> float:
+    """The maximum of x over the ranks (CUDA tensor under NCCL, CPU under gloo)."""
     if ws <= 1:
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
 
@@ -331,6 +335,51 @@ def run_reference(args):
     return 0
 
 
+def run_adjoint(args, ws, rank, local):
+    """Gradient workload: each benchmark step is one full J + gradient evaluation
+    (forward with checkpoints, backward with recomputation); the value counts the
+    forward cell-updates per second of that evaluation."""
+    import torch
+    from paper_1710_09799_gb300 import mln
+    p = W.adjoint_ring()
+    src = torch.as_tensor(p.source_samples(0, p.n_steps), dtype=torch.float64, device="cuda")
+    par = make_params(p, args.precision, "strang")
+    times = []
+    for i in range(args.warmup + args.steps):
+        s = mln.Solver(par, E0=p.e_init())
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        J, dsrc, dmu, dG = mln.mln_adjoint(s.ctx, p.N, p.n_steps, src.data_ptr(), p.meta["probe_cell"], 256)
+        torch.cuda.synchronize()
+        if i >= args.warmup:
+            times.append(time.perf_counter() - t)
+        s.close()
+    # the plain forward of the same workload, for comparison
+    s = mln.Solver(par, E0=p.e_init())
+    s.autotune(3)
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    s.step(p.n_steps, src)
+    s.sync()
+    t_fwd = time.perf_counter() - t
+    s.close()
+    tot = float(np.sum(times))
+    value = ws * p.n_cells * p.n_steps * len(times) / max_over_ranks(ws, tot)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * tot / len(times), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if args.precision == "fp64" else "f32", "data": "synthetic (seeded)",
+        "config": {"workload": WORKLOADS["adjoint"], "n_cells": p.n_cells, "time_steps": p.n_steps,
+                   "checkpoint_every": 256, "gradients": "512 source samples, 9 dipole parameters, 81 x 81 G"},
+        "forward_only_cell_updates_per_s": p.n_cells * p.n_steps / t_fwd,
+        "gradient_cost_over_forward": (tot / len(times)) / t_fwd,
+        "J": J, "dJ_dmu12": float(dmu[p.N]),
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_batched(args, ws, rank, local):
     vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
     smi_index = int(vis.split(",")[local]) if vis and vis.split(",")[local].isdigit() else local
@@ -383,6 +432,8 @@ def main():
         build()
     if args.workload == "batched":
         return run_batched(args, ws, rank, local)
+    if args.workload == "adjoint":
+        return run_adjoint(args, ws, rank, local)
     p = W.config(args.workload)
     D, q = p.D, p.N * (p.N - 1) // 2
 

@@ -73,9 +73,14 @@ enum { MLN_FORM_STRANG = 0, MLN_FORM_MERGED = 1, MLN_FORM_RODRIGUES = 2 };
  * MLN_KERNEL_SPARSE (FP64, merged form only) keeps the vectors in shared
  * memory and multiplies only by the entries of the constant matrices that
  * are not exactly zero; the sums run in the same order, so both give the
- * same result. MLN_KERNEL_AUTO picks SPARSE for FP64 merged, REGISTER
- * otherwise. */
-enum { MLN_KERNEL_AUTO = 0, MLN_KERNEL_REGISTER = 1, MLN_KERNEL_SPARSE = 2 };
+ * same result. MLN_KERNEL_AUTO picks SPARSE for FP64 merged, JIT for FP32
+ * merged when NVRTC is available, REGISTER otherwise. */
+/* MLN_KERNEL_JIT (merged form) generates, at mln_create, this problem's step
+ * as straight-line CUDA with the constants as literals and the exactly-zero
+ * entries left out, compiles it for sm_103a at run time (NVRTC) and launches
+ * it; same arithmetic and order as MLN_KERNEL_REGISTER, so the same bits.
+ * It needs libnvrtc at run time (MLN_EUNSUPPORTED otherwise). */
+enum { MLN_KERNEL_AUTO = 0, MLN_KERNEL_REGISTER = 1, MLN_KERNEL_SPARSE = 2, MLN_KERNEL_JIT = 3 };
 
 #define MLN_MIN_N 2
 #define MLN_MAX_N 6
@@ -109,7 +114,7 @@ enum { MLN_KERNEL_AUTO = 0, MLN_KERNEL_REGISTER = 1, MLN_KERNEL_SPARSE = 2 };
  *   block_steps   steps fused into one kernel launch (temporal blocking);
  *                 0 picks a default. 1..64.
  *   tile_cells    cells written by one thread block; 0 picks a default.
- *   kernel        MLN_KERNEL_AUTO, MLN_KERNEL_REGISTER or MLN_KERNEL_SPARSE.
+ *   kernel        MLN_KERNEL_AUTO, MLN_KERNEL_REGISTER, MLN_KERNEL_SPARSE or MLN_KERNEL_JIT.
  */
 typedef struct mln_params {
     int32_t N;
@@ -240,6 +245,38 @@ mln_status mln_load_state(mln_ctx *ctx, const double *d_host, const double *Ez_h
                           const double *Hy_host);
 
 /*
+ * Adjoint gradients (reverse-time, discrete adjoint of the step as computed).
+ * Objective J = dt * sum_{n=1..n_steps} (E_z^n at probe_cell)^2, the field
+ * energy density at an output cell integrated over the run, starting from the
+ * context's current state; the context ends advanced by n_steps. Needs
+ * MLN_FORM_STRANG, MLN_BC_PERIODIC and N <= 4.
+ *   src         as for mln_step (device, n_steps samples) or NULL.
+ *   every       checkpoint interval: the forward pass saves the state every
+ *               `every` steps; the backward pass recomputes each segment from
+ *               its checkpoint and keeps its every + 1 states (device memory
+ *               about (n_steps / every + every) x the state and field bytes).
+ *   out->J      the objective.
+ *   out->dJ_dsrc  NULL or n_steps doubles: dJ / d(source sample k).
+ *   out->dJ_dmu   NULL or N*N doubles: dJ / d mu_ll (l = 0..N-1), then
+ *               dJ / d Re mu_jk, then dJ / d Im mu_jk for j < k in row-major
+ *               order (mu_kj follows as the conjugate). The eigenvalues of mu
+ *               must be distinct (MLN_ENUMERIC otherwise).
+ *   out->dJ_dG    NULL or (N*N)^2 complex (interleaved): Gamma with
+ *               dJ = Re sum_rc conj(Gamma_rc) dG_rc for the relaxation
+ *               superoperator of the parameter set (zero rows and columns included).
+ * Device memory for checkpoints and adjoints is allocated inside the call and
+ * freed before it returns. Synchronises.
+ */
+typedef struct mln_adjoint_out {
+    double J;
+    double *dJ_dsrc;
+    double *dJ_dmu;
+    double *dJ_dG;
+} mln_adjoint_out;
+mln_status mln_adjoint(mln_ctx *ctx, int64_t n_steps, const double *src, int64_t probe_cell, int32_t every,
+                       mln_adjoint_out *out);
+
+/*
  * Batches: many independent grids advanced together. Every launch covers
  * every tile of every grid (one work list, tiles of the costliest grids
  * first), so small and large grids of different N share the GPU; the
@@ -364,6 +401,13 @@ mln_status mln_rotation_terms(int32_t precision, const double *x, int64_t n, dou
 #define MLN_STATIC_SCRATCH_BYTES (32u * 1024u * 1024u)
 mln_status mln_step_noalloc(const mln_params *p, void *d_state, void *Ez, void *Hy, int32_t init_state,
                             int64_t n_steps, const double *src, void *stream);
+
+/*
+ * Diagnostic: the CUDA source that MLN_KERNEL_JIT would compile for p (merged
+ * form), written to buf (capacity cap bytes, NUL-terminated when it fits);
+ * *len receives the length without the NUL. Host only.
+ */
+mln_status mln_kernel_source(const mln_params *p, char *buf, size_t cap, size_t *len);
 
 /* Library version string. */
 const char *mln_version(void);

@@ -17,11 +17,11 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libmln.so")
 
-SOURCES = ["api.cu", "kernels_fp64.cu", "kernels_fp32.cu", "setup.cpp", "static_scratch.cu", "batch.cu"]
-HEADERS = ["kernels.cuh", "dispatch.cuh", "setup.h", "ctx.h"]
+SOURCES = ["api.cu", "kernels_fp64.cu", "kernels_fp32.cu", "setup.cpp", "static_scratch.cu", "batch.cu", "adjoint.cu", "jit.cu"]
+HEADERS = ["kernels.cuh", "dispatch.cuh", "setup.h", "ctx.h", "adjoint.cuh", "jit.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
-         "--expt-relaxed-constexpr", "-I", INCLUDE, "-I", CSRC]
+         "--expt-relaxed-constexpr", "-I", INCLUDE, "-I", CSRC, "-I", BUILD]
 
 
 def nvcc() -> str:
@@ -37,8 +37,22 @@ def _stale(obj: str, src: str) -> bool:
     return any(os.path.getmtime(d) > t for d in deps)
 
 
+def write_jit_source() -> str:
+    """kernels.cuh as a C++ string literal, compiled into the library for the
+    per-problem kernels it generates and compiles at run time (NVRTC)."""
+    src = open(os.path.join(CSRC, "kernels.cuh")).read()
+    assert ")MLNSRC" not in src
+    path = os.path.join(BUILD, "jit_source.inc")
+    text = "static const char *kKernelsSource = R\"MLNSRC(" + src + ")MLNSRC\";\n"
+    if not os.path.exists(path) or open(path).read() != text:
+        with open(path, "w") as f:
+            f.write(text)
+    return path
+
+
 def build(force: bool = False, verbose: bool = False, extra: list[str] | None = None) -> str:
     os.makedirs(BUILD, exist_ok=True)
+    write_jit_source()
     extra = list(extra or [])
     procs = []
     objs = []
@@ -66,7 +80,7 @@ def build(force: bool = False, verbose: bool = False, extra: list[str] | None = 
         raise RuntimeError(f"nvcc failed:\n{msg}")
     if force or procs or not os.path.exists(LIB):
         tmp = LIB + f".tmp{os.getpid()}"
-        cmd = [nvcc()] + ARCH + ["-shared", "-o", tmp] + objs + ["-cudart", "static"]
+        cmd = [nvcc()] + ARCH + ["-shared", "-o", tmp] + objs + ["-cudart", "static", "-ldl"]
         subprocess.check_call(cmd)
         os.replace(tmp, LIB)
     return LIB

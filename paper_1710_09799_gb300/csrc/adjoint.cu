@@ -1,0 +1,210 @@
+// mln_adjoint: gradients of a probe-field objective by the discrete adjoint
+// (reverse-time) method with checkpointing and recomputation.
+//
+// Forward: the fused step kernel advances the context, saving the state at
+// the start of every segment of `every` steps. Backward: for the segments in
+// reverse order, the segment is recomputed from its checkpoint one step per
+// launch (all its states kept), then the reverse step kernel runs from the
+// segment's last step to its first, carrying the adjoint of (E, H, d) and
+// accumulating the gradients of the step's constants. The host then maps
+// those to the dipole operator and the relaxation superoperator (exact
+// Frechet derivatives, see adjoint_chain).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "adjoint.cuh"
+#include "ctx.h"
+#include "dispatch.cuh"
+#include "mln.h"
+#include "setup.h"
+
+namespace {
+
+#define MLN_ACK(c, call)                                                        \
+    do {                                                                        \
+        cudaError_t e_ = (call);                                                \
+        if (e_ != cudaSuccess) {                                                \
+            (c)->err = std::string(#call) + ": " + cudaGetErrorString(e_);      \
+            st = MLN_ECUDA;                                                     \
+            goto done;                                                          \
+        }                                                                       \
+    } while (0)
+
+template <int N, typename R>
+mln::AdjConsts<N, R> adj_consts(const mln::Setup &s, double dt) {
+    constexpr int D = mln::Dims<N>::D, Q = mln::Dims<N>::Q;
+    mln::AdjConsts<N, R> k;
+    std::memset(&k, 0, sizeof(k));
+    for (int i = 0; i < D; ++i)
+        for (int j = 0; j < D; ++j) {
+            k.Dl[i * D + j] = static_cast<R>(s.A0[i * D + j] - (i == j ? 1.0 : 0.0));
+            k.T[i * D + j] = static_cast<R>(s.T[i * D + j]);
+        }
+    for (int i = 0; i < D; ++i) {
+        k.b[i] = static_cast<R>(s.b[i]);
+        k.w[i] = static_cast<R>(s.w[i]);
+    }
+    for (int a = 0; a < N - 1; ++a) k.psi_dt[a] = static_cast<R>(s.psi[a] * dt);
+    for (int p = 0; p < Q; ++p) k.theta_dt[p] = static_cast<R>(s.theta[p] * dt);
+    return k;
+}
+
+// Buffers of one (state, E, H) set inside a larger allocation.
+template <typename R>
+struct Set {
+    R *E, *H, *S;
+};
+
+template <int N, typename R>
+mln_status adjoint_t(mln_ctx *c, int64_t n_steps, const double *src, int64_t probe, int every, mln_adjoint_out *out) {
+    using L = mln::AccLayout<N>;
+    mln_status st = MLN_OK;
+    const int64_t n = c->p.n_cells;
+    const size_t sb = c->state_bytes, fb = c->field_bytes;
+    const size_t set_bytes = (sb + 2 * fb + 255) / 256 * 256;
+    const int64_t nseg = (n_steps + every - 1) / every;
+    unsigned char *ckpt = nullptr, *slots = nullptr, *adj = nullptr;
+    double *dsrc = nullptr, *acc = nullptr;
+    std::vector<double> hacc(L::size, 0.0);
+    const mln::AdjConsts<N, R> k = adj_consts<N, R>(c->s, c->p.dt);
+    auto set_at = [&](unsigned char *base, int64_t i) {
+        unsigned char *p = base + i * set_bytes;
+        return Set<R>{reinterpret_cast<R *>(p + sb), reinterpret_cast<R *>(p + sb + fb), reinterpret_cast<R *>(p)};
+    };
+    auto copy_set = [&](Set<R> dst, Set<R> from) {
+        cudaError_t e = cudaMemcpyAsync(dst.S, from.S, sb, cudaMemcpyDeviceToDevice, c->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(dst.E, from.E, fb, cudaMemcpyDeviceToDevice, c->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(dst.H, from.H, fb, cudaMemcpyDeviceToDevice, c->stream);
+        return e;
+    };
+    const Set<R> user{static_cast<R *>(c->E[0]), static_cast<R *>(c->H[0]), static_cast<R *>(c->st[0])};
+    mln::BlockArgs<R> fa = mln::base_args<R>(c);
+    const int rtile = 254, rthreads = 256;  // recompute shape: one step per launch
+    fa.halo = 1;
+    fa.tile = rtile;
+    fa.nsteps = 1;
+    mln::AdjArgs<R> aa{};
+    Set<R> A0s, A1s;
+
+    MLN_ACK(c, cudaMalloc(&ckpt, nseg * set_bytes));
+    MLN_ACK(c, cudaMalloc(&slots, (every + 1) * set_bytes));
+    MLN_ACK(c, cudaMalloc(&adj, 2 * set_bytes));
+    MLN_ACK(c, cudaMalloc(&acc, L::size * sizeof(double)));
+    if (src) MLN_ACK(c, cudaMalloc(&dsrc, n_steps * sizeof(double)));
+
+    // forward with checkpoints
+    for (int64_t s = 0; s < nseg; ++s) {
+        const int64_t len = std::min<int64_t>(every, n_steps - s * every);
+        MLN_ACK(c, copy_set(set_at(ckpt, s), user));
+        mln_status r = mln_step(c, len, src ? src + s * every : nullptr);
+        if (r != MLN_OK) {
+            st = r;
+            goto done;
+        }
+    }
+    // backward
+    MLN_ACK(c, cudaMemsetAsync(adj, 0, 2 * set_bytes, c->stream));
+    MLN_ACK(c, cudaMemsetAsync(acc, 0, L::size * sizeof(double), c->stream));
+    A0s = set_at(adj, 0);
+    A1s = set_at(adj, 1);
+    aa.acc = acc;
+    aa.n_cells = n;
+    aa.mb = c->p.medium_begin;
+    aa.me = c->p.medium_end;
+    aa.stride = c->stride;
+    aa.source_cell = c->p.source_cell;
+    aa.probe_cell = probe;
+    aa.source_kind = c->p.source_kind;
+    aa.dt = c->p.dt;
+    aa.ch = fa.ch;
+    aa.ca = fa.ca;
+    aa.cb = fa.cb;
+    aa.inv_dx = fa.inv_dx;
+    for (int64_t s = nseg - 1; s >= 0; --s) {
+        const int64_t s0 = s * every, len = std::min<int64_t>(every, n_steps - s0);
+        MLN_ACK(c, copy_set(set_at(slots, 0), set_at(ckpt, s)));
+        for (int64_t j = 0; j < len; ++j) {
+            const Set<R> in = set_at(slots, j), o = set_at(slots, j + 1);
+            fa.E_in = in.E;
+            fa.H_in = in.H;
+            fa.s_in = in.S;
+            fa.E_out = o.E;
+            fa.H_out = o.H;
+            fa.s_out = o.S;
+            fa.src = (src && c->p.source_kind != MLN_SRC_NONE) ? src + s0 + j : nullptr;
+            MLN_ACK(c, mln::launch_block(c->p.N, MLN_FORM_STRANG, fa, c->consts,
+                                         dim3(static_cast<unsigned>((n + rtile - 1) / rtile)), dim3(rthreads),
+                                         2 * rthreads * sizeof(R), c->stream));
+        }
+        for (int64_t j = len - 1; j >= 0; --j) {
+            const Set<R> f0 = set_at(slots, j), f1 = set_at(slots, j + 1);
+            aa.E0 = f0.E;
+            aa.E1 = f1.E;
+            aa.S0 = f0.S;
+            aa.Ea = A0s.E;
+            aa.Ha = A0s.H;
+            aa.Sa = A0s.S;
+            aa.Eb = A1s.E;
+            aa.Hb = A1s.H;
+            aa.Sb = A1s.S;
+            aa.dsrc = (src && c->p.source_kind != MLN_SRC_NONE) ? dsrc + s0 + j : nullptr;
+            mln::mln_adjoint_step<N, R><<<static_cast<unsigned>((n + 255) / 256), 256, 0, c->stream>>>(aa, k);
+            MLN_ACK(c, cudaGetLastError());
+            std::swap(A0s, A1s);
+        }
+    }
+    MLN_ACK(c, cudaMemcpyAsync(hacc.data(), acc, L::size * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    if (out->dJ_dsrc) {
+        if (src && c->p.source_kind != MLN_SRC_NONE)
+            MLN_ACK(c, cudaMemcpyAsync(out->dJ_dsrc, dsrc, n_steps * sizeof(double), cudaMemcpyDeviceToHost,
+                                       c->stream));
+        else
+            std::fill(out->dJ_dsrc, out->dJ_dsrc + n_steps, 0.0);
+    }
+    MLN_ACK(c, cudaStreamSynchronize(c->stream));
+    out->J = hacc[L::J];
+    {
+        std::string err;
+        st = mln::adjoint_chain(c->p, c->s, hacc.data(), out->dJ_dmu, out->dJ_dG, err);
+        if (st != MLN_OK) c->err = err;
+    }
+done:
+    cudaStreamSynchronize(c->stream);
+    cudaFree(ckpt);
+    cudaFree(slots);
+    cudaFree(adj);
+    cudaFree(acc);
+    cudaFree(dsrc);
+    return st;
+}
+
+}  // namespace
+
+extern "C" {
+
+mln_status mln_adjoint(mln_ctx *c, int64_t n_steps, const double *src, int64_t probe_cell, int32_t every,
+                       mln_adjoint_out *out) {
+    if (!c || !out || n_steps < 1 || every < 1 || probe_cell < 0 || probe_cell >= c->p.n_cells) {
+        if (c) c->err = "invalid adjoint arguments";
+        return MLN_EINVAL;
+    }
+    if (c->p.form != MLN_FORM_STRANG || c->p.boundary != MLN_BC_PERIODIC || c->p.N > 4 || c->sparse) {
+        c->err = "mln_adjoint needs MLN_FORM_STRANG, MLN_BC_PERIODIC and N <= 4";
+        return MLN_EUNSUPPORTED;
+    }
+    switch (c->p.N) {
+    case 2: return c->p.precision == MLN_FP64 ? adjoint_t<2, double>(c, n_steps, src, probe_cell, every, out)
+                                              : adjoint_t<2, float>(c, n_steps, src, probe_cell, every, out);
+    case 3: return c->p.precision == MLN_FP64 ? adjoint_t<3, double>(c, n_steps, src, probe_cell, every, out)
+                                              : adjoint_t<3, float>(c, n_steps, src, probe_cell, every, out);
+    case 4: return c->p.precision == MLN_FP64 ? adjoint_t<4, double>(c, n_steps, src, probe_cell, every, out)
+                                              : adjoint_t<4, float>(c, n_steps, src, probe_cell, every, out);
+    default: return MLN_EUNSUPPORTED;
+    }
+}
+
+}  // extern "C"

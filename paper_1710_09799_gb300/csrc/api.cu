@@ -10,6 +10,7 @@
 
 #include "ctx.h"
 #include "dispatch.cuh"
+#include "jit.h"
 #include "mln.h"
 #include "setup.h"
 
@@ -118,11 +119,13 @@ void pick_launch_shape(mln_ctx *c) {
 }
 
 cudaError_t launch(mln_ctx *c, const mln::BlockArgs<double> &a, dim3 g, dim3 b, size_t smem) {
+    if (c->jit_fn) return mln::jit_launch(c->jit_fn, a, g, b, smem, c->stream);
     if (c->sparse) return mln::launch_block_sparse(c->p.N, a, c->consts, g, b, smem, c->stream);
     return mln::launch_block(c->p.N, c->p.form, a, c->consts, g, b, smem, c->stream);
 }
 
 cudaError_t launch(mln_ctx *c, const mln::BlockArgs<float> &a, dim3 g, dim3 b, size_t smem) {
+    if (c->jit_fn) return mln::jit_launch(c->jit_fn, a, g, b, smem, c->stream);
     return mln::launch_block(c->p.N, c->p.form, a, c->consts, g, b, smem, c->stream);
 }
 
@@ -313,6 +316,26 @@ extern "C" {
 
 const char *mln_version(void) { return kVersion; }
 
+mln_status mln_kernel_source(const mln_params *p, char *buf, size_t cap, size_t *len) {
+    if (!p) return MLN_EINVAL;
+    std::string err;
+    mln_status st = mln::validate(*p, err);
+    mln::Setup s;
+    if (st == MLN_OK) st = mln::build_setup(*p, s, err);
+    if (st != MLN_OK) {
+        mln::create_error() = err;
+        return st;
+    }
+    const std::string src = mln::jit_merged_source(s, p->dt, p->precision == MLN_FP32);
+    if (len) *len = src.size();
+    if (buf && cap > 0) {
+        const size_t k = std::min(cap - 1, src.size());
+        std::memcpy(buf, src.data(), k);
+        buf[k] = '\0';
+    }
+    return MLN_OK;
+}
+
 mln_status mln_rotation_terms(int32_t precision, const double *x, int64_t n, double *s, double *c1) {
     if ((n > 0 && (!x || !s || !c1)) || n < 0 || (precision != MLN_FP64 && precision != MLN_FP32)) return MLN_EINVAL;
     if (n == 0) return MLN_OK;
@@ -502,6 +525,23 @@ mln_status mln_create(const mln_params *p, void *d_state, void *Ez, void *Hy, vo
     } else {
         ok = p->precision == MLN_FP64 ? mln::pack_consts(c->s, p->form, p->dt, 0.0, c->consts)
                                       : mln::pack_consts(c->s, p->form, p->dt, 0.0f, c->consts);
+        const bool want_jit = p->kernel == MLN_KERNEL_JIT ||
+                              (p->kernel == MLN_KERNEL_AUTO && p->precision == MLN_FP32 && p->form == MLN_FORM_MERGED);
+        if (ok && want_jit) {
+            std::string why, log;
+            cudaError_t e = cudaErrorNotSupported;
+            if (mln::jit_available(&why))
+                e = mln::jit_compile(mln::jit_merged_source(c->s, p->dt, p->precision == MLN_FP32), &c->jit_fn, log);
+            else
+                log = why;
+            if (e != cudaSuccess) {
+                c->jit_fn = nullptr;
+                if (p->kernel == MLN_KERNEL_JIT) {
+                    c->err = "run-time compiled kernel unavailable: " + log;
+                    return fail(MLN_EUNSUPPORTED);
+                }
+            }
+        }
     }
     if (!ok) {
         c->err = "no kernel for this N";

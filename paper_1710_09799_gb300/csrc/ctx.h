@@ -27,6 +27,7 @@ struct mln_ctx {
     int K = 16, tile = 0, threads = 0, max_threads = mln::kMaxThreads;
     int64_t steps = 0, launches = 0;
     bool sparse = false;               // shared-memory sparse cell model (FP64 merged)
+    void *jit_fn = nullptr;            // run-time compiled step kernel (CUfunction), or nullptr
     void *prog = nullptr;              // its program: rowptr | cols | vals
     int nnz = 0, nrowptr = 0;
     // output tables (FP64, device): rows x D matrix followed by rows offsets

@@ -1,0 +1,259 @@
+// Per-problem kernels: the merged-form step of one context written out as
+// straight-line code with the constants as literals and the exactly-zero
+// entries of the set-up matrices left out, compiled at run time for sm_103a
+// (NVRTC) and launched through the driver API. The arithmetic and its order
+// are those of the register cell model, so the results are bit-identical; the
+// kernel just skips multiplications by zero and needs no constant-bank loads.
+//
+// NVRTC and the driver entry points are looked up at run time (dlopen and
+// cudaGetDriverEntryPointByVersion): without them the JIT model is reported
+// unavailable and the other cell models still work.
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <dlfcn.h>
+
+#include <cstdio>
+#include <map>
+#include <mutex>
+#include <sstream>
+#include <string>
+#include <vector>
+
+#include "dispatch.cuh"
+#include "jit.h"
+#include "setup.h"
+
+#include "jit_source.inc"
+
+namespace mln {
+namespace {
+
+// ---- NVRTC, loaded on first use
+typedef int nvrtcResult_t;
+typedef struct _nvrtcProgram *nvrtcProgram_t;
+struct Nvrtc {
+    nvrtcResult_t (*create)(nvrtcProgram_t *, const char *, const char *, int, const char *const *,
+                            const char *const *) = nullptr;
+    nvrtcResult_t (*compile)(nvrtcProgram_t, int, const char *const *) = nullptr;
+    nvrtcResult_t (*log_size)(nvrtcProgram_t, size_t *) = nullptr;
+    nvrtcResult_t (*log)(nvrtcProgram_t, char *) = nullptr;
+    nvrtcResult_t (*cubin_size)(nvrtcProgram_t, size_t *) = nullptr;
+    nvrtcResult_t (*cubin)(nvrtcProgram_t, char *) = nullptr;
+    nvrtcResult_t (*destroy)(nvrtcProgram_t *) = nullptr;
+    bool ok = false;
+};
+
+// ---- driver API, through the runtime's entry-point query
+struct Driver {
+    CUresult (*load)(CUmodule *, const void *) = nullptr;
+    CUresult (*get)(CUfunction *, CUmodule, const char *) = nullptr;
+    CUresult (*launch)(CUfunction, unsigned, unsigned, unsigned, unsigned, unsigned, unsigned, unsigned, CUstream,
+                       void **, void **) = nullptr;
+    CUresult (*set_attr)(CUfunction, CUfunction_attribute, int) = nullptr;
+    bool ok = false;
+};
+
+std::mutex g_mu;
+Nvrtc g_nvrtc;
+Driver g_drv;
+bool g_tried = false;
+std::string g_why;
+std::map<std::pair<int, std::string>, CUfunction> g_cache;  // (device, source) -> kernel
+
+template <typename F>
+bool sym(void *h, const char *name, F &f) {
+    f = reinterpret_cast<F>(dlsym(h, name));
+    return f != nullptr;
+}
+
+template <typename F>
+bool entry(const char *name, F &f) {
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion(name, &p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !p)
+        return false;
+    f = reinterpret_cast<F>(p);
+    return true;
+}
+
+bool load_tools() {
+    if (g_tried) return g_nvrtc.ok && g_drv.ok;
+    g_tried = true;
+    const char *names[] = {"libnvrtc.so.13", "libnvrtc.so", "/usr/local/cuda/lib64/libnvrtc.so.13",
+                           "/usr/local/cuda/lib64/libnvrtc.so"};
+    void *h = nullptr;
+    for (const char *n : names)
+        if ((h = dlopen(n, RTLD_NOW | RTLD_LOCAL))) break;
+    if (!h) {
+        g_why = "libnvrtc not found";
+        return false;
+    }
+    Nvrtc &r = g_nvrtc;
+    r.ok = sym(h, "nvrtcCreateProgram", r.create) && sym(h, "nvrtcCompileProgram", r.compile) &&
+           sym(h, "nvrtcGetProgramLogSize", r.log_size) && sym(h, "nvrtcGetProgramLog", r.log) &&
+           sym(h, "nvrtcGetCUBINSize", r.cubin_size) && sym(h, "nvrtcGetCUBIN", r.cubin) &&
+           sym(h, "nvrtcDestroyProgram", r.destroy);
+    Driver &d = g_drv;
+    d.ok = entry("cuModuleLoadData", d.load) && entry("cuModuleGetFunction", d.get) &&
+           entry("cuLaunchKernel", d.launch) && entry("cuFuncSetAttribute", d.set_attr);
+    if (!r.ok) g_why = "NVRTC symbols missing";
+    else if (!d.ok) g_why = "driver entry points unavailable";
+    return r.ok && d.ok;
+}
+
+std::string lit(double v, bool fp32) {
+    char buf[64];
+    if (fp32) std::snprintf(buf, sizeof(buf), "%af", static_cast<double>(static_cast<float>(v)));
+    else std::snprintf(buf, sizeof(buf), "%a", v);
+    return buf;
+}
+
+bool nz(double v, bool fp32) { return fp32 ? static_cast<float>(v) != 0.0f : v != 0.0; }
+
+// sum_j A[i][j] x_j over the non-zero entries, in column order, as the dense
+// product does: first term a product, then fused multiply-adds onto it.
+std::string row_sum(const std::vector<double> &A, int ld, int i, int ncols, const std::string &x, bool fp32,
+                    const std::string &init = "") {
+    std::string acc = init;
+    for (int j = 0; j < ncols; ++j) {
+        double a = A[i * ld + j];
+        if (!nz(a, fp32)) continue;
+        std::string t = x + "[" + std::to_string(j) + "]";
+        if (acc.empty()) acc = lit(a, fp32) + " * " + t;
+        else acc = "fma(" + lit(a, fp32) + ", " + t + ", " + acc + ")";
+    }
+    return acc;
+}
+
+}  // namespace
+
+std::string jit_merged_source(const Setup &s, double dt, bool fp32) {
+    const int N = s.N, D = s.D, Q = s.q, P = 2 * Q;
+    const char *R = fp32 ? "float" : "double";
+    std::ostringstream o;
+    o << "#define MLN_JIT 1\n"
+      << "#ifdef __CUDACC_RTC__\ntypedef long long int64_t;\ntypedef int int32_t;\n#endif\n"
+      << kKernelsSource << "\nnamespace mln {\n"
+      << "struct JitConsts { int unused; };\n"
+      << "struct JitCell {\n  static constexpr int D = " << D << ";\n  using Consts = JitConsts;\n  " << R
+      << " s[D];\n"
+      << "  __device__ __forceinline__ void setup(unsigned char *, const Consts &) {}\n"
+      << "  __device__ __forceinline__ void load(const " << R
+      << " *src, int64_t stride, int64_t m) { for (int i = 0; i < D; ++i) s[i] = src[i * stride + m]; }\n"
+      << "  __device__ __forceinline__ void store(" << R
+      << " *dst, int64_t stride, int64_t m) const { for (int i = 0; i < D; ++i) dst[i * stride + m] = s[i]; }\n"
+      << "  __device__ __forceinline__ void end_step() {}\n"
+      << "  __device__ __forceinline__ " << R << " step(" << R << " e, const Consts &) {\n"
+      << "    " << R << " z[D], y[D];\n";
+    // z = T^T y on the plane rows (T^T row k = T column k)
+    std::vector<double> Tt((size_t)D * D);
+    for (int i = 0; i < D; ++i)
+        for (int k = 0; k < D; ++k) Tt[k * D + i] = s.T[i * D + k];
+    for (int k = 0; k < P; ++k) {
+        std::string e = row_sum(Tt, D, k, D, "s", fp32);
+        o << "    z[" << k << "] = " << (e.empty() ? std::string(fp32 ? "0.0f" : "0.0") : e) << ";\n";
+    }
+    for (int k = P; k < D; ++k) o << "    z[" << k << "] = " << (fp32 ? "0.0f" : "0.0") << ";\n";
+    o << "    const " << R << " psi[" << (N - 1) << "] = {";
+    for (int a = 0; a < N - 1; ++a) o << (a ? ", " : "") << lit(s.psi[a] * dt, fp32);
+    o << "};\n    rotation_increment<" << N << ">(z, psi, e);\n";
+    // y'' = y + T (R - I) z on the plane columns
+    for (int i = 0; i < D; ++i) {
+        std::string e = row_sum(s.T, D, i, P, "z", fp32);
+        o << "    y[" << i << "] = " << (e.empty() ? "s[" + std::to_string(i) + "]" : "s[" + std::to_string(i) + "] + (" + e + ")")
+          << ";\n";
+    }
+    // dP/dt = wm . y'' + cm
+    {
+        std::string acc = lit(s.cm, fp32);
+        for (int i = 0; i < D; ++i)
+            if (nz(s.wm[i], fp32)) acc = "fma(" + lit(s.wm[i], fp32) + ", y[" + std::to_string(i) + "], " + acc + ")";
+        o << "    const " << R << " dpdt = " << acc << ";\n";
+    }
+    // y = y'' + (C1 y'' + b2)
+    for (int i = 0; i < D; ++i) {
+        std::string e = row_sum(s.C1, D, i, D, "y", fp32, lit(s.b2[i], fp32));
+        o << "    s[" << i << "] = y[" << i << "] + (" << e << ");\n";
+    }
+    o << "    return dpdt;\n  }\n};\n"
+      << "extern \"C\" __global__ void __launch_bounds__(kMaxThreads, 1) mln_jit_step(const __grid_constant__ BlockArgs<"
+      << R << "> a, const __grid_constant__ JitConsts k) {\n"
+      << "  extern __shared__ __align__(16) unsigned char smem_raw[];\n"
+      << "  block_body<" << N << ", " << R << ", JitCell>(a, k, static_cast<int64_t>(blockIdx.x), smem_raw);\n}\n"
+      << "}  // namespace mln\n";
+    return o.str();
+}
+
+bool jit_available(std::string *why) {
+    std::lock_guard<std::mutex> lock(g_mu);
+    bool ok = load_tools();
+    if (!ok && why) *why = g_why;
+    return ok;
+}
+
+cudaError_t jit_compile(const std::string &src, void **fn, std::string &log) {
+    std::lock_guard<std::mutex> lock(g_mu);
+    if (!load_tools()) {
+        log = g_why;
+        return cudaErrorNotSupported;
+    }
+    int dev = 0;
+    cudaGetDevice(&dev);
+    auto key = std::make_pair(dev, src);
+    auto it = g_cache.find(key);
+    if (it != g_cache.end()) {
+        *fn = it->second;
+        return cudaSuccess;
+    }
+    nvrtcProgram_t prog = nullptr;
+    if (g_nvrtc.create(&prog, src.c_str(), "mln_jit.cu", 0, nullptr, nullptr) != 0) {
+        log = "nvrtcCreateProgram failed";
+        return cudaErrorUnknown;
+    }
+    const char *opts[] = {"--gpu-architecture=sm_103a", "-std=c++17", "--fmad=true", "-default-device"};
+    int rc = g_nvrtc.compile(prog, 4, opts);
+    size_t ls = 0;
+    g_nvrtc.log_size(prog, &ls);
+    std::string lg(ls, '\0');
+    if (ls) g_nvrtc.log(prog, &lg[0]);
+    if (rc != 0) {
+        log = "NVRTC: " + lg;
+        g_nvrtc.destroy(&prog);
+        return cudaErrorUnknown;
+    }
+    size_t cs = 0;
+    g_nvrtc.cubin_size(prog, &cs);
+    std::vector<char> cubin(cs);
+    g_nvrtc.cubin(prog, cubin.data());
+    g_nvrtc.destroy(&prog);
+    CUmodule mod = nullptr;
+    CUfunction f = nullptr;
+    if (g_drv.load(&mod, cubin.data()) != CUDA_SUCCESS || g_drv.get(&f, mod, "mln_jit_step") != CUDA_SUCCESS) {
+        log = "loading the compiled kernel failed";
+        return cudaErrorUnknown;
+    }
+    g_cache[key] = f;  // modules stay loaded until the process exits
+    *fn = f;
+    return cudaSuccess;
+}
+
+template <typename R>
+cudaError_t jit_launch_t(void *fn, const BlockArgs<R> &a, dim3 g, dim3 b, size_t smem, cudaStream_t st) {
+    struct {
+        int unused;
+    } k{0};
+    void *params[] = {const_cast<BlockArgs<R> *>(&a), &k};
+    CUresult r = g_drv.launch(static_cast<CUfunction>(fn), g.x, g.y, g.z, b.x, b.y, b.z, static_cast<unsigned>(smem),
+                              static_cast<CUstream>(st), params, nullptr);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorLaunchFailure;
+}
+
+cudaError_t jit_launch(void *fn, const BlockArgs<double> &a, dim3 g, dim3 b, size_t smem, cudaStream_t st) {
+    return jit_launch_t<double>(fn, a, g, b, smem, st);
+}
+cudaError_t jit_launch(void *fn, const BlockArgs<float> &a, dim3 g, dim3 b, size_t smem, cudaStream_t st) {
+    return jit_launch_t<float>(fn, a, g, b, smem, st);
+}
+
+}  // namespace mln

@@ -17,8 +17,10 @@
 //   boundary (ring, or held cell 0 + first-order Mur at the right), source.
 #pragma once
 
+#ifndef __CUDACC_RTC__
 #include <cuda_runtime.h>
 #include <stdint.h>
+#endif
 
 namespace mln {
 

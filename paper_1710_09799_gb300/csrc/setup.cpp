@@ -223,6 +223,143 @@ bool finite_all(const double *p, size_t n) {
 
 }  // namespace
 
+mln_status adjoint_chain(const mln_params &p, const Setup &s, const double *acc, double *dJ_dmu, double *dJ_dG,
+                         std::string &err) {
+    const int n = s.N, nn = n * n, D = s.D, q = s.q, Da = D + 1;
+    // accumulator layout: Dl (D x D) | b (D) | w (D) | c | T (D x D) | theta (q) | J
+    const double *Abar = acc, *bbar = acc + D * D, *wbar = bbar + D, cbar = wbar[D];
+    const double *Tbar = wbar + D + 1, *thbar = Tbar + D * D;
+    std::vector<CMat> g = make_generators(n);
+
+    // M_bar and d_eq_bar from the augmented propagator [[A0, b], [0, 1]] = exp(X),
+    // X = [[M, d_eq], [0, 0]] dt/2. The adjoint of the Frechet derivative of exp
+    // at X is the Frechet derivative at X^T, read off the block-triangular
+    // exponential exp([[X^T, G], [0, X^T]]) (Van Loan 1978).
+    const int D2 = 2 * Da;
+    RMat big((size_t)D2 * D2, 0.0);
+    const double h = 0.5 * p.dt;
+    for (int i = 0; i < D; ++i) {
+        for (int j = 0; j < D; ++j) {
+            big[j * D2 + i] = s.M[i * D + j] * h;               // X^T, top-left
+            big[(Da + j) * D2 + Da + i] = s.M[i * D + j] * h;   // X^T, bottom-right
+            big[i * D2 + Da + j] = Abar[i * D + j];             // G = [[A0_bar, b_bar], [0, 0]]
+        }
+        big[D * D2 + i] = s.d_eq[i] * h;                        // (X^T)_{D, i} = X_{i, D}
+        big[(Da + D) * D2 + Da + i] = s.d_eq[i] * h;
+        big[i * D2 + Da + D] = bbar[i];
+    }
+    RMat eb = expm_taylor(big, D2);
+    std::vector<double> Mbar((size_t)D * D), deqbar(D);
+    for (int i = 0; i < D; ++i) {
+        for (int j = 0; j < D; ++j) Mbar[i * D + j] = h * eb[i * D2 + Da + j];
+        deqbar[i] = h * eb[i * D2 + Da + D];
+    }
+    // polarisation coefficients: w_j = N_a/2 sum_k v_k M_kj, c = N_a/2 sum_k v_k d_eq_k
+    std::vector<double> vbar(D, 0.0);
+    for (int k = 0; k < D; ++k) {
+        for (int j = 0; j < D; ++j) {
+            Mbar[k * D + j] += 0.5 * p.N_a * s.v[k] * wbar[j];
+            vbar[k] += 0.5 * p.N_a * s.M[k * D + j] * wbar[j];
+        }
+        deqbar[k] += 0.5 * p.N_a * s.v[k] * cbar;
+        vbar[k] += 0.5 * p.N_a * s.d_eq[k] * cbar;
+    }
+    // G: g_jk = Re(1/2 Tr{G(s_k) s_j}), d_eq_j = Re(1/N Tr{G(I) s_j}), and
+    // Tr{G(X) Y} = sum_{(a,b), c} G[(a,b), c] vec(X)_c Y_{ba}
+    if (dJ_dG) {
+        for (int a = 0; a < n; ++a)
+            for (int bb = 0; bb < n; ++bb) {
+                const int r = a * n + bb;
+                for (int cc = 0; cc < nn; ++cc) {
+                    cd tot(0, 0);
+                    for (int j = 0; j < D; ++j) {
+                        const cd sj = g[j][bb * n + a];
+                        if (sj == cd(0, 0)) continue;
+                        cd inner(0, 0);
+                        for (int k = 0; k < D; ++k) inner += Mbar[j * D + k] * 0.5 * g[k][cc];
+                        const int ci = cc / n, cj = cc % n;
+                        if (ci == cj) inner += deqbar[j] / n;
+                        tot += inner * sj;
+                    }
+                    const cd gam = std::conj(tot);
+                    dJ_dG[2 * (r * nn + cc)] = gam.real();
+                    dJ_dG[2 * (r * nn + cc) + 1] = gam.imag();
+                }
+            }
+    }
+    if (!dJ_dmu) return MLN_OK;
+    // mu: v_k = Tr{mu s_k}; T and theta from mu = W diag(m) W^+ by first-order
+    // perturbation: dm_a = Delta_aa, dW = W C, C_ca = Delta_ca / (m_a - m_c)
+    // (c != a), C_aa = 0, Delta = W^+ dmu W. (A phase change of an eigenvector
+    // turns T within its planes, which commutes with the plane rotations, so the
+    // choice C_aa = 0 does not change the result.)
+    double mscale = 1e-300;
+    for (double m : s.mev) mscale = std::max(mscale, std::fabs(m));
+    for (int a = 0; a < n; ++a)
+        for (int c = a + 1; c < n; ++c)
+            if (std::fabs(s.mev[a] - s.mev[c]) < 1e-9 * mscale) {
+                err = "dipole operator has (nearly) degenerate eigenvalues: its gradient is not defined this way";
+                return MLN_ENUMERIC;
+            }
+    const CMat &W = s.Wmu;
+    const CMat Wh = cadj(W, n);
+    std::vector<CMat> dirs;
+    for (int l = 0; l < n; ++l) {
+        CMat e(nn, cd(0, 0));
+        e[l * n + l] = 1.0;
+        dirs.push_back(e);
+    }
+    for (int j = 0; j < n; ++j)
+        for (int k = j + 1; k < n; ++k) {
+            CMat e(nn, cd(0, 0));
+            e[j * n + k] = 1.0;
+            e[k * n + j] = 1.0;
+            dirs.push_back(e);
+        }
+    for (int j = 0; j < n; ++j)
+        for (int k = j + 1; k < n; ++k) {
+            CMat e(nn, cd(0, 0));
+            e[j * n + k] = cd(0, 1);
+            e[k * n + j] = cd(0, -1);
+            dirs.push_back(e);
+        }
+    auto coords = [&](const CMat &X, int j) { return 0.5 * trace_of_product(X, g[j], n).real(); };
+    for (size_t di = 0; di < dirs.size(); ++di) {
+        const CMat &dmu = dirs[di];
+        CMat Delta = cmul(Wh, cmul(dmu, W, n), n);
+        CMat C(nn, cd(0, 0));
+        std::vector<double> dm(n);
+        for (int a = 0; a < n; ++a) {
+            dm[a] = Delta[a * n + a].real();
+            for (int c = 0; c < n; ++c)
+                if (c != a) C[c * n + a] = Delta[c * n + a] / (s.mev[a] - s.mev[c]);
+        }
+        CMat Ch = cadj(C, n);
+        double dJ = 0;
+        // T columns of the planes (only their gradient is non-zero)
+        int k = 0;
+        for (int a = 0; a < n; ++a)
+            for (int b = a + 1; b < n; ++b, ++k) {
+                CMat X(nn, cd(0, 0)), Y(nn, cd(0, 0));
+                X[a * n + b] = 1.0;
+                X[b * n + a] = 1.0;
+                Y[a * n + b] = cd(0, -1);
+                Y[b * n + a] = cd(0, 1);
+                for (int col = 0; col < 2; ++col) {
+                    const CMat &E0 = col == 0 ? X : Y;
+                    CMat inner = cmul(C, E0, n), tmp = cmul(E0, Ch, n);
+                    for (int t = 0; t < nn; ++t) inner[t] += tmp[t];
+                    CMat dX = cmul(W, cmul(inner, Wh, n), n);
+                    for (int j = 0; j < D; ++j) dJ += Tbar[j * D + 2 * k + col] * coords(dX, j);
+                }
+                dJ += thbar[k] * (dm[a] - dm[b]) / kHbar;
+            }
+        for (int j = 0; j < D; ++j) dJ += vbar[j] * trace_of_product(dmu, g[j], n).real();
+        dJ_dmu[di] = dJ;
+    }
+    return MLN_OK;
+}
+
 int64_t state_stride(const mln_params &p) {
     int64_t nm = p.medium_end - p.medium_begin;
     return (nm + 63) / 64 * 64;
@@ -293,8 +430,12 @@ mln_status validate(const mln_params &p, std::string &err) {
         err = "block_steps must be in [0, 64]";
         return MLN_EINVAL;
     }
-    if (p.kernel < MLN_KERNEL_AUTO || p.kernel > MLN_KERNEL_SPARSE) {
-        err = "kernel must be MLN_KERNEL_AUTO, MLN_KERNEL_REGISTER or MLN_KERNEL_SPARSE";
+    if (p.kernel < MLN_KERNEL_AUTO || p.kernel > MLN_KERNEL_JIT) {
+        err = "kernel must be MLN_KERNEL_AUTO, MLN_KERNEL_REGISTER, MLN_KERNEL_SPARSE or MLN_KERNEL_JIT";
+        return MLN_EINVAL;
+    }
+    if (p.kernel == MLN_KERNEL_JIT && p.form != MLN_FORM_MERGED) {
+        err = "MLN_KERNEL_JIT needs MLN_FORM_MERGED";
         return MLN_EINVAL;
     }
     if (p.kernel == MLN_KERNEL_SPARSE && (p.precision != MLN_FP64 || p.form != MLN_FORM_MERGED)) {
@@ -459,6 +600,8 @@ mln_status build_setup(const mln_params &p, Setup &s, std::string &err) {
     std::vector<double> mev;
     CMat Wm;
     hermitian_eig(mu, n, mev, Wm);
+    s.Wmu = Wm;
+    s.mev = mev;
     CMat Wh = cadj(Wm, n);
     s.T.assign((size_t)D * D, 0.0);
     s.theta.assign(q, 0.0);

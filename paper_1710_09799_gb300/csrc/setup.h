@@ -24,6 +24,8 @@ struct Setup {
     std::vector<double> A0inv, binv;      // exp(-M dt/2) of the same affine flow
     std::vector<double> T, theta;         // real eigenbasis of U (Eq. 26), plane rotation rates
     std::vector<double> psi;              // (m_a - m_{N-1})/hbar, a < N-1: base rates of the planes
+    std::vector<cd> Wmu;                  // eigenvectors of mu (columns), N x N
+    std::vector<double> mev;              // eigenvalues of mu, ascending
     std::vector<double> w;                // N_a/2 M^T v  (Eq. 17)
     double c = 0;                         // N_a/2 v^T d_eq
     std::vector<double> d0;               // adjoint vector of rho0 (Eq. 6)
@@ -42,6 +44,14 @@ mln_status validate(const mln_params &p, std::string &err);
 
 // Compute every FP64 constant of the set-up. p must have passed validate().
 mln_status build_setup(const mln_params &p, Setup &s, std::string &err);
+
+// Chain rule of the adjoint: from the accumulated gradients of the step's
+// constants (acc: A0 - I, b, w, c, T, theta; layout of AccLayout) to the
+// gradients of J with respect to the N*N real parameters of mu (diagonal,
+// then real and imaginary parts of the upper triangle, row-major) and to the
+// relaxation superoperator G (Gamma with dJ = Re sum conj(Gamma_rc) dG_rc).
+mln_status adjoint_chain(const mln_params &p, const Setup &s, const double *acc, double *dJ_dmu, double *dJ_dG,
+                         std::string &err);
 
 // Stride (in elements) of one adjoint component in the device state.
 int64_t state_stride(const mln_params &p);

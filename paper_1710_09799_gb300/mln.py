@@ -24,7 +24,7 @@ MLN_BC_PERIODIC, MLN_BC_OPEN = 0, 1
 MLN_SRC_NONE, MLN_SRC_HARD, MLN_SRC_SOFT = 0, 1, 2
 MLN_FP64, MLN_FP32 = 0, 1
 MLN_FORM_STRANG, MLN_FORM_MERGED, MLN_FORM_RODRIGUES = 0, 1, 2
-MLN_KERNEL_AUTO, MLN_KERNEL_REGISTER, MLN_KERNEL_SPARSE = 0, 1, 2
+MLN_KERNEL_AUTO, MLN_KERNEL_REGISTER, MLN_KERNEL_SPARSE, MLN_KERNEL_JIT = 0, 1, 2, 3
 MLN_MIN_N, MLN_MAX_N = 2, 6
 _DMAX = MLN_MAX_N * MLN_MAX_N - 1
 
@@ -32,7 +32,8 @@ BOUNDARY = {"periodic": MLN_BC_PERIODIC, "open": MLN_BC_OPEN}
 SOURCE = {"none": MLN_SRC_NONE, "hard": MLN_SRC_HARD, "soft": MLN_SRC_SOFT}
 PRECISION = {"fp64": MLN_FP64, "fp32": MLN_FP32}
 FORM = {"strang": MLN_FORM_STRANG, "merged": MLN_FORM_MERGED, "rodrigues": MLN_FORM_RODRIGUES}
-KERNEL = {"auto": MLN_KERNEL_AUTO, "register": MLN_KERNEL_REGISTER, "sparse": MLN_KERNEL_SPARSE}
+KERNEL = {"auto": MLN_KERNEL_AUTO, "register": MLN_KERNEL_REGISTER, "sparse": MLN_KERNEL_SPARSE,
+          "jit": MLN_KERNEL_JIT}
 
 _dp = C.POINTER(C.c_double)
 
@@ -65,6 +66,10 @@ class mln_setup(C.Structure):
     ]
 
 
+class mln_adjoint_out(C.Structure):
+    _fields_ = [("J", C.c_double), ("dJ_dsrc", _dp), ("dJ_dmu", _dp), ("dJ_dG", _dp)]
+
+
 # Every exported symbol of include/mln.h with (restype, argtypes).
 _P = C.POINTER(mln_params)
 _SIGS = {
@@ -89,6 +94,9 @@ _SIGS = {
     "mln_create_error": (C.c_char_p, []),
     "mln_setup_host": (C.c_int, [_P, C.POINTER(mln_setup)]),
     "mln_version": (C.c_char_p, []),
+    "mln_kernel_source": (C.c_int, [_P, C.c_char_p, C.c_size_t, C.POINTER(C.c_size_t)]),
+    "mln_adjoint": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_int64, C.c_int32,
+                              C.POINTER(mln_adjoint_out)]),
     "mln_batch_create": (C.c_int, [C.c_int32, _P, C.POINTER(C.c_void_p), C.POINTER(C.c_void_p),
                                    C.POINTER(C.c_void_p), C.POINTER(C.c_void_p), C.c_int64, C.c_void_p,
                                    C.POINTER(C.c_void_p)]),
@@ -294,6 +302,14 @@ def mln_step_noalloc(params: Params, d_state_ptr: int, ez_ptr: int, hy_ptr: int,
                                   None if src_ptr is None else C.c_void_p(src_ptr), C.c_void_p(stream_ptr)))
 
 
+def mln_kernel_source(params: Params) -> str:
+    n = C.c_size_t()
+    _check(lib().mln_kernel_source(C.byref(params.s), None, 0, C.byref(n)))
+    buf = C.create_string_buffer(n.value + 1)
+    _check(lib().mln_kernel_source(C.byref(params.s), buf, n.value + 1, C.byref(n)))
+    return buf.value.decode()
+
+
 def mln_version() -> str:
     return lib().mln_version().decode()
 
@@ -385,6 +401,95 @@ class Solver:
             self.close()
         except Exception:
             pass
+
+
+# ------------------------------------------------------------------ adjoint
+
+def mln_adjoint(ctx, N: int, n_steps: int, src_ptr: int | None, probe_cell: int, every: int):
+    """J and its gradients: (J, dJ/dsrc (n_steps), dJ/dmu params (N*N), dJ/dG (N^2 x N^2 complex))."""
+    NN = N * N
+    dsrc, dmu, dG = np.zeros(n_steps), np.zeros(NN), np.zeros(2 * NN * NN)
+    out = mln_adjoint_out(0.0, _ptr(dsrc), _ptr(dmu), _ptr(dG))
+    _check(lib().mln_adjoint(ctx, n_steps, None if src_ptr is None else C.c_void_p(src_ptr), probe_cell, every,
+                             C.byref(out)), ctx)
+    return out.J, dsrc, dmu, dG.view(np.complex128).reshape(NN, NN)
+
+
+def mu_from_params(N: int, x):
+    """The Hermitian dipole operator from its N*N real parameters in the order of
+    mln_adjoint (diagonal, Re of the upper triangle, Im of the upper triangle)."""
+    import torch
+    x = torch.as_tensor(x)
+    mu = torch.zeros((N, N), dtype=torch.complex128, device=x.device)
+    idx = N
+    q = N * (N - 1) // 2
+    for l in range(N):
+        mu[l, l] = x[l]
+    for j in range(N):
+        for k in range(j + 1, N):
+            z = torch.complex(x[idx], x[idx + q])
+            mu[j, k] = z
+            mu[k, j] = z.conj()
+            idx += 1
+    return mu
+
+
+def mu_to_params(mu) -> np.ndarray:
+    mu = np.asarray(mu)
+    N = mu.shape[0]
+    up = [(j, k) for j in range(N) for k in range(j + 1, N)]
+    return np.array([mu[l, l].real for l in range(N)] + [mu[j, k].real for j, k in up] +
+                    [mu[j, k].imag for j, k in up])
+
+
+def _make_probe_energy():
+    import torch
+
+    class ProbeEnergy(torch.autograd.Function):
+        """J = dt sum_n (E_z^n at probe)^2 as a differentiable function of the
+        source samples, the dipole-operator parameters (mu_to_params order) and
+        the relaxation superoperator (a real view (N^2, N^2, 2) of the complex
+        matrix). Forward and gradients run in libmln.so (mln_adjoint); autograd
+        chains them to whatever produced these tensors."""
+
+        @staticmethod
+        def forward(fctx, src, mu_params, G_real, base: dict):
+            import torch as _t
+            N = base["N"]
+            mu = mu_from_params(N, mu_params.detach().cpu()).numpy()
+            G = _t.view_as_complex(G_real.detach().cpu().contiguous()).numpy()
+            par = Params(N=N, H0=base["H0"], mu=mu, G=G, rho0=base["rho0"], N_a=base["N_a"],
+                         n_cells=base["n_cells"], medium_begin=base["medium_begin"], medium_end=base["medium_end"],
+                         dx=base["dx"], dt=base["dt"], boundary="periodic", source_kind=base["source_kind"],
+                         source_cell=base["source_cell"], precision=base.get("precision", "fp64"), form="strang")
+            s = Solver(par, E0=base["E0"])
+            srcd = src.detach().to(device="cuda", dtype=_t.float64).contiguous()
+            J, dsrc, dmu, dG = mln_adjoint(s.ctx, N, srcd.numel(), srcd.data_ptr(), base["probe_cell"],
+                                           base.get("every", 256))
+            s.close()
+            fctx.save_for_backward(_t.as_tensor(dsrc), _t.as_tensor(dmu), _t.view_as_real(_t.as_tensor(dG)))
+            fctx.devices = (src.device, mu_params.device, G_real.device)
+            return _t.tensor(J, dtype=_t.float64)
+
+        @staticmethod
+        def backward(fctx, gJ):
+            dsrc, dmu, dG = fctx.saved_tensors
+            dv = fctx.devices
+            g = gJ.cpu()
+            return (g * dsrc).to(dv[0]), (g * dmu).to(dv[1]), (g * dG).to(dv[2]), None
+
+    return ProbeEnergy
+
+
+_probe_energy = None
+
+
+def probe_energy(src, mu_params, G_real, base: dict):
+    """torch.autograd entry: see _make_probe_energy."""
+    global _probe_energy
+    if _probe_energy is None:
+        _probe_energy = _make_probe_energy()
+    return _probe_energy.apply(src, mu_params, G_real, base)
 
 
 # ------------------------------------------------------------------ batches

@@ -289,18 +289,19 @@ def test_rotation_terms_against_exact(precision):
 
 
 @pytest.mark.parametrize("N", [2, 3, 6])
-def test_sparse_and_register_models_agree_bitwise(N):
-    """The shared-memory sparse cell model skips the exact zeros of the
-    constant matrices but sums the other terms in the dense order: FP64 merged
-    results are bit-identical to the register model's."""
+@pytest.mark.parametrize("precision,kernel", [("fp64", "sparse"), ("fp64", "jit"), ("fp32", "jit")])
+def test_cell_models_agree_bitwise(N, precision, kernel):
+    """The shared-memory sparse and the run-time compiled cell models skip the
+    exact zeros of the constant matrices but sum the other terms in the dense
+    order: merged-form results are bit-identical to the register model's."""
     if N == 2:
         p = W.two_level_sit(n_cells=700, medium=(100, 600), n_steps=400)
     elif N == 3:
         p = W.three_level_ring(n_cells=3000, n_steps=300)
     else:
         p = W.six_level_pulse(n_cells=600, n_steps=200, t0=15e-15, fwhm=10e-15)
-    E0, H0, r0, _ = gpu_run(p, p.n_steps, "fp64", "merged", kernel="register")
-    E1, H1, r1, _ = gpu_run(p, p.n_steps, "fp64", "merged", kernel="sparse")
+    E0, H0, r0, _ = gpu_run(p, p.n_steps, precision, "merged", kernel="register")
+    E1, H1, r1, _ = gpu_run(p, p.n_steps, precision, "merged", kernel=kernel)
     assert np.array_equal(E0, E1) and np.array_equal(H0, H1) and np.array_equal(r0, r1)
 
 

@@ -346,6 +346,34 @@ def batched_devices(count: int = 256, n_steps: int = 20000, seed: int = 0, min_c
     return out
 
 
+def adjoint_ring(n_cells: int = 8192, n_steps: int = 5000, seed: int = 0, n_src: int = 512,
+                 amplitude: float = 1e5) -> Problem:
+    """The gradient workload: the three-level ring's medium (same seeded levels,
+    dipoles and rates) on n_cells cells, a soft source at cell 0 carrying n_src
+    free samples (a Gaussian-envelope carrier at the mean transition frequency,
+    amplitude `amplitude`) followed by zeros, the probe at cell n_cells / 8 (the
+    pulse moves half a cell per step, so a probe at n_cells / 2 of an 8192-cell
+    ring would not see it within 5000 steps).
+    meta holds what the gradients are taken against: the rate table and one
+    unit-rate superoperator per rate, the dipole pairs."""
+    p = three_level_ring(n_cells=n_cells, n_steps=n_steps, seed=seed)
+    lev = np.real(np.diag(p.H0))
+    diffs = [abs(lev[a] - lev[b]) for a in range(3) for b in range(a + 1, 3)]
+    omega = float(np.mean(diffs)) / HBAR
+    k = np.arange(n_steps, dtype=np.float64)
+    src = np.zeros(n_steps)
+    env = np.exp(-((k[:n_src] - n_src / 2) / (n_src / 5)) ** 2)
+    src[:n_src] = amplitude * env * np.sin(omega * (k[:n_src] + 1) * p.dt)
+    rates = p.meta["rates"]
+    keys = sorted(rates)
+    unit = [lindblad_superop(3, {key: 1.0}) for key in keys]
+    q = p.with_(source_kind=SRC_SOFT, source_cell=0, src=src, name="adjoint_ring")
+    q.meta = dict(seed=seed, rate_keys=keys, rate_values=np.array([rates[k_] for k_ in keys]),
+                  unit_superops=unit, probe_cell=n_cells // 8, n_src=n_src,
+                  dipole_pairs=[(0, 1), (0, 2), (1, 2)])
+    return q
+
+
 def config(name: str, **kw) -> Problem:
     """The named workload at its full size (keyword overrides allowed)."""
     table = {
