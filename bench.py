@@ -55,6 +55,31 @@ FP64_FLOP_PER_CLK_SM = 4
 FP32_FLOP_PER_CLK_SM = 256
 
 
+# DRAM bytes (read + write) per launch of the step kernel from one ncu capture
+# (profiles/*.md), keyed by (cell model, precision, workload, steps per launch).
+# An entry is used only while the kernel sources hash to the value recorded
+# with it; after any change to them the traffic is reported as null.
+MEASURED_TRAFFIC = {
+    ("sparse", "fp64", "three_level_ring", 20): (5273344.0, "see profiles/mln_block_kernel_fp64_sparse_three_level_ring.md"),
+}
+TRAFFIC_SOURCES_SHA = None  # set with the captures: sha256 of the kernel sources at capture time
+
+
+def kernel_sources_sha() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for f in ("kernels.cuh", "jit.cu", "dispatch.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_1710_09799_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()
+
+
+def measured_traffic(kernel: str, precision: str, workload: str, block_steps: int):
+    if TRAFFIC_SOURCES_SHA is None or kernel_sources_sha() != TRAFFIC_SOURCES_SHA:
+        return None
+    hit = MEASURED_TRAFFIC.get((kernel, precision, workload, block_steps))
+    return None if hit is None else hit[0]
+
+
 def alu_peak_tflops(precision: str, mhz: float = SM_MAX_MHZ) -> float:
     per = FP64_FLOP_PER_CLK_SM if precision == "fp64" else FP32_FLOP_PER_CLK_SM
     return SMS * per * mhz * 1e6 / 1e12
@@ -202,8 +227,10 @@ def time_device(p, precision, form, seg, steps, warmup, block_steps, tile_cells,
     ms_max = max_over_ranks(ws, ms)
     shape = s.launch_shape
     work = s.work_per_step
+    kern = s.kernel_in_use
     s.close()
-    return dict(ms=ms_max, ms_local=ms, wall_s=t_wall, launches=launches, shape=shape, clocks=clocks, work=work)
+    return dict(ms=ms_max, ms_local=ms, wall_s=t_wall, launches=launches, shape=shape, clocks=clocks, work=work,
+                kernel=kern)
 
 
 def time_batch(precision, seg, steps, warmup, sampler=None):
@@ -417,7 +444,7 @@ def main():
     ap.add_argument("--seg", type=int, default=1000, help="time steps per benchmark step")
     ap.add_argument("--block-steps", type=int, default=0, help="0: autotuned")
     ap.add_argument("--tile", type=int, default=0)
-    ap.add_argument("--kernel", default="auto", choices=["auto", "register", "sparse"])
+    ap.add_argument("--kernel", default="auto", choices=["auto", "register", "sparse", "jit"])
     ap.add_argument("--workload", default="three_level_ring", choices=sorted(WORKLOADS))
     ap.add_argument("--quick", action="store_true", help="skip variants, e2e and the CPU baseline")
     args = ap.parse_args()
@@ -453,9 +480,11 @@ def main():
     flops_per_step = p.n_medium * f_med + p.n_cells * f_cell
     achieved = flops_per_step * (args.seg * args.steps / max(launches, 1)) / per_launch_s / 1e12
     peak = alu_peak_tflops(args.precision)
+    kname = "mln_jit_step" if main_run["kernel"] == "jit" else f"mln_block_kernel ({main_run['kernel']} cell model)"
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "kernel": "mln_block_kernel",
-                "frac": achieved / peak, "traffic": None,
+                "kernel": kname,
+                "frac": achieved / peak,
+                "traffic": measured_traffic(main_run["kernel"], args.precision, args.workload, main_run["shape"][0]),
                 "peak_source": f"derived: {SMS} SMs x {FP64_FLOP_PER_CLK_SM if args.precision == 'fp64' else FP32_FLOP_PER_CLK_SM} "
                                f"flop/clk x {SM_MAX_MHZ:.0f} MHz",
                 "flops_per_medium_cell_update": f_med, "flops_per_grid_cell": f_cell,
@@ -471,7 +500,7 @@ def main():
         "data": "synthetic (seeded: levels, dipoles, rates, noise E^0)",
         "config": {"workload": WORKLOADS[args.workload], "n_cells": p.n_cells, "levels": p.N,
                    "time_steps_per_step": args.seg, "time_steps_total": args.seg * args.steps,
-                   "form": args.form, "precision": args.precision, "kernel": args.kernel,
+                   "form": args.form, "precision": args.precision, "kernel": main_run["kernel"],
                    "block_steps": main_run["shape"][0], "tile_cells": main_run["shape"][1],
                    "threads_per_block": main_run["shape"][2],
                    "l2": "flushed between steps (256 MiB write); state 5.2 MB stays on chip within a step",

@@ -189,6 +189,9 @@ int64_t mln_step_count(const mln_ctx *ctx);
 /* Number of fused-step kernel launches queued so far, and the launch shape
  * in use: steps fused per launch and cells written per thread block. */
 int64_t mln_launch_count(const mln_ctx *ctx);
+/* The cell model the context's step kernel uses (MLN_KERNEL_REGISTER,
+ * MLN_KERNEL_SPARSE or MLN_KERNEL_JIT), -1 for NULL. */
+int32_t mln_kernel_in_use(const mln_ctx *ctx);
 mln_status mln_launch_shape(const mln_ctx *ctx, int32_t *block_steps, int32_t *tile_cells,
                             int32_t *threads_per_block);
 

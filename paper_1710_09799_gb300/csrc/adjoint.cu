@@ -68,7 +68,7 @@ mln_status adjoint_t(mln_ctx *c, int64_t n_steps, const double *src, int64_t pro
     const size_t set_bytes = (sb + 2 * fb + 255) / 256 * 256;
     const int64_t nseg = (n_steps + every - 1) / every;
     unsigned char *ckpt = nullptr, *slots = nullptr, *adj = nullptr;
-    double *dsrc = nullptr, *acc = nullptr;
+    double *dsrc = nullptr, *acc = nullptr, *accsum = nullptr;
     std::vector<double> hacc(L::size, 0.0);
     const mln::AdjConsts<N, R> k = adj_consts<N, R>(c->s, c->p.dt);
     auto set_at = [&](unsigned char *base, int64_t i) {
@@ -93,7 +93,8 @@ mln_status adjoint_t(mln_ctx *c, int64_t n_steps, const double *src, int64_t pro
     MLN_ACK(c, cudaMalloc(&ckpt, nseg * set_bytes));
     MLN_ACK(c, cudaMalloc(&slots, (every + 1) * set_bytes));
     MLN_ACK(c, cudaMalloc(&adj, 2 * set_bytes));
-    MLN_ACK(c, cudaMalloc(&acc, L::size * sizeof(double)));
+    MLN_ACK(c, cudaMalloc(&acc, L::size * n * sizeof(double)));
+    MLN_ACK(c, cudaMalloc(&accsum, L::size * sizeof(double)));
     if (src) MLN_ACK(c, cudaMalloc(&dsrc, n_steps * sizeof(double)));
 
     // forward with checkpoints
@@ -108,7 +109,7 @@ mln_status adjoint_t(mln_ctx *c, int64_t n_steps, const double *src, int64_t pro
     }
     // backward
     MLN_ACK(c, cudaMemsetAsync(adj, 0, 2 * set_bytes, c->stream));
-    MLN_ACK(c, cudaMemsetAsync(acc, 0, L::size * sizeof(double), c->stream));
+    MLN_ACK(c, cudaMemsetAsync(acc, 0, L::size * n * sizeof(double), c->stream));
     A0s = set_at(adj, 0);
     A1s = set_at(adj, 1);
     aa.acc = acc;
@@ -157,7 +158,9 @@ mln_status adjoint_t(mln_ctx *c, int64_t n_steps, const double *src, int64_t pro
             std::swap(A0s, A1s);
         }
     }
-    MLN_ACK(c, cudaMemcpyAsync(hacc.data(), acc, L::size * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    mln::mln_adjoint_reduce<<<L::size, 256, 0, c->stream>>>(acc, n, accsum);
+    MLN_ACK(c, cudaGetLastError());
+    MLN_ACK(c, cudaMemcpyAsync(hacc.data(), accsum, L::size * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
     if (out->dJ_dsrc) {
         if (src && c->p.source_kind != MLN_SRC_NONE)
             MLN_ACK(c, cudaMemcpyAsync(out->dJ_dsrc, dsrc, n_steps * sizeof(double), cudaMemcpyDeviceToHost,
@@ -178,6 +181,7 @@ done:
     cudaFree(slots);
     cudaFree(adj);
     cudaFree(acc);
+    cudaFree(accsum);
     cudaFree(dsrc);
     return st;
 }

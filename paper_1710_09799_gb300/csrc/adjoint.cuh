@@ -32,7 +32,7 @@ struct AdjArgs {
     const R *Ea, *Ha, *Sa;        // adjoints after the step (of E^{n+1}, H^{n+1/2}, d^{n+1/2})
     R *Eb, *Hb, *Sb;              // adjoints before the step (of E^n, H^{n-1/2}, d^{n-1/2})
     double *dsrc;                 // adjoint of this step's source sample (one double), or nullptr
-    double *acc;                  // accumulators, see adjoint_acc_size
+    double *acc;                  // per-cell accumulators: entry k of cell i at k * n_cells + i (AccLayout)
     int64_t n_cells, mb, me, stride, source_cell, probe_cell;
     int32_t source_kind, pad_;
     double dt, E_step;            // dt; unused
@@ -48,16 +48,26 @@ struct AccLayout {
                          size = J + 1;
 };
 
-__device__ __forceinline__ double warp_sum(double v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
+// Each cell owns one column of the accumulators and adds to it at every
+// step (no atomics, no shuffles); mln_adjoint_reduce sums over the cells.
+__device__ __forceinline__ void acc_add(double *acc, int64_t n, int64_t i, int idx, double v) {
+    acc[idx * n + i] += v;
 }
 
-// every lane of the warp calls it (zero where it has nothing to add)
-__device__ __forceinline__ void acc_add(double *acc, int idx, double v) {
-    v = warp_sum(v);
-    if ((threadIdx.x & 31) == 0 && v != 0.0) atomicAdd(acc + idx, v);
+// acc_out[k] = sum_i acc[k * n + i], one block per k, fixed summation order.
+__global__ void __launch_bounds__(256) mln_adjoint_reduce(const double *__restrict__ acc, int64_t n,
+                                                          double *__restrict__ out) {
+    __shared__ double part[256];
+    const int k = blockIdx.x;
+    double s = 0.0;
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) s += acc[k * n + i];
+    part[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if (threadIdx.x < w) part[threadIdx.x] += part[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[k] = part[0];
 }
 
 template <int N, typename R>
@@ -93,7 +103,7 @@ __global__ void __launch_bounds__(256) mln_adjoint_step(const __grid_constant__ 
     }
     if (live && ii == a.probe_cell) {
         const double e1 = static_cast<double>(a.E1[ii]);
-        atomicAdd(a.acc + L::J, a.dt * e1 * e1);
+        a.acc[L::J * n + ii] += a.dt * e1 * e1;
     }
     // adjoint of H'_i and H'_{i-1} (used by E'_i, E'_{i+1} and E'_{i-1}, E'_i)
     R hh_i = R(0), hh_m = R(0);
@@ -183,23 +193,25 @@ __global__ void __launch_bounds__(256) mln_adjoint_step(const __grid_constant__ 
     }
     if (live) a.Eb[ii] = eb;
 
-    // parameter accumulators (every lane takes part in the warp sums)
+    // parameter accumulators of this cell
+    if (!medium) return;
 #pragma unroll
     for (int r = 0; r < D; ++r) {
 #pragma unroll
         for (int c = 0; c < D; ++c)
-            acc_add(a.acc, L::Dl + r * D + c,
+            acc_add(a.acc, n, ii, L::Dl + r * D + c,
                     static_cast<double>(dnb[r]) * y2[c] + static_cast<double>(yb[r]) * d[c]);
-        acc_add(a.acc, L::b + r, static_cast<double>(dnb[r]) + yb[r]);
-        acc_add(a.acc, L::w + r, static_cast<double>(pbar) * dn[r]);
+        acc_add(a.acc, n, ii, L::b + r, static_cast<double>(dnb[r]) + yb[r]);
+        acc_add(a.acc, n, ii, L::w + r, static_cast<double>(pbar) * dn[r]);
         // T_bar = y2b (dz)^T + y (dzb)^T on the plane columns
 #pragma unroll
         for (int c = 0; c < 2 * Q; ++c)
-            acc_add(a.acc, L::T + r * D + c, static_cast<double>(y2b[r]) * dz[c] + static_cast<double>(y[r]) * dzb[c]);
+            acc_add(a.acc, n, ii, L::T + r * D + c,
+                    static_cast<double>(y2b[r]) * dz[c] + static_cast<double>(y[r]) * dzb[c]);
     }
-    acc_add(a.acc, L::c, static_cast<double>(pbar));
+    acc_add(a.acc, n, ii, L::c, static_cast<double>(pbar));
 #pragma unroll
-    for (int p = 0; p < Q; ++p) acc_add(a.acc, L::th + p, medium ? thb[p] : 0.0);
+    for (int p = 0; p < Q; ++p) acc_add(a.acc, n, ii, L::th + p, thb[p]);
 }
 
 }  // namespace mln

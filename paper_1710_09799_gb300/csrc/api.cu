@@ -635,6 +635,11 @@ int64_t mln_step_count(const mln_ctx *c) { return c ? c->steps : -1; }
 
 int64_t mln_launch_count(const mln_ctx *c) { return c ? c->launches : -1; }
 
+int32_t mln_kernel_in_use(const mln_ctx *c) {
+    if (!c) return -1;
+    return c->jit_fn ? MLN_KERNEL_JIT : c->sparse ? MLN_KERNEL_SPARSE : MLN_KERNEL_REGISTER;
+}
+
 mln_status mln_autotune(mln_ctx *c, int32_t trials, int32_t *block_steps, int32_t *tile_cells) {
     if (!c || trials < 1) return MLN_EINVAL;
     MLN_CK(c, cudaStreamSynchronize(c->stream));

@@ -120,7 +120,9 @@ std::string row_sum(const std::vector<double> &A, int ld, int i, int ncols, cons
         double a = A[i * ld + j];
         if (!nz(a, fp32)) continue;
         std::string t = x + "[" + std::to_string(j) + "]";
-        if (acc.empty()) acc = lit(a, fp32) + " * " + t;
+        // the first product is rounded on its own (as in the dense chain, where
+        // fused multiply-adds follow it), never contracted into a later add
+        if (acc.empty()) acc = std::string(fp32 ? "__fmul_rn(" : "__dmul_rn(") + lit(a, fp32) + ", " + t + ")";
         else acc = "fma(" + lit(a, fp32) + ", " + t + ", " + acc + ")";
     }
     return acc;

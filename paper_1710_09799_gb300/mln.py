@@ -79,6 +79,7 @@ _SIGS = {
     "mln_sync": (C.c_int, [C.c_void_p]),
     "mln_step_count": (C.c_int64, [C.c_void_p]),
     "mln_launch_count": (C.c_int64, [C.c_void_p]),
+    "mln_kernel_in_use": (C.c_int32, [C.c_void_p]),
     "mln_launch_shape": (C.c_int, [C.c_void_p, C.POINTER(C.c_int32), C.POINTER(C.c_int32),
                                    C.POINTER(C.c_int32)]),
     "mln_work_per_step": (C.c_int, [C.c_void_p, _dp, _dp, _dp, _dp]),
@@ -364,6 +365,11 @@ class Solver:
     @property
     def launch_shape(self):
         return mln_launch_shape(self.ctx)
+
+    @property
+    def kernel_in_use(self) -> str:
+        k = lib().mln_kernel_in_use(self.ctx)
+        return {v: n for n, v in KERNEL.items()}[k]
 
     def autotune(self, trials: int = 3):
         return mln_autotune(self.ctx, trials)

@@ -36,7 +36,7 @@ def test_generated_source_compiles_and_skips_zeros(lib, tmp_path, prec):
     nnz_C1 = int(np.count_nonzero(cast(s["C1"])))
     body = src[src.index("struct JitCell"):]
     # products: T^T and T each once per non-zero plane entry, C1 once per non-zero entry
-    n_terms = body.count("fma(") + body.count(" * s[") + body.count(" * z[") + body.count(" * y[")
+    n_terms = body.count("fma(") + body.count("mul_rn(")
     assert n_terms <= 2 * nnz_T + nnz_C1 + D + 1
     assert nnz_T < D * 2 * q and nnz_C1 < D * D  # the ring's structure has zeros to skip
     f = tmp_path / "k.cu"
