@@ -359,6 +359,28 @@ typedef struct mln_setup {
 mln_status mln_setup_host(const mln_params *p, mln_setup *out);
 
 /*
+ * Host-only helper: the relaxation superoperator of a Lindblad dissipator
+ * with jump operators L = |a><b| (level b decays to level a at rate
+ * gamma_{b->a}) plus pure dephasing of the coherences (the linear relaxation
+ * term of Eq. 2, written in the form the G parameter takes):
+ *   G(rho) = sum_{a,b} gamma_{b->a} (L rho L^+ - (L^+ L rho + rho L^+ L) / 2)
+ *            - sum_{j != k} gamma_jk rho_jk |j><k|.
+ *   N          2 .. MLN_MAX_N.
+ *   rates      N x N row-major doubles, rates[b * N + a] = gamma_{b->a} >= 0,
+ *              1/s (a diagonal entry b = a dephases every coherence of level a
+ *              by gamma/2), or NULL for none.
+ *   dephasing  N x N row-major doubles, gamma_jk >= 0 in 1/s, symmetric
+ *              (gamma_jk == gamma_kj exactly, so that G preserves Hermiticity);
+ *              diagonal entries are not read. NULL for none.
+ *   G_out      caller-owned (N*N) x (N*N) complex superoperator (2 N^4
+ *              doubles, interleaved), on row-major vec(rho); overwritten.
+ * The result preserves trace and Hermiticity and is accepted by mln_create.
+ * Errors: MLN_EINVAL (N out of range, NULL G_out, a negative or non-finite
+ * rate, asymmetric dephasing), message in mln_create_error.
+ */
+mln_status mln_lindblad_superop(int32_t N, const double *rates, const double *dephasing, double *G_out);
+
+/*
  * Diagnostic: evaluate on the device, for n angles x (host array), the pair
  * (sin x, cos x - 1) exactly as the step kernels of the given precision do,
  * into host arrays s and c1. Synchronous; uses the legacy default stream and

@@ -426,6 +426,45 @@ mln_status mln_setup_host(const mln_params *p, mln_setup *out) {
     return MLN_OK;
 }
 
+mln_status mln_lindblad_superop(int32_t N, const double *rates, const double *dephasing, double *G_out) {
+    auto fail = [](const char *m) {
+        mln::create_error() = m;
+        return MLN_EINVAL;
+    };
+    if (N < MLN_MIN_N || N > MLN_MAX_N) return fail("N out of range");
+    if (!G_out) return fail("G_out is NULL");
+    for (int i = 0; i < N * N; ++i) {
+        if (rates && !(std::isfinite(rates[i]) && rates[i] >= 0.0)) return fail("rates must be finite and >= 0");
+        if (dephasing) {
+            const int j = i / N, k = i % N;
+            if (j == k) continue;
+            if (!(std::isfinite(dephasing[i]) && dephasing[i] >= 0.0)) return fail("dephasing must be finite and >= 0");
+            if (dephasing[i] != dephasing[k * N + j]) return fail("dephasing must be symmetric");
+        }
+    }
+    const int n2 = N * N;
+    std::fill(G_out, G_out + 2 * n2 * n2, 0.0);
+    // real part of entry (row, col) of the superoperator; all entries are real
+    auto at = [&](int j, int k, int l, int m) -> double & { return G_out[2 * ((j * N + k) * n2 + l * N + m)]; };
+    if (rates) {
+        for (int b = 0; b < N; ++b)
+            for (int a = 0; a < N; ++a) {
+                const double g = rates[b * N + a];
+                if (g == 0.0) continue;
+                at(a, a, b, b) += g;  // L rho L^+ = rho_bb |a><a|
+                for (int m = 0; m < N; ++m) {
+                    at(b, m, b, m) -= 0.5 * g;  // -(|b><b| rho) / 2
+                    at(m, b, m, b) -= 0.5 * g;  // -(rho |b><b|) / 2
+                }
+            }
+    }
+    if (dephasing)
+        for (int j = 0; j < N; ++j)
+            for (int k = 0; k < N; ++k)
+                if (j != k) at(j, k, j, k) -= dephasing[j * N + k];
+    return MLN_OK;
+}
+
 void mln_destroy(mln_ctx *c) {
     if (!c) return;
     if (c->stream) cudaStreamSynchronize(c->stream);

@@ -94,6 +94,7 @@ _SIGS = {
     "mln_last_error": (C.c_char_p, [C.c_void_p]),
     "mln_create_error": (C.c_char_p, []),
     "mln_setup_host": (C.c_int, [_P, C.POINTER(mln_setup)]),
+    "mln_lindblad_superop": (C.c_int, [C.c_int32, _dp, _dp, _dp]),
     "mln_version": (C.c_char_p, []),
     "mln_kernel_source": (C.c_int, [_P, C.c_char_p, C.c_size_t, C.POINTER(C.c_size_t)]),
     "mln_adjoint": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_int64, C.c_int32,
@@ -282,6 +283,17 @@ def mln_setup_host(params: Params) -> dict:
     return dict(N=N, D=D, q=q, M=m(out.M), U=m(out.U), A0=m(out.A0), T=m(out.T), C1=m(out.C1),
                 d_eq=v(out.d_eq), v=v(out.v), b=v(out.b), w=v(out.w), d0=v(out.d0),
                 theta=np.array(out.theta[:q]), c=out.c, gen=gen)
+
+
+def mln_lindblad_superop(N: int, rates=None, dephasing=None) -> np.ndarray:
+    """Relaxation superoperator of decay rates rates[b, a] = gamma_{b->a} and
+    pure dephasing dephasing[j, k] (both N x N, 1/s, or None); returns the
+    (N*N) x (N*N) complex matrix on row-major vec(rho)."""
+    r = None if rates is None else np.ascontiguousarray(rates, dtype=np.float64).reshape(N * N)
+    g = None if dephasing is None else np.ascontiguousarray(dephasing, dtype=np.float64).reshape(N * N)
+    out = np.zeros(2 * N ** 4, dtype=np.float64)
+    _check(lib().mln_lindblad_superop(N, _ptr(r), _ptr(g), _ptr(out)))
+    return out.view(np.complex128).reshape(N * N, N * N)
 
 
 def mln_rotation_terms(precision: str, x):
