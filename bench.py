@@ -444,7 +444,7 @@ def main():
     ap.add_argument("--seg", type=int, default=1000, help="time steps per benchmark step")
     ap.add_argument("--block-steps", type=int, default=0, help="0: autotuned")
     ap.add_argument("--tile", type=int, default=0)
-    ap.add_argument("--kernel", default="auto", choices=["auto", "register", "sparse", "jit"])
+    ap.add_argument("--kernel", default="auto", choices=["auto", "register", "sparse", "jit", "tensor", "tensor_smem"])
     ap.add_argument("--workload", default="three_level_ring", choices=sorted(WORKLOADS))
     ap.add_argument("--quick", action="store_true", help="skip variants, e2e and the CPU baseline")
     args = ap.parse_args()

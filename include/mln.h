@@ -80,7 +80,23 @@ enum { MLN_FORM_STRANG = 0, MLN_FORM_MERGED = 1, MLN_FORM_RODRIGUES = 2 };
  * entries left out, compiles it for sm_103a at run time (NVRTC) and launches
  * it; same arithmetic and order as MLN_KERNEL_REGISTER, so the same bits.
  * It needs libnvrtc at run time (MLN_EUNSUPPORTED otherwise). */
-enum { MLN_KERNEL_AUTO = 0, MLN_KERNEL_REGISTER = 1, MLN_KERNEL_SPARSE = 2, MLN_KERNEL_JIT = 3 };
+/* MLN_KERNEL_TENSOR (FP32, merged form, N = 5 or 6) runs the three dense
+ * D x D products of a step on the fifth-generation tensor cores
+ * (tcgen05.mma kind::tf32, 128 cells per MMA, accumulators in tensor memory),
+ * each FP32 operand split into a high and a low TF32 part (three MMAs per
+ * product, FP32-level accuracy, not the FP32 register model's bits); the
+ * cells' rows of the A operand are staged in tensor memory.
+ * MLN_KERNEL_TENSOR_SMEM is the same with the A operand staged in shared
+ * memory. Both fuse up to 32 steps per launch (block_steps), with tiles of
+ * 128 - 2 block_steps cells; tile_cells is ignored. */
+enum {
+    MLN_KERNEL_AUTO = 0,
+    MLN_KERNEL_REGISTER = 1,
+    MLN_KERNEL_SPARSE = 2,
+    MLN_KERNEL_JIT = 3,
+    MLN_KERNEL_TENSOR = 4,
+    MLN_KERNEL_TENSOR_SMEM = 5
+};
 
 #define MLN_MIN_N 2
 #define MLN_MAX_N 6
@@ -114,7 +130,8 @@ enum { MLN_KERNEL_AUTO = 0, MLN_KERNEL_REGISTER = 1, MLN_KERNEL_SPARSE = 2, MLN_
  *   block_steps   steps fused into one kernel launch (temporal blocking);
  *                 0 picks a default. 1..64.
  *   tile_cells    cells written by one thread block; 0 picks a default.
- *   kernel        MLN_KERNEL_AUTO, MLN_KERNEL_REGISTER, MLN_KERNEL_SPARSE or MLN_KERNEL_JIT.
+ *   kernel        MLN_KERNEL_AUTO, MLN_KERNEL_REGISTER, MLN_KERNEL_SPARSE,
+ *                 MLN_KERNEL_JIT, MLN_KERNEL_TENSOR or MLN_KERNEL_TENSOR_SMEM.
  */
 typedef struct mln_params {
     int32_t N;
@@ -180,7 +197,8 @@ mln_status mln_create(const mln_params *p, void *d_state, void *Ez, void *Hy, vo
  */
 mln_status mln_step(mln_ctx *ctx, int64_t n_steps, const double *src);
 
-/* Wait for the queued work; report device-side problems (MLN_ENONFINITE). */
+/* Wait for the queued work; report device-side problems (MLN_ENONFINITE, or
+ * MLN_ETIMEOUT when a tensor-core kernel gave up waiting for an MMA). */
 mln_status mln_sync(mln_ctx *ctx);
 
 /* Number of time steps taken so far. */
@@ -190,7 +208,8 @@ int64_t mln_step_count(const mln_ctx *ctx);
  * in use: steps fused per launch and cells written per thread block. */
 int64_t mln_launch_count(const mln_ctx *ctx);
 /* The cell model the context's step kernel uses (MLN_KERNEL_REGISTER,
- * MLN_KERNEL_SPARSE or MLN_KERNEL_JIT), -1 for NULL. */
+ * MLN_KERNEL_SPARSE, MLN_KERNEL_JIT, MLN_KERNEL_TENSOR or
+ * MLN_KERNEL_TENSOR_SMEM), -1 for NULL. */
 int32_t mln_kernel_in_use(const mln_ctx *ctx);
 mln_status mln_launch_shape(const mln_ctx *ctx, int32_t *block_steps, int32_t *tile_cells,
                             int32_t *threads_per_block);
@@ -387,6 +406,20 @@ mln_status mln_lindblad_superop(int32_t N, const double *rates, const double *de
  * allocates temporary device memory.
  */
 mln_status mln_rotation_terms(int32_t precision, const double *x, int64_t n, double *s, double *c1);
+
+/*
+ * Diagnostic: C = A B^T computed by the tensor-core product path of
+ * MLN_KERNEL_TENSOR (a_in_tmem != 0) or MLN_KERNEL_TENSOR_SMEM (a_in_tmem
+ * == 0): A split into TF32 high and low parts on the device, B (given in
+ * FP64) split on the host, three tcgen05.mma kind::tf32 per K block, FP32
+ * accumulation. Shapes: M = 128 and (nc, kc) one of (32, 40), (48, 32),
+ * (48, 40), (32, 24), (16, 8) (MLN_EINVAL otherwise).
+ *   A  host, 128 x kc row-major floats;  B  host, nc x kc row-major doubles;
+ *   C  host, 128 x nc row-major floats (out).
+ * Synchronous, allocates temporary device memory, legacy default stream.
+ * MLN_ETIMEOUT if the completion wait gave up.
+ */
+mln_status mln_tc_product(int32_t nc, int32_t kc, int32_t a_in_tmem, const float *A, const double *B, float *C);
 
 /*
  * mln_step_noalloc -- the fused step for callers that cannot allocate device

@@ -83,7 +83,13 @@ mln_status adjoint_t(mln_ctx *c, int64_t n_steps, const double *src, int64_t pro
     };
     const Set<R> user{static_cast<R *>(c->E[0]), static_cast<R *>(c->H[0]), static_cast<R *>(c->st[0])};
     mln::BlockArgs<R> fa = mln::base_args<R>(c);
-    const int rtile = 254, rthreads = 256;  // recompute shape: one step per launch
+    // Block size: the largest of 256 .. 32 threads that still gives two blocks
+    // per SM, so that small rings spread over every SM (one thread per cell).
+    int sms = 152, dev = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    int athreads = 256;
+    while (athreads > 32 && (n + athreads - 1) / athreads < 2 * sms) athreads /= 2;
+    const int rthreads = athreads, rtile = athreads - 2;  // recompute shape: one step per launch
     fa.halo = 1;
     fa.tile = rtile;
     fa.nsteps = 1;
@@ -153,7 +159,8 @@ mln_status adjoint_t(mln_ctx *c, int64_t n_steps, const double *src, int64_t pro
             aa.Hb = A1s.H;
             aa.Sb = A1s.S;
             aa.dsrc = (src && c->p.source_kind != MLN_SRC_NONE) ? dsrc + s0 + j : nullptr;
-            mln::mln_adjoint_step<N, R><<<static_cast<unsigned>((n + 255) / 256), 256, 0, c->stream>>>(aa, k);
+            mln::mln_adjoint_step<N, R><<<static_cast<unsigned>((n + athreads - 1) / athreads), athreads, 0,
+                                          c->stream>>>(aa, k);
             MLN_ACK(c, cudaGetLastError());
             std::swap(A0s, A1s);
         }

@@ -13,6 +13,7 @@
 #include "jit.h"
 #include "mln.h"
 #include "setup.h"
+#include "tc_kernel.h"
 
 namespace {
 
@@ -97,6 +98,14 @@ mln_status upload_table(mln_ctx *c, double **dst, const std::vector<double> &mat
 void pick_launch_shape(mln_ctx *c) {
     int dev = 0, sms = 152;
     if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    c->sms = sms;
+    if (c->tc) {
+        // tiles of one MMA (128 rows) including the halo of K cells on both sides
+        c->K = c->p.block_steps > 0 ? c->p.block_steps : 8;
+        c->tile = mln::tc_rows() - 2 * c->K;
+        c->threads = 512;
+        return;
+    }
     const int maxt = c->max_threads;
     c->K = c->p.block_steps > 0 ? c->p.block_steps : 16;
     if (2 * c->K > maxt - 32) c->K = (maxt - 32) / 2;
@@ -125,6 +134,7 @@ cudaError_t launch(mln_ctx *c, const mln::BlockArgs<double> &a, dim3 g, dim3 b, 
 }
 
 cudaError_t launch(mln_ctx *c, const mln::BlockArgs<float> &a, dim3 g, dim3 b, size_t smem) {
+    if (c->tc) return mln::launch_tc(c->p.N, c->tc == MLN_KERNEL_TENSOR, a, c->tc_scal, c->tc_img, c->sms, c->stream);
     if (c->jit_fn) return mln::jit_launch(c->jit_fn, a, g, b, smem, c->stream);
     return mln::launch_block(c->p.N, c->p.form, a, c->consts, g, b, smem, c->stream);
 }
@@ -163,6 +173,7 @@ mln_status autotune_t(mln_ctx *c, int trials) {
     int bestK = c->K, bestTile = c->tile;
     for (int K : Ks) {
         if (2 * K > maxt - 32) continue;
+        if (c->tc && K > 32) continue;
         std::vector<int> tiles;
         for (int m = 1; m <= 8; m *= 2) {
             int64_t nt = static_cast<int64_t>(m) * sms;
@@ -171,12 +182,13 @@ mln_status autotune_t(mln_ctx *c, int trials) {
         }
         int whole = maxt - 2 * K;  // as few blocks as possible
         if (whole >= 1) tiles.push_back(static_cast<int>(std::min<int64_t>(whole, n)));
+        if (c->tc) tiles.assign(1, mln::tc_rows() - 2 * K);  // the tile is fixed by the MMA rows
         std::sort(tiles.begin(), tiles.end());
         tiles.erase(std::unique(tiles.begin(), tiles.end()), tiles.end());
         for (int tile : tiles) {
             c->K = K;
             c->tile = tile;
-            c->threads = (tile + 2 * K + 31) / 32 * 32;
+            c->threads = c->tc ? 512 : (tile + 2 * K + 31) / 32 * 32;
             mln::BlockArgs<R> a = mln::base_args<R>(c);
             a.E_in = static_cast<const R *>(c->E[0]);
             a.H_in = static_cast<const R *>(c->H[0]);
@@ -207,7 +219,7 @@ mln_status autotune_t(mln_ctx *c, int trials) {
     cudaEventDestroy(e1);
     c->K = bestK;
     c->tile = bestTile;
-    c->threads = (bestTile + 2 * bestK + 31) / 32 * 32;
+    c->threads = c->tc ? 512 : (bestTile + 2 * bestK + 31) / 32 * 32;
     MLN_CK(c, cudaMemsetAsync(c->flags, 0, sizeof(unsigned int), c->stream));
     MLN_CK(c, cudaStreamSynchronize(c->stream));
     return MLN_OK;
@@ -355,6 +367,28 @@ mln_status mln_rotation_terms(int32_t precision, const double *x, int64_t n, dou
     return st;
 }
 
+mln_status mln_tc_product(int32_t nc, int32_t kc, int32_t a_in_tmem, const float *A, const double *B, float *C) {
+    if (!A || !B || !C) {
+        mln::create_error() = "NULL argument";
+        return MLN_EINVAL;
+    }
+    std::string err;
+    cudaError_t e = mln::tc_product(nc, kc, a_in_tmem != 0, A, B, C, err);
+    if (e == cudaErrorInvalidValue) {
+        mln::create_error() = "unsupported (nc, kc)";
+        return MLN_EINVAL;
+    }
+    if (e != cudaSuccess) {
+        mln::create_error() = std::string("tensor-core product: ") + cudaGetErrorString(e);
+        return MLN_ECUDA;
+    }
+    if (!err.empty()) {
+        mln::create_error() = err;
+        return MLN_ETIMEOUT;
+    }
+    return MLN_OK;
+}
+
 const char *mln_status_string(mln_status s) {
     switch (s) {
     case MLN_OK: return "ok";
@@ -478,6 +512,7 @@ void mln_destroy(mln_ctx *c) {
     cudaFree(c->tab_in);
     cudaFree(c->scratch);
     cudaFree(c->prog);
+    cudaFree(c->tc_img);
     delete c;
 }
 
@@ -560,6 +595,18 @@ mln_status mln_create(const mln_params *p, void *d_state, void *Ez, void *Hy, vo
         if (c->max_threads < 64) {
             c->err = "sparse program does not fit in shared memory";
             return fail(MLN_EUNSUPPORTED);
+        }
+    } else if (p->kernel == MLN_KERNEL_TENSOR || p->kernel == MLN_KERNEL_TENSOR_SMEM) {
+        std::vector<unsigned char> img;
+        ok = mln::tc_supported(p->N) && mln::pack_tc(c->s, p->dt, img, c->tc_scal);
+        if (ok) {
+            if (cudaMalloc(&c->tc_img, img.size()) != cudaSuccess ||
+                cudaMemcpy(c->tc_img, img.data(), img.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
+                cudaGetLastError();
+                c->err = "upload of the tensor-core operands failed";
+                return fail(MLN_ENOMEM);
+            }
+            c->tc = p->kernel;
         }
     } else {
         ok = p->precision == MLN_FP64 ? mln::pack_consts(c->s, p->form, p->dt, 0.0, c->consts)
@@ -662,6 +709,11 @@ mln_status mln_sync(mln_ctx *c) {
     MLN_CK(c, cudaStreamSynchronize(c->stream));
     unsigned int f = 0;
     MLN_CK(c, cudaMemcpy(&f, c->flags, sizeof(f), cudaMemcpyDeviceToHost));
+    if (f & 2u) {
+        c->err = "a tensor-core kernel gave up waiting for an MMA to complete";
+        MLN_CK(c, cudaMemset(c->flags, 0, sizeof(unsigned int)));
+        return MLN_ETIMEOUT;
+    }
     if (f & 1u) {
         c->err = "non-finite E_z on the device";
         MLN_CK(c, cudaMemset(c->flags, 0, sizeof(unsigned int)));
@@ -676,6 +728,7 @@ int64_t mln_launch_count(const mln_ctx *c) { return c ? c->launches : -1; }
 
 int32_t mln_kernel_in_use(const mln_ctx *c) {
     if (!c) return -1;
+    if (c->tc) return c->tc;
     return c->jit_fn ? MLN_KERNEL_JIT : c->sparse ? MLN_KERNEL_SPARSE : MLN_KERNEL_REGISTER;
 }
 

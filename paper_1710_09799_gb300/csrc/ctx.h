@@ -29,6 +29,10 @@ struct mln_ctx {
     bool sparse = false;               // shared-memory sparse cell model (FP64 merged)
     void *jit_fn = nullptr;            // run-time compiled step kernel (CUfunction), or nullptr
     void *prog = nullptr;              // its program: rowptr | cols | vals
+    int tc = 0;                        // tensor-core cell model: 0 none, MLN_KERNEL_TENSOR(_SMEM)
+    int sms = 152;                     // SMs of the context's device
+    void *tc_img = nullptr;            // its B-operand image (device)
+    std::vector<unsigned char> tc_scal;  // and scalar constants
     int nnz = 0, nrowptr = 0;
     // output tables (FP64, device): rows x D matrix followed by rows offsets
     double *tab_rho = nullptr, *tab_pop = nullptr, *tab_d = nullptr, *tab_in = nullptr;

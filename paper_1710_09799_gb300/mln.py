@@ -24,7 +24,8 @@ MLN_BC_PERIODIC, MLN_BC_OPEN = 0, 1
 MLN_SRC_NONE, MLN_SRC_HARD, MLN_SRC_SOFT = 0, 1, 2
 MLN_FP64, MLN_FP32 = 0, 1
 MLN_FORM_STRANG, MLN_FORM_MERGED, MLN_FORM_RODRIGUES = 0, 1, 2
-MLN_KERNEL_AUTO, MLN_KERNEL_REGISTER, MLN_KERNEL_SPARSE, MLN_KERNEL_JIT = 0, 1, 2, 3
+(MLN_KERNEL_AUTO, MLN_KERNEL_REGISTER, MLN_KERNEL_SPARSE, MLN_KERNEL_JIT, MLN_KERNEL_TENSOR,
+ MLN_KERNEL_TENSOR_SMEM) = 0, 1, 2, 3, 4, 5
 MLN_MIN_N, MLN_MAX_N = 2, 6
 _DMAX = MLN_MAX_N * MLN_MAX_N - 1
 
@@ -33,7 +34,7 @@ SOURCE = {"none": MLN_SRC_NONE, "hard": MLN_SRC_HARD, "soft": MLN_SRC_SOFT}
 PRECISION = {"fp64": MLN_FP64, "fp32": MLN_FP32}
 FORM = {"strang": MLN_FORM_STRANG, "merged": MLN_FORM_MERGED, "rodrigues": MLN_FORM_RODRIGUES}
 KERNEL = {"auto": MLN_KERNEL_AUTO, "register": MLN_KERNEL_REGISTER, "sparse": MLN_KERNEL_SPARSE,
-          "jit": MLN_KERNEL_JIT}
+          "jit": MLN_KERNEL_JIT, "tensor": MLN_KERNEL_TENSOR, "tensor_smem": MLN_KERNEL_TENSOR_SMEM}
 
 _dp = C.POINTER(C.c_double)
 
@@ -111,6 +112,8 @@ _SIGS = {
     "mln_batch_error": (C.c_char_p, [C.c_void_p]),
     "mln_batch_destroy": (None, [C.c_void_p]),
     "mln_rotation_terms": (C.c_int, [C.c_int32, _dp, C.c_int64, _dp, _dp]),
+    "mln_tc_product": (C.c_int, [C.c_int32, C.c_int32, C.c_int32, C.POINTER(C.c_float), _dp,
+                                 C.POINTER(C.c_float)]),
     "mln_step_noalloc": (C.c_int, [_P, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_int64, C.c_void_p,
                                    C.c_void_p]),
 }
@@ -301,6 +304,19 @@ def mln_rotation_terms(precision: str, x):
     s, c1 = np.zeros_like(x), np.zeros_like(x)
     _check(lib().mln_rotation_terms(PRECISION.get(precision, precision), _ptr(x), len(x), _ptr(s), _ptr(c1)))
     return s, c1
+
+
+def mln_tc_product(A, B, a_in_tmem: bool = True) -> np.ndarray:
+    """C = A B^T through the tensor-core product path (A: 128 x kc float32,
+    B: nc x kc float64); returns C (128 x nc, float32)."""
+    A = np.ascontiguousarray(A, dtype=np.float32)
+    B = np.ascontiguousarray(B, dtype=np.float64)
+    nc, kc = B.shape
+    C_ = np.zeros((A.shape[0], nc), dtype=np.float32)
+    fp = C.POINTER(C.c_float)
+    _check(lib().mln_tc_product(nc, kc, int(a_in_tmem), A.ctypes.data_as(fp), B.ctypes.data_as(_dp),
+                                C_.ctypes.data_as(fp)))
+    return C_
 
 
 MLN_STATIC_SCRATCH_BYTES = 32 * 1024 * 1024

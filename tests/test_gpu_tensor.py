@@ -1,0 +1,137 @@
+"""Tensor-core cell model (MLN_KERNEL_TENSOR, MLN_KERNEL_TENSOR_SMEM): the
+three dense products of the merged step (Eqs. 23, 25-26, 17) on tcgen05 MMAs
+with 3 x TF32 operands, FP32 state, for N = 5 and 6.
+
+* the product path alone (mln_tc_product) against FP64 numpy, with a bound
+  that a single TF32 product (or a transposed or mis-laid operand) misses;
+* six-level runs against the FP64 oracle at the FP32 tolerance, and against
+  the FP32 register model;
+* a five-level periodic ring against the oracle;
+* the result does not depend on the launch shape (steps fused per launch,
+  chunking of the steps): each cell's row of the MMA is computed alone;
+* input validation.
+"""
+import numpy as np
+import pytest
+
+import workloads as W
+from helpers import gpu_run, params_of, rel_inf
+
+pytestmark = pytest.mark.gpu
+
+FP32_E_PER_KSTEP = 2e-3
+FP32_POP_PER_KSTEP = 2e-5
+KERNELS = ["tensor", "tensor_smem"]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_1710_09799_gb300 import build
+    build()
+
+
+def pops(rho):
+    return np.einsum("cii->ci", rho).real
+
+
+def tf32(x):
+    """Round to TF32 (nearest, ties away from zero) as the split does."""
+    b = np.asarray(x, dtype=np.float32).view(np.uint32)
+    return ((b + np.uint32(0x1000)) & np.uint32(0xFFFFE000)).view(np.float32)
+
+
+@pytest.mark.parametrize("a_in_tmem", [True, False])
+@pytest.mark.parametrize("nc,kc", [(32, 40), (48, 32), (48, 40), (32, 24), (16, 8)])
+def test_product_path_against_fp64(nc, kc, a_in_tmem):
+    from paper_1710_09799_gb300 import mln
+    rng = np.random.default_rng(nc * 100 + kc)
+    A = rng.normal(size=(128, kc)).astype(np.float32)
+    B = rng.normal(size=(nc, kc))
+    C = mln.mln_tc_product(A, B, a_in_tmem)
+    ref = A.astype(np.float64) @ B.T
+    scale = np.abs(A).astype(np.float64) @ np.abs(B).T
+    err = np.abs(C - ref)
+    # 3 x TF32 with FP32 accumulation: a few units of 2^-22 of sum |a||b|
+    assert np.all(err <= 2.0 ** -19 * scale), float((err / scale).max())
+    # a single TF32 product is off by ~2^-11 relative: the bound tells them apart
+    hi_only = tf32(A).astype(np.float64) @ tf32(B.astype(np.float32)).astype(np.float64).T
+    assert np.abs(hi_only - ref).max() > 2.0 ** -16 * scale.max()
+
+
+@pytest.mark.parametrize("kernel", KERNELS)
+def test_six_level_against_oracle(orc, kernel):
+    p = W.six_level_pulse(n_cells=4096, n_steps=1000)
+    st, _ = orc.run(p, n_steps=p.n_steps)
+    E, H, rho, s = gpu_run(p, p.n_steps, "fp32", "merged", kernel=kernel)
+    assert s.kernel_in_use == kernel
+    e_err = rel_inf(E, st.E)
+    p_err = np.abs(pops(rho) - pops(st.rho)).max()
+    print(f"tensor ({kernel}) six-level: E rel {e_err:.3e}  pop abs {p_err:.3e}")
+    assert e_err < FP32_E_PER_KSTEP and p_err < FP32_POP_PER_KSTEP
+
+
+@pytest.mark.parametrize("kernel", KERNELS)
+def test_six_level_close_to_fp32_register_model(kernel):
+    p = W.six_level_pulse(n_cells=600, n_steps=200, t0=15e-15, fwhm=10e-15)
+    E0, H0, r0, _ = gpu_run(p, p.n_steps, "fp32", "merged", kernel="register")
+    E1, H1, r1, _ = gpu_run(p, p.n_steps, "fp32", "merged", kernel=kernel)
+    assert rel_inf(E1, E0) < 1e-4 and np.abs(r1 - r0).max() < 1e-5
+
+
+@pytest.mark.parametrize("kernel", KERNELS)
+def test_five_level_ring_against_oracle(orc, kernel):
+    p = W.multi_level_ring(5, n_cells=1000, n_steps=500, seed=3)
+    st, _ = orc.run(p, n_steps=p.n_steps)
+    E, H, rho, _ = gpu_run(p, p.n_steps, "fp32", "merged", kernel=kernel)
+    e_err = rel_inf(E, st.E)
+    p_err = np.abs(pops(rho) - pops(st.rho)).max()
+    print(f"tensor ({kernel}) five-level ring: E rel {e_err:.3e}  pop abs {p_err:.3e}")
+    assert e_err < FP32_E_PER_KSTEP * 0.5 and p_err < FP32_POP_PER_KSTEP * 0.5
+
+
+def test_launch_shape_does_not_change_the_bits():
+    p = W.six_level_pulse(n_cells=1500, n_steps=96, t0=15e-15, fwhm=10e-15)
+    ref = gpu_run(p, p.n_steps, "fp32", "merged", kernel="tensor", block_steps=8)
+    for bs, chunks in [(1, None), (5, [7, 40, 49]), (32, None)]:
+        out = gpu_run(p, p.n_steps, "fp32", "merged", kernel="tensor", block_steps=bs, chunks=chunks)
+        for a, b in zip(out[:3], ref[:3]):
+            assert np.array_equal(a, b), bs
+    # the shared-memory A operand gives the same products
+    out = gpu_run(p, p.n_steps, "fp32", "merged", kernel="tensor_smem", block_steps=8)
+    for a, b in zip(out[:3], ref[:3]):
+        assert np.array_equal(a, b)
+
+
+def test_autotune_keeps_state():
+    from paper_1710_09799_gb300 import mln
+    p = W.six_level_pulse(n_cells=3000, n_steps=40, t0=15e-15, fwhm=10e-15)
+    s = mln.Solver(params_of(p, precision="fp32", form="merged", kernel="tensor"), E0=p.e_init())
+    before = s.save()
+    K, tile = s.autotune(2)
+    after = s.save()
+    for a, b in zip(before, after):
+        assert np.array_equal(a, b)
+    assert 1 <= K <= 32 and tile == 128 - 2 * K
+    assert s.launch_shape[2] == 512
+    s.close()
+
+
+@pytest.mark.parametrize("case", ["fp64", "strang", "n3", "block_steps"])
+def test_invalid_parameters(case):
+    from paper_1710_09799_gb300 import mln
+    p = W.six_level_pulse(n_cells=256, n_steps=10)
+    kw = dict(precision="fp32", form="merged", kernel="tensor")
+    if case == "fp64":
+        kw["precision"] = "fp64"
+    elif case == "strang":
+        kw["form"] = "strang"
+    elif case == "block_steps":
+        kw["block_steps"] = 40
+    else:
+        p = W.three_level_ring(n_cells=256)
+    with pytest.raises(mln.MLNError) as e:
+        mln.Solver(params_of(p, **kw), E0=p.e_init())
+    assert e.value.status == mln.MLN_EINVAL
