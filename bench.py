@@ -85,6 +85,38 @@ def alu_peak_tflops(precision: str, mhz: float = SM_MAX_MHZ) -> float:
     return SMS * per * mhz * 1e6 / 1e12
 
 
+def tensor_roofline(p, args, run, launches, per_launch_s, clk):
+    """Roofline of the tensor-core kernel against the TF32 tensor peak (the
+    measured sustained bf16 GEMM rate x the nominal TF32 / bf16 ratio 1/2).
+    achieved counts the method's two dense products per medium cell update
+    (T^T y: 2 D P; [C1, A0^2 T; wm^T, wm^T T] [y; dz]: 2 (D + 1)(D + P)) once;
+    issued counts what the MMAs execute (3 x TF32 split, K and N padded to the
+    MMA shape, halo rows of every tile)."""
+    D, Q = p.D, p.N * (p.N - 1) // 2
+    P = 2 * Q
+    up = lambda x, m: (x + m - 1) // m * m
+    KA, KP, N1, N3 = up(D, 8), up(P, 8), up(P, 16), up(D + 1, 16)
+    K, tile = run["shape"][0], run["shape"][1]
+    algo_per_cell = 2 * D * P + 2 * (D + 1) * (D + P)
+    issued_per_row = 3 * (2 * N1 * KA + 2 * N3 * (KA + KP))
+    steps_per_launch = args.seg * args.steps / max(launches, 1)
+    ntiles = -(-p.n_cells // tile)
+    algo = p.n_medium * algo_per_cell * steps_per_launch / per_launch_s / 1e12
+    issued = ntiles * 128 * issued_per_row * steps_per_launch / per_launch_s / 1e12
+    peaks = load_peaks()
+    bf16 = peaks.get("bf16_tflops_sustained") or peaks.get("bf16_tflops")
+    src = "measured bf16_tflops_sustained x 0.5 (nominal tf32 / bf16)"
+    if not bf16:
+        bf16, src = 1700.0, "fallback 1.7 PFLOP/s bf16 sustained x 0.5"
+    peak = 0.5 * bf16
+    return {"bound": "tensor", "achieved": algo, "peak": peak, "unit": "TFLOP/s", "frac": algo / peak,
+            "kernel": "mln_tc_kernel (tcgen05.mma kind::tf32, 3 x TF32)", "traffic": None, "peak_source": src,
+            "issued": issued, "frac_issued": issued / peak, "flops_per_medium_cell_update": algo_per_cell,
+            "issued_per_tile_row_step": issued_per_row,
+            "counted": "achieved: the two dense products once per medium cell update; issued: MMA work incl. "
+                       "split, padding and halo rows"}
+
+
 def load_peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -444,7 +476,7 @@ def main():
     ap.add_argument("--seg", type=int, default=1000, help="time steps per benchmark step")
     ap.add_argument("--block-steps", type=int, default=0, help="0: autotuned")
     ap.add_argument("--tile", type=int, default=0)
-    ap.add_argument("--kernel", default="auto", choices=["auto", "register", "sparse", "jit", "tensor", "tensor_smem"])
+    ap.add_argument("--kernel", default="auto", choices=["auto", "register", "sparse", "jit", "tensor"])
     ap.add_argument("--workload", default="three_level_ring", choices=sorted(WORKLOADS))
     ap.add_argument("--quick", action="store_true", help="skip variants, e2e and the CPU baseline")
     args = ap.parse_args()
@@ -492,6 +524,8 @@ def main():
     clk = main_run["clocks"] or {}
     if clk.get("sm_mhz"):
         roofline["frac_at_measured_clock"] = achieved / alu_peak_tflops(args.precision, clk["sm_mhz"])
+    if main_run["kernel"] == "tensor":
+        roofline = tensor_roofline(p, args, main_run, launches, per_launch_s, clk)
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,

@@ -80,22 +80,20 @@ enum { MLN_FORM_STRANG = 0, MLN_FORM_MERGED = 1, MLN_FORM_RODRIGUES = 2 };
  * entries left out, compiles it for sm_103a at run time (NVRTC) and launches
  * it; same arithmetic and order as MLN_KERNEL_REGISTER, so the same bits.
  * It needs libnvrtc at run time (MLN_EUNSUPPORTED otherwise). */
-/* MLN_KERNEL_TENSOR (FP32, merged form, N = 5 or 6) runs the three dense
- * D x D products of a step on the fifth-generation tensor cores
- * (tcgen05.mma kind::tf32, 128 cells per MMA, accumulators in tensor memory),
- * each FP32 operand split into a high and a low TF32 part (three MMAs per
- * product, FP32-level accuracy, not the FP32 register model's bits); the
- * cells' rows of the A operand are staged in tensor memory.
- * MLN_KERNEL_TENSOR_SMEM is the same with the A operand staged in shared
- * memory. Both fuse up to 32 steps per launch (block_steps), with tiles of
+/* MLN_KERNEL_TENSOR (FP32, merged form, N = 5 or 6) runs the dense products
+ * of a step on the fifth-generation tensor cores (tcgen05.mma kind::tf32, 128
+ * cells per MMA, accumulators in tensor memory), regrouped into two per step
+ * (the plane coordinates T^T y, then the increment of y and dP/dt from
+ * [y ; dz] in one product), each FP32 operand split into a high and a low
+ * TF32 part (three MMAs per K block: FP32-level accuracy, not the FP32
+ * register model's bits). Up to 32 steps per launch (block_steps), tiles of
  * 128 - 2 block_steps cells; tile_cells is ignored. */
 enum {
     MLN_KERNEL_AUTO = 0,
     MLN_KERNEL_REGISTER = 1,
     MLN_KERNEL_SPARSE = 2,
     MLN_KERNEL_JIT = 3,
-    MLN_KERNEL_TENSOR = 4,
-    MLN_KERNEL_TENSOR_SMEM = 5
+    MLN_KERNEL_TENSOR = 4
 };
 
 #define MLN_MIN_N 2
@@ -131,7 +129,7 @@ enum {
  *                 0 picks a default. 1..64.
  *   tile_cells    cells written by one thread block; 0 picks a default.
  *   kernel        MLN_KERNEL_AUTO, MLN_KERNEL_REGISTER, MLN_KERNEL_SPARSE,
- *                 MLN_KERNEL_JIT, MLN_KERNEL_TENSOR or MLN_KERNEL_TENSOR_SMEM.
+ *                 MLN_KERNEL_JIT or MLN_KERNEL_TENSOR.
  */
 typedef struct mln_params {
     int32_t N;
@@ -208,8 +206,7 @@ int64_t mln_step_count(const mln_ctx *ctx);
  * in use: steps fused per launch and cells written per thread block. */
 int64_t mln_launch_count(const mln_ctx *ctx);
 /* The cell model the context's step kernel uses (MLN_KERNEL_REGISTER,
- * MLN_KERNEL_SPARSE, MLN_KERNEL_JIT, MLN_KERNEL_TENSOR or
- * MLN_KERNEL_TENSOR_SMEM), -1 for NULL. */
+ * MLN_KERNEL_SPARSE, MLN_KERNEL_JIT or MLN_KERNEL_TENSOR), -1 for NULL. */
 int32_t mln_kernel_in_use(const mln_ctx *ctx);
 mln_status mln_launch_shape(const mln_ctx *ctx, int32_t *block_steps, int32_t *tile_cells,
                             int32_t *threads_per_block);
@@ -299,11 +296,11 @@ mln_status mln_adjoint(mln_ctx *ctx, int64_t n_steps, const double *src, int64_t
                        mln_adjoint_out *out);
 
 /*
- * Batches: many independent grids advanced together. Every launch covers
- * every tile of every grid (one work list, tiles of the costliest grids
- * first), so small and large grids of different N share the GPU; the
- * launches of one mln_batch_step call are captured into a CUDA graph and
- * replayed as one graph launch.
+ * Batches: many independent grids advanced together. Every K steps, one
+ * launch per N present covers every tile of every grid with that N (a kernel
+ * compiled for each N, so each gets the registers of its own cell size), so
+ * small and large grids share the GPU; the launches of one mln_batch_step
+ * call are captured into a CUDA graph and replayed as one graph launch.
  *
  * mln_batch_create: count grids, params[i] as for mln_create with one common
  * precision, form MLN_FORM_MERGED, N <= 4 and kernel AUTO or REGISTER;
@@ -323,7 +320,8 @@ mln_status mln_adjoint(mln_ctx *ctx, int64_t n_steps, const double *src, int64_t
  * mln_batch_context: the internal context of grid i, for reading results
  * (mln_get_fields, mln_get_rho, mln_save_state, ...); owned by the batch:
  * do not step or destroy it.
- * mln_batch_shape: steps per launch, tile, work items per launch, launches.
+ * mln_batch_shape: steps per launch, tile, work items (tiles of every grid,
+ * over the per-N launches of one step of K), kernel launches queued so far.
  * mln_batch_error: message of the last failed call on the batch.
  */
 typedef struct mln_batch mln_batch;
@@ -409,10 +407,10 @@ mln_status mln_rotation_terms(int32_t precision, const double *x, int64_t n, dou
 
 /*
  * Diagnostic: C = A B^T computed by the tensor-core product path of
- * MLN_KERNEL_TENSOR (a_in_tmem != 0) or MLN_KERNEL_TENSOR_SMEM (a_in_tmem
- * == 0): A split into TF32 high and low parts on the device, B (given in
- * FP64) split on the host, three tcgen05.mma kind::tf32 per K block, FP32
- * accumulation. Shapes: M = 128 and (nc, kc) one of (32, 40), (48, 32),
+ * MLN_KERNEL_TENSOR, with A staged in tensor memory (a_in_tmem != 0, as for
+ * the state y) or in shared memory (a_in_tmem == 0, as for dz): A split into
+ * TF32 high and low parts on the device, B (given in FP64) split on the host,
+ * three tcgen05.mma kind::tf32 per K block, FP32 accumulation. Shapes: M = 128 and (nc, kc) one of (32, 40), (48, 32),
  * (48, 40), (32, 24), (16, 8) (MLN_EINVAL otherwise).
  *   A  host, 128 x kc row-major floats;  B  host, nc x kc row-major doubles;
  *   C  host, 128 x nc row-major floats (out).

@@ -145,7 +145,7 @@ mln_status adjoint_t(mln_ctx *c, int64_t n_steps, const double *src, int64_t pro
             fa.src = (src && c->p.source_kind != MLN_SRC_NONE) ? src + s0 + j : nullptr;
             MLN_ACK(c, mln::launch_block(c->p.N, MLN_FORM_STRANG, fa, c->consts,
                                          dim3(static_cast<unsigned>((n + rtile - 1) / rtile)), dim3(rthreads),
-                                         2 * rthreads * sizeof(R), c->stream));
+                                         mln::field_smem<R>(rthreads), c->stream));
         }
         for (int64_t j = len - 1; j >= 0; --j) {
             const Set<R> f0 = set_at(slots, j), f1 = set_at(slots, j + 1);

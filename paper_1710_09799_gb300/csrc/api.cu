@@ -134,7 +134,7 @@ cudaError_t launch(mln_ctx *c, const mln::BlockArgs<double> &a, dim3 g, dim3 b, 
 }
 
 cudaError_t launch(mln_ctx *c, const mln::BlockArgs<float> &a, dim3 g, dim3 b, size_t smem) {
-    if (c->tc) return mln::launch_tc(c->p.N, c->tc == MLN_KERNEL_TENSOR, a, c->tc_scal, c->tc_img, c->sms, c->stream);
+    if (c->tc) return mln::launch_tc(c->p.N, a, c->tc_scal, c->tc_img, c->sms, c->stream);
     if (c->jit_fn) return mln::jit_launch(c->jit_fn, a, g, b, smem, c->stream);
     return mln::launch_block(c->p.N, c->p.form, a, c->consts, g, b, smem, c->stream);
 }
@@ -144,7 +144,7 @@ int sparse_max_threads(mln_ctx *c) {
     const size_t limit = 227 * 1024 - 1024;
     int best = 0;
     for (int t = 32; t <= mln::kMaxThreads; t += 32) {
-        size_t bytes = 2 * static_cast<size_t>(t) * sizeof(double) + mln::sparse_smem_bytes(c->p.N, t, c->nnz, c->nrowptr);
+        size_t bytes = mln::field_smem<double>(t) + mln::sparse_smem_bytes(c->p.N, t, c->nnz, c->nrowptr);
         if (bytes <= limit) best = t;
     }
     return best;
@@ -152,7 +152,7 @@ int sparse_max_threads(mln_ctx *c) {
 
 template <typename R>
 size_t smem_for(mln_ctx *c, int threads) {
-    size_t smem = 2 * static_cast<size_t>(threads) * sizeof(R);
+    size_t smem = mln::field_smem<R>(threads);
     if (c->sparse) smem += mln::sparse_smem_bytes(c->p.N, threads, c->nnz, c->nrowptr);
     return smem;
 }
@@ -596,7 +596,7 @@ mln_status mln_create(const mln_params *p, void *d_state, void *Ez, void *Hy, vo
             c->err = "sparse program does not fit in shared memory";
             return fail(MLN_EUNSUPPORTED);
         }
-    } else if (p->kernel == MLN_KERNEL_TENSOR || p->kernel == MLN_KERNEL_TENSOR_SMEM) {
+    } else if (p->kernel == MLN_KERNEL_TENSOR) {
         std::vector<unsigned char> img;
         ok = mln::tc_supported(p->N) && mln::pack_tc(c->s, p->dt, img, c->tc_scal);
         if (ok) {

@@ -1,7 +1,8 @@
 // Batched solver: many independent grids (any mix of N = 2..4, lengths and
-// boundaries, one precision) advanced together, each launch covering every
-// tile of every grid. The sequence of launches of one mln_batch_step call is
-// captured once into a CUDA graph and replayed.
+// boundaries, one precision) advanced together: every K steps, one launch per
+// N present covers every tile of every grid with that N. The sequence of
+// launches of one mln_batch_step call is captured once into a CUDA graph and
+// replayed.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -18,10 +19,100 @@
 
 namespace mln {
 
-// Shared-memory room for one grid's constants (the merged-form constants of
-// N = 4 in FP64 are 3.9 KB).
-constexpr int kBatchConstsMax = 4096;
+// Shared-memory room for one grid's constants (the padded merged-form
+// constants of N = 4 in FP64 are 6.0 KB).
+constexpr int kBatchConstsMax = 8192;
 constexpr int kBatchMaxN = 4;
+
+// Merged-form constants of one grid with every row padded to a whole number
+// of 16-byte vectors, and T also stored transposed, so that each product
+// reads its row with vector loads from shared memory.
+template <int N, typename R>
+struct PaddedConsts {
+    static constexpr int D = Dims<N>::D, V = 16 / static_cast<int>(sizeof(R)), DP = (D + V - 1) / V * V;
+    R C1[D * DP];  // C1[i * DP + j] = (A0^2 - I)_ij
+    R T[D * DP];   // T[i * DP + j] = T_ij
+    R Tt[D * DP];  // Tt[k * DP + i] = T_ik
+    R b2[DP];
+    R wm[DP];
+    R psi_dt[N - 1];
+    R cm;
+};
+
+template <typename R>
+struct Vec;
+template <>
+struct Vec<float> {
+    static constexpr int n = 4;
+    __device__ __forceinline__ static void get(const float *p, float (&o)[4]) {
+        const float4 v = *reinterpret_cast<const float4 *>(p);
+        o[0] = v.x;
+        o[1] = v.y;
+        o[2] = v.z;
+        o[3] = v.w;
+    }
+};
+template <>
+struct Vec<double> {
+    static constexpr int n = 2;
+    __device__ __forceinline__ static void get(const double *p, double (&o)[2]) {
+        const double2 v = *reinterpret_cast<const double2 *>(p);
+        o[0] = v.x;
+        o[1] = v.y;
+    }
+};
+
+// sum_j row[j] x[j] in ascending j, as the dense products of the register
+// model: starting from row[0] x[0] (first_mul) or as fma's onto acc.
+template <int D, bool first_mul, typename R>
+__device__ __forceinline__ R dot_row(const R *row, const R (&x)[D], R acc) {
+    constexpr int V = Vec<R>::n;
+#pragma unroll
+    for (int j0 = 0; j0 < D; j0 += V) {
+        R c[V];
+        Vec<R>::get(row + j0, c);
+#pragma unroll
+        for (int e = 0; e < V; ++e) {
+            const int j = j0 + e;
+            if (j < D) acc = (first_mul && j == 0) ? c[e] * x[0] : fma(c[e], x[j], acc);
+        }
+    }
+    return acc;
+}
+
+// The register cell model's merged step (same operations in the same order,
+// hence the same bits) with the constants read from the padded layout.
+template <int N, typename R>
+struct PaddedCell {
+    static constexpr int D = Dims<N>::D;
+    using Consts = PaddedConsts<N, R>;
+    static constexpr int DP = Consts::DP;
+    R s[D];
+    __device__ __forceinline__ void setup(unsigned char *, const Consts &) {}
+    __device__ __forceinline__ void load(const R *src, int64_t stride, int64_t m) {
+#pragma unroll
+        for (int i = 0; i < D; ++i) s[i] = src[i * stride + m];
+    }
+    __device__ __forceinline__ void store(R *dst, int64_t stride, int64_t m) const {
+#pragma unroll
+        for (int i = 0; i < D; ++i) dst[i * stride + m] = s[i];
+    }
+    __device__ __forceinline__ R step(R e, const Consts &k) {
+        R z[D];
+#pragma unroll
+        for (int c = 0; c < D; ++c) z[c] = dot_row<D, true>(k.Tt + c * DP, s, R(0));  // z = T^T y
+        rotation_increment<N>(z, k.psi_dt, e);
+#pragma unroll
+        for (int i = 0; i < D; ++i) s[i] = s[i] + dot_row<D, true>(k.T + i * DP, z, R(0));  // y + T (R - I) z
+        const R dpdt = dot_row<D, false>(k.wm, s, k.cm);
+#pragma unroll
+        for (int i = 0; i < D; ++i) z[i] = s[i] + dot_row<D, false>(k.C1 + i * DP, s, k.b2[i]);
+#pragma unroll
+        for (int i = 0; i < D; ++i) s[i] = z[i];
+        return dpdt;
+    }
+    __device__ __forceinline__ void end_step() {}
+};
 
 template <typename R>
 struct BatchGrid {
@@ -37,20 +128,19 @@ struct BatchItem {
     int32_t grid, tile;
 };
 
-template <int N, typename R>
-__device__ __forceinline__ void batch_tile(const BlockArgs<R> &a, const unsigned char *consts, int64_t tile,
-                                           unsigned char *rest) {
-    using K = MergedConsts<N, R>;
-    block_body<N, R, RegisterCell<N, R, K>>(a, *reinterpret_cast<const K *>(consts), tile, rest);
-}
+// Threads per block of the batched kernels (tile + 2 K <= this).
+constexpr int kBatchThreads = 256;
 
-// One block per work item (grid, tile). The grid's constants are staged in
-// shared memory (every thread of a warp reads the same entry: broadcasts).
-template <typename R>
-__global__ void __launch_bounds__(kMaxThreads, 1)
+// One block per work item (grid, tile) of the grids with N levels; one kernel
+// per N, so that each gets the registers of its own cell size. The grid's
+// constants are staged in shared memory (padded rows read with 16-byte
+// vector loads; every thread of a warp reads the same entry: broadcasts).
+template <int N, typename R>
+__global__ void __launch_bounds__(kBatchThreads, 1)
     mln_batch_kernel(const BatchGrid<R> *__restrict__ grids, const BatchItem *__restrict__ items,
                      const unsigned char *__restrict__ consts, int parity, int nsteps, int halo, int tile,
                      int64_t step_offset) {
+    using K = PaddedConsts<N, R>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const BatchItem it = items[blockIdx.x];
     const BatchGrid<R> &g = grids[it.grid];
@@ -82,13 +172,8 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
     a.cb = g.cb;
     a.inv_dx = g.inv_dx;
     a.kappa = g.kappa;
-    unsigned char *rest = smem_raw + kBatchConstsMax;
-    switch (g.N) {
-    case 2: batch_tile<2, R>(a, smem_raw, it.tile, rest); break;
-    case 3: batch_tile<3, R>(a, smem_raw, it.tile, rest); break;
-    case 4: batch_tile<4, R>(a, smem_raw, it.tile, rest); break;
-    default: break;
-    }
+    block_body<N, R, PaddedCell<N, R>>(a, *reinterpret_cast<const K *>(smem_raw), it.tile,
+                                       smem_raw + kBatchConstsMax);
 }
 
 }  // namespace mln
@@ -104,6 +189,7 @@ struct mln_batch {
     std::vector<const double *> src;
     void *d_grids = nullptr, *d_items = nullptr, *d_consts = nullptr;
     int64_t n_items = 0;
+    int64_t item_off[mln::kBatchMaxN + 1] = {}, item_cnt[mln::kBatchMaxN + 1] = {};  // work items by N
     // captured launch sequences, by step count
     std::map<int64_t, cudaGraphExec_t> graphs;
     std::string err;
@@ -125,8 +211,49 @@ void drop_graphs(mln_batch *b) {
     b->graphs.clear();
 }
 
-// Grid table and work list for the current tile size (tiles sorted by
-// decreasing cost, D^2 per cell, so the largest start first).
+// Padded constants of one grid from its context's merged-form constants
+// (the same values, rearranged).
+template <int N, typename R>
+bool pad_consts_t(const std::vector<unsigned char> &merged, std::vector<unsigned char> &out) {
+    using M = mln::MergedConsts<N, R>;
+    using P = mln::PaddedConsts<N, R>;
+    static_assert(sizeof(P) <= mln::kBatchConstsMax, "padded constants exceed the shared-memory room");
+    if (merged.size() != sizeof(M)) return false;
+    M m;
+    std::memcpy(&m, merged.data(), sizeof(M));
+    P p;
+    std::memset(&p, 0, sizeof(P));
+    constexpr int D = P::D, DP = P::DP;
+    for (int i = 0; i < D; ++i)
+        for (int j = 0; j < D; ++j) {
+            p.C1[i * DP + j] = m.C1[i * D + j];
+            p.T[i * DP + j] = m.T[i * D + j];
+            p.Tt[j * DP + i] = m.T[i * D + j];
+        }
+    for (int i = 0; i < D; ++i) {
+        p.b2[i] = m.b2[i];
+        p.wm[i] = m.wm[i];
+    }
+    for (int a = 0; a < N - 1; ++a) p.psi_dt[a] = m.psi_dt[a];
+    p.cm = m.cm;
+    out.resize(sizeof(P));
+    std::memcpy(out.data(), &p, sizeof(P));
+    return true;
+}
+
+template <typename R>
+bool pad_consts(int N, const std::vector<unsigned char> &merged, std::vector<unsigned char> &out) {
+    switch (N) {
+    case 2: return pad_consts_t<2, R>(merged, out);
+    case 3: return pad_consts_t<3, R>(merged, out);
+    case 4: return pad_consts_t<4, R>(merged, out);
+    default: return false;
+    }
+}
+
+// Grid table and work list for the current tile size: the tiles of the
+// grids with N levels form one contiguous run per N (largest N first), the
+// work of one launch of that N's kernel.
 template <typename R>
 mln_status build_tables(mln_batch *b) {
     std::vector<mln::BatchGrid<R>> grids;
@@ -151,23 +278,34 @@ mln_status build_tables(mln_batch *b) {
         g.N = c->p.N;
         g.boundary = c->p.boundary;
         g.source_kind = c->p.source_kind;
+        std::vector<unsigned char> padded;
+        if (!pad_consts<R>(c->p.N, c->consts, padded)) {
+            b->err = "batch: no padded constants for this N";
+            return MLN_EUNSUPPORTED;
+        }
         g.consts_off = static_cast<int32_t>(blob.size());
-        g.consts_bytes = static_cast<int32_t>((c->consts.size() + 15) / 16 * 16);
+        g.consts_bytes = static_cast<int32_t>((padded.size() + 15) / 16 * 16);
         g.ch = a.ch;
         g.ca = a.ca;
         g.cb = a.cb;
         g.inv_dx = a.inv_dx;
         g.kappa = a.kappa;
-        blob.insert(blob.end(), c->consts.begin(), c->consts.end());
+        blob.insert(blob.end(), padded.begin(), padded.end());
         blob.resize((blob.size() + 15) / 16 * 16, 0);
         grids.push_back(g);
         const int64_t nt = (c->p.n_cells + b->tile - 1) / b->tile;
-        const int cost = c->D * c->D;
-        for (int64_t t = 0; t < nt; ++t) items.push_back({cost, mln::BatchItem{static_cast<int32_t>(i), static_cast<int32_t>(t)}});
+        for (int64_t t = 0; t < nt; ++t)
+            items.push_back({c->p.N, mln::BatchItem{static_cast<int32_t>(i), static_cast<int32_t>(t)}});
     }
     std::stable_sort(items.begin(), items.end(), [](const auto &x, const auto &y) { return x.first > y.first; });
     std::vector<mln::BatchItem> list;
-    for (auto &x : items) list.push_back(x.second);
+    for (int N = 0; N <= mln::kBatchMaxN; ++N) b->item_off[N] = b->item_cnt[N] = 0;
+    for (size_t k = 0; k < items.size(); ++k) {
+        const int N = items[k].first;
+        if (b->item_cnt[N] == 0) b->item_off[N] = static_cast<int64_t>(k);
+        ++b->item_cnt[N];
+        list.push_back(items[k].second);
+    }
     cudaFree(b->d_grids);
     cudaFree(b->d_items);
     cudaFree(b->d_consts);
@@ -184,18 +322,34 @@ mln_status build_tables(mln_batch *b) {
 
 template <typename R>
 size_t batch_smem(int threads) {
-    return mln::kBatchConstsMax + 2 * static_cast<size_t>(threads) * sizeof(R);
+    return mln::kBatchConstsMax + mln::field_smem<R>(threads);
 }
 
-template <typename R>
-cudaError_t launch_batch(mln_batch *b, int parity, int nsteps, int64_t step_offset) {
-    // at most 4 KB + 2 x 512 x 8 B = 12 KB: below the 48 KB default, no attribute needed
+template <int N, typename R>
+cudaError_t launch_batch_n(mln_batch *b, int parity, int nsteps, int64_t step_offset) {
+    if (b->item_cnt[N] == 0) return cudaSuccess;
+    // at most 8 KB + 4 x 256 x 8 B = 16 KB: below the 48 KB default, no attribute needed
     const size_t smem = batch_smem<R>(b->threads);
-    auto kern = mln::mln_batch_kernel<R>;
-    kern<<<static_cast<unsigned>(b->n_items), b->threads, smem, b->stream>>>(
-        static_cast<const mln::BatchGrid<R> *>(b->d_grids), static_cast<const mln::BatchItem *>(b->d_items),
+    mln::mln_batch_kernel<N, R><<<static_cast<unsigned>(b->item_cnt[N]), b->threads, smem, b->stream>>>(
+        static_cast<const mln::BatchGrid<R> *>(b->d_grids),
+        static_cast<const mln::BatchItem *>(b->d_items) + b->item_off[N],
         static_cast<const unsigned char *>(b->d_consts), parity, nsteps, b->K, b->tile, step_offset);
     return cudaGetLastError();
+}
+
+// One launch per N present (largest first), all on the batch's stream.
+template <typename R>
+cudaError_t launch_batch(mln_batch *b, int parity, int nsteps, int64_t step_offset) {
+    cudaError_t e = launch_batch_n<4, R>(b, parity, nsteps, step_offset);
+    if (e == cudaSuccess) e = launch_batch_n<3, R>(b, parity, nsteps, step_offset);
+    if (e == cudaSuccess) e = launch_batch_n<2, R>(b, parity, nsteps, step_offset);
+    return e;
+}
+
+int batch_kernels(const mln_batch *b) {
+    int k = 0;
+    for (int N = 2; N <= mln::kBatchMaxN; ++N) k += b->item_cnt[N] > 0;
+    return k;
 }
 
 // Queue the launches of n_steps steps from the batch's current step count;
@@ -232,7 +386,7 @@ mln_status autotune_batch(mln_batch *b, int trials) {
     int bestK = b->K, bestTile = b->tile;
     for (int K : Ks)
         for (int tile : tiles) {
-            if (tile + 2 * K > mln::kMaxThreads) continue;
+            if (tile + 2 * K > mln::kBatchThreads) continue;
             b->K = K;
             b->tile = tile;
             b->threads = (tile + 2 * K + 31) / 32 * 32;
@@ -328,8 +482,8 @@ mln_status mln_batch_create(int32_t count, const mln_params *params, void *const
         b->src.push_back(src && src_len > 0 ? src[i] : nullptr);
     }
     b->K = 16;
-    b->tile = 256;
-    b->threads = (b->tile + 2 * b->K + 31) / 32 * 32;
+    b->tile = mln::kBatchThreads - 2 * b->K;
+    b->threads = mln::kBatchThreads;
     mln_status st = b->precision == MLN_FP64 ? build_tables<double>(b) : build_tables<float>(b);
     if (st != MLN_OK) {
         mln::create_error() = b->err;
@@ -392,7 +546,7 @@ mln_status mln_batch_step(mln_batch *b, int64_t n_steps) {
     MLN_BCK(b, cudaEventRecord(b->ev_out, b->stream));
     MLN_BCK(b, cudaStreamWaitEvent(b->user, b->ev_out, 0));
     const int64_t per = (n_steps + b->K - 1) / b->K;
-    b->launches += per;
+    b->launches += per * batch_kernels(b);
     b->steps += n_steps;
     for (mln_ctx *c : b->ctx) {
         c->steps += n_steps;

@@ -338,6 +338,12 @@ __global__ void sin_cosm1_kernel(const double *x, int64_t n, double *s, double *
 // Blocks have at most kMaxThreads threads, which leaves up to 128 registers per thread.
 constexpr int kMaxThreads = 512;
 
+// Shared memory of a block's field exchange: E and H, two buffers each.
+template <typename R>
+__host__ __device__ constexpr size_t field_smem(int threads) {
+    return 4 * static_cast<size_t>(threads) * sizeof(R);
+}
+
 // Cell model with the medium state in registers and dense D x D products
 // whose constants are kernel-parameter (constant-bank) operands (or, in the
 // batched kernel, a structure in shared memory).
@@ -465,8 +471,11 @@ struct SharedSparseCell {
 template <int N, typename R, typename Cell>
 __device__ __forceinline__ void block_body(const BlockArgs<R> &a, const typename Cell::Consts &k, int64_t tile_index,
                                            unsigned char *smem) {
-    R *sE = reinterpret_cast<R *>(smem);
-    R *sH = sE + blockDim.x;
+    // E and H of the block, two buffers each: step st reads one and writes the other
+    R *cE = reinterpret_cast<R *>(smem);
+    R *cH = cE + blockDim.x;
+    R *nE = cH + blockDim.x;
+    R *nH = nE + blockDim.x;
 
     const int j = threadIdx.x;
     const int64_t n = a.n_cells;
@@ -487,36 +496,37 @@ __device__ __forceinline__ void block_body(const BlockArgs<R> &a, const typename
     const int64_t m = gm - a.mb;
 
     Cell cell;
-    cell.setup(reinterpret_cast<unsigned char *>(sH + blockDim.x), k);
+    cell.setup(smem + field_smem<R>(blockDim.x), k);
     R e = loaded ? a.E_in[gm] : R(0);
     R h = loaded ? a.H_in[gm] : R(0);
-    sE[j] = e;
-    sH[j] = h;
+    cE[j] = e;
+    cH[j] = h;
     if (medium) cell.load(a.s_in, a.stride, m);
 
     // H_{i+1/2} exists for every cell of a ring and for cells 0..n-2 of an open grid;
     // it needs E of the next loaded cell.
     const bool h_upd = loaded && (j + 1 < L) && (periodic || gm < n - 1);
-    // E needs H_{i-1/2} of the previous loaded cell. On an open grid cell 0 is held
-    // (hard source only) and cell n-1 is set by the Mur rule of cell n-2's thread.
+    // E needs H_{i-1/2} of the previous loaded cell (whose H update always
+    // exists then). On an open grid cell 0 is held (hard source only) and cell
+    // n-1 is set by the Mur rule of cell n-2's thread.
     const bool e_upd = loaded && j >= 1 && (periodic || (gm > 0 && gm < n - 1));
     const bool mur = !periodic && loaded && gm == n - 2 && j + 1 < L;
+    const bool mur_cell = !periodic && loaded && gm == n - 1;
     const bool is_src = a.src != nullptr && loaded && gm == a.source_cell;
     __syncthreads();
 
     for (int st = 0; st < a.nsteps; ++st) {
-        if (h_upd) {
-            h = fma(a.ch, sE[j + 1] - e, h);
-            sH[j] = h;
-        }
-        __syncthreads();
+        if (h_upd) h = fma(a.ch, cE[j + 1] - e, h);
+        // the previous cell's new H, with the operands and operations of its own thread
+        R hl = R(0);
+        if (e_upd) hl = fma(a.ch, e - cE[j - 1], cH[j - 1]);
         R dpdt = R(0);
         if (medium) dpdt = cell.step(e, k);
         cell.end_step();
         R en = e;
-        if (e_upd) en = fma(a.ca, e, a.cb * fma(h - sH[j - 1], a.inv_dx, -dpdt));
+        if (e_upd) en = fma(a.ca, e, a.cb * fma(h - hl, a.inv_dx, -dpdt));
         R e_mur = R(0);
-        if (mur) e_mur = fma(a.kappa, en - sE[j + 1], e);
+        if (mur) e_mur = fma(a.kappa, en - cE[j + 1], e);  // from E^{n+1} before any source
         if (is_src) {
             R v = static_cast<R>(a.src[st]);
             en = (a.source_kind == 1) ? v : en + v;
@@ -526,13 +536,20 @@ __device__ __forceinline__ void block_body(const BlockArgs<R> &a, const typename
                 R v = static_cast<R>(a.src[st]);
                 e_mur = (a.source_kind == 1) ? v : e_mur + v;
             }
-            sE[j + 1] = e_mur;
+            nE[j + 1] = e_mur;
         }
         e = en;
-        if (loaded && !(!periodic && gm == n - 1)) sE[j] = e;
+        if (!mur_cell) nE[j] = e;
+        nH[j] = h;
         __syncthreads();
         // the Mur cell takes its new value from shared memory
-        if (!periodic && loaded && gm == n - 1) e = sE[j];
+        if (mur_cell) e = nE[j];
+        R *t = cE;
+        cE = nE;
+        nE = t;
+        t = cH;
+        cH = nH;
+        nH = t;
     }
 
     const bool interior = loaded && j >= a.halo && j < a.halo + static_cast<int>(t1 - t0);

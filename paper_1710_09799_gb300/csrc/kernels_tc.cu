@@ -1,22 +1,24 @@
-// Tensor-core cell model (FP32 state, merged form, N = 5 and 6): the three
-// dense products of a step,
-//   z  = T^T y                       (plane coordinates only, Eq. 26)
-//   r  = y + T (R(phi) - I) z        (Eq. 25 in increment form)
-//   y' = r + (A0^2 - I) r + A0 b + b,  dP/dt = (A0^T w) . r + c'   (Eqs. 23, 17)
-// run as tcgen05.mma kind::tf32 over 128 cells at a time, each FP32 operand
-// split into a TF32 high part and a TF32 low part (three MMAs per product:
-// lo*hi + hi*lo + hi*hi, FP32 accumulation in tensor memory). The rotation,
-// the additions of the increments and the FDTD update stay on the FP32 pipe.
+// Tensor-core cell model (FP32 state, merged form, N = 5 and 6). The merged
+// step (Eqs. 23, 25-26, 17)
+//   z = T^T y,  dz = (R(phi) - I) z,  r = y + T dz,
+//   y' = r + (A0^2 - I) r + A0 b + b,  dP/dt = (A0^T w) . r + c'
+// is regrouped into two dense products per step,
+//   z = T^T y                                                (before the rotation)
+//   [y' - y ; dP/dt] = [C1, b2, A0^2 T ; wm^T, c', wm^T T] [y ; 1 ; dz]   (after it)
+// with C1 = A0^2 - I, b2 = A0 b + b and wm = A0^T w (the constant offsets ride
+// on a column of ones); the increment (second product) is added to y in FP32. Both run as tcgen05.mma kind::tf32 over 128 cells at a time,
+// each FP32 operand split into a TF32 high and low part (three MMAs per K
+// block: lo*hi + hi*lo + hi*hi, FP32 accumulation in tensor memory). The
+// rotation, the FP32 additions and the FDTD update run on the FP32 pipe.
 //
 // A CTA holds four independent tiles of 128 cells (one warpgroup each, with
 // its own K-cell halo on both sides, as in the temporal blocking of the other
 // cell models); the warpgroups synchronise only among themselves, so the
-// tensor core works on one tile while the others rotate and update fields.
-// The CTA is persistent: the B operands (hi and lo images of T^T, T and
-// [A0^2 - I; (A0^T w)^T]) are staged once in shared memory, and the
-// warpgroups loop over tiles. The A operand (a row per cell) is written by
-// its thread either into tensor memory with tcgen05.st (TA = true: the
-// tensor core then reads only B from shared memory) or into shared memory.
+// tensor core works for one tile while the others rotate and update fields.
+// The CTA is persistent: the B operands (hi and lo images) are staged once in
+// shared memory and the warpgroups loop over tiles. Each cell's row of y is
+// written by its thread into tensor memory (tcgen05.st), where both products
+// read it; its row of dz goes to shared memory.
 #include <cuda_runtime.h>
 
 #include <cstring>
@@ -30,67 +32,74 @@
 
 namespace mln {
 
-// Layout of one CTA of the tensor-core kernel for N levels; TA: A operand in
-// tensor memory (else in shared memory).
-template <int N, bool TA>
+// Layout of one CTA of the tensor-core kernel for N levels.
+template <int N>
 struct TcShape {
     static constexpr int D = Dims<N>::D, Q = Dims<N>::Q, P = 2 * Q;
-    static constexpr int KA = (D + 7) / 8 * 8;         // K of the products over the state
-    static constexpr int KP = (P + 7) / 8 * 8;         // K of the product over plane coordinates
+    static constexpr int KA = (D + 1 + 7) / 8 * 8;     // K over the state and the constant-1 column
+    static constexpr int KP = (P + 7) / 8 * 8;         // K over the plane coordinates
     static constexpr int N1 = (P + 15) / 16 * 16;      // MMA N of z = T^T y
-    static constexpr int N2 = (D + 15) / 16 * 16;      // MMA N of T dz
-    static constexpr int N3 = (D + 1 + 15) / 16 * 16;  // MMA N of [C1; wm^T] r
-    static constexpr int NMAX = N2 > N3 ? (N2 > N1 ? N2 : N1) : (N3 > N1 ? N3 : N1);
+    static constexpr int N3 = (D + 1 + 15) / 16 * 16;  // MMA N of the increment and dP/dt
     static constexpr int L1 = (P + 7) / 8 * 8;         // accumulator columns read back
-    static constexpr int L2 = (D + 7) / 8 * 8;
     static constexpr int L3 = (D + 1 + 7) / 8 * 8;
     static constexpr int G = 4;                        // warpgroups (tiles) per CTA
     static constexpr int ROWS = 128;
-    // tensor-memory columns of one group: [A hi | A lo] (TA only), then the accumulator
-    static constexpr int TA_HI = 0, TA_LO = KA, ACC = TA ? 2 * KA : 0;
-    static constexpr int GCOLS = TA ? 128 : 64;
+    // tensor-memory columns of one group: y hi | y lo | accumulator
+    static constexpr int Y_HI = 0, Y_LO = KA, ACC = 2 * KA, GCOLS = 128;
     static constexpr uint32_t TMEM_COLS = static_cast<uint32_t>(G * GCOLS);
-    static constexpr int B1 = N1 * KA * 4, B2 = N2 * KP * 4, B3 = N3 * KA * 4;  // bytes of one image
-    static constexpr int BIMG = 2 * (B1 + B2 + B3);
-    static constexpr int ABYTES = TA ? 0 : ROWS * KA * 4;
-    static constexpr int OFF_A = (BIMG + 127) / 128 * 128;
-    static constexpr int OFF_E = OFF_A + G * 2 * ABYTES;
+    // B images (hi, lo each): T^T (N1 x KA), [C1; wm^T] (N3 x KA), [A0^2 T; wm^T T] (N3 x KP)
+    static constexpr int B1 = N1 * KA * 4, BY = N3 * KA * 4, BZ = N3 * KP * 4;
+    static constexpr int BIMG = 2 * (B1 + BY + BZ);
+    static constexpr int ZBYTES = ROWS * KP * 4;       // one dz image of a group
+    static constexpr int OFF_Z = (BIMG + 127) / 128 * 128;
+    static constexpr int OFF_E = OFF_Z + G * 2 * ZBYTES;
     static constexpr int OFF_H = OFF_E + G * ROWS * 4;
     static constexpr int OFF_BAR = OFF_H + G * ROWS * 4;
     static constexpr int SMEM = OFF_BAR + 8 * G + 16;
-    static_assert(ACC + NMAX <= GCOLS, "tensor-memory columns of one group");
-    static_assert(L1 <= N1 && L2 <= N2 && L3 <= N3, "read-back beyond the accumulator");
+    static_assert(ACC + (N1 > N3 ? N1 : N3) <= GCOLS, "tensor-memory columns of one group");
+    static_assert(L1 <= N1 && L3 <= N3, "read-back beyond the accumulator");
     static_assert(SMEM <= 227 * 1024, "shared memory");
 };
 
 template <int N>
 struct TcScalars {
-    float b2[Dims<N>::D];
-    float psi_dt[N - 1];
-    float cm;
+    float psi_dt[N - 1];  // (m_a - m_{N-1}) dt / hbar: base angles per unit field
 };
 
 namespace {
 
-__device__ __forceinline__ float tf32_round(float x) { return __uint_as_float(tc::tf32_bits(__float_as_uint(x))); }
+// x = hi + lo exactly: hi is x rounded to TF32 (integer add and mask: the
+// conversion instruction issues on a slower pipe), lo = x - hi in FP32, which
+// the MMA reads as TF32 (its 13 low bits ignored), so hi + lo(TF32) = x up to
+// 2^-21 |x|.
+__device__ __forceinline__ void split_tf32(float x, uint32_t &hi, uint32_t &lo) {
+    hi = tc::tf32_bits(__float_as_uint(x));
+    lo = __float_as_uint(x - __uint_as_float(hi));
+}
 
-// Stage row `row` of an A operand from v[0..n), zero-padded to kx columns (a
-// multiple of 8): hi and lo TF32 parts. TA: into tensor memory at columns
-// t_hi, t_lo of this thread's lane (t_* carry the warp's lane base); else into
-// shared memory (hi image at a, lo image ABYTES later, layout K extent K).
-template <bool TA, int K, int kx, int n, int ABYTES>
+// Stage row `row` of an A operand from v[0..n), then `one` (1.0 at column n
+// when set: the column that carries constant offsets through the product),
+// zero-padded to kx columns (a multiple of 8): hi and lo TF32 parts. TA: into
+// tensor memory at columns t_hi, t_lo of this thread's lane (t_* carry the
+// warp's lane base); else into shared memory (hi image at a, lo image ABYTES
+// later, layout K extent K).
+template <bool TA, int K, int kx, int n, int ABYTES, bool one = false>
 __device__ __forceinline__ void stage_row(unsigned char *a, uint32_t t_hi, uint32_t t_lo, int row, const float *v) {
+    static_assert(n + (one ? 1 : 0) <= kx, "row longer than the staged width");
+    auto split = [&](int k, uint32_t &h, uint32_t &l) {
+        if (k < n) {
+            split_tf32(v[k], h, l);
+        } else {
+            h = (one && k == n) ? 0x3F800000u : 0u;
+            l = 0u;
+        }
+    };
     if constexpr (TA) {
 #pragma unroll
         for (int c = 0; c < kx; c += 8) {
             uint32_t h[8], l[8];
 #pragma unroll
-            for (int e = 0; e < 8; ++e) {
-                const float x = c + e < n ? v[c + e] : 0.0f;
-                const float hx = tf32_round(x);
-                h[e] = __float_as_uint(hx);
-                l[e] = tc::tf32_bits(__float_as_uint(x - hx));
-            }
+            for (int e = 0; e < 8; ++e) split(c + e, h[e], l[e]);
             tc::st_x8(t_hi + c, h);
             tc::st_x8(t_lo + c, l);
         }
@@ -98,17 +107,12 @@ __device__ __forceinline__ void stage_row(unsigned char *a, uint32_t t_hi, uint3
     } else {
 #pragma unroll
         for (int kg = 0; kg < kx / 4; ++kg) {
-            float h[4], l[4];
+            uint32_t h[4], l[4];
 #pragma unroll
-            for (int e = 0; e < 4; ++e) {
-                const int k = kg * 4 + e;
-                const float x = k < n ? v[k] : 0.0f;
-                h[e] = tf32_round(x);
-                l[e] = tf32_round(x - h[e]);
-            }
+            for (int e = 0; e < 4; ++e) split(kg * 4 + e, h[e], l[e]);
             const int off = tc::core_offset(row, kg * 4, K);
-            *reinterpret_cast<float4 *>(a + off) = make_float4(h[0], h[1], h[2], h[3]);
-            *reinterpret_cast<float4 *>(a + ABYTES + off) = make_float4(l[0], l[1], l[2], l[3]);
+            *reinterpret_cast<uint4 *>(a + off) = make_uint4(h[0], h[1], h[2], h[3]);
+            *reinterpret_cast<uint4 *>(a + ABYTES + off) = make_uint4(l[0], l[1], l[2], l[3]);
         }
         tc::fence_async_smem();
     }
@@ -157,15 +161,15 @@ __device__ __forceinline__ void read_cols(uint32_t taddr, float (&v)[cols]) {
 
 }  // namespace
 
-template <int N, bool TA>
+template <int N>
 __global__ void __launch_bounds__(512, 1)
     mln_tc_kernel(const __grid_constant__ BlockArgs<float> a, const __grid_constant__ TcScalars<N> k,
                   const uint4 *__restrict__ bimg, int64_t ntiles) {
-    using S = TcShape<N, TA>;
+    using S = TcShape<N>;
     constexpr int D = S::D, Q = S::Q, P = S::P, G = S::G, ROWS = S::ROWS;
     extern __shared__ __align__(128) unsigned char smem[];
     const int tid = threadIdx.x, g = tid / ROWS, j = tid % ROWS, warp = tid / 32;
-    unsigned char *sA = smem + S::OFF_A + g * 2 * S::ABYTES;
+    unsigned char *sZ = smem + S::OFF_Z + g * 2 * S::ZBYTES;
     float *sE = reinterpret_cast<float *>(smem + S::OFF_E) + g * ROWS;
     float *sH = reinterpret_cast<float *>(smem + S::OFF_H) + g * ROWS;
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem + S::OFF_BAR);
@@ -184,27 +188,55 @@ __global__ void __launch_bounds__(512, 1)
     tc::fence_after_sync();
     const uint32_t tmem = *tslot;
     const uint32_t tg = tmem + static_cast<uint32_t>(g * S::GCOLS);                // group's columns, lane 0
-    const uint32_t tl = tg + (static_cast<uint32_t>((warp % 4) * 32) << 16);      // this warp's lanes
+    const uint32_t lanes = static_cast<uint32_t>((warp % 4) * 32) << 16;          // this warp's lanes
     const uint32_t bar = tc::smem_addr(&bars[g]);
-    // A operand: tensor-memory columns (TA) or shared-memory images
-    const uint32_t a_hi = TA ? tg + S::TA_HI : tc::smem_addr(sA);
-    const uint32_t a_lo = TA ? tg + S::TA_LO : a_hi + S::ABYTES;
+    const uint32_t y_hi = tg + S::Y_HI, y_lo = tg + S::Y_LO, acc = tg + S::ACC;
+    const uint32_t z_hi = tc::smem_addr(sZ), z_lo = z_hi + S::ZBYTES;
     const uint32_t b1h = tc::smem_addr(smem), b1l = b1h + S::B1;
-    const uint32_t b2h = b1l + S::B1, b2l = b2h + S::B2;
-    const uint32_t b3h = b2l + S::B2, b3l = b3h + S::B3;
-    const uint32_t acc = tg + S::ACC, acc_l = tl + S::ACC;
+    const uint32_t byh = b1l + S::B1, byl = byh + S::BY;
+    const uint32_t bzh = byl + S::BY, bzl = bzh + S::BZ;
+    const uint32_t id1 = tc::idesc_tf32(S::N1), id3 = tc::idesc_tf32(S::N3);
     const int bar_id = 1 + g;
     uint32_t phase = 0;
     bool ok = true;
-    // one product: stage A (all threads), issue (thread 0 of the group), wait
-    auto run = [&](auto issue) {
-        tc::fence_before_sync();
-        tc::bar_sync(bar_id, ROWS);
+
+    // z = T^T y: A = y from tensor memory (one thread)
+    auto issue_z = [&] {
+#pragma unroll
+        for (int kb = 0; kb < S::KA / 8; ++kb)
+            tc::mma_tf32_ts(acc, y_lo + kb * 8, tc::smem_desc(b1h + kb * 256, 128, S::KA * 32), id1, kb > 0);
+#pragma unroll
+        for (int kb = 0; kb < S::KA / 8; ++kb)
+            tc::mma_tf32_ts(acc, y_hi + kb * 8, tc::smem_desc(b1l + kb * 256, 128, S::KA * 32), id1, 1u);
+#pragma unroll
+        for (int kb = 0; kb < S::KA / 8; ++kb)
+            tc::mma_tf32_ts(acc, y_hi + kb * 8, tc::smem_desc(b1h + kb * 256, 128, S::KA * 32), id1, 1u);
+    };
+    // [increment ; dP/dt - c'] = [C1, A0^2 T ; wm^T, wm^T T] [y ; dz]: y from
+    // tensor memory, dz from shared memory (one thread)
+    auto issue_inc = [&] {
+        auto part = [&](uint32_t ya, uint32_t yb, uint32_t za, uint32_t zb, bool first) {
+#pragma unroll
+            for (int kb = 0; kb < S::KA / 8; ++kb)
+                tc::mma_tf32_ts(acc, ya + kb * 8, tc::smem_desc(yb + kb * 256, 128, S::KA * 32), id3,
+                                (first && kb == 0) ? 0u : 1u);
+#pragma unroll
+            for (int kb = 0; kb < S::KP / 8; ++kb)
+                tc::mma_tf32(acc, tc::smem_desc(za + kb * 256, 128, S::KP * 32),
+                             tc::smem_desc(zb + kb * 256, 128, S::KP * 32), id3, 1u);
+        };
+        part(y_lo, byh, z_lo, bzh, true);
+        part(y_hi, byl, z_hi, bzl, false);
+        part(y_hi, byh, z_hi, bzh, false);
+    };
+    auto issue = [&](auto f) {
         if (j == 0) {
             tc::fence_after_sync();
-            issue();
+            f();
             tc::mma_commit(bar);
         }
+    };
+    auto wait = [&] {
         ok = tc::mbar_wait(bar, phase) && ok;
         phase ^= 1;
         tc::fence_after_sync();
@@ -239,20 +271,21 @@ __global__ void __launch_bounds__(512, 1)
         const bool e_upd = loaded && j >= 1 && (periodic || (gm > 0 && gm < n - 1));
         const bool mur = !periodic && loaded && gm == n - 2 && j + 1 < L;
         const bool is_src = a.src != nullptr && loaded && gm == a.source_cell;
+        stage_row<true, S::KA, S::KA, D, 0, true>(nullptr, y_hi + lanes, y_lo + lanes, j, y);
+        tc::fence_before_sync();
         tc::bar_sync(bar_id, ROWS);
+        if (a.nsteps > 0) issue(issue_z);
 
         for (int st = 0; st < a.nsteps; ++st) {
             if (h_upd) {
                 h = fma(a.ch, sE[j + 1] - e, h);
                 sH[j] = h;
             }
-            // z = T^T y (plane coordinates)
-            stage_row<TA, S::KA, S::KA, D, S::ABYTES>(sA, a_hi + (tl - tg), a_lo + (tl - tg), j, y);
-            run([&] { issue_product<TA, S::KA>(acc, a_hi, a_lo, S::KA * 32, b1h, b1l, S::KA * 32, tc::idesc_tf32(S::N1)); });
+            wait();
             float z[S::L1];
-            read_cols<S::L1>(acc_l, z);
+            read_cols<S::L1>(acc + lanes, z);
             tc::ld_wait();
-            // dz = (R(phi) - I) z, zero for cells without medium
+            // dz = (R(phi) - I) z with phi from E^n; zero for cells without medium
             float dz[P];
             {
                 float sn[Q], c1[Q];
@@ -263,27 +296,20 @@ __global__ void __launch_bounds__(512, 1)
                     dz[2 * p + 1] = medium ? fma(c1[p], z[2 * p + 1], -(sn[p] * z[2 * p])) : 0.0f;
                 }
             }
-            stage_row<TA, S::KA, S::KP, P, S::ABYTES>(sA, a_hi + (tl - tg), a_lo + (tl - tg), j, dz);
-            run([&] { issue_product<TA, S::KP>(acc, a_hi, a_lo, S::KA * 32, b2h, b2l, S::KP * 32, tc::idesc_tf32(S::N2)); });
-            {
-                float d2[S::L2];
-                read_cols<S::L2>(acc_l, d2);
-                tc::ld_wait();
-#pragma unroll
-                for (int i = 0; i < D; ++i) y[i] = y[i] + d2[i];  // r = y + T dz
-            }
-            stage_row<TA, S::KA, S::KA, D, S::ABYTES>(sA, a_hi + (tl - tg), a_lo + (tl - tg), j, y);
-            run([&] { issue_product<TA, S::KA>(acc, a_hi, a_lo, S::KA * 32, b3h, b3l, S::KA * 32, tc::idesc_tf32(S::N3)); });
+            stage_row<false, S::KP, S::KP, P, S::ZBYTES>(sZ, 0, 0, j, dz);
+            tc::fence_before_sync();
+            tc::bar_sync(bar_id, ROWS);  // dz staged, H^{n+1/2} published
+            issue(issue_inc);
+            wait();
             float dpdt;
             {
                 float d3[S::L3];
-                read_cols<S::L3>(acc_l, d3);
+                read_cols<S::L3>(acc + lanes, d3);
                 tc::ld_wait();
 #pragma unroll
-                for (int i = 0; i < D; ++i) y[i] = medium ? y[i] + (d3[i] + k.b2[i]) : 0.0f;
-                dpdt = medium ? d3[D] + k.cm : 0.0f;
+                for (int i = 0; i < D; ++i) y[i] = medium ? y[i] + d3[i] : 0.0f;
+                dpdt = medium ? d3[D] : 0.0f;
             }
-
             float en = e;
             if (e_upd) en = fma(a.ca, e, a.cb * fma(h - sH[j - 1], a.inv_dx, -dpdt));
             float e_mur = 0.0f;
@@ -301,8 +327,11 @@ __global__ void __launch_bounds__(512, 1)
             }
             e = en;
             if (loaded && !(!periodic && gm == n - 1)) sE[j] = e;
-            tc::bar_sync(bar_id, ROWS);
+            stage_row<true, S::KA, S::KA, D, 0, true>(nullptr, y_hi + lanes, y_lo + lanes, j, y);
+            tc::fence_before_sync();
+            tc::bar_sync(bar_id, ROWS);  // E^{n+1} published, y staged for the next step
             if (!periodic && loaded && gm == n - 1) e = sE[j];
+            if (st + 1 < a.nsteps) issue(issue_z);
         }
 
         const bool interior = loaded && j >= a.halo && j < a.halo + static_cast<int>(t1 - t0);
@@ -419,36 +448,53 @@ void append_image(std::vector<unsigned char> &out, int R, int K, F f) {
 
 template <int N>
 void pack_tc_t(const Setup &s, double dt, std::vector<unsigned char> &img, std::vector<unsigned char> &scal) {
-    using S = TcShape<N, true>;
+    using S = TcShape<N>;
     constexpr int D = S::D, P = S::P;
+    // A0^2 T = T + C1 T and wm^T T, in FP64
+    std::vector<double> A2T(static_cast<size_t>(D) * P), wT(P);
+    for (int i = 0; i < D; ++i)
+        for (int p = 0; p < P; ++p) {
+            double acc = s.T[i * D + p];
+            for (int l = 0; l < D; ++l) acc += s.C1[i * D + l] * s.T[l * D + p];
+            A2T[i * P + p] = acc;
+        }
+    for (int p = 0; p < P; ++p) {
+        double acc = 0.0;
+        for (int i = 0; i < D; ++i) acc += s.wm[i] * s.T[i * D + p];
+        wT[p] = acc;
+    }
     img.clear();
-    // B1 (N1 x KA): row p, column k = T[k][p] (plane columns p < P)
+    // B1 (N1 x KA): row p, column k = T[k][p] (plane columns p < P; zero at the constant column)
     append_image(img, S::N1, S::KA, [&](int p, int k) { return (p < P && k < D) ? s.T[k * D + p] : 0.0; });
-    // B2 (N2 x KP): row i, column p = T[i][p]
-    append_image(img, S::N2, S::KP, [&](int i, int p) { return (i < D && p < P) ? s.T[i * D + p] : 0.0; });
-    // B3 (N3 x KA): rows i < D = A0^2 - I, row D = A0^T w
+    // BY (N3 x KA): rows i < D = [C1 | b2] (C1 = A0^2 - I, b2 = A0 b + b at the
+    // constant column D), row D = [wm | c'] (wm = A0^T w)
     append_image(img, S::N3, S::KA, [&](int i, int k) {
-        if (k >= D) return 0.0;
-        if (i < D) return s.C1[i * D + k];
-        return i == D ? s.wm[k] : 0.0;
+        if (k > D) return 0.0;
+        if (i < D) return k < D ? s.C1[i * D + k] : s.b2[i];
+        if (i == D) return k < D ? s.wm[k] : s.cm;
+        return 0.0;
+    });
+    // BZ (N3 x KP): rows i < D = A0^2 T (plane columns), row D = wm^T T
+    append_image(img, S::N3, S::KP, [&](int i, int p) {
+        if (p >= P) return 0.0;
+        if (i < D) return A2T[i * P + p];
+        return i == D ? wT[p] : 0.0;
     });
     TcScalars<N> t;
     std::memset(&t, 0, sizeof(t));
-    for (int i = 0; i < D; ++i) t.b2[i] = static_cast<float>(s.b2[i]);
     for (int a = 0; a < N - 1; ++a) t.psi_dt[a] = static_cast<float>(s.psi[a] * dt);
-    t.cm = static_cast<float>(s.cm);
     scal.resize(sizeof(t));
     std::memcpy(scal.data(), &t, sizeof(t));
 }
 
-template <int N, bool TA>
+template <int N>
 cudaError_t launch_tc_t(const BlockArgs<float> &a, const std::vector<unsigned char> &scal, const void *bimg,
                         int sms, cudaStream_t st) {
-    using S = TcShape<N, TA>;
+    using S = TcShape<N>;
     if (a.tile + 2 * a.halo != S::ROWS || scal.size() != sizeof(TcScalars<N>)) return cudaErrorInvalidValue;
     TcScalars<N> k;
     std::memcpy(&k, scal.data(), sizeof(k));
-    auto kern = mln_tc_kernel<N, TA>;
+    auto kern = mln_tc_kernel<N>;
     static bool attr_set = false;  // per instantiation; the attribute is per device function
     if (!attr_set) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, S::SMEM);
@@ -466,7 +512,7 @@ cudaError_t launch_tc_t(const BlockArgs<float> &a, const std::vector<unsigned ch
 
 bool tc_supported(int N) { return N == 5 || N == 6; }
 
-int tc_rows() { return TcShape<6, true>::ROWS; }
+int tc_rows() { return TcShape<6>::ROWS; }
 
 bool pack_tc(const Setup &s, double dt, std::vector<unsigned char> &img, std::vector<unsigned char> &scal) {
     switch (s.N) {
@@ -476,11 +522,11 @@ bool pack_tc(const Setup &s, double dt, std::vector<unsigned char> &img, std::ve
     }
 }
 
-cudaError_t launch_tc(int N, bool tmem_a, const BlockArgs<float> &a, const std::vector<unsigned char> &scal,
-                      const void *bimg, int sms, cudaStream_t st) {
+cudaError_t launch_tc(int N, const BlockArgs<float> &a, const std::vector<unsigned char> &scal, const void *bimg,
+                      int sms, cudaStream_t st) {
     switch (N) {
-    case 5: return tmem_a ? launch_tc_t<5, true>(a, scal, bimg, sms, st) : launch_tc_t<5, false>(a, scal, bimg, sms, st);
-    case 6: return tmem_a ? launch_tc_t<6, true>(a, scal, bimg, sms, st) : launch_tc_t<6, false>(a, scal, bimg, sms, st);
+    case 5: return launch_tc_t<5>(a, scal, bimg, sms, st);
+    case 6: return launch_tc_t<6>(a, scal, bimg, sms, st);
     default: return cudaErrorInvalidValue;
     }
 }
@@ -530,10 +576,10 @@ cudaError_t tc_product(int nc, int kc, bool tmem_a, const float *A, const double
     return cudaErrorInvalidValue;
 }
 
-int tc_smem_bytes(int N, bool tmem_a) {
+int tc_smem_bytes(int N) {
     switch (N) {
-    case 5: return tmem_a ? TcShape<5, true>::SMEM : TcShape<5, false>::SMEM;
-    case 6: return tmem_a ? TcShape<6, true>::SMEM : TcShape<6, false>::SMEM;
+    case 5: return TcShape<5>::SMEM;
+    case 6: return TcShape<6>::SMEM;
     default: return 0;
     }
 }

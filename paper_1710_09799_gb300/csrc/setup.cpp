@@ -430,18 +430,17 @@ mln_status validate(const mln_params &p, std::string &err) {
         err = "block_steps must be in [0, 64]";
         return MLN_EINVAL;
     }
-    if (p.kernel < MLN_KERNEL_AUTO || p.kernel > MLN_KERNEL_TENSOR_SMEM) {
-        err = "kernel must be MLN_KERNEL_AUTO, MLN_KERNEL_REGISTER, MLN_KERNEL_SPARSE, MLN_KERNEL_JIT, "
-              "MLN_KERNEL_TENSOR or MLN_KERNEL_TENSOR_SMEM";
+    if (p.kernel < MLN_KERNEL_AUTO || p.kernel > MLN_KERNEL_TENSOR) {
+        err = "kernel must be MLN_KERNEL_AUTO, MLN_KERNEL_REGISTER, MLN_KERNEL_SPARSE, MLN_KERNEL_JIT or "
+              "MLN_KERNEL_TENSOR";
         return MLN_EINVAL;
     }
-    if ((p.kernel == MLN_KERNEL_TENSOR || p.kernel == MLN_KERNEL_TENSOR_SMEM) &&
-        (p.precision != MLN_FP32 || p.form != MLN_FORM_MERGED || p.N < 5)) {
-        err = "the tensor-core kernels need MLN_FP32, MLN_FORM_MERGED and N = 5 or 6";
+    if (p.kernel == MLN_KERNEL_TENSOR && (p.precision != MLN_FP32 || p.form != MLN_FORM_MERGED || p.N < 5)) {
+        err = "MLN_KERNEL_TENSOR needs MLN_FP32, MLN_FORM_MERGED and N = 5 or 6";
         return MLN_EINVAL;
     }
-    if ((p.kernel == MLN_KERNEL_TENSOR || p.kernel == MLN_KERNEL_TENSOR_SMEM) && p.block_steps > 32) {
-        err = "the tensor-core kernels fuse at most 32 steps per launch";
+    if (p.kernel == MLN_KERNEL_TENSOR && p.block_steps > 32) {
+        err = "MLN_KERNEL_TENSOR fuses at most 32 steps per launch";
         return MLN_EINVAL;
     }
     if (p.kernel == MLN_KERNEL_JIT && p.form != MLN_FORM_MERGED) {

@@ -149,7 +149,7 @@ mln_status run_static(const mln_params &p, const mln::Setup &s, void *d_state, v
     a.inv_dx = static_cast<R>(1.0 / p.dx);
     a.kappa = static_cast<R>((cv * p.dt - p.dx) / (cv * p.dt + p.dx));
     void *st[2] = {d_state, st_alt}, *E[2] = {Ez, E_alt}, *H[2] = {Hy, H_alt};
-    const size_t smem = 2 * static_cast<size_t>(threads) * sizeof(R);
+    const size_t smem = mln::field_smem<R>(threads);
     int cur = 0;
     for (int64_t done = 0; done < n_steps;) {
         int ns = static_cast<int>(n_steps - done < K ? n_steps - done : K);

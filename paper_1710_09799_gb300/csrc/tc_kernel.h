@@ -16,13 +16,14 @@ bool tc_supported(int N);
 // Rows (cells incl. halo) of one tile: the MMA M.
 int tc_rows();
 // Dynamic shared memory of one CTA.
-int tc_smem_bytes(int N, bool tmem_a);
+int tc_smem_bytes(int N);
 // B-operand image (uploaded to the device once) and the scalar constants.
 bool pack_tc(const Setup &s, double dt, std::vector<unsigned char> &img, std::vector<unsigned char> &scal);
 // One launch of a.nsteps steps; a.tile + 2 a.halo must equal tc_rows().
-cudaError_t launch_tc(int N, bool tmem_a, const BlockArgs<float> &a, const std::vector<unsigned char> &scal,
-                      const void *bimg, int sms, cudaStream_t st);
-// C (128 x nc) = A (128 x kc) B (nc x kc)^T through the kernel's product path.
+cudaError_t launch_tc(int N, const BlockArgs<float> &a, const std::vector<unsigned char> &scal, const void *bimg,
+                      int sms, cudaStream_t st);
+// C (128 x nc) = A (128 x kc) B (nc x kc)^T through the kernel's product
+// path, with A staged in tensor memory (tmem_a) or in shared memory.
 cudaError_t tc_product(int nc, int kc, bool tmem_a, const float *A, const double *B, float *C, std::string &err);
 
 }  // namespace mln

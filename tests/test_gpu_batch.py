@@ -1,5 +1,5 @@
 """Batched grids (mln_batch_*): many independent grids of mixed N, lengths and
-boundaries in one launch per group of fused steps, replayed from a CUDA graph.
+boundaries, one launch per N for every group of fused steps, replayed from a CUDA graph.
 
 Every cell of every grid does the same arithmetic as in a single-grid run, so
 the batch must reproduce the single-grid results bit for bit; one grid is

@@ -1,9 +1,10 @@
-"""Tensor-core cell model (MLN_KERNEL_TENSOR, MLN_KERNEL_TENSOR_SMEM): the
-three dense products of the merged step (Eqs. 23, 25-26, 17) on tcgen05 MMAs
-with 3 x TF32 operands, FP32 state, for N = 5 and 6.
+"""Tensor-core cell model (MLN_KERNEL_TENSOR): the dense products of the
+merged step (Eqs. 23, 25-26, 17), regrouped into two per step, on tcgen05
+MMAs with 3 x TF32 operands, FP32 state, for N = 5 and 6.
 
-* the product path alone (mln_tc_product) against FP64 numpy, with a bound
-  that a single TF32 product (or a transposed or mis-laid operand) misses;
+* the product path alone (mln_tc_product, A from tensor memory as for y and
+  from shared memory as for dz) against FP64 numpy, with a bound that a
+  single TF32 product (or a transposed or mis-laid operand) misses;
 * six-level runs against the FP64 oracle at the FP32 tolerance, and against
   the FP32 register model;
 * a five-level periodic ring against the oracle;
@@ -21,7 +22,6 @@ pytestmark = pytest.mark.gpu
 
 FP32_E_PER_KSTEP = 2e-3
 FP32_POP_PER_KSTEP = 2e-5
-KERNELS = ["tensor", "tensor_smem"]
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -54,15 +54,15 @@ def test_product_path_against_fp64(nc, kc, a_in_tmem):
     ref = A.astype(np.float64) @ B.T
     scale = np.abs(A).astype(np.float64) @ np.abs(B).T
     err = np.abs(C - ref)
-    # 3 x TF32 with FP32 accumulation: a few units of 2^-22 of sum |a||b|
+    # 3 x TF32 with FP32 accumulation: a few units of 2^-21 of sum |a||b|
     assert np.all(err <= 2.0 ** -19 * scale), float((err / scale).max())
     # a single TF32 product is off by ~2^-11 relative: the bound tells them apart
     hi_only = tf32(A).astype(np.float64) @ tf32(B.astype(np.float32)).astype(np.float64).T
     assert np.abs(hi_only - ref).max() > 2.0 ** -16 * scale.max()
 
 
-@pytest.mark.parametrize("kernel", KERNELS)
-def test_six_level_against_oracle(orc, kernel):
+def test_six_level_against_oracle(orc):
+    kernel = "tensor"
     p = W.six_level_pulse(n_cells=4096, n_steps=1000)
     st, _ = orc.run(p, n_steps=p.n_steps)
     E, H, rho, s = gpu_run(p, p.n_steps, "fp32", "merged", kernel=kernel)
@@ -73,16 +73,16 @@ def test_six_level_against_oracle(orc, kernel):
     assert e_err < FP32_E_PER_KSTEP and p_err < FP32_POP_PER_KSTEP
 
 
-@pytest.mark.parametrize("kernel", KERNELS)
-def test_six_level_close_to_fp32_register_model(kernel):
+def test_six_level_close_to_fp32_register_model():
+    kernel = "tensor"
     p = W.six_level_pulse(n_cells=600, n_steps=200, t0=15e-15, fwhm=10e-15)
     E0, H0, r0, _ = gpu_run(p, p.n_steps, "fp32", "merged", kernel="register")
     E1, H1, r1, _ = gpu_run(p, p.n_steps, "fp32", "merged", kernel=kernel)
     assert rel_inf(E1, E0) < 1e-4 and np.abs(r1 - r0).max() < 1e-5
 
 
-@pytest.mark.parametrize("kernel", KERNELS)
-def test_five_level_ring_against_oracle(orc, kernel):
+def test_five_level_ring_against_oracle(orc):
+    kernel = "tensor"
     p = W.multi_level_ring(5, n_cells=1000, n_steps=500, seed=3)
     st, _ = orc.run(p, n_steps=p.n_steps)
     E, H, rho, _ = gpu_run(p, p.n_steps, "fp32", "merged", kernel=kernel)
@@ -99,10 +99,6 @@ def test_launch_shape_does_not_change_the_bits():
         out = gpu_run(p, p.n_steps, "fp32", "merged", kernel="tensor", block_steps=bs, chunks=chunks)
         for a, b in zip(out[:3], ref[:3]):
             assert np.array_equal(a, b), bs
-    # the shared-memory A operand gives the same products
-    out = gpu_run(p, p.n_steps, "fp32", "merged", kernel="tensor_smem", block_steps=8)
-    for a, b in zip(out[:3], ref[:3]):
-        assert np.array_equal(a, b)
 
 
 def test_autotune_keeps_state():
