@@ -265,14 +265,14 @@ def time_device(p, precision, form, seg, steps, warmup, block_steps, tile_cells,
                 kernel=kern)
 
 
-def time_batch(precision, seg, steps, warmup, sampler=None):
+def time_batch(precision, seg, steps, warmup, sampler=None, kernel="auto"):
     """Batched workload: every bench step advances all devices by seg steps (one
     graph launch); returns the same fields as time_device."""
     import torch
     from paper_1710_09799_gb300 import mln
     total = (warmup + steps) * seg
     devs = W.batched_devices(n_steps=total)
-    pars = [make_params(d, precision, "merged", kernel="register") for d in devs]
+    pars = [make_params(d, precision, "merged", kernel=kernel) for d in devs]
     srcs = [d.source_samples(0, total) for d in devs]
     b = mln.Batch(pars, [d.e_init() for d in devs], srcs, total)
     shape = b.autotune(3)
@@ -303,10 +303,11 @@ def time_batch(precision, seg, steps, warmup, sampler=None):
     for i, d in enumerate(devs):
         f_med, f_cell, _, _ = mln.mln_work_per_step(mln.mln_batch_context(b.b, i))
         flops += d.n_medium * f_med + d.n_cells * f_cell
+    kernels = {N: b.kernel_in_use(N) for N in (2, 3, 4)}
     items = b.shape[2]
     b.close()
     return dict(ms=ms, ms_local=ms, launches=launches, shape=(shape[0], shape[1], items), clocks=clocks,
-                cells=cells, flops_per_step=flops, devices=len(devs))
+                cells=cells, flops_per_step=flops, devices=len(devs), kernels=kernels)
 
 
 def time_e2e(p, precision, form, seg, steps):
@@ -443,7 +444,8 @@ def run_batched(args, ws, rank, local):
     vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
     smi_index = int(vis.split(",")[local]) if vis and vis.split(",")[local].isdigit() else local
     prec = args.precision
-    r = time_batch(prec, args.seg, args.steps, args.warmup, ClockSampler(smi_index))
+    r = time_batch(prec, args.seg, args.steps, args.warmup, ClockSampler(smi_index),
+                   kernel=args.kernel if args.kernel in ("register", "jit") else "auto")
     total_s = max_over_ranks(ws, r["ms"]) / 1e3
     value = ws * r["cells"] * args.seg * args.steps / total_s
     per_launch_s = r["ms"] / 1e3 / max(r["launches"], 1)
@@ -455,9 +457,11 @@ def run_batched(args, ws, rank, local):
         "dtype": "f64" if prec == "fp64" else "f32", "data": "synthetic (seeded devices)",
         "config": {"workload": WORKLOADS["batched"], "devices": r["devices"], "cells": r["cells"],
                    "time_steps_per_step": args.seg, "block_steps": r["shape"][0], "tile_cells": r["shape"][1],
-                   "work_items_per_launch": r["shape"][2], "l2": "flushed between steps (256 MiB write)"},
+                   "work_items_per_launch": r["shape"][2], "cell_model_by_N": r["kernels"],
+                   "l2": "flushed between steps (256 MiB write)"},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                     "traffic": None, "kernel": "mln_batch_kernel"},
+                     "traffic": None,
+                     "kernel": "mln_jit_batch" if "jit" in r["kernels"].values() else "mln_batch_kernel"},
         "gpu_launches": r["launches"], "clocks": r["clocks"],
     }
     if rank == 0:

@@ -303,7 +303,7 @@ mln_status mln_adjoint(mln_ctx *ctx, int64_t n_steps, const double *src, int64_t
  * call are captured into a CUDA graph and replayed as one graph launch.
  *
  * mln_batch_create: count grids, params[i] as for mln_create with one common
- * precision, form MLN_FORM_MERGED, N <= 4 and kernel AUTO or REGISTER;
+ * precision, form MLN_FORM_MERGED, N <= 4 and kernel AUTO, REGISTER or JIT;
  * d_state[i], Ez[i], Hy[i] caller-owned device buffers as for mln_create;
  * src NULL or count device pointers to src_len source samples per grid
  * (sample k applies to the batch's step k; NULL entries for grids without a
@@ -323,6 +323,16 @@ mln_status mln_adjoint(mln_ctx *ctx, int64_t n_steps, const double *src, int64_t
  * mln_batch_shape: steps per launch, tile, work items (tiles of every grid,
  * over the per-N launches of one step of K), kernel launches queued so far.
  * mln_batch_error: message of the last failed call on the batch.
+ * mln_batch_kernel_in_use: the cell model of the batch's N-level grids:
+ * MLN_KERNEL_JIT (a kernel compiled at mln_batch_create for the union of the
+ * non-zero entries of those grids' constant matrices, each grid's constants
+ * staged in shared memory and, when they fit, held in registers; the default
+ * when NVRTC is available and no grid asks for MLN_KERNEL_REGISTER) or
+ * MLN_KERNEL_REGISTER (dense products, padded constants in shared memory);
+ * -1 if the batch has no grid with N levels. Both give the register model's
+ * bits.
+ * mln_batch_kernel_source: host only; the CUDA source that the batch with
+ * these params would compile for its N-level grids (as mln_kernel_source).
  */
 typedef struct mln_batch mln_batch;
 mln_status mln_batch_create(int32_t count, const mln_params *params, void *const *d_state, void *const *Ez,
@@ -335,6 +345,9 @@ mln_ctx *mln_batch_context(mln_batch *b, int32_t i);
 mln_status mln_batch_shape(const mln_batch *b, int32_t *block_steps, int32_t *tile_cells, int64_t *items,
                            int64_t *launches);
 const char *mln_batch_error(const mln_batch *b);
+int32_t mln_batch_kernel_in_use(const mln_batch *b, int32_t N);
+mln_status mln_batch_kernel_source(int32_t count, const mln_params *params, int32_t N, char *buf, size_t cap,
+                                   size_t *len);
 void mln_batch_destroy(mln_batch *b);
 
 /* Free the context (NULL-safe). Caller buffers are not touched. */

@@ -14,15 +14,11 @@
 
 #include "ctx.h"
 #include "dispatch.cuh"
+#include "jit.h"
 #include "mln.h"
 #include "setup.h"
 
 namespace mln {
-
-// Shared-memory room for one grid's constants (the padded merged-form
-// constants of N = 4 in FP64 are 6.0 KB).
-constexpr int kBatchConstsMax = 8192;
-constexpr int kBatchMaxN = 4;
 
 // Merged-form constants of one grid with every row padded to a whole number
 // of 16-byte vectors, and T also stored transposed, so that each product
@@ -114,23 +110,6 @@ struct PaddedCell {
     __device__ __forceinline__ void end_step() {}
 };
 
-template <typename R>
-struct BatchGrid {
-    R *E[2], *H[2], *S[2];   // buffer set 0 (caller's) and 1 (context's)
-    const double *src;       // source samples from the batch's step 0, or nullptr
-    unsigned int *flags;
-    int64_t n_cells, mb, me, stride, source_cell;
-    int32_t N, boundary, source_kind, consts_off, consts_bytes, pad_;
-    R ch, ca, cb, inv_dx, kappa;
-};
-
-struct BatchItem {
-    int32_t grid, tile;
-};
-
-// Threads per block of the batched kernels (tile + 2 K <= this).
-constexpr int kBatchThreads = 256;
-
 // One block per work item (grid, tile) of the grids with N levels; one kernel
 // per N, so that each gets the registers of its own cell size. The grid's
 // constants are staged in shared memory (padded rows read with 16-byte
@@ -140,40 +119,8 @@ __global__ void __launch_bounds__(kBatchThreads, 1)
     mln_batch_kernel(const BatchGrid<R> *__restrict__ grids, const BatchItem *__restrict__ items,
                      const unsigned char *__restrict__ consts, int parity, int nsteps, int halo, int tile,
                      int64_t step_offset) {
-    using K = PaddedConsts<N, R>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const BatchItem it = items[blockIdx.x];
-    const BatchGrid<R> &g = grids[it.grid];
-    for (int o = threadIdx.x * 16; o < g.consts_bytes; o += blockDim.x * 16)
-        *reinterpret_cast<uint4 *>(smem_raw + o) = *reinterpret_cast<const uint4 *>(consts + g.consts_off + o);
-    __syncthreads();
-    BlockArgs<R> a;
-    a.E_in = g.E[parity];
-    a.H_in = g.H[parity];
-    a.s_in = g.S[parity];
-    a.E_out = g.E[parity ^ 1];
-    a.H_out = g.H[parity ^ 1];
-    a.s_out = g.S[parity ^ 1];
-    a.src = g.src ? g.src + step_offset : nullptr;
-    a.flags = g.flags;
-    a.n_cells = g.n_cells;
-    a.mb = g.mb;
-    a.me = g.me;
-    a.stride = g.stride;
-    a.source_cell = g.source_cell;
-    a.nsteps = nsteps;
-    a.halo = halo;
-    a.tile = tile;
-    a.boundary = g.boundary;
-    a.source_kind = g.source_kind;
-    a.pad_ = 0;
-    a.ch = g.ch;
-    a.ca = g.ca;
-    a.cb = g.cb;
-    a.inv_dx = g.inv_dx;
-    a.kappa = g.kappa;
-    block_body<N, R, PaddedCell<N, R>>(a, *reinterpret_cast<const K *>(smem_raw), it.tile,
-                                       smem_raw + kBatchConstsMax);
+    batch_body<N, R, PaddedCell<N, R>>(grids, items, consts, parity, nsteps, halo, tile, step_offset, smem_raw);
 }
 
 }  // namespace mln
@@ -190,6 +137,10 @@ struct mln_batch {
     void *d_grids = nullptr, *d_items = nullptr, *d_consts = nullptr;
     int64_t n_items = 0;
     int64_t item_off[mln::kBatchMaxN + 1] = {}, item_cnt[mln::kBatchMaxN + 1] = {};  // work items by N
+    // per N: run-time compiled kernel over the union sparsity pattern (or
+    // nullptr: the padded-constant kernel)
+    void *jit[mln::kBatchMaxN + 1] = {};
+    mln::BatchPattern pat[mln::kBatchMaxN + 1];
     // captured launch sequences, by step count
     std::map<int64_t, cudaGraphExec_t> graphs;
     std::string err;
@@ -279,8 +230,14 @@ mln_status build_tables(mln_batch *b) {
         g.boundary = c->p.boundary;
         g.source_kind = c->p.source_kind;
         std::vector<unsigned char> padded;
-        if (!pad_consts<R>(c->p.N, c->consts, padded)) {
+        if (b->jit[c->p.N]) {
+            mln::batch_pack(b->pat[c->p.N], c->s, c->p.dt, sizeof(R) == 4, padded);
+        } else if (!pad_consts<R>(c->p.N, c->consts, padded)) {
             b->err = "batch: no padded constants for this N";
+            return MLN_EUNSUPPORTED;
+        }
+        if (padded.size() > static_cast<size_t>(mln::kBatchConstsMax)) {
+            b->err = "batch: constants of grid " + std::to_string(i) + " exceed the shared-memory room";
             return MLN_EUNSUPPORTED;
         }
         g.consts_off = static_cast<int32_t>(blob.size());
@@ -330,6 +287,10 @@ cudaError_t launch_batch_n(mln_batch *b, int parity, int nsteps, int64_t step_of
     if (b->item_cnt[N] == 0) return cudaSuccess;
     // at most 8 KB + 4 x 256 x 8 B = 16 KB: below the 48 KB default, no attribute needed
     const size_t smem = batch_smem<R>(b->threads);
+    if (b->jit[N])
+        return mln::jit_launch_batch(b->jit[N], b->d_grids, static_cast<const mln::BatchItem *>(b->d_items) + b->item_off[N],
+                                     b->d_consts, parity, nsteps, b->K, b->tile, step_offset,
+                                     static_cast<unsigned>(b->item_cnt[N]), b->threads, smem, b->stream);
     mln::mln_batch_kernel<N, R><<<static_cast<unsigned>(b->item_cnt[N]), b->threads, smem, b->stream>>>(
         static_cast<const mln::BatchGrid<R> *>(b->d_grids),
         static_cast<const mln::BatchItem *>(b->d_items) + b->item_off[N],
@@ -445,9 +406,9 @@ mln_status mln_batch_create(int32_t count, const mln_params *params, void *const
     for (int32_t i = 0; i < count; ++i) {
         const mln_params &p = params[i];
         if (p.precision != params[0].precision || p.form != MLN_FORM_MERGED || p.N > mln::kBatchMaxN ||
-            p.kernel == MLN_KERNEL_SPARSE) {
-            mln::create_error() = "batch grids need one precision, MLN_FORM_MERGED, N <= 4 and the register kernel "
-                                  "(grid " + std::to_string(i) + ")";
+            (p.kernel != MLN_KERNEL_AUTO && p.kernel != MLN_KERNEL_REGISTER && p.kernel != MLN_KERNEL_JIT)) {
+            mln::create_error() = "batch grids need one precision, MLN_FORM_MERGED, N <= 4 and kernel AUTO, "
+                                  "REGISTER or JIT (grid " + std::to_string(i) + ")";
             return MLN_EINVAL;
         }
         if (p.source_kind != MLN_SRC_NONE && src_len > 0 && (!src || !src[i])) {
@@ -480,6 +441,36 @@ mln_status mln_batch_create(int32_t count, const mln_params *params, void *const
         }
         b->ctx.push_back(c);
         b->src.push_back(src && src_len > 0 ? src[i] : nullptr);
+    }
+    // Cell model per N: the run-time compiled kernel over the union sparsity
+    // pattern of that N's grids unless a grid asks for the register model
+    // (MLN_KERNEL_REGISTER); MLN_KERNEL_JIT makes its absence an error.
+    bool want_jit = true, need_jit = false;
+    for (int32_t i = 0; i < count; ++i) {
+        want_jit = want_jit && params[i].kernel != MLN_KERNEL_REGISTER;
+        need_jit = need_jit || params[i].kernel == MLN_KERNEL_JIT;
+    }
+    std::string why;
+    if (want_jit && mln::jit_available(&why)) {
+        const bool fp32 = b->precision == MLN_FP32;
+        for (mln_ctx *c : b->ctx) mln::batch_pattern_add(b->pat[c->p.N], c->s, fp32);
+        for (int N = 2; N <= mln::kBatchMaxN; ++N) {
+            if (b->pat[N].N == 0) continue;
+            std::string log;
+            if (mln::jit_compile(mln::jit_batch_source(b->pat[N], fp32), &b->jit[N], log, "mln_jit_batch") !=
+                cudaSuccess) {
+                b->jit[N] = nullptr;
+                why = log;
+            }
+        }
+    }
+    if (need_jit) {
+        for (mln_ctx *c : b->ctx)
+            if (!b->jit[c->p.N]) {
+                mln::create_error() = "run-time compiled batch kernel unavailable: " + why;
+                mln_batch_destroy(b);
+                return MLN_EUNSUPPORTED;
+            }
     }
     b->K = 16;
     b->tile = mln::kBatchThreads - 2 * b->K;
@@ -585,5 +576,44 @@ mln_status mln_batch_shape(const mln_batch *b, int32_t *block_steps, int32_t *ti
 }
 
 const char *mln_batch_error(const mln_batch *b) { return b ? b->err.c_str() : ""; }
+
+int32_t mln_batch_kernel_in_use(const mln_batch *b, int32_t N) {
+    if (!b || N < 2 || N > mln::kBatchMaxN || b->item_cnt[N] == 0) return -1;
+    return b->jit[N] ? MLN_KERNEL_JIT : MLN_KERNEL_REGISTER;
+}
+
+mln_status mln_batch_kernel_source(int32_t count, const mln_params *params, int32_t N, char *buf, size_t cap,
+                                   size_t *len) {
+    if (count < 1 || !params || N < 2 || N > mln::kBatchMaxN) {
+        mln::create_error() = "invalid arguments";
+        return MLN_EINVAL;
+    }
+    mln::BatchPattern pat;
+    bool fp32 = params[0].precision == MLN_FP32;
+    for (int32_t i = 0; i < count; ++i) {
+        if (params[i].N != N) continue;
+        std::string err;
+        mln::Setup s;
+        mln_status st = mln::validate(params[i], err);
+        if (st == MLN_OK) st = mln::build_setup(params[i], s, err);
+        if (st != MLN_OK) {
+            mln::create_error() = "grid " + std::to_string(i) + ": " + err;
+            return st;
+        }
+        mln::batch_pattern_add(pat, s, fp32);
+    }
+    if (pat.N == 0) {
+        mln::create_error() = "no grid with this N";
+        return MLN_EINVAL;
+    }
+    const std::string src = mln::jit_batch_source(pat, fp32);
+    if (len) *len = src.size();
+    if (buf && cap > 0) {
+        const size_t k = std::min(cap - 1, src.size());
+        std::memcpy(buf, src.data(), k);
+        buf[k] = '\0';
+    }
+    return MLN_OK;
+}
 
 }  // extern "C"

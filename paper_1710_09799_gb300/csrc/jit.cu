@@ -187,6 +187,147 @@ std::string jit_merged_source(const Setup &s, double dt, bool fp32) {
     return o.str();
 }
 
+void batch_pattern_add(BatchPattern &pat, const Setup &s, bool fp32) {
+    const int D = s.D, P = 2 * s.q;
+    if (pat.N == 0) {
+        pat.N = s.N;
+        pat.tt.assign(static_cast<size_t>(P) * D, 0);
+        pat.t.assign(static_cast<size_t>(D) * P, 0);
+        pat.wm.assign(D, 0);
+        pat.c1.assign(static_cast<size_t>(D) * D, 0);
+    }
+    for (int k = 0; k < P; ++k)
+        for (int i = 0; i < D; ++i) pat.tt[k * D + i] |= nz(s.T[i * D + k], fp32);
+    for (int i = 0; i < D; ++i)
+        for (int p = 0; p < P; ++p) pat.t[i * P + p] |= nz(s.T[i * D + p], fp32);
+    for (int i = 0; i < D; ++i) pat.wm[i] |= nz(s.wm[i], fp32);
+    for (int i = 0; i < D * D; ++i) pat.c1[i] |= nz(s.C1[i], fp32);
+}
+
+// The constants of the batched step in their order of use: f(value) for each.
+// T^T plane rows, psi dt, T plane columns, c', wm, then per row of C1: b2_i
+// and the row's entries. Only the entries in the pattern appear.
+template <typename F>
+void batch_walk(const BatchPattern &pat, const Setup *s, double dt, F f) {
+    const int N = pat.N, D = N * N - 1, P = N * (N - 1);
+    auto v = [&](double x) { return s ? x : 0.0; };
+    for (int k = 0; k < P; ++k)
+        for (int i = 0; i < D; ++i)
+            if (pat.tt[k * D + i]) f(v(s ? s->T[i * D + k] : 0));
+    for (int a = 0; a < N - 1; ++a) f(v(s ? s->psi[a] * dt : 0));
+    for (int i = 0; i < D; ++i)
+        for (int p = 0; p < P; ++p)
+            if (pat.t[i * P + p]) f(v(s ? s->T[i * D + p] : 0));
+    f(v(s ? s->cm : 0));
+    for (int i = 0; i < D; ++i)
+        if (pat.wm[i]) f(v(s ? s->wm[i] : 0));
+    for (int i = 0; i < D; ++i) {
+        f(v(s ? s->b2[i] : 0));
+        for (int j = 0; j < D; ++j)
+            if (pat.c1[i * D + j]) f(v(s ? s->C1[i * D + j] : 0));
+    }
+}
+
+int batch_consts_count(const BatchPattern &pat) {
+    int n = 0;
+    batch_walk(pat, nullptr, 0.0, [&](double) { ++n; });
+    return n;
+}
+
+void batch_pack(const BatchPattern &pat, const Setup &s, double dt, bool fp32, std::vector<unsigned char> &out) {
+    out.clear();
+    batch_walk(pat, &s, dt, [&](double x) {
+        if (fp32) {
+            const float f = static_cast<float>(x);
+            const unsigned char *b = reinterpret_cast<const unsigned char *>(&f);
+            out.insert(out.end(), b, b + 4);
+        } else {
+            const unsigned char *b = reinterpret_cast<const unsigned char *>(&x);
+            out.insert(out.end(), b, b + 8);
+        }
+    });
+    out.resize((out.size() + 15) / 16 * 16, 0);
+}
+
+std::string jit_batch_source(const BatchPattern &pat, bool fp32) {
+    const int N = pat.N, D = N * N - 1, P = N * (N - 1);
+    const char *R = fp32 ? "float" : "double";
+    const int nc = batch_consts_count(pat);
+    const int words = nc * (fp32 ? 1 : 2);
+    const bool regs = words <= 96;  // constants in registers when they fit, else read from shared memory
+    const int ncp = (nc * (fp32 ? 4 : 8) + 15) / 16 * 16 / (fp32 ? 4 : 8);
+    int idx = 0;
+    auto C = [&]() { return std::string(regs ? "c[" : "k.c[") + std::to_string(idx++) + "]"; };
+    std::ostringstream o;
+    o << "#define MLN_JIT 1\n"
+      << "#ifdef __CUDACC_RTC__\ntypedef long long int64_t;\ntypedef int int32_t;\ntypedef unsigned int uint32_t;\n#endif\n"
+      << kKernelsSource << "\nnamespace mln {\n"
+      << "struct JitBatchConsts { " << R << " c[" << ncp << "]; };\n"
+      << "struct JitBatchCell {\n  static constexpr int D = " << D << ";\n  using Consts = JitBatchConsts;\n  " << R
+      << " s[D];\n";
+    if (regs) o << "  " << R << " c[" << nc << "];\n";
+    o << "  __device__ __forceinline__ void setup(unsigned char *, const Consts &k) {";
+    if (regs) o << " for (int i = 0; i < " << nc << "; ++i) c[i] = k.c[i];";
+    o << " }\n"
+      << "  __device__ __forceinline__ void load(const " << R
+      << " *src, int64_t stride, int64_t m) { for (int i = 0; i < D; ++i) s[i] = src[i * stride + m]; }\n"
+      << "  __device__ __forceinline__ void store(" << R
+      << " *dst, int64_t stride, int64_t m) const { for (int i = 0; i < D; ++i) dst[i * stride + m] = s[i]; }\n"
+      << "  __device__ __forceinline__ void end_step() {}\n"
+      << "  __device__ __forceinline__ " << R << " step(" << R << " e, const Consts &k) {\n"
+      << "    " << R << " z[D], y[D];\n";
+    const std::string mul = fp32 ? "__fmul_rn(" : "__dmul_rn(";
+    const std::string zero = fp32 ? "0.0f" : "0.0";
+    // z = T^T y on the plane rows
+    for (int k = 0; k < P; ++k) {
+        std::string acc;
+        for (int i = 0; i < D; ++i) {
+            if (!pat.tt[k * D + i]) continue;
+            const std::string t = "s[" + std::to_string(i) + "]";
+            acc = acc.empty() ? mul + C() + ", " + t + ")" : "fma(" + C() + ", " + t + ", " + acc + ")";
+        }
+        o << "    z[" << k << "] = " << (acc.empty() ? zero : acc) << ";\n";
+    }
+    for (int k = P; k < D; ++k) o << "    z[" << k << "] = " << zero << ";\n";
+    o << "    const " << R << " psi[" << (N - 1) << "] = {";
+    for (int a = 0; a < N - 1; ++a) o << (a ? ", " : "") << C();
+    o << "};\n    rotation_increment<" << N << ">(z, psi, e);\n";
+    // y'' = y + T (R - I) z on the plane columns
+    for (int i = 0; i < D; ++i) {
+        std::string acc;
+        for (int p = 0; p < P; ++p) {
+            if (!pat.t[i * P + p]) continue;
+            const std::string t = "z[" + std::to_string(p) + "]";
+            acc = acc.empty() ? mul + C() + ", " + t + ")" : "fma(" + C() + ", " + t + ", " + acc + ")";
+        }
+        const std::string si = "s[" + std::to_string(i) + "]";
+        o << "    y[" << i << "] = " << (acc.empty() ? si : si + " + (" + acc + ")") << ";\n";
+    }
+    // dP/dt = wm . y'' + c'
+    {
+        std::string acc = C();
+        for (int i = 0; i < D; ++i)
+            if (pat.wm[i]) acc = "fma(" + C() + ", y[" + std::to_string(i) + "], " + acc + ")";
+        o << "    const " << R << " dpdt = " << acc << ";\n";
+    }
+    // y = y'' + (C1 y'' + b2)
+    for (int i = 0; i < D; ++i) {
+        std::string acc = C();
+        for (int j = 0; j < D; ++j)
+            if (pat.c1[i * D + j]) acc = "fma(" + C() + ", y[" + std::to_string(j) + "], " + acc + ")";
+        o << "    s[" << i << "] = y[" << i << "] + (" << acc << ");\n";
+    }
+    o << "    return dpdt;\n  }\n};\n"
+      << "extern \"C\" __global__ void __launch_bounds__(kBatchThreads, 1) mln_jit_batch(const BatchGrid<" << R
+      << "> *grids, const BatchItem *items, const unsigned char *consts, int parity, int nsteps, int halo, int tile, "
+         "int64_t step_offset) {\n"
+      << "  extern __shared__ __align__(16) unsigned char smem_raw[];\n"
+      << "  batch_body<" << N << ", " << R
+      << ", JitBatchCell>(grids, items, consts, parity, nsteps, halo, tile, step_offset, smem_raw);\n}\n"
+      << "}  // namespace mln\n";
+    return o.str();
+}
+
 bool jit_available(std::string *why) {
     std::lock_guard<std::mutex> lock(g_mu);
     bool ok = load_tools();
@@ -194,7 +335,7 @@ bool jit_available(std::string *why) {
     return ok;
 }
 
-cudaError_t jit_compile(const std::string &src, void **fn, std::string &log) {
+cudaError_t jit_compile(const std::string &src, void **fn, std::string &log, const char *name) {
     std::lock_guard<std::mutex> lock(g_mu);
     if (!load_tools()) {
         log = g_why;
@@ -231,7 +372,7 @@ cudaError_t jit_compile(const std::string &src, void **fn, std::string &log) {
     g_nvrtc.destroy(&prog);
     CUmodule mod = nullptr;
     CUfunction f = nullptr;
-    if (g_drv.load(&mod, cubin.data()) != CUDA_SUCCESS || g_drv.get(&f, mod, "mln_jit_step") != CUDA_SUCCESS) {
+    if (g_drv.load(&mod, cubin.data()) != CUDA_SUCCESS || g_drv.get(&f, mod, name) != CUDA_SUCCESS) {
         log = "loading the compiled kernel failed";
         return cudaErrorUnknown;
     }
@@ -247,6 +388,15 @@ cudaError_t jit_launch_t(void *fn, const BlockArgs<R> &a, dim3 g, dim3 b, size_t
     } k{0};
     void *params[] = {const_cast<BlockArgs<R> *>(&a), &k};
     CUresult r = g_drv.launch(static_cast<CUfunction>(fn), g.x, g.y, g.z, b.x, b.y, b.z, static_cast<unsigned>(smem),
+                              static_cast<CUstream>(st), params, nullptr);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorLaunchFailure;
+}
+
+cudaError_t jit_launch_batch(void *fn, const void *grids, const void *items, const void *consts, int parity,
+                             int nsteps, int halo, int tile, int64_t step_offset, unsigned nblocks, unsigned threads,
+                             size_t smem, cudaStream_t st) {
+    void *params[] = {&grids, &items, &consts, &parity, &nsteps, &halo, &tile, &step_offset};
+    CUresult r = g_drv.launch(static_cast<CUfunction>(fn), nblocks, 1, 1, threads, 1, 1, static_cast<unsigned>(smem),
                               static_cast<CUstream>(st), params, nullptr);
     return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorLaunchFailure;
 }

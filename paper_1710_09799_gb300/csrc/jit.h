@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <string>
+#include <vector>
 
 #include "kernels.cuh"
 #include "setup.h"
@@ -17,8 +18,33 @@ std::string jit_merged_source(const Setup &s, double dt, bool fp32);
 // Whether NVRTC and the driver entry points could be loaded (reason if not).
 bool jit_available(std::string *why);
 
-// Compile (or reuse from the cache) a source for the current device.
-cudaError_t jit_compile(const std::string &src, void **fn, std::string &log);
+// Compile (or reuse from the cache) a source for the current device; the
+// kernel is looked up by name.
+cudaError_t jit_compile(const std::string &src, void **fn, std::string &log, const char *name = "mln_jit_step");
+
+// Union sparsity pattern of the merged-form constants of the grids of a
+// batch that have the same N: an entry is kept when it is non-zero (in the
+// batch's precision) for at least one of them.
+struct BatchPattern {
+    int N = 0;
+    std::vector<char> tt;  // 2q x D: T^T plane rows
+    std::vector<char> t;   // D x 2q: T plane columns
+    std::vector<char> wm;  // D
+    std::vector<char> c1;  // D x D
+};
+void batch_pattern_add(BatchPattern &pat, const Setup &s, bool fp32);
+// Number of constants of one grid in the pattern's compacted order.
+int batch_consts_count(const BatchPattern &pat);
+// One grid's constants in that order (precision's reals, padded to 16 bytes).
+void batch_pack(const BatchPattern &pat, const Setup &s, double dt, bool fp32, std::vector<unsigned char> &out);
+// Source of the batched step kernel for the pattern's N (kernel mln_jit_batch):
+// the products over the pattern's entries only, same order as the register
+// model; each grid's constants are staged in shared memory and, when they
+// fit, held in registers for the launch.
+std::string jit_batch_source(const BatchPattern &pat, bool fp32);
+cudaError_t jit_launch_batch(void *fn, const void *grids, const void *items, const void *consts, int parity,
+                             int nsteps, int halo, int tile, int64_t step_offset, unsigned nblocks, unsigned threads,
+                             size_t smem, cudaStream_t st);
 
 cudaError_t jit_launch(void *fn, const BlockArgs<double> &a, dim3 g, dim3 b, size_t smem, cudaStream_t st);
 cudaError_t jit_launch(void *fn, const BlockArgs<float> &a, dim3 g, dim3 b, size_t smem, cudaStream_t st);

@@ -561,6 +561,71 @@ __device__ __forceinline__ void block_body(const BlockArgs<R> &a, const typename
     }
 }
 
+// ---------------------------------------------------------------------------
+// Batches of independent grids: a table of grids and a work list of (grid,
+// tile) items; one block per item.
+
+// Shared-memory room for one grid's constants.
+constexpr int kBatchConstsMax = 8192;
+constexpr int kBatchMaxN = 4;
+// Threads per block of the batched kernels (tile + 2 K <= this).
+constexpr int kBatchThreads = 256;
+
+template <typename R>
+struct BatchGrid {
+    R *E[2], *H[2], *S[2];   // buffer set 0 (caller's) and 1 (context's)
+    const double *src;       // source samples from the batch's step 0, or nullptr
+    unsigned int *flags;
+    int64_t n_cells, mb, me, stride, source_cell;
+    int32_t N, boundary, source_kind, consts_off, consts_bytes, pad_;
+    R ch, ca, cb, inv_dx, kappa;
+};
+
+struct BatchItem {
+    int32_t grid, tile;
+};
+
+// The block of one work item: stage the grid's constants (consts_bytes at
+// consts + consts_off, a multiple of 16) at the start of shared memory, where
+// the cell model reads them as its Consts, then run the fused steps.
+template <int N, typename R, typename Cell>
+__device__ __forceinline__ void batch_body(const BatchGrid<R> *__restrict__ grids, const BatchItem *__restrict__ items,
+                                           const unsigned char *__restrict__ consts, int parity, int nsteps,
+                                           int halo, int tile, int64_t step_offset, unsigned char *smem_raw) {
+    const BatchItem it = items[blockIdx.x];
+    const BatchGrid<R> &g = grids[it.grid];
+    for (int o = threadIdx.x * 16; o < g.consts_bytes; o += blockDim.x * 16)
+        *reinterpret_cast<uint4 *>(smem_raw + o) = *reinterpret_cast<const uint4 *>(consts + g.consts_off + o);
+    __syncthreads();
+    BlockArgs<R> a;
+    a.E_in = g.E[parity];
+    a.H_in = g.H[parity];
+    a.s_in = g.S[parity];
+    a.E_out = g.E[parity ^ 1];
+    a.H_out = g.H[parity ^ 1];
+    a.s_out = g.S[parity ^ 1];
+    a.src = g.src ? g.src + step_offset : nullptr;
+    a.flags = g.flags;
+    a.n_cells = g.n_cells;
+    a.mb = g.mb;
+    a.me = g.me;
+    a.stride = g.stride;
+    a.source_cell = g.source_cell;
+    a.nsteps = nsteps;
+    a.halo = halo;
+    a.tile = tile;
+    a.boundary = g.boundary;
+    a.source_kind = g.source_kind;
+    a.pad_ = 0;
+    a.ch = g.ch;
+    a.ca = g.ca;
+    a.cb = g.cb;
+    a.inv_dx = g.inv_dx;
+    a.kappa = g.kappa;
+    block_body<N, R, Cell>(a, *reinterpret_cast<const typename Cell::Consts *>(smem_raw), it.tile,
+                           smem_raw + kBatchConstsMax);
+}
+
 template <int N, typename R, typename Cell>
 __global__ void __launch_bounds__(kMaxThreads, 1)
     mln_block_kernel(const __grid_constant__ BlockArgs<R> a, const __grid_constant__ typename Cell::Consts k) {

@@ -109,6 +109,8 @@ _SIGS = {
     "mln_batch_shape": (C.c_int, [C.c_void_p, C.POINTER(C.c_int32), C.POINTER(C.c_int32),
                                   C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
     "mln_batch_error": (C.c_char_p, [C.c_void_p]),
+    "mln_batch_kernel_in_use": (C.c_int32, [C.c_void_p, C.c_int32]),
+    "mln_batch_kernel_source": (C.c_int, [C.c_int32, _P, C.c_int32, C.c_char_p, C.c_size_t, C.POINTER(C.c_size_t)]),
     "mln_batch_destroy": (None, [C.c_void_p]),
     "mln_rotation_terms": (C.c_int, [C.c_int32, _dp, C.c_int64, _dp, _dp]),
     "mln_tc_product": (C.c_int, [C.c_int32, C.c_int32, C.c_int32, C.POINTER(C.c_float), _dp,
@@ -562,6 +564,16 @@ def mln_batch_context(b, i: int):
     return C.c_void_p(lib().mln_batch_context(b, i))
 
 
+def mln_batch_kernel_source(params: list, N: int) -> str:
+    """CUDA source that a batch of these grids compiles for its N-level grids (host only)."""
+    arr = (mln_params * len(params))(*[p.s for p in params])
+    n = C.c_size_t(0)
+    _check(lib().mln_batch_kernel_source(len(params), arr, N, None, 0, C.byref(n)))
+    buf = C.create_string_buffer(n.value + 1)
+    _check(lib().mln_batch_kernel_source(len(params), arr, N, buf, n.value + 1, None))
+    return buf.value.decode()
+
+
 def mln_batch_shape(b):
     k, t, it, la = C.c_int32(), C.c_int32(), C.c_int64(), C.c_int64()
     _bcheck(lib().mln_batch_shape(b, C.byref(k), C.byref(t), C.byref(it), C.byref(la)), b)
@@ -603,6 +615,11 @@ class Batch:
 
     def autotune(self, trials: int = 3):
         return mln_batch_autotune(self.b, trials)
+
+    def kernel_in_use(self, N: int) -> str | None:
+        """Cell model of the N-level grids ("jit" or "register"), None if none."""
+        k = lib().mln_batch_kernel_in_use(self.b, N)
+        return None if k < 0 else {v: n for n, v in KERNEL.items()}[k]
 
     def step(self, n_steps: int):
         mln_batch_step(self.b, n_steps)

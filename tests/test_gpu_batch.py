@@ -23,9 +23,9 @@ def _built():
     build()
 
 
-def make_batch(devs, precision, n_steps):
+def make_batch(devs, precision, n_steps, kernel="auto"):
     from paper_1710_09799_gb300 import mln
-    pars = [params_of(p, precision=precision, form="merged", kernel="register") for p in devs]
+    pars = [params_of(p, precision=precision, form="merged", kernel=kernel) for p in devs]
     srcs = [p.source_samples(0, n_steps) for p in devs]
     has = any(s is not None for s in srcs)
     return mln.Batch(pars, [p.e_init() for p in devs], srcs if has else None, n_steps if has else 0)
@@ -39,11 +39,17 @@ def single(p, precision, n_steps):
     return E, H, s.rho()
 
 
+@pytest.mark.parametrize("kernel", ["jit", "register"])
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
-def test_batch_matches_single_grids_bitwise(precision):
+def test_batch_matches_single_grids_bitwise(precision, kernel):
+    """Both batched cell models (run-time compiled over the union sparsity
+    pattern, and dense products over padded constants) give the single-grid
+    register model's bits."""
     devs = W.batched_devices(count=7, n_steps=260, seed=3, min_cells=100, max_cells=3000)
     assert {p.N for p in devs} == {2, 3, 4}
-    b = make_batch(devs, precision, 260)
+    b = make_batch(devs, precision, 260, kernel)
+    for N in (2, 3, 4):
+        assert b.kernel_in_use(N) == kernel
     b.step(130)
     b.step(130)
     b.sync()

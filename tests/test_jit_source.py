@@ -44,3 +44,39 @@ def test_generated_source_compiles_and_skips_zeros(lib, tmp_path, prec):
     r = subprocess.run([nvcc, "-gencode", "arch=compute_103a,code=sm_103a", "-std=c++17", "-c", str(f),
                         "-o", str(tmp_path / "k.o")], capture_output=True, text=True)
     assert r.returncode == 0, r.stderr[-3000:]
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+@pytest.mark.parametrize("N", [2, 3, 4])
+def test_batch_source_compiles_and_follows_the_union_pattern(lib, tmp_path, prec, N):
+    """The batched kernel of the N-level grids of a batch: one term per entry
+    that is non-zero in at least one grid (the union pattern), valid CUDA."""
+    nvcc = shutil.which("nvcc") or "/usr/local/cuda/bin/nvcc"
+    if not os.path.exists(nvcc):
+        pytest.skip("nvcc not found")
+    devs = W.batched_devices(count=12, n_steps=10)
+    pars = [params_of(d, precision=prec, form="merged") for d in devs]
+    mine = [p for d, p in zip(devs, pars) if d.N == N]
+    if not mine:
+        pytest.skip("no grid with this N in the sample")
+    src = mln.mln_batch_kernel_source(pars, N)
+    cast = (lambda x: np.float32(x)) if prec == "fp32" else (lambda x: x)
+    union_T = union_C1 = None
+    for p in mine:
+        s = mln.mln_setup_host(p)
+        q = s["q"]
+        t = cast(s["T"][:, :2 * q]) != 0
+        c = cast(s["C1"]) != 0
+        union_T = t if union_T is None else union_T | t
+        union_C1 = c if union_C1 is None else union_C1 | c
+    D = N * N - 1
+    body = src[src.index("struct JitBatchCell"):]
+    n_terms = body.count("fma(") + body.count("mul_rn(")
+    # T^T and T once per union entry, C1 once per union entry, at most D terms of wm
+    assert n_terms <= 2 * int(union_T.sum()) + int(union_C1.sum()) + D
+    assert n_terms >= 2 * int(union_T.sum()) + int(union_C1.sum())
+    f = tmp_path / "b.cu"
+    f.write_text(src)
+    r = subprocess.run([nvcc, "-gencode", "arch=compute_103a,code=sm_103a", "-std=c++17", "-c", str(f),
+                        "-o", str(tmp_path / "b.o")], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr[-3000:]
