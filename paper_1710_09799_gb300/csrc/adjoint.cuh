@@ -79,7 +79,7 @@ __global__ void __launch_bounds__(256) mln_adjoint_step(const __grid_constant__ 
     const int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
     const bool live = i < n;
     const int64_t ii = live ? i : 0;
-    const int64_t ip = (ii + 1) % n, im = (ii + n - 1) % n;
+    const int64_t ip = ii + 1 == n ? 0 : ii + 1, im = ii == 0 ? n - 1 : ii - 1;
     const R jdt = static_cast<R>(2.0 * a.dt);
 
     // adjoint of E' at a cell, with the objective term and a hard source (which cuts the path)

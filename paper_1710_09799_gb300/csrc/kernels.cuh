@@ -338,6 +338,20 @@ __global__ void sin_cosm1_kernel(const double *x, int64_t n, double *s, double *
 // Blocks have at most kMaxThreads threads, which leaves up to 128 registers per thread.
 constexpr int kMaxThreads = 512;
 
+// g mod n in [0, n) for a cell index of a periodic ring. Tiles and halos keep
+// g within one ring length of [0, n), so one compare and add or subtract
+// does it; a 64-bit remainder (a long instruction sequence on the FP64-poor
+// pipes of this GPU) runs only for halos wider than the ring.
+__host__ __device__ __forceinline__ int64_t wrap_index(int64_t g, int64_t n) {
+    if (g < 0) g += n;
+    else if (g >= n) g -= n;
+    if (g < 0 || g >= n) {
+        g %= n;
+        if (g < 0) g += n;
+    }
+    return g;
+}
+
 // Shared memory of a block's field exchange: E and H, two buffers each.
 template <typename R>
 __host__ __device__ constexpr size_t field_smem(int threads) {
@@ -487,8 +501,7 @@ __device__ __forceinline__ void block_body(const BlockArgs<R> &a, const typename
     int64_t gm = g;
     bool loaded = j < L;
     if (periodic) {
-        gm = g % n;
-        if (gm < 0) gm += n;
+        gm = wrap_index(g, n);
     } else {
         loaded = loaded && g >= 0 && g < n;
     }

@@ -253,8 +253,7 @@ __global__ void __launch_bounds__(512, 1)
         int64_t gm = gi;
         bool loaded = j < L;
         if (periodic) {
-            gm = gi % n;
-            if (gm < 0) gm += n;
+            gm = wrap_index(gi, n);
         } else {
             loaded = loaded && gi >= 0 && gi < n;
         }
