@@ -68,7 +68,7 @@ TRAFFIC_SOURCES_SHA = None  # set with the captures: sha256 of the kernel source
 def kernel_sources_sha() -> str:
     import hashlib
     h = hashlib.sha256()
-    for f in ("kernels.cuh", "jit.cu", "dispatch.cuh"):
+    for f in ("kernels.cuh", "jit.cu", "dispatch.cuh", "kernels_fp64.cu", "kernels_fp32.cu"):
         h.update(open(os.path.join(ROOT, "paper_1710_09799_gb300", "csrc", f), "rb").read())
     return h.hexdigest()
 

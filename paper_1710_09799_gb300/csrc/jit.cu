@@ -204,27 +204,24 @@ void batch_pattern_add(BatchPattern &pat, const Setup &s, bool fp32) {
     for (int i = 0; i < D * D; ++i) pat.c1[i] |= nz(s.C1[i], fp32);
 }
 
-// The constants of the batched step in their order of use: f(value) for each.
-// T^T plane rows, psi dt, T plane columns, c', wm, then per row of C1: b2_i
-// and the row's entries. Only the entries in the pattern appear.
+// The distinct constants of the batched step, in a fixed order: the entries
+// of T in the pattern (plane columns, row by row: each is used twice, by
+// T^T y and by T dz), psi dt, c', wm, then per row of C1: b2_i and the
+// row's entries. f(value) for each; the index of a constant is its position.
 template <typename F>
 void batch_walk(const BatchPattern &pat, const Setup *s, double dt, F f) {
     const int N = pat.N, D = N * N - 1, P = N * (N - 1);
-    auto v = [&](double x) { return s ? x : 0.0; };
-    for (int k = 0; k < P; ++k)
-        for (int i = 0; i < D; ++i)
-            if (pat.tt[k * D + i]) f(v(s ? s->T[i * D + k] : 0));
-    for (int a = 0; a < N - 1; ++a) f(v(s ? s->psi[a] * dt : 0));
     for (int i = 0; i < D; ++i)
         for (int p = 0; p < P; ++p)
-            if (pat.t[i * P + p]) f(v(s ? s->T[i * D + p] : 0));
-    f(v(s ? s->cm : 0));
+            if (pat.t[i * P + p] || pat.tt[p * D + i]) f(s ? s->T[i * D + p] : 0.0);
+    for (int a = 0; a < N - 1; ++a) f(s ? s->psi[a] * dt : 0.0);
+    f(s ? s->cm : 0.0);
     for (int i = 0; i < D; ++i)
-        if (pat.wm[i]) f(v(s ? s->wm[i] : 0));
+        if (pat.wm[i]) f(s ? s->wm[i] : 0.0);
     for (int i = 0; i < D; ++i) {
-        f(v(s ? s->b2[i] : 0));
+        f(s ? s->b2[i] : 0.0);
         for (int j = 0; j < D; ++j)
-            if (pat.c1[i * D + j]) f(v(s ? s->C1[i * D + j] : 0));
+            if (pat.c1[i * D + j]) f(s ? s->C1[i * D + j] : 0.0);
     }
 }
 
@@ -254,10 +251,27 @@ std::string jit_batch_source(const BatchPattern &pat, bool fp32) {
     const char *R = fp32 ? "float" : "double";
     const int nc = batch_consts_count(pat);
     const int words = nc * (fp32 ? 1 : 2);
-    const bool regs = words <= 96;  // constants in registers when they fit, else read from shared memory
+    // constants in registers (read from shared memory once per launch) when
+    // they fit next to the state; else read from shared memory at each use
+    const bool regs = words <= 176;
     const int ncp = (nc * (fp32 ? 4 : 8) + 15) / 16 * 16 / (fp32 ? 4 : 8);
-    int idx = 0;
-    auto C = [&]() { return std::string(regs ? "c[" : "k.c[") + std::to_string(idx++) + "]"; };
+    // index of each distinct constant (the order of batch_walk)
+    std::vector<int> iT(static_cast<size_t>(D) * P, -1), iW(D, -1), iB(D, -1), iC(static_cast<size_t>(D) * D, -1);
+    std::vector<int> iPsi(N - 1);
+    int idx = 0, iCm = -1;
+    for (int i = 0; i < D; ++i)
+        for (int p = 0; p < P; ++p)
+            if (pat.t[i * P + p] || pat.tt[p * D + i]) iT[i * P + p] = idx++;
+    for (int a = 0; a < N - 1; ++a) iPsi[a] = idx++;
+    iCm = idx++;
+    for (int i = 0; i < D; ++i)
+        if (pat.wm[i]) iW[i] = idx++;
+    for (int i = 0; i < D; ++i) {
+        iB[i] = idx++;
+        for (int j = 0; j < D; ++j)
+            if (pat.c1[i * D + j]) iC[i * D + j] = idx++;
+    }
+    auto C = [&](int k) { return std::string(regs ? "c[" : "k.c[") + std::to_string(k) + "]"; };
     std::ostringstream o;
     o << "#define MLN_JIT 1\n"
       << "#ifdef __CUDACC_RTC__\ntypedef long long int64_t;\ntypedef int int32_t;\ntypedef unsigned int uint32_t;\n#endif\n"
@@ -278,43 +292,43 @@ std::string jit_batch_source(const BatchPattern &pat, bool fp32) {
       << "    " << R << " z[D], y[D];\n";
     const std::string mul = fp32 ? "__fmul_rn(" : "__dmul_rn(";
     const std::string zero = fp32 ? "0.0f" : "0.0";
-    // z = T^T y on the plane rows
+    // z = T^T y on the plane rows (T^T row k = T column k)
     for (int k = 0; k < P; ++k) {
         std::string acc;
         for (int i = 0; i < D; ++i) {
             if (!pat.tt[k * D + i]) continue;
-            const std::string t = "s[" + std::to_string(i) + "]";
-            acc = acc.empty() ? mul + C() + ", " + t + ")" : "fma(" + C() + ", " + t + ", " + acc + ")";
+            const std::string t = "s[" + std::to_string(i) + "]", c = C(iT[i * P + k]);
+            acc = acc.empty() ? mul + c + ", " + t + ")" : "fma(" + c + ", " + t + ", " + acc + ")";
         }
         o << "    z[" << k << "] = " << (acc.empty() ? zero : acc) << ";\n";
     }
     for (int k = P; k < D; ++k) o << "    z[" << k << "] = " << zero << ";\n";
     o << "    const " << R << " psi[" << (N - 1) << "] = {";
-    for (int a = 0; a < N - 1; ++a) o << (a ? ", " : "") << C();
+    for (int a = 0; a < N - 1; ++a) o << (a ? ", " : "") << C(iPsi[a]);
     o << "};\n    rotation_increment<" << N << ">(z, psi, e);\n";
     // y'' = y + T (R - I) z on the plane columns
     for (int i = 0; i < D; ++i) {
         std::string acc;
         for (int p = 0; p < P; ++p) {
             if (!pat.t[i * P + p]) continue;
-            const std::string t = "z[" + std::to_string(p) + "]";
-            acc = acc.empty() ? mul + C() + ", " + t + ")" : "fma(" + C() + ", " + t + ", " + acc + ")";
+            const std::string t = "z[" + std::to_string(p) + "]", c = C(iT[i * P + p]);
+            acc = acc.empty() ? mul + c + ", " + t + ")" : "fma(" + c + ", " + t + ", " + acc + ")";
         }
         const std::string si = "s[" + std::to_string(i) + "]";
         o << "    y[" << i << "] = " << (acc.empty() ? si : si + " + (" + acc + ")") << ";\n";
     }
     // dP/dt = wm . y'' + c'
     {
-        std::string acc = C();
+        std::string acc = C(iCm);
         for (int i = 0; i < D; ++i)
-            if (pat.wm[i]) acc = "fma(" + C() + ", y[" + std::to_string(i) + "], " + acc + ")";
+            if (pat.wm[i]) acc = "fma(" + C(iW[i]) + ", y[" + std::to_string(i) + "], " + acc + ")";
         o << "    const " << R << " dpdt = " << acc << ";\n";
     }
     // y = y'' + (C1 y'' + b2)
     for (int i = 0; i < D; ++i) {
-        std::string acc = C();
+        std::string acc = C(iB[i]);
         for (int j = 0; j < D; ++j)
-            if (pat.c1[i * D + j]) acc = "fma(" + C() + ", y[" + std::to_string(j) + "], " + acc + ")";
+            if (pat.c1[i * D + j]) acc = "fma(" + C(iC[i * D + j]) + ", y[" + std::to_string(j) + "], " + acc + ")";
         o << "    s[" << i << "] = y[" << i << "] + (" << acc << ");\n";
     }
     o << "    return dpdt;\n  }\n};\n"

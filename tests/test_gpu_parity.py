@@ -173,10 +173,19 @@ def test_step_splitting_is_exact():
 
 
 @pytest.mark.parametrize("case", ["tiny_ring", "tiny_open", "vacuum", "one_cell_medium", "soft_source",
-                                  "lossy", "dielectric"])
+                                  "lossy", "dielectric", "no_relaxation", "degenerate_dipoles"])
 def test_edge_cases(orc, case):
     base = W.three_level_ring(n_cells=64, n_steps=120)
-    if case == "tiny_ring":
+    if case == "no_relaxation":
+        # G = 0: M = -i[H0, .] is singular (populations undamped), the augmented
+        # half-step exponential still defines A0 and b (b = 0)
+        p = base.with_(G=None, E_init=base.e_init() * 1e5)
+    elif case == "degenerate_dipoles":
+        # mu = mu0 (J - I): eigenvalues 2 mu0, -mu0, -mu0; the plane of the
+        # degenerate pair turns by zero angle and its basis is not unique
+        mu = 2 * W.NM_E * (np.ones((3, 3)) - np.eye(3)).astype(np.complex128)
+        p = base.with_(mu=mu, E_init=base.e_init() * 1e5)
+    elif case == "tiny_ring":
         p = W.three_level_ring(n_cells=4, n_steps=50)
     elif case == "tiny_open":
         p = W.two_level_sit(n_cells=6, medium=(1, 5), n_steps=80)
