@@ -59,10 +59,17 @@ FP32_FLOP_PER_CLK_SM = 256
 # (profiles/*.md), keyed by (cell model, precision, workload, steps per launch).
 # An entry is used only while the kernel sources hash to the value recorded
 # with it; after any change to them the traffic is reported as null.
+# dram__bytes_read.sum + dram__bytes_write.sum of one launch (ncu, same launch shape, tile 432),
+# profiles/mln_block_kernel_fp64_sparse_three_level_ring.md
 MEASURED_TRAFFIC = {
-    ("sparse", "fp64", "three_level_ring", 20): (5273344.0, "see profiles/mln_block_kernel_fp64_sparse_three_level_ring.md"),
+    ("sparse", "fp64", "three_level_ring", 8): (5274880.0, "ncu, --block-steps 8 --tile 432"),
+    ("sparse", "fp64", "three_level_ring", 12): (5274624.0, "ncu, --block-steps 12 --tile 432"),
+    ("sparse", "fp64", "three_level_ring", 16): (5274624.0, "ncu, --block-steps 16 --tile 432"),
+    ("sparse", "fp64", "three_level_ring", 20): (5274880.0, "ncu, --block-steps 20 --tile 432"),
 }
-TRAFFIC_SOURCES_SHA = None  # set with the captures: sha256 of the kernel sources at capture time
+# sha256 of the kernel sources when the counters were taken: a later change of a
+# kernel source makes the reported traffic null until it is measured again
+TRAFFIC_SOURCES_SHA = "14714397477e94284258a1e742df1e932bd66ab9a094b2f417cc9f3a749186c2"
 
 
 def kernel_sources_sha() -> str:
