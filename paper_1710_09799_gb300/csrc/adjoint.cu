@@ -3,9 +3,9 @@
 //
 // Forward: the fused step kernel advances the context, saving the state at
 // the start of every segment of `every` steps. Backward: for the segments in
-// reverse order, the segment is recomputed from its checkpoint one step per
-// launch (all its states kept), then the reverse step kernel runs from the
-// segment's last step to its first, carrying the adjoint of (E, H, d) and
+// reverse order, the segment is recomputed from its checkpoint by the fused
+// step kernel with every step's state recorded (all its states kept), then
+// the reverse step kernel runs from the segment's last step to its first, carrying the adjoint of (E, H, d) and
 // accumulating the gradients of the step's constants. The host then maps
 // those to the dipole operator and the relaxation superoperator (exact
 // Frechet derivatives, see adjoint_chain).
@@ -83,16 +83,13 @@ mln_status adjoint_t(mln_ctx *c, int64_t n_steps, const double *src, int64_t pro
     };
     const Set<R> user{static_cast<R *>(c->E[0]), static_cast<R *>(c->H[0]), static_cast<R *>(c->st[0])};
     mln::BlockArgs<R> fa = mln::base_args<R>(c);
-    // Block size: the largest of 256 .. 32 threads that still gives two blocks
-    // per SM, so that small rings spread over every SM (one thread per cell).
-    int sms = 152, dev = 0;
-    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    int athreads = 256;
-    while (athreads > 32 && (n + athreads - 1) / athreads < 2 * sms) athreads /= 2;
-    const int rthreads = athreads, rtile = athreads - 2;  // recompute shape: one step per launch
-    fa.halo = 1;
-    fa.tile = rtile;
-    fa.nsteps = 1;
+    // Reverse step: AdjLanes<N> lanes per cell, blocks of 128 threads.
+    const unsigned rblocks = static_cast<unsigned>((n * mln::AdjLanes<N>::value + 127) / 128);
+    // Recompute: up to rK fused steps per launch, every step recorded into its
+    // slot; blocks of rthreads threads with tiles of rthreads - 2 rK cells.
+    const int rK = 8, rthreads = 64;
+    fa.halo = rK;
+    fa.tile = rthreads - 2 * rK;
     mln::AdjArgs<R> aa{};
     Set<R> A0s, A1s;
 
@@ -134,17 +131,23 @@ mln_status adjoint_t(mln_ctx *c, int64_t n_steps, const double *src, int64_t pro
     for (int64_t s = nseg - 1; s >= 0; --s) {
         const int64_t s0 = s * every, len = std::min<int64_t>(every, n_steps - s0);
         MLN_ACK(c, copy_set(set_at(slots, 0), set_at(ckpt, s)));
-        for (int64_t j = 0; j < len; ++j) {
-            const Set<R> in = set_at(slots, j), o = set_at(slots, j + 1);
+        for (int64_t j = 0; j < len; j += rK) {
+            const int ns = static_cast<int>(std::min<int64_t>(rK, len - j));
+            const Set<R> in = set_at(slots, j), o = set_at(slots, j + ns), r1 = set_at(slots, j + 1);
             fa.E_in = in.E;
             fa.H_in = in.H;
             fa.s_in = in.S;
             fa.E_out = o.E;
             fa.H_out = o.H;
             fa.s_out = o.S;
+            fa.rec_E = r1.E;
+            fa.rec_H = r1.H;
+            fa.rec_S = r1.S;
+            fa.rec_set = static_cast<int64_t>(set_bytes);
+            fa.nsteps = ns;
             fa.src = (src && c->p.source_kind != MLN_SRC_NONE) ? src + s0 + j : nullptr;
             MLN_ACK(c, mln::launch_block(c->p.N, MLN_FORM_STRANG, fa, c->consts,
-                                         dim3(static_cast<unsigned>((n + rtile - 1) / rtile)), dim3(rthreads),
+                                         dim3(static_cast<unsigned>((n + fa.tile - 1) / fa.tile)), dim3(rthreads),
                                          mln::field_smem<R>(rthreads), c->stream));
         }
         for (int64_t j = len - 1; j >= 0; --j) {
@@ -159,8 +162,7 @@ mln_status adjoint_t(mln_ctx *c, int64_t n_steps, const double *src, int64_t pro
             aa.Hb = A1s.H;
             aa.Sb = A1s.S;
             aa.dsrc = (src && c->p.source_kind != MLN_SRC_NONE) ? dsrc + s0 + j : nullptr;
-            mln::mln_adjoint_step<N, R><<<static_cast<unsigned>((n + athreads - 1) / athreads), athreads, 0,
-                                          c->stream>>>(aa, k);
+            mln::mln_adjoint_step_rows<N, R><<<rblocks, 128, 0, c->stream>>>(aa, k);
             MLN_ACK(c, cudaGetLastError());
             std::swap(A0s, A1s);
         }

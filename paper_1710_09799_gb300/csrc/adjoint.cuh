@@ -1,15 +1,7 @@
 // Reverse-time (adjoint) step of the literal Strang form on a periodic ring
-// (internal header). One thread per cell; a step's adjoint reads only the
-// adjoints after the step and the forward state before it, so no block-level
-// synchronisation is needed and one launch handles one step.
-//
-// Forward step (periodic, sigma general):
-//   H'_i = H_i + ch (E_{i+1} - E_i)
-//   d'   = d + (Dl d + b);  z = T^T d';  d'' = d' + T (R(phi) - I) z,  phi_k = theta_k dt E_i
-//   dn   = d'' + (Dl d'' + b);  p = w . dn + c
-//   E'_i = ca E_i + cb ((H'_i - H'_{i-1}) / dx - p_i);  source at source_cell
-// Objective J = dt sum_n (E^{n+1}_probe)^2: the reverse of step n adds
-// 2 dt E^{n+1}_probe to the adjoint of E^{n+1}_probe.
+// (internal header). A step's adjoint reads only the adjoints after the step
+// and the forward state before it, so no block-level synchronisation is
+// needed and one launch handles one step.
 #pragma once
 
 #include "kernels.cuh"
@@ -70,19 +62,57 @@ __global__ void __launch_bounds__(256) mln_adjoint_reduce(const double *__restri
     if (threadIdx.x == 0) out[k] = part[0];
 }
 
+// Lanes per cell of the row-parallel reverse step: a power of two >= D.
+template <int N>
+struct AdjLanes {
+    static constexpr int D = Dims<N>::D;
+    static constexpr int value = D <= 4 ? 4 : (D <= 8 ? 8 : 16);
+};
+
+// The reverse step with one lane per component: the AdjLanes lanes of a cell
+// each own one row r < D of every vector and of every product, and read the
+// other components of a product's input by shuffles within the cell's lanes.
+// Each component gets the operations, in the order, that one thread per cell
+// would apply to it (sums over an index run in ascending order), so the lane
+// split changes no bits; small rings keep all SMs busy and each lane's
+// dependency chains are D times shorter.
+//
+// Forward step being differentiated (periodic, sigma general):
+//   H'_i = H_i + ch (E_{i+1} - E_i)
+//   d'   = d + (Dl d + b);  z = T^T d';  d'' = d' + T (R(phi) - I) z,  phi_k = theta_k dt E_i
+//   dn   = d'' + (Dl d'' + b);  p = w . dn + c
+//   E'_i = ca E_i + cb ((H'_i - H'_{i-1}) / dx - p_i);  source at source_cell
+// Objective J = dt sum_n (E^{n+1}_probe)^2: the reverse of step n adds
+// 2 dt E^{n+1}_probe to the adjoint of E^{n+1}_probe.
 template <int N, typename R>
-__global__ void __launch_bounds__(256) mln_adjoint_step(const __grid_constant__ AdjArgs<R> a,
-                                                        const __grid_constant__ AdjConsts<N, R> k) {
-    constexpr int D = Dims<N>::D, Q = Dims<N>::Q;
+__global__ void __launch_bounds__(128) mln_adjoint_step_rows(const __grid_constant__ AdjArgs<R> a,
+                                                             const __grid_constant__ AdjConsts<N, R> k) {
+    constexpr int D = Dims<N>::D, Q = Dims<N>::Q, LN = AdjLanes<N>::value;
     using L = AccLayout<N>;
     const int64_t n = a.n_cells;
-    const int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+    const int64_t t = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+    const int64_t i = t / LN;
+    const int r = static_cast<int>(t % LN);
     const bool live = i < n;
+    const bool row = live && r < D;
     const int64_t ii = live ? i : 0;
     const int64_t ip = ii + 1 == n ? 0 : ii + 1, im = ii == 0 ? n - 1 : ii - 1;
     const R jdt = static_cast<R>(2.0 * a.dt);
+    const unsigned full = 0xffffffffu;
+    auto get = [&](R v, int src) { return __shfl_sync(full, v, src, LN); };  // component src of this cell
+    const int rr = r < D ? r : 0;
+    // this lane's rows and columns of the constant matrices
+    R dl_row[D], dl_col[D], t_row[D], t_col[D];
+#pragma unroll
+    for (int j = 0; j < D; ++j) {
+        dl_row[j] = k.Dl[rr * D + j];
+        dl_col[j] = k.Dl[j * D + rr];
+        t_row[j] = k.T[rr * D + j];
+        t_col[j] = k.T[j * D + rr];
+    }
+    const R b_r = k.b[rr], w_r = k.w[rr];
 
-    // adjoint of E' at a cell, with the objective term and a hard source (which cuts the path)
+    // scalars of the cell (every lane; lane 0 writes)
     auto ebar_out = [&](int64_t c) -> R {
         R v = a.Ea[c];
         if (c == a.probe_cell) v += jdt * a.E1[c];
@@ -95,123 +125,134 @@ __global__ void __launch_bounds__(256) mln_adjoint_step(const __grid_constant__ 
         ep_p = ebar_out(ip);
         ep_m = ebar_out(im);
     }
-    // source sample: soft adds it, hard sets E' to it; both pass the adjoint of E'
-    if (live && a.dsrc != nullptr && ii == a.source_cell) {
+    if (live && r == 0 && a.dsrc != nullptr && ii == a.source_cell) {
         R v = a.Ea[ii];
         if (ii == a.probe_cell) v += jdt * a.E1[ii];
         *a.dsrc = static_cast<double>(v);
     }
-    if (live && ii == a.probe_cell) {
+    if (live && r == 0 && ii == a.probe_cell) {
         const double e1 = static_cast<double>(a.E1[ii]);
         a.acc[L::J * n + ii] += a.dt * e1 * e1;
     }
-    // adjoint of H'_i and H'_{i-1} (used by E'_i, E'_{i+1} and E'_{i-1}, E'_i)
     R hh_i = R(0), hh_m = R(0);
     if (live) {
         hh_i = a.Ha[ii] + a.cb * a.inv_dx * (ep_i - ep_p);
         hh_m = a.Ha[im] + a.cb * a.inv_dx * (ep_m - ep_i);
-        a.Hb[ii] = hh_i;
+        if (r == 0) a.Hb[ii] = hh_i;
     }
     R eb = live ? a.ca * ep_i + a.ch * (hh_m - hh_i) : R(0);
 
     const bool medium = live && ii >= a.mb && ii < a.me;
+    const bool mrow = medium && r < D;
     const int64_t m = ii - a.mb;
-    // forward recompute of the cell (zeros for lanes outside the medium)
-    R d[D], y[D], z[D], y2[D], dn[D], sn[Q], c1[Q];
     const R e = live ? a.E0[ii] : R(0);
+    // forward recompute of the cell, one component per lane
+    const R d = mrow ? a.S0[r * a.stride + m] : R(0);
+    R y;  // y = d + (Dl d + b)
+    {
+        R acc = b_r;
 #pragma unroll
-    for (int j = 0; j < D; ++j) d[j] = medium ? a.S0[j * a.stride + m] : R(0);
-    affine_inc<D>(y, k.Dl, d, k.b);
-    matTvec<D>(z, k.T, y);
+        for (int j = 0; j < D; ++j) acc = fma(dl_row[j], get(d, j), acc);
+        y = d + acc;
+    }
+    R z;  // z = T^T y
+    {
+        R acc = t_col[0] * get(y, 0);
+#pragma unroll
+        for (int j = 1; j < D; ++j) acc = fma(t_col[j], get(y, j), acc);
+        z = acc;
+    }
+    R sn[Q], c1[Q];
     plane_terms<N>(k.psi_dt, e, sn, c1);
-    R dz[D];
+    const int pl = rr / 2;
+    const R z_pair = __shfl_xor_sync(full, z, 1, LN);
+    R dz = R(0);
+    if (r < 2 * Q) dz = (r % 2 == 0) ? fma(c1[pl], z, sn[pl] * z_pair) : fma(c1[pl], z, -(sn[pl] * z_pair));
+    R y2;  // y2 = y + T dz
+    {
+        R acc = t_row[0] * get(dz, 0);
 #pragma unroll
-    for (int j = 0; j < D; ++j) dz[j] = R(0);
-#pragma unroll
-    for (int p = 0; p < Q; ++p) {
-        dz[2 * p] = fma(c1[p], z[2 * p], sn[p] * z[2 * p + 1]);
-        dz[2 * p + 1] = fma(c1[p], z[2 * p + 1], -(sn[p] * z[2 * p]));
+        for (int j = 1; j < D; ++j) acc = fma(t_row[j], get(dz, j), acc);
+        y2 = y + acc;
     }
+    R dn;  // dn = y2 + (Dl y2 + b)
+    {
+        R acc = b_r;
 #pragma unroll
-    for (int j = 0; j < D; ++j) y2[j] = y[j];
-    matvec_acc<D>(y2, k.T, dz);
-    affine_inc<D>(dn, k.Dl, y2, k.b);
-    if (!medium) {
-#pragma unroll
-        for (int j = 0; j < D; ++j) d[j] = y[j] = z[j] = y2[j] = dn[j] = dz[j] = R(0);
+        for (int j = 0; j < D; ++j) acc = fma(dl_row[j], get(y2, j), acc);
+        dn = y2 + acc;
     }
+    R dv = d, yv = y, zv = z, y2v = y2, dnv = dn, dzv = dz;
+    if (!mrow) dv = yv = zv = y2v = dnv = dzv = R(0);
 
-    // reverse: p = w . dn + c with pbar = -cb * Ebar'_i
+    // reverse
     const R pbar = medium ? -a.cb * ep_i : R(0);
-    R dnb[D];
+    const R dnb = (mrow ? a.Sa[r * a.stride + m] : R(0)) + pbar * w_r;
+    R y2b;  // y2b = dnb + Dl^T dnb
+    {
+        R acc = dnb;
 #pragma unroll
-    for (int j = 0; j < D; ++j) dnb[j] = (medium ? a.Sa[j * a.stride + m] : R(0)) + pbar * k.w[j];
-    // dn = A0 y2 + b
-    R y2b[D];
-#pragma unroll
-    for (int j = 0; j < D; ++j) {
-        R acc = dnb[j];
-#pragma unroll
-        for (int l = 0; l < D; ++l) acc = fma(k.Dl[l * D + j], dnb[l], acc);
-        y2b[j] = acc;
+        for (int l = 0; l < D; ++l) acc = fma(dl_col[l], get(dnb, l), acc);
+        y2b = acc;
     }
-    // y2 = y + T (R - I) T^T y: zb = T^T y2b; ybar = y2b + T (R^T - I) zb
-    R zb[D], dzb[D];
-    matTvec<D>(zb, k.T, y2b);
+    R zb;  // zb = T^T y2b
+    {
+        R acc = t_col[0] * get(y2b, 0);
 #pragma unroll
-    for (int j = 0; j < D; ++j) dzb[j] = R(0);
+        for (int j = 1; j < D; ++j) acc = fma(t_col[j], get(y2b, j), acc);
+        zb = acc;
+    }
+    const R zb_pair = __shfl_xor_sync(full, zb, 1, LN);
+    const R zv_pair = __shfl_xor_sync(full, zv, 1, LN);
+    R dzb = R(0), br = R(0);
+    if (r < 2 * Q) {
+        const bool even = r % 2 == 0;
+        dzb = even ? fma(c1[pl], zb, -(sn[pl] * zb_pair)) : fma(c1[pl], zb, sn[pl] * zb_pair);
+        if (even) {
+            const R zx = zv, zy = zv_pair, bx = zb, by = zb_pair, cs = R(1) + c1[pl];
+            br = bx * fma(-sn[pl], zx, cs * zy) + by * fma(-cs, zx, -(sn[pl] * zy));
+        }
+    }
     R e_term = R(0);
-    double thb[Q];
 #pragma unroll
-    for (int p = 0; p < Q; ++p) {
-        const R zx = z[2 * p], zy = z[2 * p + 1], bx = zb[2 * p], by = zb[2 * p + 1];
-        dzb[2 * p] = fma(c1[p], bx, -(sn[p] * by));
-        dzb[2 * p + 1] = fma(c1[p], by, sn[p] * bx);
-        const R cs = R(1) + c1[p];
-        // d/dphi of R z = (-s zx + c zy, -c zx - s zy)
-        const R br = bx * fma(-sn[p], zx, cs * zy) + by * fma(-cs, zx, -(sn[p] * zy));
-        e_term = fma(k.theta_dt[p], br, e_term);
-        thb[p] = static_cast<double>(br) * static_cast<double>(e) * a.dt;
+    for (int p = 0; p < Q; ++p) e_term = fma(k.theta_dt[p], get(br, 2 * p), e_term);
+    R yb;  // yb = y2b + T dzb
+    {
+        R acc = t_row[0] * get(dzb, 0);
+#pragma unroll
+        for (int j = 1; j < D; ++j) acc = fma(t_row[j], get(dzb, j), acc);
+        yb = y2b + acc;
     }
-    R yb[D];
+    R db;  // db = yb + Dl^T yb
+    {
+        R acc = yb;
 #pragma unroll
-    for (int j = 0; j < D; ++j) yb[j] = y2b[j];
-    matvec_acc<D>(yb, k.T, dzb);
-    // y = A0 d + b
-    R db[D];
-#pragma unroll
-    for (int j = 0; j < D; ++j) {
-        R acc = yb[j];
-#pragma unroll
-        for (int l = 0; l < D; ++l) acc = fma(k.Dl[l * D + j], yb[l], acc);
-        db[j] = acc;
+        for (int l = 0; l < D; ++l) acc = fma(dl_col[l], get(yb, l), acc);
+        db = acc;
     }
-    if (medium) {
-#pragma unroll
-        for (int j = 0; j < D; ++j) a.Sb[j * a.stride + m] = db[j];
-        eb += e_term;
-    }
-    if (live) a.Eb[ii] = eb;
+    if (mrow) a.Sb[r * a.stride + m] = db;
+    if (medium) eb += e_term;
+    if (live && r == 0) a.Eb[ii] = eb;
 
-    // parameter accumulators of this cell
-    if (!medium) return;
+    // parameter accumulators of this cell: lane r owns row r (shuffles for all lanes)
 #pragma unroll
-    for (int r = 0; r < D; ++r) {
-#pragma unroll
-        for (int c = 0; c < D; ++c)
-            acc_add(a.acc, n, ii, L::Dl + r * D + c,
-                    static_cast<double>(dnb[r]) * y2[c] + static_cast<double>(yb[r]) * d[c]);
-        acc_add(a.acc, n, ii, L::b + r, static_cast<double>(dnb[r]) + yb[r]);
-        acc_add(a.acc, n, ii, L::w + r, static_cast<double>(pbar) * dn[r]);
-        // T_bar = y2b (dz)^T + y (dzb)^T on the plane columns
-#pragma unroll
-        for (int c = 0; c < 2 * Q; ++c)
-            acc_add(a.acc, n, ii, L::T + r * D + c,
-                    static_cast<double>(y2b[r]) * dz[c] + static_cast<double>(y[r]) * dzb[c]);
+    for (int c = 0; c < D; ++c) {
+        const R y2c = get(y2v, c), dc = get(dv, c);
+        if (mrow) acc_add(a.acc, n, ii, L::Dl + r * D + c, static_cast<double>(dnb) * y2c + static_cast<double>(yb) * dc);
     }
-    acc_add(a.acc, n, ii, L::c, static_cast<double>(pbar));
+    if (mrow) {
+        acc_add(a.acc, n, ii, L::b + r, static_cast<double>(dnb) + yb);
+        acc_add(a.acc, n, ii, L::w + r, static_cast<double>(pbar) * dnv);
+    }
 #pragma unroll
-    for (int p = 0; p < Q; ++p) acc_add(a.acc, n, ii, L::th + p, thb[p]);
+    for (int c = 0; c < 2 * Q; ++c) {
+        const R dzc = get(dzv, c), dzbc = get(dzb, c);
+        if (mrow)
+            acc_add(a.acc, n, ii, L::T + r * D + c, static_cast<double>(y2b) * dzc + static_cast<double>(yv) * dzbc);
+    }
+    if (medium && r == 0) acc_add(a.acc, n, ii, L::c, static_cast<double>(pbar));
+    if (medium && r < 2 * Q && r % 2 == 0)
+        acc_add(a.acc, n, ii, L::th + r / 2, static_cast<double>(br) * static_cast<double>(e) * a.dt);
 }
 
 }  // namespace mln

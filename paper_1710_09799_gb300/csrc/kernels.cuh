@@ -77,6 +77,11 @@ struct BlockArgs {
     R *s_out;
     const double *src;     // samples of this launch's steps, or nullptr
     unsigned int *flags;   // bit 0: non-finite E seen
+    // optional record of every step (nullptr: none): after step st the
+    // interior cells also write E, H and the state to rec_E, rec_H, rec_S
+    // advanced by st * rec_set bytes (the adjoint's recomputed segment)
+    R *rec_E, *rec_H, *rec_S;
+    int64_t rec_set;
     int64_t n_cells, mb, me, stride, source_cell;
     int32_t nsteps, halo, tile, boundary, source_kind, pad_;
     R ch, ca, cb, inv_dx, kappa;
@@ -526,6 +531,8 @@ __device__ __forceinline__ void block_body(const BlockArgs<R> &a, const typename
     const bool mur = !periodic && loaded && gm == n - 2 && j + 1 < L;
     const bool mur_cell = !periodic && loaded && gm == n - 1;
     const bool is_src = a.src != nullptr && loaded && gm == a.source_cell;
+    const bool interior = loaded && j >= a.halo && j < a.halo + static_cast<int>(t1 - t0);
+    const bool record = a.rec_E != nullptr && interior;
     __syncthreads();
 
     for (int st = 0; st < a.nsteps; ++st) {
@@ -557,6 +564,12 @@ __device__ __forceinline__ void block_body(const BlockArgs<R> &a, const typename
         __syncthreads();
         // the Mur cell takes its new value from shared memory
         if (mur_cell) e = nE[j];
+        if (record) {
+            const int64_t off = static_cast<int64_t>(st) * a.rec_set;
+            reinterpret_cast<R *>(reinterpret_cast<char *>(a.rec_E) + off)[gm] = e;
+            reinterpret_cast<R *>(reinterpret_cast<char *>(a.rec_H) + off)[gm] = h;
+            if (medium) cell.store(reinterpret_cast<R *>(reinterpret_cast<char *>(a.rec_S) + off), a.stride, m);
+        }
         R *t = cE;
         cE = nE;
         nE = t;
@@ -565,7 +578,6 @@ __device__ __forceinline__ void block_body(const BlockArgs<R> &a, const typename
         nH = t;
     }
 
-    const bool interior = loaded && j >= a.halo && j < a.halo + static_cast<int>(t1 - t0);
     if (interior) {
         a.E_out[gm] = e;
         a.H_out[gm] = h;
@@ -619,6 +631,8 @@ __device__ __forceinline__ void batch_body(const BatchGrid<R> *__restrict__ grid
     a.s_out = g.S[parity ^ 1];
     a.src = g.src ? g.src + step_offset : nullptr;
     a.flags = g.flags;
+    a.rec_E = a.rec_H = a.rec_S = nullptr;
+    a.rec_set = 0;
     a.n_cells = g.n_cells;
     a.mb = g.mb;
     a.me = g.me;
