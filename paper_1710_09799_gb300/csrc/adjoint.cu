@@ -85,11 +85,9 @@ mln_status adjoint_t(mln_ctx *c, int64_t n_steps, const double *src, int64_t pro
     mln::BlockArgs<R> fa = mln::base_args<R>(c);
     // Reverse step: AdjLanes<N> lanes per cell, blocks of 128 threads.
     const unsigned rblocks = static_cast<unsigned>((n * mln::AdjLanes<N>::value + 127) / 128);
-    // Recompute: up to rK fused steps per launch, every step recorded into its
-    // slot; blocks of rthreads threads with tiles of rthreads - 2 rK cells.
-    const int rK = 8, rthreads = 64;
-    fa.halo = rK;
-    fa.tile = rthreads - 2 * rK;
+    // Recompute: the context's launch shape (fused steps per launch, tile,
+    // threads; autotuned if the caller did), every step recorded into its slot.
+    const int rK = c->K, rthreads = c->threads;
     mln::AdjArgs<R> aa{};
     Set<R> A0s, A1s;
 
@@ -147,7 +145,7 @@ mln_status adjoint_t(mln_ctx *c, int64_t n_steps, const double *src, int64_t pro
             fa.nsteps = ns;
             fa.src = (src && c->p.source_kind != MLN_SRC_NONE) ? src + s0 + j : nullptr;
             MLN_ACK(c, mln::launch_block(c->p.N, MLN_FORM_STRANG, fa, c->consts,
-                                         dim3(static_cast<unsigned>((n + fa.tile - 1) / fa.tile)), dim3(rthreads),
+                                         dim3(static_cast<unsigned>((n + c->tile - 1) / c->tile)), dim3(rthreads),
                                          mln::field_smem<R>(rthreads), c->stream));
         }
         for (int64_t j = len - 1; j >= 0; --j) {
