@@ -55,7 +55,7 @@ struct TcShape {
     static constexpr int OFF_E = OFF_Z + G * 2 * ZBYTES;
     static constexpr int OFF_H = OFF_E + G * ROWS * 4;
     static constexpr int OFF_BAR = OFF_H + G * ROWS * 4;
-    static constexpr int SMEM = OFF_BAR + 8 * G + 16;
+    static constexpr int SMEM = OFF_BAR + 8 * (G + 1) + 16;  // one MMA barrier per group, one for the B copy
     static_assert(ACC + (N1 > N3 ? N1 : N3) <= GCOLS, "tensor-memory columns of one group");
     static_assert(L1 <= N1 && L3 <= N3, "read-back beyond the accumulator");
     static_assert(SMEM <= 227 * 1024, "shared memory");
@@ -173,16 +173,21 @@ __global__ void __launch_bounds__(512, 1)
     float *sE = reinterpret_cast<float *>(smem + S::OFF_E) + g * ROWS;
     float *sH = reinterpret_cast<float *>(smem + S::OFF_H) + g * ROWS;
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem + S::OFF_BAR);
-    uint32_t *tslot = reinterpret_cast<uint32_t *>(smem + S::OFF_BAR + 8 * G);
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(smem + S::OFF_BAR + 8 * (G + 1));
 
-    for (int o = tid; o < S::BIMG / 16; o += blockDim.x) reinterpret_cast<uint4 *>(smem)[o] = bimg[o];
-    if (tid < G) tc::mbar_init(tc::smem_addr(&bars[tid]), 1);
+    // B images: one bulk copy into shared memory, completion on bars[G]
+    if (tid <= G) tc::mbar_init(tc::smem_addr(&bars[tid]), 1);
+    tc::mbar_init_fence();
+    __syncthreads();
+    if (tid == 0) {
+        tc::mbar_expect_tx(tc::smem_addr(&bars[G]), S::BIMG);
+        tc::bulk_load(tc::smem_addr(smem), bimg, S::BIMG, tc::smem_addr(&bars[G]));
+    }
     if (warp == 0) {
         tc::tmem_alloc(tc::smem_addr(tslot), S::TMEM_COLS);
         tc::tmem_relinquish();
     }
-    tc::mbar_init_fence();
-    tc::fence_async_smem();
+    bool ok = tc::mbar_wait(tc::smem_addr(&bars[G]), 0);
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
@@ -198,7 +203,6 @@ __global__ void __launch_bounds__(512, 1)
     const uint32_t id1 = tc::idesc_tf32(S::N1), id3 = tc::idesc_tf32(S::N3);
     const int bar_id = 1 + g;
     uint32_t phase = 0;
-    bool ok = true;
 
     // z = T^T y: A = y from tensor memory (one thread)
     auto issue_z = [&] {

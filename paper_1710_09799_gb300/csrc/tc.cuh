@@ -1,6 +1,7 @@
 // Fifth-generation tensor core primitives for sm_103a (internal header):
-// tensor memory allocation, tcgen05.mma of kind::tf32 with both operands in
-// shared memory, completion through an mbarrier, and accumulator reads.
+// tensor memory allocation, tcgen05.mma of kind::tf32 (A in tensor or shared
+// memory, B in shared memory), completion through an mbarrier, accumulator
+// reads and writes, and bulk global-to-shared copies.
 //
 // Operand layout (both A and B "K-major", no swizzle): a matrix of R rows and
 // K columns (K a multiple of 4) is stored as 8-row x 16-byte core matrices;
@@ -124,6 +125,21 @@ __device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
         if (ok) return true;
     }
     return false;
+}
+
+// --- bulk copies (the asynchronous copy engine) -------------------------------
+
+// Arm the mbarrier for `bytes` of incoming transactions (this thread's arrival).
+__device__ __forceinline__ void mbar_expect_tx(uint32_t mbar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mbar), "r"(bytes) : "memory");
+}
+
+// Copy `bytes` (a multiple of 16; both addresses 16-byte aligned) from global
+// to this CTA's shared memory; completion is counted on the mbarrier.
+__device__ __forceinline__ void bulk_load(uint32_t dst, const void *src, uint32_t bytes, uint32_t mbar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+                 "l"(src), "r"(bytes), "r"(mbar)
+                 : "memory");
 }
 
 // --- accumulator reads -------------------------------------------------------
