@@ -195,6 +195,23 @@ mln_status mln_create(const mln_params *p, void *d_state, void *Ez, void *Hy, vo
  */
 mln_status mln_step(mln_ctx *ctx, int64_t n_steps, const double *src);
 
+/*
+ * Positivity projection of the medium state (optional; FP64 on the device, off
+ * the step path). Trace and Hermiticity of every cell's rho hold by
+ * construction in the adjoint representation (Eq. 6); rounding (most of all
+ * in FP32) can leave rho with a slightly negative eigenvalue. For each such
+ * cell this replaces rho by the nearest positive semidefinite unit-trace
+ * matrix in the Frobenius norm (eigenvalues projected onto the probability
+ * simplex, eigenvectors kept; Hermitian eigen-decomposition by complex Jacobi
+ * rotations). Cells whose smallest eigenvalue is at least -16 N u (u = 2^-53
+ * in FP64, 2^-24 in FP32: a zero eigenvalue after rounding) keep their state
+ * bit for bit. Queued on the context's stream after the work already there;
+ * synchronous.
+ *   n_projected  NULL or receives the number of cells changed.
+ * Call it every K steps for a periodic re-projection.
+ */
+mln_status mln_project_positive(mln_ctx *ctx, int64_t *n_projected);
+
 /* Wait for the queued work; report device-side problems (MLN_ENONFINITE, or
  * MLN_ETIMEOUT when a tensor-core kernel gave up waiting for an MMA). */
 mln_status mln_sync(mln_ctx *ctx);

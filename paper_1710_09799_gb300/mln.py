@@ -94,6 +94,7 @@ _SIGS = {
     "mln_last_error": (C.c_char_p, [C.c_void_p]),
     "mln_create_error": (C.c_char_p, []),
     "mln_setup_host": (C.c_int, [_P, C.POINTER(mln_setup)]),
+    "mln_project_positive": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64)]),
     "mln_lindblad_superop": (C.c_int, [C.c_int32, _dp, _dp, _dp]),
     "mln_version": (C.c_char_p, []),
     "mln_kernel_source": (C.c_int, [_P, C.c_char_p, C.c_size_t, C.POINTER(C.c_size_t)]),
@@ -402,6 +403,13 @@ class Solver:
 
     def autotune(self, trials: int = 3):
         return mln_autotune(self.ctx, trials)
+
+    def project_positive(self) -> int:
+        """Project every cell's rho with a negative eigenvalue onto the nearest
+        state (see include/mln.h); returns the number of cells changed."""
+        k = C.c_int64(0)
+        _check(lib().mln_project_positive(self.ctx, C.byref(k)), self.ctx)
+        return k.value
 
     @property
     def work_per_step(self):
