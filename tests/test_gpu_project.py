@@ -100,3 +100,25 @@ def test_projection_leaves_physical_states_alone():
     for a, b in zip(before, after):
         assert np.array_equal(a, b)
     s.close()
+
+
+def test_fp32_run_with_periodic_projection(orc):
+    """FP32 six-level run with the projection every 100 steps: the error
+    against the FP64 oracle stays within the FP32 tolerance."""
+    p = W.six_level_pulse(n_cells=2048, n_steps=600)
+    st, _ = orc.run(p, n_steps=p.n_steps)
+    from helpers import src_tensor
+    s = make_solver(p, "fp32", "merged")
+    projected = 0
+    for k in range(0, p.n_steps, 100):
+        s.step(100, src_tensor(p, k, 100))
+        projected += s.project_positive()
+    s.sync()
+    E, _ = s.fields()
+    rho = s.rho()
+    e_err = float(np.abs(E - st.E).max() / np.abs(st.E).max())
+    p_err = float(np.abs(np.einsum("cii->ci", rho - st.rho).real).max())
+    print(f"fp32 six-level with projection every 100 steps: {projected} cell projections, "
+          f"E rel {e_err:.3e}, pop abs {p_err:.3e}")
+    assert e_err < 2e-3 * 0.6 and p_err < 2e-5 * 0.6
+    s.close()
