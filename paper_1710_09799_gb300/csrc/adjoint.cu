@@ -83,8 +83,9 @@ mln_status adjoint_t(mln_ctx *c, int64_t n_steps, const double *src, int64_t pro
     };
     const Set<R> user{static_cast<R *>(c->E[0]), static_cast<R *>(c->H[0]), static_cast<R *>(c->st[0])};
     mln::BlockArgs<R> fa = mln::base_args<R>(c);
-    // Reverse step: AdjLanes<N> lanes per cell, blocks of 128 threads.
-    const unsigned rblocks = static_cast<unsigned>((n * mln::AdjLanes<N>::value + 127) / 128);
+    // Reverse step: AdjLanes<N> lanes per cell, blocks of 64 threads (all resident
+    // at once for rings of this size; small blocks spread evenly over the SMs).
+    const unsigned rblocks = static_cast<unsigned>((n * mln::AdjLanes<N>::value + 63) / 64);
     // Recompute: the context's launch shape (fused steps per launch, tile,
     // threads; autotuned if the caller did), every step recorded into its slot.
     const int rK = c->K, rthreads = c->threads;
@@ -160,7 +161,7 @@ mln_status adjoint_t(mln_ctx *c, int64_t n_steps, const double *src, int64_t pro
             aa.Hb = A1s.H;
             aa.Sb = A1s.S;
             aa.dsrc = (src && c->p.source_kind != MLN_SRC_NONE) ? dsrc + s0 + j : nullptr;
-            mln::mln_adjoint_step_rows<N, R><<<rblocks, 128, 0, c->stream>>>(aa, k);
+            mln::mln_adjoint_step_rows<N, R><<<rblocks, 64, 0, c->stream>>>(aa, k);
             MLN_ACK(c, cudaGetLastError());
             std::swap(A0s, A1s);
         }
