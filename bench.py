@@ -348,6 +348,25 @@ def time_e2e(p, precision, form, seg, steps):
                 d2h_bytes_per_step=d2h, steps=steps, seconds=t)
 
 
+def cpu_model() -> str:
+    """The host CPU's model name (as the kernel reports it), for the baseline record."""
+    import platform
+    try:
+        part = None
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                key = line.split(":")[0].strip().lower()
+                if key in ("model name", "cpu model", "hardware"):
+                    return line.split(":", 1)[1].strip()
+                if key == "cpu part" and part is None:
+                    part = line.split(":", 1)[1].strip()
+        if part is not None:  # Arm: the part number (0xd4f: Neoverse V2, as in Grace)
+            return f"{platform.machine()} CPU part {part}"
+        return platform.processor() or platform.machine()
+    except OSError:
+        return platform.machine() or "unknown"
+
+
 def oracle_rate(p, target_s: float, threads: int, max_steps: int = 100000):
     """Oracle cell-updates/s on the full grid for about target_s seconds."""
     import oracle
@@ -541,6 +560,7 @@ def main():
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": main_run["ms"] / args.steps, "higher_is_better": True,
+        "medium_cell_updates_per_s": value * p.n_medium / p.n_cells,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32",
         "data": "synthetic (seeded: levels, dipoles, rates, noise E^0)",
         "config": {"workload": WORKLOADS[args.workload], "n_cells": p.n_cells, "levels": p.N,
@@ -570,8 +590,12 @@ def main():
         if ws == 1:
             threads = os.cpu_count() or 1
             rate, n, secs = oracle_rate(p, 10.0, threads)
+            rate1, n1, secs1 = oracle_rate(p, 3.0, 1)  # one thread: the paper's own protocol
             line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle",
-                                    "sample": f"full 65536-cell ring, {n} time steps ({secs:.1f} s), FP64"}
+                                    "sample": f"full 65536-cell ring, {n} time steps ({secs:.1f} s), FP64",
+                                    "cpu_model": cpu_model(),
+                                    "single_thread": {"value": rate1, "unit": UNIT, "cores": 1,
+                                                      "sample": f"{n1} time steps ({secs1:.1f} s)"}}
             line["vs_oracle"] = value / rate
     if rank == 0:
         print(json.dumps(line), flush=True)
