@@ -414,7 +414,8 @@ def run_reference(args):
                    "levels": p.N, "l2": "n/a (CPU)"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
                          "sample": f"full 65536-cell ring, {seg} time steps per step, "
-                                   f"{args.steps} steps after {args.warmup} warm-up"},
+                                   f"{args.steps} steps after {args.warmup} warm-up",
+                         "cpu_model": cpu_model()},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
