@@ -73,8 +73,9 @@ enum { MLN_FORM_STRANG = 0, MLN_FORM_MERGED = 1, MLN_FORM_RODRIGUES = 2 };
  * MLN_KERNEL_SPARSE (FP64, merged form only) keeps the vectors in shared
  * memory and multiplies only by the entries of the constant matrices that
  * are not exactly zero; the sums run in the same order, so both give the
- * same result. MLN_KERNEL_AUTO picks SPARSE for FP64 merged, JIT for FP32
- * merged when NVRTC is available, REGISTER otherwise. */
+ * same result. MLN_KERNEL_AUTO picks SPARSE for FP64 merged, TENSOR for FP32
+ * merged with N = 5 or 6 (the dense case), JIT for the other FP32 merged
+ * problems when NVRTC is available, REGISTER otherwise. */
 /* MLN_KERNEL_JIT (merged form) generates, at mln_create, this problem's step
  * as straight-line CUDA with the constants as literals and the exactly-zero
  * entries left out, compiles it for sm_103a at run time (NVRTC) and launches
@@ -86,8 +87,10 @@ enum { MLN_FORM_STRANG = 0, MLN_FORM_MERGED = 1, MLN_FORM_RODRIGUES = 2 };
  * (the plane coordinates T^T y, then the increment of y and dP/dt from
  * [y ; dz] in one product), each FP32 operand split into a high and a low
  * TF32 part (three MMAs per K block: FP32-level accuracy, not the FP32
- * register model's bits). Up to 32 steps per launch (block_steps), tiles of
- * 128 - 2 block_steps cells; tile_cells is ignored. */
+ * register model's bits). Up to 32 steps per launch (block_steps; larger
+ * values are an error with MLN_KERNEL_TENSOR and are capped at 32 when
+ * MLN_KERNEL_AUTO picks it), tiles of 128 - 2 block_steps cells; tile_cells is
+ * ignored. */
 enum {
     MLN_KERNEL_AUTO = 0,
     MLN_KERNEL_REGISTER = 1,

@@ -101,7 +101,7 @@ void pick_launch_shape(mln_ctx *c) {
     c->sms = sms;
     if (c->tc) {
         // tiles of one MMA (128 rows) including the halo of K cells on both sides
-        c->K = c->p.block_steps > 0 ? c->p.block_steps : 8;
+        c->K = std::min(c->p.block_steps > 0 ? c->p.block_steps : 8, 32);
         c->tile = mln::tc_rows() - 2 * c->K;
         c->threads = 512;
         return;
@@ -596,7 +596,9 @@ mln_status mln_create(const mln_params *p, void *d_state, void *Ez, void *Hy, vo
             c->err = "sparse program does not fit in shared memory";
             return fail(MLN_EUNSUPPORTED);
         }
-    } else if (p->kernel == MLN_KERNEL_TENSOR) {
+    } else if (p->kernel == MLN_KERNEL_TENSOR ||
+               (p->kernel == MLN_KERNEL_AUTO && p->precision == MLN_FP32 && p->form == MLN_FORM_MERGED &&
+                mln::tc_supported(p->N))) {
         std::vector<unsigned char> img;
         ok = mln::tc_supported(p->N) && mln::pack_tc(c->s, p->dt, img, c->tc_scal);
         if (ok) {
@@ -606,7 +608,7 @@ mln_status mln_create(const mln_params *p, void *d_state, void *Ez, void *Hy, vo
                 c->err = "upload of the tensor-core operands failed";
                 return fail(MLN_ENOMEM);
             }
-            c->tc = p->kernel;
+            c->tc = MLN_KERNEL_TENSOR;
         }
     } else {
         ok = p->precision == MLN_FP64 ? mln::pack_consts(c->s, p->form, p->dt, 0.0, c->consts)
