@@ -179,3 +179,50 @@ def test_autograd_function(small):
     assert np.allclose(s_t.grad.numpy(), dsrc, rtol=1e-12, atol=0)
     assert np.allclose(mu_p.grad.numpy(), dmu, rtol=1e-12, atol=0)
     assert np.allclose(rates.grad.numpy(), rate_grad(dG, p), rtol=1e-10)
+
+
+def test_full_size_gradient_along_seeded_directions():
+    """The gradient workload at full size (8192 cells, 5000 steps, 512 source
+    samples, checkpoints every 256 steps, the benchmark's launch shape): the
+    adjoint directional derivative along 10 seeded directions in the joint
+    space of the 3 real dipole elements, the 3 relaxation rates and the 512
+    source samples against central finite differences (h = 1e-6 relative)."""
+    from paper_1710_09799_gb300 import mln
+    p = W.adjoint_ring()
+    src = p.source_samples(0, p.n_steps)
+    ns = p.meta["n_src"]
+    mu0 = mln.mu_to_params(p.mu)
+    r0 = p.meta["rate_values"]
+
+    def run(mu_x, rates, s, grads=False):
+        q = p.with_(mu=mln.mu_from_params(p.N, mu_x).numpy(), G=G_of(p, rates))
+        sol = mln.Solver(params_of(q, precision="fp64", form="strang"), E0=q.e_init())
+        sol.autotune(2)
+        t = __import__("torch").as_tensor(s, dtype=__import__("torch").float64, device="cuda")
+        out = mln.mln_adjoint(sol.ctx, q.N, len(s), t.data_ptr(), p.meta["probe_cell"], 256)
+        sol.close()
+        return out if grads else out[0]
+
+    J, dsrc, dmu, dG = run(mu0, r0, src, grads=True)
+    g_rates = rate_grad(dG, p)
+    idx = [p.N + k for k in range(3)]  # Re mu_12, mu_13, mu_23
+    scale_mu = np.abs(mu0[idx])
+    scale_src = np.abs(src[:ns]).max()
+    rng = np.random.default_rng(2024)
+    h = 1e-6
+    for trial in range(10):
+        u_mu, u_r, u_s = rng.normal(size=3), rng.normal(size=3), rng.normal(size=ns)
+        d_mu = h * scale_mu * u_mu
+        d_r = h * r0 * u_r
+        d_s = h * scale_src * u_s
+        ad = float(dmu[idx] @ d_mu + g_rates @ d_r + dsrc[:ns] @ d_s)
+
+        def shifted(sign):
+            mu_x = mu0.copy()
+            mu_x[idx] += sign * d_mu
+            s = src.copy()
+            s[:ns] += sign * d_s
+            return run(mu_x, r0 + sign * d_r, s)
+
+        fd = (shifted(+1) - shifted(-1)) / 2
+        assert abs(fd - ad) < 1e-5 * abs(ad) + 1e-13 * J, (trial, fd, ad)
