@@ -500,9 +500,15 @@ __device__ __forceinline__ void block_body(const BlockArgs<R> &a, const typename
     const int64_t n = a.n_cells;
     const int64_t t0 = tile_index * a.tile;
     const int64_t t1 = min(t0 + a.tile, n);
-    const int L = static_cast<int>(t1 - t0) + 2 * a.halo;
     const bool periodic = a.boundary == 0;
-    const int64_t g = t0 - a.halo + j;
+    // The Mur cell's value comes from its left neighbour's thread in the same
+    // step, so its dependence reaches one cell further left than a step's:
+    // a tile that starts at the Mur cell loads one more cell on the left
+    // (that tile has one cell, and a block of at least 2 halo + 1 threads,
+    // rounded up to a warp, has a thread to spare).
+    const int lh = a.halo + ((!periodic && t0 == n - 1) ? 1 : 0);
+    const int L = static_cast<int>(t1 - t0) + lh + a.halo;
+    const int64_t g = t0 - lh + j;
     int64_t gm = g;
     bool loaded = j < L;
     if (periodic) {
@@ -531,36 +537,47 @@ __device__ __forceinline__ void block_body(const BlockArgs<R> &a, const typename
     const bool mur = !periodic && loaded && gm == n - 2 && j + 1 < L;
     const bool mur_cell = !periodic && loaded && gm == n - 1;
     const bool is_src = a.src != nullptr && loaded && gm == a.source_cell;
-    const bool interior = loaded && j >= a.halo && j < a.halo + static_cast<int>(t1 - t0);
+    const int tlen = static_cast<int>(t1 - t0);
+    const bool interior = loaded && j >= lh && j < lh + tlen;
     const bool record = a.rec_E != nullptr && interior;
+    // Light cone: the tile's values after nsteps steps depend on the values
+    // after step st only within nsteps - 1 - st cells of the tile; one cell
+    // more keeps the Mur cell's left neighbour, whose thread computes the Mur
+    // cell's value in the same step. A warp with no cell within
+    // nsteps - st of the tile skips step st (and every later one: the region
+    // only shrinks, so the values it leaves stale are never read).
+    const int w0 = j & ~31;
+    const int active = min(w0 + 32 - lh, lh + tlen - w0) + a.nsteps;  // steps this warp computes
     __syncthreads();
 
     for (int st = 0; st < a.nsteps; ++st) {
-        if (h_upd) h = fma(a.ch, cE[j + 1] - e, h);
-        // the previous cell's new H, with the operands and operations of its own thread
-        R hl = R(0);
-        if (e_upd) hl = fma(a.ch, e - cE[j - 1], cH[j - 1]);
-        R dpdt = R(0);
-        if (medium) dpdt = cell.step(e, k);
-        cell.end_step();
-        R en = e;
-        if (e_upd) en = fma(a.ca, e, a.cb * fma(h - hl, a.inv_dx, -dpdt));
-        R e_mur = R(0);
-        if (mur) e_mur = fma(a.kappa, en - cE[j + 1], e);  // from E^{n+1} before any source
-        if (is_src) {
-            R v = static_cast<R>(a.src[st]);
-            en = (a.source_kind == 1) ? v : en + v;
-        }
-        if (mur) {
-            if (a.src != nullptr && a.source_cell == n - 1) {
+        if (st < active) {  // warp-uniform
+            if (h_upd) h = fma(a.ch, cE[j + 1] - e, h);
+            // the previous cell's new H, with the operands and operations of its own thread
+            R hl = R(0);
+            if (e_upd) hl = fma(a.ch, e - cE[j - 1], cH[j - 1]);
+            R dpdt = R(0);
+            if (medium) dpdt = cell.step(e, k);
+            cell.end_step();
+            R en = e;
+            if (e_upd) en = fma(a.ca, e, a.cb * fma(h - hl, a.inv_dx, -dpdt));
+            R e_mur = R(0);
+            if (mur) e_mur = fma(a.kappa, en - cE[j + 1], e);  // from E^{n+1} before any source
+            if (is_src) {
                 R v = static_cast<R>(a.src[st]);
-                e_mur = (a.source_kind == 1) ? v : e_mur + v;
+                en = (a.source_kind == 1) ? v : en + v;
             }
-            nE[j + 1] = e_mur;
+            if (mur) {
+                if (a.src != nullptr && a.source_cell == n - 1) {
+                    R v = static_cast<R>(a.src[st]);
+                    e_mur = (a.source_kind == 1) ? v : e_mur + v;
+                }
+                nE[j + 1] = e_mur;
+            }
+            e = en;
+            if (!mur_cell) nE[j] = e;
+            nH[j] = h;
         }
-        e = en;
-        if (!mur_cell) nE[j] = e;
-        nH[j] = h;
         __syncthreads();
         // the Mur cell takes its new value from shared memory
         if (mur_cell) e = nE[j];

@@ -252,8 +252,12 @@ __global__ void __launch_bounds__(512, 1)
          tile_index += static_cast<int64_t>(gridDim.x) * G) {
         const int64_t t0 = tile_index * a.tile;
         const int64_t t1 = min(t0 + a.tile, n);
-        const int L = static_cast<int>(t1 - t0) + 2 * a.halo;
-        const int64_t gi = t0 - a.halo + j;
+        // a tile that starts at the Mur cell loads one more cell on the left:
+        // the Mur cell's value comes from its left neighbour's row in the same
+        // step (that tile has one cell, so 2 halo + 2 <= 128 rows)
+        const int lh = a.halo + ((!periodic && t0 == n - 1) ? 1 : 0);
+        const int L = static_cast<int>(t1 - t0) + lh + a.halo;
+        const int64_t gi = t0 - lh + j;
         int64_t gm = gi;
         bool loaded = j < L;
         if (periodic) {
@@ -337,7 +341,7 @@ __global__ void __launch_bounds__(512, 1)
             if (st + 1 < a.nsteps) issue(issue_z);
         }
 
-        const bool interior = loaded && j >= a.halo && j < a.halo + static_cast<int>(t1 - t0);
+        const bool interior = loaded && j >= lh && j < lh + static_cast<int>(t1 - t0);
         if (interior) {
             a.E_out[gm] = e;
             a.H_out[gm] = h;

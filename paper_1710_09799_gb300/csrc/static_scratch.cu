@@ -23,7 +23,7 @@
 namespace {
 
 // Every device that loads this library holds this array until the process exits.
-__device__ __align__(256) unsigned char g_static_scratch[MLN_STATIC_SCRATCH_BYTES];
+static __device__ __align__(256) unsigned char g_static_scratch[MLN_STATIC_SCRATCH_BYTES];
 
 constexpr int kMaxDevices = 64;
 std::mutex g_mutex;

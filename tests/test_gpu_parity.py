@@ -149,6 +149,28 @@ def test_launch_shape_does_not_change_results(shape):
     assert np.array_equal(E0, E1) and np.array_equal(H0, H1) and np.array_equal(r0, r1)
 
 
+@pytest.mark.parametrize("K,tile", [(8, 200), (40, 100), (64, 40), (1, 50), (33, 8)])
+def test_tile_made_of_the_mur_cell_alone(orc, K, tile):
+    """Open grid of 201 cells whose last tile is the Mur cell (cell 200) alone:
+    its value comes from cell 199's update in the same step, so its dependence
+    reaches one cell beyond a K-step halo. The pulse reaches the boundary within
+    the run, so a wrong Mur cell would show in E_z. Against the oracle, and bit
+    for bit against a shape whose tiles never start at the Mur cell."""
+    p = W.two_level_sit(n_cells=201, medium=(50, 150), n_steps=1200)
+    assert (p.n_cells - 1) % tile == 0
+    ref = oracle_ref(orc, p, p.n_steps)
+    E, H, rho, s = gpu_run(p, p.n_steps, "fp64", "merged", kernel="register", block_steps=K, tile_cells=tile)
+    s.close()
+    assert np.abs(ref.E[-5:]).max() > 1e3  # the field has reached the Mur cell
+    assert rel_inf(E, ref.E) < FP64_E and np.abs(pops(rho) - pops(ref.rho)).max() < FP64_POP
+    for precision in ("fp64", "fp32"):
+        a = gpu_run(p, p.n_steps, precision, "merged", kernel="register", block_steps=K, tile_cells=tile)
+        b = gpu_run(p, p.n_steps, precision, "merged", kernel="register", block_steps=7, tile_cells=30)
+        assert all(np.array_equal(x, y) for x, y in zip(a[:3], b[:3])), precision
+        a[3].close()
+        b[3].close()
+
+
 @pytest.mark.parametrize("precision,form", [("fp64", "merged"), ("fp32", "merged"), ("fp64", "strang")])
 def test_autotune_changes_no_state_and_no_result(precision, form):
     """The autotuner times candidate shapes without touching the state, and

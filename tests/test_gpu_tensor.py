@@ -101,6 +101,20 @@ def test_launch_shape_does_not_change_the_bits():
             assert np.array_equal(a, b), bs
 
 
+def test_tile_made_of_the_mur_cell_alone():
+    """337 cells and 8 steps per launch (tiles of 112 rows): the last tile is
+    the Mur cell alone, whose value comes from its left neighbour's row in the
+    same step; the bits match a shape whose tiles never start there (4 steps,
+    tiles of 120), after the pulse has reached the boundary."""
+    p = W.six_level_pulse(n_cells=337, n_steps=800, t0=15e-15, fwhm=10e-15)
+    assert (p.n_cells - 1) % 112 == 0 and (p.n_cells - 1) % 120 != 0
+    a = gpu_run(p, p.n_steps, "fp32", "merged", kernel="tensor", block_steps=8)
+    b = gpu_run(p, p.n_steps, "fp32", "merged", kernel="tensor", block_steps=4)
+    assert np.abs(b[0][-5:]).max() > 0.0
+    for x, y in zip(a[:3], b[:3]):
+        assert np.array_equal(x, y)
+
+
 def test_autotune_keeps_state():
     from paper_1710_09799_gb300 import mln
     p = W.six_level_pulse(n_cells=3000, n_steps=40, t0=15e-15, fwhm=10e-15)
