@@ -22,6 +22,7 @@ _LIB = os.path.join(_BUILD, "liboracle.so")
 
 BC = {"periodic": 0, "open": 1, "window": 2}
 SRC = {"none": 0, "hard": 1, "soft": 2}
+MAXWELL = {"fdtd": 0, "pstd": 1}
 
 
 class OrcProblem(C.Structure):
@@ -36,6 +37,7 @@ class OrcProblem(C.Structure):
         ("mu_r", C.c_double), ("sigma", C.c_double),
         ("boundary", C.c_int), ("source_kind", C.c_int),
         ("source_cell", C.c_long),
+        ("maxwell", C.c_int),
     ]
 
 
@@ -68,7 +70,9 @@ def lib():
             l.orc_dpdt.argtypes = [pp, dp, dp]
             l.orc_cell.argtypes = [pp, dp, C.c_long, dp, dp]
             l.orc_run.argtypes = [pp, dp, dp, dp, C.c_long, dp, C.c_long, dp, C.c_int]
-            for f in (l.orc_expm, l.orc_liouvillian, l.orc_dpdt, l.orc_cell, l.orc_run):
+            l.orc_spectral_derivative.argtypes = [C.c_long, C.c_double, C.c_double, dp, dp]
+            for f in (l.orc_expm, l.orc_liouvillian, l.orc_dpdt, l.orc_cell, l.orc_run,
+                      l.orc_spectral_derivative):
                 f.restype = C.c_int
             _lib = l
     return _lib
@@ -101,7 +105,8 @@ class _Bound:
             mu_r=prob.mu_r, sigma=prob.sigma,
             boundary=BC[prob.boundary if boundary is None else boundary],
             source_kind=SRC[prob.source_kind],
-            source_cell=prob.source_cell if source_cell is None else source_cell)
+            source_cell=prob.source_cell if source_cell is None else source_cell,
+            maxwell=MAXWELL[getattr(prob, "maxwell", "fdtd")])
 
 
 def expm(A: np.ndarray) -> np.ndarray:
@@ -149,6 +154,18 @@ def cell(prob, rho: np.ndarray, E_seq: np.ndarray):
     if rc:
         raise RuntimeError(f"orc_cell failed ({rc})")
     return r.view(np.complex128).reshape(prob.N, prob.N), dp
+
+
+def spectral_derivative(x: np.ndarray, dx: float, half: float) -> np.ndarray:
+    """Derivative of the trigonometric interpolant of the periodic samples x
+    (spacing dx) at the points shifted by half * dx (+1/2: E to H points,
+    -1/2: H to E points), as the PSTD field solver computes it."""
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    out = np.zeros_like(x)
+    rc = lib().orc_spectral_derivative(len(x), dx, half, _ptr(x), _ptr(out))
+    if rc:
+        raise RuntimeError(f"orc_spectral_derivative failed ({rc})")
+    return out
 
 
 class State:

@@ -43,6 +43,17 @@
  *     (hard: replace, soft: add);
  *   - vacuum cells (outside [medium_begin, medium_end)) carry no rho and
  *     contribute dP/dt = 0.
+ *
+ * Field solver: besides the FDTD differences of Fig. 1, the pseudo-spectral
+ * (PSTD) variant that Secs. 1 and 3 say the method carries over to: on a
+ * periodic grid of n cells, dE/dx at the H points and dH/dx at the E points are
+ * the derivatives of the trigonometric interpolants of the samples, i.e. the
+ * DFT multiplied by i k e^{+i k dx/2} (E -> H points) or i k e^{-i k dx/2}
+ * (H -> E points), k = 2 pi m / (n dx) for m = 0 .. n/2 and 2 pi (m - n) /
+ * (n dx) above; the time stepping and the Liouville step are unchanged. Here
+ * each derivative is a circulant matrix whose first column comes from that
+ * definition (inverse DFT of the multipliers, summed term by term), applied
+ * by a plain O(n^2) sum: no FFT.
  */
 #include <complex.h>
 #include <math.h>
@@ -60,6 +71,7 @@ typedef double complex cplx;
 
 enum { ORC_BC_PERIODIC = 0, ORC_BC_OPEN = 1, ORC_BC_WINDOW = 2 };
 enum { ORC_SRC_NONE = 0, ORC_SRC_HARD = 1, ORC_SRC_SOFT = 2 };
+enum { ORC_FDTD = 0, ORC_PSTD = 1 };
 
 typedef struct {
     int N;
@@ -71,6 +83,7 @@ typedef struct {
     double dx, dt, eps_r, mu_r, sigma;
     int boundary, source_kind;
     long source_cell;
+    int maxwell;       /* ORC_FDTD or ORC_PSTD (periodic grids only) */
 } orc_problem;
 
 /* ---------------------------------------------------------------- matrices */
@@ -324,7 +337,54 @@ static int cell_step(const cell_ops *ops, cplx *rho, double E, double *dPdt)
     return 0;
 }
 
+/*
+ * Circulant kernel of the staggered spectral derivative on n points of spacing
+ * dx: out_j = sum_i c[(j - i) mod n] in_i gives the derivative of the
+ * trigonometric interpolant of in at the points shifted by half * dx
+ * (half = +1/2: from E points to H points; -1/2: from H points to E points).
+ * c[d] = (1/n) sum_m i k_m e^{i k_m half dx} e^{2 pi i m d / n}; the imaginary
+ * parts cancel (the interpolant of real samples is real), so only the real
+ * part is kept.
+ */
+static void spectral_kernel(long n, double dx, double half, double *c)
+{
+    const double two_pi = 6.283185307179586476925286766559;
+    for (long d = 0; d < n; ++d) {
+        long double complex acc = 0.0L;
+        for (long m = 0; m < n; ++m) {
+            const long ms = (m <= n / 2) ? m : m - n;
+            const double k = two_pi * (double)ms / ((double)n * dx);
+            const long double complex mult = I * k * cexpl(I * (long double)(k * half * dx));
+            acc += mult * cexpl(I * (long double)(two_pi * (double)((m * d) % n) / (double)n));
+        }
+        c[d] = (double)(creall(acc) / (long double)n);
+    }
+}
+
+/* out_j = sum_i c[(j - i) mod n] in_i */
+static void circulant_apply(long n, const double *c, const double *in, double *out)
+{
+    for (long j = 0; j < n; ++j) {
+        double acc = 0.0;
+        for (long i = 0; i < n; ++i)
+            acc += c[((j - i) % n + n) % n] * in[i];
+        out[j] = acc;
+    }
+}
+
 /* ---------------------------------------------------------------- exported */
+
+/* The staggered spectral derivative of n periodic samples (see above). */
+int orc_spectral_derivative(long n, double dx, double half, const double *in, double *out)
+{
+    if (n < 2) return -1;
+    double *c = malloc((size_t)n * sizeof(double));
+    if (!c) return -2;
+    spectral_kernel(n, dx, half, c);
+    circulant_apply(n, c, in, out);
+    free(c);
+    return 0;
+}
 
 /* exp(A) of an n x n complex matrix (interleaved re/im, row-major). */
 int orc_expm(int n, const double *A, double *X)
@@ -419,10 +479,21 @@ int orc_run(const orc_problem *p, double *E, double *H, double *rho, long n_step
     int rc = cell_ops_init(p, &ops);
     if (rc) { cell_ops_free(&ops); return rc; }
 
+    const int pstd = p->maxwell == ORC_PSTD;
+    if (pstd && p->boundary != ORC_BC_PERIODIC) { cell_ops_free(&ops); return -1; }
     cplx *r = malloc((size_t)(nm > 0 ? nm : 1) * NN * sizeof(cplx));
     double *dP = calloc((size_t)n, sizeof(double));
     double *En = malloc((size_t)n * sizeof(double));
-    if (!r || !dP || !En) { free(r); free(dP); free(En); cell_ops_free(&ops); return -2; }
+    double *cp = pstd ? malloc((size_t)n * sizeof(double)) : NULL;
+    double *cm = pstd ? malloc((size_t)n * sizeof(double)) : NULL;
+    double *dv = pstd ? malloc((size_t)n * sizeof(double)) : NULL;
+    if (!r || !dP || !En || (pstd && (!cp || !cm || !dv))) {
+        free(r); free(dP); free(En); free(cp); free(cm); free(dv); cell_ops_free(&ops); return -2;
+    }
+    if (pstd) {
+        spectral_kernel(n, p->dx, 0.5, cp);
+        spectral_kernel(n, p->dx, -0.5, cm);
+    }
     load_c((size_t)nm * NN, rho, r);
 
 #ifdef _OPENMP
@@ -434,7 +505,11 @@ int orc_run(const orc_problem *p, double *E, double *H, double *rho, long n_step
 
     for (long step = 0; step < n_steps && rc == 0; ++step) {
         /* H^{n+1/2} from E^n (Eq. 1b on the staggered grid of Fig. 1) */
-        if (p->boundary == ORC_BC_PERIODIC) {
+        if (pstd) {
+            circulant_apply(n, cp, E, dv);
+            for (long i = 0; i < n; ++i)
+                H[i] += (p->dt / muu) * dv[i];
+        } else if (p->boundary == ORC_BC_PERIODIC) {
             for (long i = 0; i < n; ++i)
                 H[i] += ch * (E[(i + 1) % n] - E[i]);
         } else {
@@ -454,9 +529,15 @@ int orc_run(const orc_problem *p, double *E, double *H, double *rho, long n_step
         if (bad) { rc = -3; break; }
 
         /* E^{n+1} from H^{n+1/2} and dP/dt^{n+1/2} (Eq. 1a) */
-        for (long i = 0; i < n; ++i) {
-            long im1 = (i == 0) ? n - 1 : i - 1;
-            En[i] = ca * E[i] + cb * ((H[i] - H[im1]) / p->dx - dP[i]);
+        if (pstd) {
+            circulant_apply(n, cm, H, dv);
+            for (long i = 0; i < n; ++i)
+                En[i] = ca * E[i] + cb * (dv[i] - dP[i]);
+        } else {
+            for (long i = 0; i < n; ++i) {
+                long im1 = (i == 0) ? n - 1 : i - 1;
+                En[i] = ca * E[i] + cb * ((H[i] - H[im1]) / p->dx - dP[i]);
+            }
         }
         if (p->boundary == ORC_BC_OPEN) {
             En[0] = E[0];
@@ -474,7 +555,7 @@ int orc_run(const orc_problem *p, double *E, double *H, double *rho, long n_step
             probe[step] = E[probe_cell];
     }
     store_c((size_t)nm * NN, r, rho);
-    free(r); free(dP); free(En);
+    free(r); free(dP); free(En); free(cp); free(cm); free(dv);
     cell_ops_free(&ops);
     return rc;
 }

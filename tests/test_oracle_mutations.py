@@ -32,6 +32,11 @@ MUTATIONS = [
     ("dP/dt from the wrong state", "superop_apply(NN, ops->L, rho, r1);", "superop_apply(NN, ops->L, r2, r1);"),
     ("H coefficient", "const double ch = p->dt / (muu * p->dx);", "const double ch = p->dt / (muu * p->dx * 1.0000001);"),
     ("V instead of V^+", "mat_mul(N, T, Vh, r2);", "mat_mul(N, T, V, r2);"),
+    ("PSTD shift of dE/dx", "spectral_kernel(n, p->dx, 0.5, cp);", "spectral_kernel(n, p->dx, -0.5, cp);"),
+    ("PSTD derivative sign", "I * k * cexpl(", "-I * k * cexpl("),
+    ("PSTD wavenumber not folded", "(m <= n / 2) ? m : m - n;", "m;"),
+    ("PSTD dP/dt sign", "cb * (dv[i] - dP[i]);", "cb * (dv[i] + dP[i]);"),
+    ("PSTD H coefficient", "H[i] += (p->dt / muu) * dv[i];", "H[i] += (p->dt / muu) * 1.0000001 * dv[i];"),
 ]
 
 
@@ -46,7 +51,8 @@ def test_mutation_is_caught(tmp_path, name, old, new):
     text = src.read_text()
     assert text.count(old) == 1, name
     src.write_text(text.replace(old, new))
-    files = [f"tests/{f}" for f in ("test_oracle_expm.py", "test_oracle_liouville.py", "test_oracle_fdtd.py")]
+    files = [f"tests/{f}" for f in ("test_oracle_expm.py", "test_oracle_liouville.py", "test_oracle_fdtd.py",
+                                            "test_oracle_pstd.py")]
     r = subprocess.run([sys.executable, "-m", "pytest", "-q", "-x", "-m", "not gpu", *files],
                        cwd=tmp_path, capture_output=True, text=True, timeout=600)
     assert r.returncode != 0, f"mutation '{name}' was not caught:\n{r.stdout[-2000:]}"

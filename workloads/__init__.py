@@ -69,6 +69,7 @@ class Problem:
     boundary: str = BC_PERIODIC
     source_kind: str = SRC_NONE
     source_cell: int = 0
+    maxwell: str = "fdtd"            # field solver: "fdtd" (Fig. 1) or "pstd" (spectral derivatives, periodic)
     n_steps: int = 0
     E_init: np.ndarray | None = None   # (n_cells,) float64; None = zeros
     src: np.ndarray | None = None      # (n_steps,) float64 source samples; None = no source
