@@ -40,6 +40,8 @@ WORKLOADS = {
     "three_level_ring": "three-level QCL-like medium, periodic ring, 65536 cells x 100000 steps",
     "six_level_pulse": "six-level manifold (D = 35), Gaussian pulse, hard source + Mur, 1048576 cells x 10000 steps",
     "two_level_sit": "two-level SIT, sech pulse of area 2 pi, 2000 cells x 20000 steps",
+    "three_level_ring_pstd": "three-level QCL-like medium, periodic ring, 65536 cells x 100000 steps, "
+                             "pseudo-spectral (FFT) field solver",
     "batched": "256 independent devices, N in {2,3,4}, 1k-64k cells (log-uniform), 20000 steps, one graph per call",
     "adjoint": "gradient of the probe energy: three-level ring, 8192 cells x 5000 steps, soft source (512 samples), "
                "checkpoints every 256 steps",
@@ -90,6 +92,31 @@ def measured_traffic(kernel: str, precision: str, workload: str, block_steps: in
 def alu_peak_tflops(precision: str, mhz: float = SM_MAX_MHZ) -> float:
     per = FP64_FLOP_PER_CLK_SM if precision == "fp64" else FP32_FLOP_PER_CLK_SM
     return SMS * per * mhz * 1e6 / 1e12
+
+
+def pstd_flops_per_step(n: int) -> float:
+    """Field part of a PSTD step: two derivatives, each a forward and an inverse
+    complex FFT of n points (5 n log2 n flops each, the usual count), the
+    spectral multiply (6 n) and the update of the real part (H: n, E: 4 n)."""
+    import math
+    return 2 * (2 * 5 * n * math.log2(n) + 6 * n) + 5 * n
+
+
+def pstd_roofline(p, args, run, f_med, clk):
+    """Whole-step roofline of the PSTD solver (several kernels per step: the
+    medium cell kernel and the FFT passes) against the ALU peak of the
+    precision: achieved = (medium flops + FFT flops) per step / step time."""
+    steps = args.seg * args.steps
+    per_step_s = run["ms"] / 1e3 / steps
+    f_step = p.n_medium * f_med + pstd_flops_per_step(p.n_cells)
+    achieved = f_step / per_step_s / 1e12
+    peak = alu_peak_tflops(args.precision)
+    return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+            "traffic": None, "kernel": "pstd_cell_kernel + fft_pass (whole step)",
+            "scope": "whole step: one medium launch and 4 x (FFT passes) launches per step",
+            "flops_per_step": f_step, "fft_flops_per_step": pstd_flops_per_step(p.n_cells),
+            "peak_source": f"derived: {SMS} SMs x {FP64_FLOP_PER_CLK_SM if args.precision == 'fp64' else FP32_FLOP_PER_CLK_SM} "
+                           f"flop/clk x {SM_MAX_MHZ:.0f} MHz"}
 
 
 def tensor_roofline(p, args, run, launches, per_launch_s, clk):
@@ -221,7 +248,7 @@ def make_params(p, precision, form, block_steps=0, tile_cells=0, kernel="auto"):
     return mln.Params(N=p.N, H0=p.H0, mu=p.mu, G=p.G, rho0=p.rho0, N_a=p.N_a, n_cells=p.n_cells,
                       medium_begin=p.medium_begin, medium_end=p.medium_end, dx=p.dx, dt=p.dt,
                       boundary=p.boundary, precision=precision, form=form, block_steps=block_steps,
-                      tile_cells=tile_cells, kernel=kernel)
+                      tile_cells=tile_cells, kernel=kernel, maxwell=p.maxwell)
 
 
 def time_device(p, precision, form, seg, steps, warmup, block_steps, tile_cells, ws, flush=True,
@@ -557,6 +584,8 @@ def main():
         roofline["frac_at_measured_clock"] = achieved / alu_peak_tflops(args.precision, clk["sm_mhz"])
     if main_run["kernel"] == "tensor":
         roofline = tensor_roofline(p, args, main_run, launches, per_launch_s, clk)
+    if p.maxwell == "pstd":
+        roofline = pstd_roofline(p, args, main_run, f_med, clk)
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,

@@ -99,6 +99,24 @@ enum {
     MLN_KERNEL_TENSOR = 4
 };
 
+/* Field solver (mln_params.maxwell). MLN_MAXWELL_FDTD: the staggered finite
+ * differences of the paper's Fig. 1, fused with the medium update and
+ * temporal blocking. MLN_MAXWELL_PSTD: the pseudo-spectral variant that the
+ * paper's Secs. 1 and 3 say the method carries over to: on a periodic grid,
+ * dE_z/dx at the H_y points and dH_y/dx at the E_z points are the derivatives
+ * of the trigonometric interpolant of the samples (FFT, multiplier
+ * i k e^{+-i k dx/2}); the time stepping and the medium step are unchanged.
+ * PSTD needs MLN_BC_PERIODIC, n_cells a power of two in [16, 2^24], and
+ * kernel MLN_KERNEL_AUTO, MLN_KERNEL_REGISTER or MLN_KERNEL_SPARSE (AUTO picks
+ * SPARSE for FP64 merged problems, REGISTER otherwise). Each step is several
+ * kernel launches (the medium, then the FFT passes of the two derivatives);
+ * it runs in place on the caller's buffers. Batches, mln_adjoint and
+ * mln_step_noalloc take FDTD problems only. */
+enum {
+    MLN_MAXWELL_FDTD = 0,
+    MLN_MAXWELL_PSTD = 1
+};
+
 #define MLN_MIN_N 2
 #define MLN_MAX_N 6
 
@@ -133,6 +151,7 @@ enum {
  *   tile_cells    cells written by one thread block; 0 picks a default.
  *   kernel        MLN_KERNEL_AUTO, MLN_KERNEL_REGISTER, MLN_KERNEL_SPARSE,
  *                 MLN_KERNEL_JIT or MLN_KERNEL_TENSOR.
+ *   maxwell       MLN_MAXWELL_FDTD (0) or MLN_MAXWELL_PSTD.
  */
 typedef struct mln_params {
     int32_t N;
@@ -157,6 +176,7 @@ typedef struct mln_params {
     double eps_r;
     double mu_r;
     double sigma;
+    int32_t maxwell;
 } mln_params;
 
 typedef struct mln_ctx mln_ctx;

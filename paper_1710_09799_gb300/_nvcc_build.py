@@ -18,8 +18,9 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libmln.so")
 
 SOURCES = ["api.cu", "kernels_fp64.cu", "kernels_fp32.cu", "kernels_tc.cu", "setup.cpp", "static_scratch.cu", "batch.cu",
-           "adjoint.cu", "jit.cu", "project.cu"]
-HEADERS = ["kernels.cuh", "dispatch.cuh", "setup.h", "ctx.h", "adjoint.cuh", "jit.h", "tc.cuh", "tc_kernel.h"]
+           "adjoint.cu", "jit.cu", "project.cu", "pstd.cu"]
+HEADERS = ["kernels.cuh", "dispatch.cuh", "setup.h", "ctx.h", "adjoint.cuh", "jit.h", "tc.cuh", "tc_kernel.h",
+           "pstd.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "--expt-relaxed-constexpr", "-I", INCLUDE, "-I", CSRC, "-I", BUILD]

@@ -204,8 +204,9 @@ mln_status mln_adjoint(mln_ctx *c, int64_t n_steps, const double *src, int64_t p
         if (c) c->err = "invalid adjoint arguments";
         return MLN_EINVAL;
     }
-    if (c->p.form != MLN_FORM_STRANG || c->p.boundary != MLN_BC_PERIODIC || c->p.N > 4 || c->sparse) {
-        c->err = "mln_adjoint needs MLN_FORM_STRANG, MLN_BC_PERIODIC and N <= 4";
+    if (c->p.form != MLN_FORM_STRANG || c->p.boundary != MLN_BC_PERIODIC || c->p.N > 4 || c->sparse ||
+        c->p.maxwell != MLN_MAXWELL_FDTD) {
+        c->err = "mln_adjoint needs MLN_FORM_STRANG, MLN_BC_PERIODIC, MLN_MAXWELL_FDTD and N <= 4";
         return MLN_EUNSUPPORTED;
     }
     switch (c->p.N) {

@@ -9,6 +9,7 @@
 #include <vector>
 
 #include "ctx.h"
+#include "pstd.h"
 #include "dispatch.cuh"
 #include "jit.h"
 #include "mln.h"
@@ -161,6 +162,7 @@ size_t smem_for(mln_ctx *c, int threads) {
 // buffer set 0 and writing set 1, which leaves the caller's state untouched.
 template <typename R>
 mln_status autotune_t(mln_ctx *c, int trials) {
+    if (c->pstd) return MLN_OK;  // one step per launch: no launch shape to choose
     int dev = 0, sms = 152;
     if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const int64_t n = c->p.n_cells;
@@ -227,6 +229,7 @@ mln_status autotune_t(mln_ctx *c, int trials) {
 
 template <typename R>
 mln_status run_steps(mln_ctx *c, int64_t n_steps, const double *src) {
+    if (c->pstd) return mln::pstd_steps(c, n_steps, src);
     const int64_t ntiles = (c->p.n_cells + c->tile - 1) / c->tile;
     mln::BlockArgs<R> a = mln::base_args<R>(c);
     const size_t smem = smem_for<R>(c, c->threads);
@@ -513,6 +516,7 @@ void mln_destroy(mln_ctx *c) {
     cudaFree(c->scratch);
     cudaFree(c->prog);
     cudaFree(c->tc_img);
+    mln::pstd_free(c);
     delete c;
 }
 
@@ -598,7 +602,7 @@ mln_status mln_create(const mln_params *p, void *d_state, void *Ez, void *Hy, vo
         }
     } else if (p->kernel == MLN_KERNEL_TENSOR ||
                (p->kernel == MLN_KERNEL_AUTO && p->precision == MLN_FP32 && p->form == MLN_FORM_MERGED &&
-                mln::tc_supported(p->N))) {
+                p->maxwell == MLN_MAXWELL_FDTD && mln::tc_supported(p->N))) {
         std::vector<unsigned char> img;
         ok = mln::tc_supported(p->N) && mln::pack_tc(c->s, p->dt, img, c->tc_scal);
         if (ok) {
@@ -614,7 +618,8 @@ mln_status mln_create(const mln_params *p, void *d_state, void *Ez, void *Hy, vo
         ok = p->precision == MLN_FP64 ? mln::pack_consts(c->s, p->form, p->dt, 0.0, c->consts)
                                       : mln::pack_consts(c->s, p->form, p->dt, 0.0f, c->consts);
         const bool want_jit = p->kernel == MLN_KERNEL_JIT ||
-                              (p->kernel == MLN_KERNEL_AUTO && p->precision == MLN_FP32 && p->form == MLN_FORM_MERGED);
+                              (p->kernel == MLN_KERNEL_AUTO && p->precision == MLN_FP32 && p->form == MLN_FORM_MERGED &&
+                               p->maxwell == MLN_MAXWELL_FDTD);
         if (ok && want_jit) {
             std::string why, log;
             cudaError_t e = cudaErrorNotSupported;
@@ -647,6 +652,7 @@ mln_status mln_create(const mln_params *p, void *d_state, void *Ez, void *Hy, vo
         c->err = "flag reset failed";
         return fail(MLN_ECUDA);
     }
+    if (p->maxwell == MLN_MAXWELL_PSTD && (st = mln::pstd_init(c)) != MLN_OK) return fail(st);
     // output tables: rho = rho_c + Z (sd0 + Sd s), populations, d = sd0 + Sd s
     const int D = c->D, n = p->N, nn = n * n;
     std::vector<double> zr((size_t)2 * nn * D, 0.0), zo(2 * nn, 0.0);

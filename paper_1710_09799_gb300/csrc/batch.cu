@@ -406,8 +406,9 @@ mln_status mln_batch_create(int32_t count, const mln_params *params, void *const
     for (int32_t i = 0; i < count; ++i) {
         const mln_params &p = params[i];
         if (p.precision != params[0].precision || p.form != MLN_FORM_MERGED || p.N > mln::kBatchMaxN ||
+            p.maxwell != MLN_MAXWELL_FDTD ||
             (p.kernel != MLN_KERNEL_AUTO && p.kernel != MLN_KERNEL_REGISTER && p.kernel != MLN_KERNEL_JIT)) {
-            mln::create_error() = "batch grids need one precision, MLN_FORM_MERGED, N <= 4 and kernel AUTO, "
+            mln::create_error() = "batch grids need one precision, MLN_FORM_MERGED, MLN_MAXWELL_FDTD, N <= 4 and kernel AUTO, "
                                   "REGISTER or JIT (grid " + std::to_string(i) + ")";
             return MLN_EINVAL;
         }

@@ -33,6 +33,8 @@ struct mln_ctx {
     int sms = 152;                     // SMs of the context's device
     void *tc_img = nullptr;            // its B-operand image (device)
     std::vector<unsigned char> tc_scal;  // and scalar constants
+    void *pstd = nullptr;              // PSTD field solver: tables and work arrays (nullptr: FDTD)
+    void *pstd_host = nullptr;         // and its stream, events and captured step graphs
     int nnz = 0, nrowptr = 0;
     // output tables (FP64, device): rows x D matrix followed by rows offsets
     double *tab_rho = nullptr, *tab_pop = nullptr, *tab_d = nullptr, *tab_in = nullptr;

@@ -430,6 +430,21 @@ mln_status validate(const mln_params &p, std::string &err) {
         err = "block_steps must be in [0, 64]";
         return MLN_EINVAL;
     }
+    if (p.maxwell != MLN_MAXWELL_FDTD && p.maxwell != MLN_MAXWELL_PSTD) {
+        err = "maxwell must be MLN_MAXWELL_FDTD or MLN_MAXWELL_PSTD";
+        return MLN_EINVAL;
+    }
+    if (p.maxwell == MLN_MAXWELL_PSTD) {
+        const bool pow2 = p.n_cells >= 16 && p.n_cells <= (int64_t(1) << 24) && (p.n_cells & (p.n_cells - 1)) == 0;
+        if (p.boundary != MLN_BC_PERIODIC || !pow2) {
+            err = "MLN_MAXWELL_PSTD needs a periodic grid of 2^k cells, 16 <= n_cells <= 2^24";
+            return MLN_EINVAL;
+        }
+        if (p.kernel != MLN_KERNEL_AUTO && p.kernel != MLN_KERNEL_REGISTER && p.kernel != MLN_KERNEL_SPARSE) {
+            err = "MLN_MAXWELL_PSTD runs with kernel MLN_KERNEL_AUTO, MLN_KERNEL_REGISTER or MLN_KERNEL_SPARSE";
+            return MLN_EINVAL;
+        }
+    }
     if (p.kernel < MLN_KERNEL_AUTO || p.kernel > MLN_KERNEL_TENSOR) {
         err = "kernel must be MLN_KERNEL_AUTO, MLN_KERNEL_REGISTER, MLN_KERNEL_SPARSE, MLN_KERNEL_JIT or "
               "MLN_KERNEL_TENSOR";

@@ -34,6 +34,7 @@ PRECISION = {"fp64": MLN_FP64, "fp32": MLN_FP32}
 FORM = {"strang": MLN_FORM_STRANG, "merged": MLN_FORM_MERGED, "rodrigues": MLN_FORM_RODRIGUES}
 KERNEL = {"auto": MLN_KERNEL_AUTO, "register": MLN_KERNEL_REGISTER, "sparse": MLN_KERNEL_SPARSE,
           "jit": MLN_KERNEL_JIT, "tensor": MLN_KERNEL_TENSOR}
+MAXWELL = {"fdtd": 0, "pstd": 1}
 
 _dp = C.POINTER(C.c_double)
 
@@ -48,7 +49,7 @@ class mln_params(C.Structure):
         ("n_cells", C.c_int64), ("medium_begin", C.c_int64), ("medium_end", C.c_int64),
         ("source_cell", C.c_int64),
         ("dx", C.c_double), ("dt", C.c_double), ("eps_r", C.c_double), ("mu_r", C.c_double),
-        ("sigma", C.c_double),
+        ("sigma", C.c_double), ("maxwell", C.c_int32),
     ]
 
 
@@ -176,7 +177,7 @@ class Params:
     def __init__(self, *, N, H0, mu, rho0, N_a, n_cells, medium_begin, medium_end, dx, dt,
                  G=None, eps_r=1.0, mu_r=1.0, sigma=0.0, boundary="periodic", source_kind="none",
                  source_cell=0, precision="fp64", form="strang", block_steps=0, tile_cells=0,
-                 kernel="auto"):
+                 kernel="auto", maxwell="fdtd"):
         self._H0, self._mu, self._rho0 = _cplx(H0), _cplx(mu), _cplx(rho0)
         self._G = None if G is None else _cplx(G)
         self.s = mln_params(
@@ -185,7 +186,8 @@ class Params:
             block_steps=block_steps, tile_cells=tile_cells, kernel=KERNEL.get(kernel, kernel),
             H0=_ptr(self._H0), mu=_ptr(self._mu), G=_ptr(self._G), rho0=_ptr(self._rho0),
             N_a=N_a, n_cells=n_cells, medium_begin=medium_begin, medium_end=medium_end,
-            source_cell=source_cell, dx=dx, dt=dt, eps_r=eps_r, mu_r=mu_r, sigma=sigma)
+            source_cell=source_cell, dx=dx, dt=dt, eps_r=eps_r, mu_r=mu_r, sigma=sigma,
+            maxwell=MAXWELL.get(maxwell, maxwell))
 
     @property
     def D(self):

@@ -9,7 +9,7 @@ def params_of(p, **kw):
     args = dict(N=p.N, H0=p.H0, mu=p.mu, G=p.G, rho0=p.rho0, N_a=p.N_a, n_cells=p.n_cells,
                 medium_begin=p.medium_begin, medium_end=p.medium_end, dx=p.dx, dt=p.dt,
                 eps_r=p.eps_r, mu_r=p.mu_r, sigma=p.sigma, boundary=p.boundary,
-                source_kind=p.source_kind, source_cell=p.source_cell)
+                source_kind=p.source_kind, source_cell=p.source_cell, maxwell=p.maxwell)
     args.update(kw)
     return mln.Params(**args)
 

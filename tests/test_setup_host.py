@@ -33,7 +33,7 @@ def params_of(p, **kw):
     args = dict(N=p.N, H0=p.H0, mu=p.mu, G=p.G, rho0=p.rho0, N_a=p.N_a, n_cells=p.n_cells,
                 medium_begin=p.medium_begin, medium_end=p.medium_end, dx=p.dx, dt=p.dt,
                 eps_r=p.eps_r, mu_r=p.mu_r, sigma=p.sigma, boundary=p.boundary,
-                source_kind=p.source_kind, source_cell=p.source_cell)
+                source_kind=p.source_kind, source_cell=p.source_cell, maxwell=p.maxwell)
     args.update(kw)
     return mln.Params(**args)
 
@@ -207,6 +207,16 @@ def test_validation(lib):
     assert ok(source_cell=100) == mln.MLN_EINVAL
     assert ok(precision=7) == mln.MLN_EINVAL
     assert ok(block_steps=65) == mln.MLN_EINVAL
+    # the pseudo-spectral field solver: periodic grids of 2^k cells, no JIT or tensor-core cell model
+    r = W.three_level_ring(n_cells=256, n_steps=1).with_(maxwell="pstd")
+    okr = lambda **kw: _status_of(lambda: mln.mln_query_buffers(params_of(r, **kw)))
+    assert okr() == mln.MLN_OK and okr(form="merged", kernel="sparse") == mln.MLN_OK
+    assert okr(n_cells=255, medium_end=255) == mln.MLN_EINVAL
+    assert okr(n_cells=8, medium_end=8) == mln.MLN_EINVAL
+    assert okr(kernel="jit", form="merged") == mln.MLN_EINVAL
+    assert okr(kernel="tensor", form="merged", precision="fp32") == mln.MLN_EINVAL
+    assert ok(maxwell="pstd") == mln.MLN_EINVAL                   # open grid
+    assert ok(maxwell=2) == mln.MLN_EINVAL
     q = random_problem(7, 1, G=False)
     assert _status_of(lambda: mln.mln_query_buffers(params_of(q))) == mln.MLN_EUNSUPPORTED
     sb, fb = mln.mln_query_buffers(params_of(p, precision="fp32"))

@@ -375,11 +375,19 @@ def adjoint_ring(n_cells: int = 8192, n_steps: int = 5000, seed: int = 0, n_src:
     return q
 
 
+def three_level_ring_pstd(**kw) -> Problem:
+    """The three-level ring with the pseudo-spectral field solver (65536 = 2^16
+    cells, periodic; same medium, grid and time step)."""
+    p = three_level_ring(**kw)
+    return p.with_(name=p.name + "_pstd", maxwell="pstd")
+
+
 def config(name: str, **kw) -> Problem:
     """The named workload at its full size (keyword overrides allowed)."""
     table = {
         "two_level_sit": two_level_sit,
         "three_level_ring": three_level_ring,
+        "three_level_ring_pstd": three_level_ring_pstd,
         "six_level_pulse": six_level_pulse,
     }
     return table[name](**kw)
