@@ -760,17 +760,37 @@ mln_status mln_work_per_step(const mln_ctx *c, double *flops_medium, double *flo
             for (int j = 0; j < cols; ++j) n += (v[i * ld + j] - (i == j ? diag : 0.0)) != 0.0;
         return n;
     };
+    // Exact operation counts of the method on this input (FMA = 2 flops): a
+    // product row with k non-zero entries is k multiplications and k - 1
+    // additions; added onto a vector, k additions; a non-zero offset, one more.
     const double nT = nz(s.T, D, P, D, 0.0);          // T on the plane columns (= T^T on the plane rows)
-    const double rot = 6.0 * q + 12.0 * (q - (N - 1)) + 8.0 * (N - 1);
+    double planes_used = 0;                           // plane rows of T^T with a non-zero entry
+    for (int k = 0; k < P; ++k) {
+        bool any = false;
+        for (int i = 0; i < D; ++i) any = any || s.T[i * D + k] != 0.0;
+        planes_used += any;
+    }
+    auto dot = [&](const std::vector<double> &w, double c0) {  // c0 + w . x
+        const double k = nz(w, 1, D, D, 0.0);
+        return k > 0 ? 2 * k - 1 + (c0 != 0.0) : 0.0;
+    };
+    // the N - 1 series for (sin, cos - 1), the other planes by the subtraction
+    // formulas (10 flops), and 6 flops per plane for the increment
+    const double rot = 6.0 * q + 10.0 * (q - (N - 1)) + 8.0 * (N - 1);
+    const double tt = 2 * nT - planes_used;           // z = T^T y
     double f;
     if (c->p.form == MLN_FORM_MERGED) {
-        f = 4 * nT + 2 * nz(s.C1, D, D, D, 0.0) + 2 * D + 2 * nz(s.wm, 1, D, D, 0.0) + rot;
-    } else if (c->p.form == MLN_FORM_RODRIGUES) {
-        // per plane: S_k d' and S_k^2 d' (dense, 2 D^2 each) and the two scaled adds (4 D)
-        f = 4 * nz(s.A0, D, D, D, 1.0) + 3 * D + 2 * nz(s.w, 1, D, D, 0.0) + q * (4.0 * D * D + 4.0 * D) +
-            (rot - 6.0 * q);
+        // y'' = y + T dz; dP/dt = c' + wm . y''; y = (y'' + b2) + C1 y''
+        f = tt + rot + 2 * nT + dot(s.wm, s.cm) + 2 * nz(s.C1, D, D, D, 0.0) + nz(s.b2, 1, D, D, 0.0);
     } else {
-        f = 4 * nz(s.A0, D, D, D, 1.0) + 4 * nT + 3 * D + 2 * nz(s.w, 1, D, D, 0.0) + rot;
+        // d' = d + ((A0 - I) d + b), twice per step
+        const double half = 2 * nz(s.A0, D, D, D, 1.0) + nz(s.b, 1, D, D, 0.0);
+        if (c->p.form == MLN_FORM_RODRIGUES) {
+            // per plane: S_k d' and S_k^2 d' (dense, 2 D^2 each) and the two scaled adds (4 D)
+            f = 2 * half + dot(s.w, s.c) + q * (4.0 * D * D + 4.0 * D) + (rot - 6.0 * q);
+        } else {
+            f = 2 * half + tt + rot + 2 * nT + dot(s.w, s.c);
+        }
     }
     if (flops_medium) *flops_medium = f;
     if (flops_cell) *flops_cell = 9.0;

@@ -99,10 +99,16 @@ struct PaddedCell {
         for (int c = 0; c < D; ++c) z[c] = dot_row<D, true>(k.Tt + c * DP, s, R(0));  // z = T^T y
         rotation_increment<N>(z, k.psi_dt, e);
 #pragma unroll
-        for (int i = 0; i < D; ++i) s[i] = s[i] + dot_row<D, true>(k.T + i * DP, z, R(0));  // y + T (R - I) z
+        for (int i = 0; i < D; ++i) {  // y + T (R - I) z: onto y in FP64, the increment first in FP32
+            if constexpr (sizeof(R) == 8) s[i] = dot_row<D, false>(k.T + i * DP, z, s[i]);
+            else s[i] = s[i] + dot_row<D, true>(k.T + i * DP, z, R(0));
+        }
         const R dpdt = dot_row<D, false>(k.wm, s, k.cm);
 #pragma unroll
-        for (int i = 0; i < D; ++i) z[i] = s[i] + dot_row<D, false>(k.C1 + i * DP, s, k.b2[i]);
+        for (int i = 0; i < D; ++i) {  // (y'' + b2) + C1 y'' in FP64; y'' + (C1 y'' + b2) in FP32
+            if constexpr (sizeof(R) == 8) z[i] = dot_row<D, false>(k.C1 + i * DP, s, s[i] + k.b2[i]);
+            else z[i] = s[i] + dot_row<D, false>(k.C1 + i * DP, s, k.b2[i]);
+        }
 #pragma unroll
         for (int i = 0; i < D; ++i) s[i] = z[i];
         return dpdt;

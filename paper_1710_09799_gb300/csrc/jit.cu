@@ -160,11 +160,16 @@ std::string jit_merged_source(const Setup &s, double dt, bool fp32) {
     o << "    const " << R << " psi[" << (N - 1) << "] = {";
     for (int a = 0; a < N - 1; ++a) o << (a ? ", " : "") << lit(s.psi[a] * dt, fp32);
     o << "};\n    rotation_increment<" << N << ">(z, psi, e);\n";
-    // y'' = y + T (R - I) z on the plane columns
+    // y'' = y + T (R - I) z on the plane columns: accumulated onto y in FP64,
+    // the increment summed first in FP32 (as the register model)
     for (int i = 0; i < D; ++i) {
-        std::string e = row_sum(s.T, D, i, P, "z", fp32);
-        o << "    y[" << i << "] = " << (e.empty() ? "s[" + std::to_string(i) + "]" : "s[" + std::to_string(i) + "] + (" + e + ")")
-          << ";\n";
+        const std::string si = "s[" + std::to_string(i) + "]";
+        if (fp32) {
+            std::string e = row_sum(s.T, D, i, P, "z", fp32);
+            o << "    y[" << i << "] = " << (e.empty() ? si : si + " + (" + e + ")") << ";\n";
+        } else {
+            o << "    y[" << i << "] = " << row_sum(s.T, D, i, P, "z", fp32, si) << ";\n";
+        }
     }
     // dP/dt = wm . y'' + cm
     {
@@ -173,10 +178,17 @@ std::string jit_merged_source(const Setup &s, double dt, bool fp32) {
             if (nz(s.wm[i], fp32)) acc = "fma(" + lit(s.wm[i], fp32) + ", y[" + std::to_string(i) + "], " + acc + ")";
         o << "    const " << R << " dpdt = " << acc << ";\n";
     }
-    // y = y'' + (C1 y'' + b2)
+    // y = (y'' + b2) + C1 y'' accumulated onto y'' + b2 (no add where b2 is
+    // zero) in FP64; y'' + (C1 y'' + b2) in FP32
     for (int i = 0; i < D; ++i) {
-        std::string e = row_sum(s.C1, D, i, D, "y", fp32, lit(s.b2[i], fp32));
-        o << "    s[" << i << "] = y[" << i << "] + (" << e << ");\n";
+        const std::string yi = "y[" + std::to_string(i) + "]";
+        if (fp32) {
+            std::string e = row_sum(s.C1, D, i, D, "y", fp32, lit(s.b2[i], fp32));
+            o << "    s[" << i << "] = " << yi << " + (" << e << ");\n";
+        } else {
+            const std::string init = nz(s.b2[i], fp32) ? "(" + yi + " + " + lit(s.b2[i], fp32) + ")" : yi;
+            o << "    s[" << i << "] = " << row_sum(s.C1, D, i, D, "y", fp32, init) << ";\n";
+        }
     }
     o << "    return dpdt;\n  }\n};\n"
       << "extern \"C\" __global__ void __launch_bounds__(kMaxThreads, 1) mln_jit_step(const __grid_constant__ BlockArgs<"
@@ -306,16 +318,17 @@ std::string jit_batch_source(const BatchPattern &pat, bool fp32) {
     o << "    const " << R << " psi[" << (N - 1) << "] = {";
     for (int a = 0; a < N - 1; ++a) o << (a ? ", " : "") << C(iPsi[a]);
     o << "};\n    rotation_increment<" << N << ">(z, psi, e);\n";
-    // y'' = y + T (R - I) z on the plane columns
+    // y'' = y + T (R - I) z on the plane columns (onto y in FP64, as the register model)
     for (int i = 0; i < D; ++i) {
-        std::string acc;
+        const std::string si = "s[" + std::to_string(i) + "]";
+        std::string acc = fp32 ? "" : si;
         for (int p = 0; p < P; ++p) {
             if (!pat.t[i * P + p]) continue;
             const std::string t = "z[" + std::to_string(p) + "]", c = C(iT[i * P + p]);
             acc = acc.empty() ? mul + c + ", " + t + ")" : "fma(" + c + ", " + t + ", " + acc + ")";
         }
-        const std::string si = "s[" + std::to_string(i) + "]";
-        o << "    y[" << i << "] = " << (acc.empty() ? si : si + " + (" + acc + ")") << ";\n";
+        if (fp32) acc = acc.empty() ? si : si + " + (" + acc + ")";
+        o << "    y[" << i << "] = " << acc << ";\n";
     }
     // dP/dt = wm . y'' + c'
     {
@@ -324,12 +337,13 @@ std::string jit_batch_source(const BatchPattern &pat, bool fp32) {
             if (pat.wm[i]) acc = "fma(" + C(iW[i]) + ", y[" + std::to_string(i) + "], " + acc + ")";
         o << "    const " << R << " dpdt = " << acc << ";\n";
     }
-    // y = y'' + (C1 y'' + b2)
+    // y = (y'' + b2) + C1 y'' onto y'' + b2 in FP64; y'' + (C1 y'' + b2) in FP32
     for (int i = 0; i < D; ++i) {
-        std::string acc = C(iB[i]);
+        const std::string yi = "y[" + std::to_string(i) + "]";
+        std::string acc = fp32 ? C(iB[i]) : "(" + yi + " + " + C(iB[i]) + ")";
         for (int j = 0; j < D; ++j)
             if (pat.c1[i * D + j]) acc = "fma(" + C(iC[i * D + j]) + ", y[" + std::to_string(j) + "], " + acc + ")";
-        o << "    s[" << i << "] = y[" << i << "] + (" << acc << ");\n";
+        o << "    s[" << i << "] = " << (fp32 ? yi + " + (" + acc + ")" : acc) << ";\n";
     }
     o << "    return dpdt;\n  }\n};\n"
       << "extern \"C\" __global__ void __launch_bounds__(kBatchThreads, 1) mln_jit_batch(const BatchGrid<" << R

@@ -237,6 +237,31 @@ __device__ __forceinline__ void matvec_acc(R (&y)[D], const R *A, const R (&x)[D
     }
 }
 
+// y += A x accumulated onto y itself: every term a fused multiply-add, so
+// each rounding is at the scale of the component it updates.
+template <int D, typename R>
+__device__ __forceinline__ void matvec_onto(R (&y)[D], const R *A, const R (&x)[D]) {
+#pragma unroll
+    for (int i = 0; i < D; ++i) {
+        R acc = y[i];
+#pragma unroll
+        for (int j = 0; j < D; ++j) acc = fma(A[i * D + j], x[j], acc);
+        y[i] = acc;
+    }
+}
+
+// z = (y + b) + A y, accumulated onto y + b.
+template <int D, typename R>
+__device__ __forceinline__ void affine_onto(R (&z)[D], const R *A, const R (&y)[D], const R *b) {
+#pragma unroll
+    for (int i = 0; i < D; ++i) {
+        R acc = y[i] + b[i];
+#pragma unroll
+        for (int j = 0; j < D; ++j) acc = fma(A[i * D + j], y[j], acc);
+        z[i] = acc;
+    }
+}
+
 // y = A^T x
 template <int D, typename R>
 __device__ __forceinline__ void matTvec(R (&y)[D], const R *A, const R (&x)[D]) {
@@ -292,9 +317,14 @@ __device__ __forceinline__ R cell_step(R (&s)[Dims<N>::D], R e, const MergedCons
     R z[D];
     matTvec<D>(z, k.T, s);                 // z = T^T y
     rotation_increment<N>(z, k.psi_dt, e);
-    matvec_acc<D>(s, k.T, z);              // y'' = y + T (R - I) z
+    // FP64 accumulates the increments onto the state (fewer operations; a few
+    // extra roundings at the state's own scale); FP32 sums each increment
+    // first, since a dense row's many roundings at the state's scale would show
+    if constexpr (sizeof(R) == 8) matvec_onto<D>(s, k.T, z);  // y'' = y + T (R - I) z
+    else matvec_acc<D>(s, k.T, z);
     const R dpdt = dot_bias<D>(k.wm, s, k.cm);
-    affine_inc<D>(z, k.C1, s, k.b2);       // y = A0^2 y'' + A0 b + b
+    if constexpr (sizeof(R) == 8) affine_onto<D>(z, k.C1, s, k.b2);  // y = (y'' + b2) + C1 y''
+    else affine_inc<D>(z, k.C1, s, k.b2);                           // y = y'' + (C1 y'' + b2)
 #pragma unroll
     for (int i = 0; i < D; ++i) s[i] = z[i];
     return dpdt;
@@ -468,13 +498,18 @@ struct SharedSparseCell {
         rotation_increment<N>(zz, k.psi_dt, e);
 #pragma unroll
         for (int i = 0; i < 2 * Q; ++i) z[i * nt] = zz[i];
-        // y'' = y + T (R - I) z
+        // y'' = y + T (R - I) z, accumulated onto y
 #pragma unroll 1
-        for (int r = 0; r < D; ++r) yc[r * nt] = yc[r * nt] + row(rT + r, z, 0.0);
+        for (int r = 0; r < D; ++r) yc[r * nt] = row(rT + r, z, yc[r * nt]);
         const double dpdt = row(rW, yc, k.cm);
-        // y = y'' + (C1 y'' + b2)
+        // y = (y'' + b2) + C1 y'', accumulated onto y'' + b2 (no add where b2 is zero:
+        // the same value as adding it)
 #pragma unroll 1
-        for (int r = 0; r < D; ++r) yn[r * nt] = yc[r * nt] + row(rC + r, yc, k.b2[r]);
+        for (int r = 0; r < D; ++r) {
+            const double b = k.b2[r];
+            const double a0 = __double_as_longlong(b) != 0 ? yc[r * nt] + b : yc[r * nt];
+            yn[r * nt] = row(rC + r, yc, a0);
+        }
         return dpdt;
     }
     // every thread of the block swaps, medium or not, so the columns stay aligned
