@@ -75,10 +75,10 @@ mln_status adjoint_t(mln_ctx *c, int64_t n_steps, const double *src, int64_t pro
         unsigned char *p = base + i * set_bytes;
         return Set<R>{reinterpret_cast<R *>(p + sb), reinterpret_cast<R *>(p + sb + fb), reinterpret_cast<R *>(p)};
     };
-    auto copy_set = [&](Set<R> dst, Set<R> from) {
-        cudaError_t e = cudaMemcpyAsync(dst.S, from.S, sb, cudaMemcpyDeviceToDevice, c->stream);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(dst.E, from.E, fb, cudaMemcpyDeviceToDevice, c->stream);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(dst.H, from.H, fb, cudaMemcpyDeviceToDevice, c->stream);
+    auto copy_set = [&](Set<R> dst, Set<R> from, cudaStream_t strm) {
+        cudaError_t e = cudaMemcpyAsync(dst.S, from.S, sb, cudaMemcpyDeviceToDevice, strm);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(dst.E, from.E, fb, cudaMemcpyDeviceToDevice, strm);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(dst.H, from.H, fb, cudaMemcpyDeviceToDevice, strm);
         return e;
     };
     const Set<R> user{static_cast<R *>(c->E[0]), static_cast<R *>(c->H[0]), static_cast<R *>(c->st[0])};
@@ -91,9 +91,51 @@ mln_status adjoint_t(mln_ctx *c, int64_t n_steps, const double *src, int64_t pro
     const int rK = c->K, rthreads = c->threads;
     mln::AdjArgs<R> aa{};
     Set<R> A0s, A1s;
+    // Two slot buffers: segment s - 1 is recomputed on a second stream while the
+    // reverse sweep of segment s runs (the two kernels are independent and each
+    // leaves most of the GPU idle on rings of this size); events order the
+    // recompute after the sweep that last used its buffer, and each sweep after
+    // its recompute.
+    cudaStream_t rs = nullptr;
+    cudaEvent_t ev_fwd = nullptr, ev_rec[2] = {nullptr, nullptr}, ev_rev[2] = {nullptr, nullptr};
+    unsigned char *slot_buf[2] = {nullptr, nullptr};
+    const size_t slot_bytes = static_cast<size_t>(every + 1) * set_bytes;
+    // segment sg from its checkpoint into slots, every step recorded, on stream strm
+    auto recompute = [&](int64_t sg, unsigned char *sl, cudaStream_t strm) -> cudaError_t {
+        const int64_t g0 = sg * every, glen = std::min<int64_t>(every, n_steps - g0);
+        cudaError_t e = copy_set(set_at(sl, 0), set_at(ckpt, sg), strm);
+        for (int64_t j = 0; e == cudaSuccess && j < glen; j += rK) {
+            const int ns = static_cast<int>(std::min<int64_t>(rK, glen - j));
+            const Set<R> in = set_at(sl, j), o = set_at(sl, j + ns), r1 = set_at(sl, j + 1);
+            fa.E_in = in.E;
+            fa.H_in = in.H;
+            fa.s_in = in.S;
+            fa.E_out = o.E;
+            fa.H_out = o.H;
+            fa.s_out = o.S;
+            fa.rec_E = r1.E;
+            fa.rec_H = r1.H;
+            fa.rec_S = r1.S;
+            fa.rec_set = static_cast<int64_t>(set_bytes);
+            fa.nsteps = ns;
+            fa.src = (src && c->p.source_kind != MLN_SRC_NONE) ? src + g0 + j : nullptr;
+            e = mln::launch_block(c->p.N, MLN_FORM_STRANG, fa, c->consts,
+                                  dim3(static_cast<unsigned>((n + c->tile - 1) / c->tile)), dim3(rthreads),
+                                  mln::field_smem<R>(rthreads), strm);
+        }
+        return e;
+    };
 
     MLN_ACK(c, cudaMalloc(&ckpt, nseg * set_bytes));
-    MLN_ACK(c, cudaMalloc(&slots, (every + 1) * set_bytes));
+    MLN_ACK(c, cudaMalloc(&slots, 2 * slot_bytes));
+    slot_buf[0] = slots;
+    slot_buf[1] = slots + slot_bytes;
+    MLN_ACK(c, cudaStreamCreateWithFlags(&rs, cudaStreamNonBlocking));
+    MLN_ACK(c, cudaEventCreateWithFlags(&ev_fwd, cudaEventDisableTiming));
+    for (int b = 0; b < 2; ++b) {
+        MLN_ACK(c, cudaEventCreateWithFlags(&ev_rec[b], cudaEventDisableTiming));
+        MLN_ACK(c, cudaEventCreateWithFlags(&ev_rev[b], cudaEventDisableTiming));
+    }
     MLN_ACK(c, cudaMalloc(&adj, 2 * set_bytes));
     MLN_ACK(c, cudaMalloc(&acc, L::size * n * sizeof(double)));
     MLN_ACK(c, cudaMalloc(&accsum, L::size * sizeof(double)));
@@ -102,7 +144,7 @@ mln_status adjoint_t(mln_ctx *c, int64_t n_steps, const double *src, int64_t pro
     // forward with checkpoints
     for (int64_t s = 0; s < nseg; ++s) {
         const int64_t len = std::min<int64_t>(every, n_steps - s * every);
-        MLN_ACK(c, copy_set(set_at(ckpt, s), user));
+        MLN_ACK(c, copy_set(set_at(ckpt, s), user, c->stream));
         mln_status r = mln_step(c, len, src ? src + s * every : nullptr);
         if (r != MLN_OK) {
             st = r;
@@ -127,30 +169,22 @@ mln_status adjoint_t(mln_ctx *c, int64_t n_steps, const double *src, int64_t pro
     aa.ca = fa.ca;
     aa.cb = fa.cb;
     aa.inv_dx = fa.inv_dx;
+    MLN_ACK(c, cudaEventRecord(ev_fwd, c->stream));
+    MLN_ACK(c, cudaStreamWaitEvent(rs, ev_fwd, 0));
+    MLN_ACK(c, recompute(nseg - 1, slot_buf[(nseg - 1) & 1], rs));
+    MLN_ACK(c, cudaEventRecord(ev_rec[(nseg - 1) & 1], rs));
     for (int64_t s = nseg - 1; s >= 0; --s) {
         const int64_t s0 = s * every, len = std::min<int64_t>(every, n_steps - s0);
-        MLN_ACK(c, copy_set(set_at(slots, 0), set_at(ckpt, s)));
-        for (int64_t j = 0; j < len; j += rK) {
-            const int ns = static_cast<int>(std::min<int64_t>(rK, len - j));
-            const Set<R> in = set_at(slots, j), o = set_at(slots, j + ns), r1 = set_at(slots, j + 1);
-            fa.E_in = in.E;
-            fa.H_in = in.H;
-            fa.s_in = in.S;
-            fa.E_out = o.E;
-            fa.H_out = o.H;
-            fa.s_out = o.S;
-            fa.rec_E = r1.E;
-            fa.rec_H = r1.H;
-            fa.rec_S = r1.S;
-            fa.rec_set = static_cast<int64_t>(set_bytes);
-            fa.nsteps = ns;
-            fa.src = (src && c->p.source_kind != MLN_SRC_NONE) ? src + s0 + j : nullptr;
-            MLN_ACK(c, mln::launch_block(c->p.N, MLN_FORM_STRANG, fa, c->consts,
-                                         dim3(static_cast<unsigned>((n + c->tile - 1) / c->tile)), dim3(rthreads),
-                                         mln::field_smem<R>(rthreads), c->stream));
+        unsigned char *sl = slot_buf[s & 1];
+        MLN_ACK(c, cudaStreamWaitEvent(c->stream, ev_rec[s & 1], 0));
+        if (s >= 1) {
+            // the buffer of segment s - 1 was last read by the sweep of segment s + 1
+            MLN_ACK(c, cudaStreamWaitEvent(rs, ev_rev[(s - 1) & 1], 0));
+            MLN_ACK(c, recompute(s - 1, slot_buf[(s - 1) & 1], rs));
+            MLN_ACK(c, cudaEventRecord(ev_rec[(s - 1) & 1], rs));
         }
         for (int64_t j = len - 1; j >= 0; --j) {
-            const Set<R> f0 = set_at(slots, j), f1 = set_at(slots, j + 1);
+            const Set<R> f0 = set_at(sl, j), f1 = set_at(sl, j + 1);
             aa.E0 = f0.E;
             aa.E1 = f1.E;
             aa.S0 = f0.S;
@@ -165,6 +199,7 @@ mln_status adjoint_t(mln_ctx *c, int64_t n_steps, const double *src, int64_t pro
             MLN_ACK(c, cudaGetLastError());
             std::swap(A0s, A1s);
         }
+        MLN_ACK(c, cudaEventRecord(ev_rev[s & 1], c->stream));
     }
     mln::mln_adjoint_reduce<<<L::size, 256, 0, c->stream>>>(acc, n, accsum);
     MLN_ACK(c, cudaGetLastError());
@@ -185,6 +220,15 @@ mln_status adjoint_t(mln_ctx *c, int64_t n_steps, const double *src, int64_t pro
     }
 done:
     cudaStreamSynchronize(c->stream);
+    if (rs) {
+        cudaStreamSynchronize(rs);
+        cudaStreamDestroy(rs);
+    }
+    if (ev_fwd) cudaEventDestroy(ev_fwd);
+    for (int b = 0; b < 2; ++b) {
+        if (ev_rec[b]) cudaEventDestroy(ev_rec[b]);
+        if (ev_rev[b]) cudaEventDestroy(ev_rev[b]);
+    }
     cudaFree(ckpt);
     cudaFree(slots);
     cudaFree(adj);
