@@ -586,6 +586,12 @@ def main():
         roofline = tensor_roofline(p, args, main_run, launches, per_launch_s, clk)
     if p.maxwell == "pstd":
         roofline = pstd_roofline(p, args, main_run, f_med, clk)
+    if args.workload == "two_level_sit":
+        # 2000 cells fit the shared memory of one SM: a latency-bound parity
+        # configuration, also stated against one SM's ALU peak
+        roofline["frac_of_one_sm_peak"] = achieved / (peak / SMS)
+        roofline["note"] = ("2000-cell grid, latency-bound; frac_of_one_sm_peak compares with the ALU peak "
+                            "of one SM")
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
