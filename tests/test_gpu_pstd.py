@@ -147,3 +147,49 @@ def test_rejected_configurations():
 def make_params_of(p):
     from helpers import params_of
     return params_of(p, precision="fp64", form="merged")
+
+
+@pytest.mark.parametrize("N", [4, 6])
+def test_more_levels_against_oracle(orc, N):
+    if N == 4:
+        p = W.multi_level_ring(4, n_cells=256, n_steps=200, seed=5).with_(maxwell="pstd")
+    else:
+        p = W.six_level_pulse(n_cells=256, n_steps=150, t0=15e-15, fwhm=10e-15).with_(
+            boundary="periodic", source_kind="soft", source_cell=5, medium_begin=0, medium_end=256, maxwell="pstd")
+    ref, _ = orc.run(p, n_steps=p.n_steps)
+    E, _, rho, s = gpu_run(p, p.n_steps, "fp64", "merged")
+    s.close()
+    assert np.abs(ref.E).max() > 0
+    assert rel_inf(E, ref.E) < FP64_TOL and np.abs(pops(rho) - pops(ref.rho)).max() < FP64_TOL
+
+
+def test_rodrigues_form_against_oracle(orc):
+    p = ring(n=256, n_steps=200)
+    ref, _ = orc.run(p, n_steps=p.n_steps)
+    E, _, rho, s = gpu_run(p, p.n_steps, "fp64", "rodrigues")
+    s.close()
+    assert rel_inf(E, ref.E) < FP64_TOL and np.abs(pops(rho) - pops(ref.rho)).max() < FP64_TOL
+
+
+def test_save_load_continues_bit_for_bit():
+    """Each mln_step call transforms E from the buffers again, so a state loaded
+    between calls continues exactly as an uninterrupted run. (Strang form: its
+    device state is d itself, so saving and loading are exact; the merged
+    form's state y = A0 d + b goes through d with FP64 maps, not bit-exact.)"""
+    p = sit_ring(n=512, n_steps=300)
+    from helpers import src_tensor
+    a = make_solver(p, "fp64", "strang")
+    a.step(100, src_tensor(p, 0, 100))
+    saved = a.save()
+    a.step(200, src_tensor(p, 100, 200))
+    a.sync()
+    Ea, Ha = a.fields()
+    ra = a.rho()
+    b = make_solver(p, "fp64", "strang")
+    b.load(*saved)
+    b.step(200, src_tensor(p, 100, 200))
+    b.sync()
+    Eb, Hb = b.fields()
+    assert np.array_equal(Ea, Eb) and np.array_equal(Ha, Hb) and np.array_equal(ra, b.rho())
+    a.close()
+    b.close()
