@@ -289,13 +289,22 @@ def time_device(p, precision, form, seg, steps, warmup, block_steps, tile_cells,
     barrier(ws)
     s.sync()
     launches = s.launches - l0
-    ms = sum(a.elapsed_time(b) for a, b in evs)
+    step_ms = [a.elapsed_time(b) for a, b in evs]
+    ms = sum(step_ms)
     ms_max = max_over_ranks(ws, ms)
     shape = s.launch_shape
     work = s.work_per_step
     kern = s.kernel_in_use
+    # d -> rho of every medium cell to host memory (off the stepped path), timed on its own
+    rho_ms = None
+    if p.n_medium > 0:
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        s.rho()
+        rho_ms = (time.perf_counter() - t) * 1e3
     s.close()
     return dict(ms=ms_max, ms_local=ms, wall_s=t_wall, launches=launches, shape=shape, clocks=clocks, work=work,
+                step_ms_median=float(np.median(step_ms)), rho_readout_ms=rho_ms,
                 kernel=kern)
 
 
@@ -596,6 +605,7 @@ def main():
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": main_run["ms"] / args.steps, "higher_is_better": True,
+        "ms_per_step_median": main_run["step_ms_median"], "rho_readout_ms": main_run["rho_readout_ms"],
         "medium_cell_updates_per_s": value * p.n_medium / p.n_cells,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32",
         "data": "synthetic (seeded: levels, dipoles, rates, noise E^0)",
