@@ -473,6 +473,17 @@ mln_status mln_rotation_terms(int32_t precision, const double *x, int64_t n, dou
 mln_status mln_tc_product(int32_t nc, int32_t kc, int32_t a_in_tmem, const float *A, const double *B, float *C);
 
 /*
+ * Failure-detection self-test: runs the product kernel above with its MMA and
+ * commit left out, so nothing arrives on the completion mbarrier and the
+ * kernel's bounded wait (the same as in MLN_KERNEL_TENSOR steps) runs out; the
+ * kernel then releases its tensor memory and returns, and the host reads the
+ * flag. Returns MLN_ETIMEOUT when that happened (the expected outcome), MLN_OK
+ * if the wait somehow completed, MLN_EUNSUPPORTED without a tcgen05 device.
+ * Synchronous; the device stays usable. Not part of the paper's method.
+ */
+mln_status mln_tc_wait_selftest(void);
+
+/*
  * mln_step_noalloc -- the fused step for callers that cannot allocate device
  * memory. (Not a part of the paper's method: it has no counterpart there.)
  *

@@ -392,6 +392,27 @@ mln_status mln_tc_product(int32_t nc, int32_t kc, int32_t a_in_tmem, const float
     return MLN_OK;
 }
 
+mln_status mln_tc_wait_selftest(void) {
+    int dev = 0, major = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev) != cudaSuccess || major < 10) {
+        cudaGetLastError();
+        mln::create_error() = "no tcgen05 device";
+        return MLN_EUNSUPPORTED;
+    }
+    std::string err;
+    cudaError_t e = mln::tc_wait_selftest(err);
+    if (e != cudaSuccess) {
+        mln::create_error() = std::string("tensor-core wait self-test: ") + cudaGetErrorString(e);
+        return MLN_ECUDA;
+    }
+    if (!err.empty()) {
+        mln::create_error() = err;
+        return MLN_ETIMEOUT;
+    }
+    return MLN_OK;
+}
+
 const char *mln_status_string(mln_status s) {
     switch (s) {
     case MLN_OK: return "ok";

@@ -365,7 +365,9 @@ __global__ void __launch_bounds__(512, 1)
 // ---------------------------------------------------------------------------
 // Diagnostic product C = A B^T (A: 128 x KC, B: NC x KC) through the same
 // staging, split and issue path as the step kernel (one warpgroup).
-template <int NC, int KC, bool TA>
+// ISSUE = false leaves the MMA and its commit out: nothing arrives on the
+// mbarrier, and the bounded completion wait runs out (the timeout path).
+template <int NC, int KC, bool TA, bool ISSUE = true>
 __global__ void __launch_bounds__(128, 1)
     mln_tc_product_kernel(const float *__restrict__ A, const uint4 *__restrict__ bimg, float *__restrict__ C,
                           unsigned int *flag) {
@@ -397,7 +399,7 @@ __global__ void __launch_bounds__(128, 1)
     stage_row<TA, KC, KC, KC, ABYTES>(sA, tmem + lane, tmem + KC + lane, j, v);
     tc::fence_before_sync();
     __syncthreads();
-    if (j == 0) {
+    if (ISSUE && j == 0) {
         tc::fence_after_sync();
         const uint32_t ah = TA ? tmem : tc::smem_addr(sA), al = TA ? tmem + KC : ah + ABYTES;
         const uint32_t bh = tc::smem_addr(sB);
@@ -538,7 +540,7 @@ cudaError_t launch_tc(int N, const BlockArgs<float> &a, const std::vector<unsign
     }
 }
 
-template <int NC, int KC, bool TA>
+template <int NC, int KC, bool TA, bool ISSUE = true>
 cudaError_t tc_product_t(const float *A, const double *B, float *C, std::string &err) {
     constexpr int ABYTES = TA ? 0 : 128 * KC * 4, BBYTES = NC * KC * 4;
     constexpr int smem = 2 * BBYTES + 2 * ABYTES + 16;
@@ -554,10 +556,10 @@ cudaError_t tc_product_t(const float *A, const double *B, float *C, std::string 
     if (e == cudaSuccess) e = cudaMemset(dflag, 0, 4);
     if (e == cudaSuccess) e = cudaMemcpy(dA, A, 128 * KC * 4, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(dB, img.data(), img.size(), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(mln_tc_product_kernel<NC, KC, TA>,
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(mln_tc_product_kernel<NC, KC, TA, ISSUE>,
                                                    cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e == cudaSuccess) {
-        mln_tc_product_kernel<NC, KC, TA><<<1, 128, smem>>>(dA, static_cast<const uint4 *>(dB), dC, dflag);
+        mln_tc_product_kernel<NC, KC, TA, ISSUE><<<1, 128, smem>>>(dA, static_cast<const uint4 *>(dB), dC, dflag);
         e = cudaGetLastError();
     }
     if (e == cudaSuccess) e = cudaMemcpy(C, dC, 128 * NC * 4, cudaMemcpyDeviceToHost);
@@ -581,6 +583,12 @@ cudaError_t tc_product(int nc, int kc, bool tmem_a, const float *A, const double
     MLN_TCP(16, 8)
 #undef MLN_TCP
     return cudaErrorInvalidValue;
+}
+
+cudaError_t tc_wait_selftest(std::string &err) {
+    std::vector<float> A(128 * 8, 0.0f), C(128 * 16);
+    std::vector<double> B(16 * 8, 0.0);
+    return tc_product_t<16, 8, true, false>(A.data(), B.data(), C.data(), err);
 }
 
 int tc_smem_bytes(int N) {

@@ -25,5 +25,8 @@ cudaError_t launch_tc(int N, const BlockArgs<float> &a, const std::vector<unsign
 // C (128 x nc) = A (128 x kc) B (nc x kc)^T through the kernel's product
 // path, with A staged in tensor memory (tmem_a) or in shared memory.
 cudaError_t tc_product(int nc, int kc, bool tmem_a, const float *A, const double *B, float *C, std::string &err);
+// The product kernel with its MMA left out: the bounded completion wait runs
+// out; err is set when it did.
+cudaError_t tc_wait_selftest(std::string &err);
 
 }  // namespace mln

@@ -81,6 +81,7 @@ _SIGS = {
     "mln_step_count": (C.c_int64, [C.c_void_p]),
     "mln_launch_count": (C.c_int64, [C.c_void_p]),
     "mln_kernel_in_use": (C.c_int32, [C.c_void_p]),
+    "mln_tc_wait_selftest": (C.c_int, []),
     "mln_launch_shape": (C.c_int, [C.c_void_p, C.POINTER(C.c_int32), C.POINTER(C.c_int32),
                                    C.POINTER(C.c_int32)]),
     "mln_work_per_step": (C.c_int, [C.c_void_p, _dp, _dp, _dp, _dp]),

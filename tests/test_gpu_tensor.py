@@ -10,7 +10,9 @@ MMAs with 3 x TF32 operands, FP32 state, for N = 5 and 6.
 * a five-level periodic ring against the oracle;
 * the result does not depend on the launch shape (steps fused per launch,
   chunking of the steps): each cell's row of the MMA is computed alone;
-* input validation.
+* input validation;
+* failure detection: the bounded completion wait, made to run out (the MMA
+  left out), is reported as MLN_ETIMEOUT and the device keeps working.
 """
 import numpy as np
 import pytest
@@ -145,3 +147,25 @@ def test_invalid_parameters(case):
     with pytest.raises(mln.MLNError) as e:
         mln.Solver(params_of(p, **kw), E0=p.e_init())
     assert e.value.status == mln.MLN_EINVAL
+
+
+def test_completion_wait_runs_out_and_is_reported():
+    """The product kernel with its MMA left out: nothing arrives on the
+    completion mbarrier, the bounded wait gives up, the kernel frees its tensor
+    memory and returns, and the host reports MLN_ETIMEOUT. A normal product on
+    the same device right after is exact to the 3 x TF32 bound."""
+    import time
+    from paper_1710_09799_gb300 import mln
+    t0 = time.perf_counter()
+    status = mln.lib().mln_tc_wait_selftest()
+    waited = time.perf_counter() - t0
+    print(f"bounded wait gave up after {waited:.3f} s")
+    assert status == mln.MLN_ETIMEOUT, status
+    assert "timed out" in mln.lib().mln_create_error().decode()
+    rng = np.random.default_rng(7)
+    A = rng.normal(size=(128, 8)).astype(np.float32)
+    B = rng.normal(size=(16, 8))
+    C = mln.mln_tc_product(A, B, True)
+    ref = A.astype(np.float64) @ B.T
+    scale = np.abs(A).astype(np.float64) @ np.abs(B).T
+    assert np.all(np.abs(C - ref) <= 2.0 ** -19 * scale)
