@@ -112,8 +112,8 @@ def pstd_roofline(p, args, run, f_med, clk):
     achieved = f_step / per_step_s / 1e12
     peak = alu_peak_tflops(args.precision)
     return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-            "traffic": None, "kernel": "pstd_cell_kernel + fft_pass (whole step)",
-            "scope": "whole step: one medium launch and 4 x (FFT passes) launches per step",
+            "traffic": None, "kernel": "fs_rows_mid + fs_cols + pstd_cell_kernel (whole step)",
+            "scope": "whole step: four transform launches and one medium launch per step",
             "flops_per_step": f_step, "fft_flops_per_step": pstd_flops_per_step(p.n_cells),
             "peak_source": f"derived: {SMS} SMs x {FP64_FLOP_PER_CLK_SM if args.precision == 'fp64' else FP32_FLOP_PER_CLK_SM} "
                            f"flop/clk x {SM_MAX_MHZ:.0f} MHz"}

@@ -350,3 +350,38 @@ def test_six_level_fp32_error_4096_cells(orc):
         print(f"fp32 six-level {form}: E rel {e_err:.3e}  pop abs {p_err:.3e}")
         assert e_err < FP32_E_PER_KSTEP * k
         assert p_err < FP32_POP_PER_KSTEP * k
+
+
+@pytest.mark.parametrize("form", ["merged", "strang"])
+@pytest.mark.parametrize("make", [lambda: W.three_level_ring(n_cells=256, n_steps=1),
+                                  lambda: W.multi_level_ring(4, n_cells=256, n_steps=1, seed=2),
+                                  lambda: W.two_level_sit(n_cells=200, medium=(50, 150), n_steps=1)])
+def test_work_count_is_the_exact_operation_count(make, form):
+    """The roofline's algorithmic flops (mln_work_per_step), recounted here from
+    the set-up matrices: a product row of k non-zero entries is k
+    multiplications and k - 1 additions, k additions when added onto a vector,
+    one more for a non-zero offset; the N - 1 angle series (8), the other
+    planes by the subtraction formulas (10) and 6 per plane increment."""
+    from paper_1710_09799_gb300 import mln
+    from helpers import params_of
+    p = make()
+    s = mln.mln_setup_host(params_of(p, precision="fp64", form=form))
+    N, D, q = s["N"], s["D"], s["q"]
+    P = 2 * q
+    T, C1, A0 = np.array(s["T"]), np.array(s["C1"]), np.array(s["A0"])
+    b, w, c = np.array(s["b"]), np.array(s["w"]), s["c"]
+    nz = lambda a: int(np.count_nonzero(a))
+    nT = nz(T[:, :P])
+    tt = 2 * nT - sum(bool(np.any(T[:, k] != 0)) for k in range(P))
+    rot = 6 * q + 10 * (q - (N - 1)) + 8 * (N - 1)
+    dot = lambda v, c0: (2 * nz(v) - 1 + (c0 != 0)) if nz(v) else 0
+    if form == "merged":
+        b2, wm, cm = A0 @ b + b, A0.T @ w, w @ b + c
+        want = tt + rot + 2 * nT + dot(wm, cm) + 2 * nz(C1) + nz(b2)
+    else:
+        half = 2 * nz(A0 - np.eye(D)) + nz(b)
+        want = 2 * half + tt + rot + 2 * nT + dot(w, c)
+    sol = make_solver(p, "fp64", form)
+    f_med, f_cell, _, _ = sol.work_per_step
+    sol.close()
+    assert f_med == want and f_cell == 9.0, (f_med, want)
