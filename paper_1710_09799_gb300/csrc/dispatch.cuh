@@ -110,14 +110,33 @@ bool pack_consts_t(const Setup &s, int form, double dt, std::vector<unsigned cha
     }
 }
 
+// A step kernel launch with a programmatic dependency on the kernel before it
+// in the stream (mln_block_kernel waits for that grid before it touches the
+// fields): the launch is prepared while the previous grid runs and its blocks
+// start as soon as that grid completes.
+template <typename... P, typename... A>
+cudaError_t launch_dependent(void (*kern)(P...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                             const A &...args) {
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, args...);
+}
+
 template <int N, typename R, typename K>
 cudaError_t launch_one(const BlockArgs<R> &a, const std::vector<unsigned char> &consts, dim3 grid,
                        dim3 block, size_t smem, cudaStream_t st) {
     K k;
     if (consts.size() != sizeof(K)) return cudaErrorInvalidValue;
     std::memcpy(&k, consts.data(), sizeof(K));
-    mln_block_kernel<N, R, RegisterCell<N, R, K>><<<grid, block, smem, st>>>(a, k);
-    return cudaGetLastError();
+    return launch_dependent(mln_block_kernel<N, R, RegisterCell<N, R, K>>, grid, block, smem, st, a, k);
 }
 
 // The sparse program of the merged FP64 step (see SparseConsts): entries of
@@ -178,8 +197,7 @@ cudaError_t launch_sparse_one(const BlockArgs<double> &a, const std::vector<unsi
     auto kern = mln_block_kernel<N, double, SharedSparseCell<N>>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
     if (e != cudaSuccess) return e;
-    kern<<<grid, block, smem, st>>>(a, k);
-    return cudaGetLastError();
+    return launch_dependent(kern, grid, block, smem, st, a, k);
 }
 
 template <typename R>

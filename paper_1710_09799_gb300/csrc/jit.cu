@@ -13,6 +13,7 @@
 #include <dlfcn.h>
 
 #include <cstdio>
+#include <cstring>
 #include <map>
 #include <mutex>
 #include <sstream>
@@ -50,6 +51,7 @@ struct Driver {
     CUresult (*launch)(CUfunction, unsigned, unsigned, unsigned, unsigned, unsigned, unsigned, unsigned, CUstream,
                        void **, void **) = nullptr;
     CUresult (*set_attr)(CUfunction, CUfunction_attribute, int) = nullptr;
+    CUresult (*launch_ex)(const CUlaunchConfig *, CUfunction, void **, void **) = nullptr;  // optional
     bool ok = false;
 };
 
@@ -97,6 +99,7 @@ bool load_tools() {
     Driver &d = g_drv;
     d.ok = entry("cuModuleLoadData", d.load) && entry("cuModuleGetFunction", d.get) &&
            entry("cuLaunchKernel", d.launch) && entry("cuFuncSetAttribute", d.set_attr);
+    if (!entry("cuLaunchKernelEx", d.launch_ex)) d.launch_ex = nullptr;
     if (!r.ok) g_why = "NVRTC symbols missing";
     else if (!d.ok) g_why = "driver entry points unavailable";
     return r.ok && d.ok;
@@ -194,6 +197,11 @@ std::string jit_merged_source(const Setup &s, double dt, bool fp32) {
       << "extern \"C\" __global__ void __launch_bounds__(kMaxThreads, 1) mln_jit_step(const __grid_constant__ BlockArgs<"
       << R << "> a, const __grid_constant__ JitConsts k) {\n"
       << "  extern __shared__ __align__(16) unsigned char smem_raw[];\n"
+      // launched with a programmatic dependency on the kernel before it:
+      // wait for that grid to complete (its fields and states visible) before
+      // any read or write, then let the next launch be placed
+      << "  asm volatile(\"griddepcontrol.wait;\" ::: \"memory\");\n"
+      << "  asm volatile(\"griddepcontrol.launch_dependents;\" ::: \"memory\");\n"
       << "  block_body<" << N << ", " << R << ", JitCell>(a, k, static_cast<int64_t>(blockIdx.x), smem_raw);\n}\n"
       << "}  // namespace mln\n";
     return o.str();
@@ -415,6 +423,29 @@ cudaError_t jit_launch_t(void *fn, const BlockArgs<R> &a, dim3 g, dim3 b, size_t
         int unused;
     } k{0};
     void *params[] = {const_cast<BlockArgs<R> *>(&a), &k};
+    if (g_drv.launch_ex) {
+        // programmatic dependency on the kernel before it in the stream: the
+        // blocks are placed on SMs as the previous grid's blocks exit and start
+        // as soon as that grid completes (the kernel waits for it first)
+        CUlaunchAttribute attr[1];
+        std::memset(attr, 0, sizeof(attr));
+        attr[0].id = CU_LAUNCH_ATTRIBUTE_PROGRAMMATIC_STREAM_SERIALIZATION;
+        attr[0].value.programmaticStreamSerializationAllowed = 1;
+        CUlaunchConfig cfg;
+        std::memset(&cfg, 0, sizeof(cfg));
+        cfg.gridDimX = g.x;
+        cfg.gridDimY = g.y;
+        cfg.gridDimZ = g.z;
+        cfg.blockDimX = b.x;
+        cfg.blockDimY = b.y;
+        cfg.blockDimZ = b.z;
+        cfg.sharedMemBytes = static_cast<unsigned>(smem);
+        cfg.hStream = static_cast<CUstream>(st);
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        const CUresult r = g_drv.launch_ex(&cfg, static_cast<CUfunction>(fn), params, nullptr);
+        return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorLaunchFailure;
+    }
     CUresult r = g_drv.launch(static_cast<CUfunction>(fn), g.x, g.y, g.z, b.x, b.y, b.z, static_cast<unsigned>(smem),
                               static_cast<CUstream>(st), params, nullptr);
     return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorLaunchFailure;

@@ -709,6 +709,12 @@ template <int N, typename R, typename Cell>
 __global__ void __launch_bounds__(kMaxThreads, 1)
     mln_block_kernel(const __grid_constant__ BlockArgs<R> a, const __grid_constant__ typename Cell::Consts k) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    // Launched with a programmatic dependency on the kernel before it in the
+    // stream: wait for that grid to complete (its fields and states visible)
+    // before any read or write, then let the next launch place its blocks as
+    // this grid's blocks exit. Without such a dependency both are no-ops.
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     block_body<N, R, Cell>(a, k, static_cast<int64_t>(blockIdx.x), smem_raw);
 }
 

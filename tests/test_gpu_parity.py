@@ -385,3 +385,30 @@ def test_work_count_is_the_exact_operation_count(make, form):
     f_med, f_cell, _, _ = sol.work_per_step
     sol.close()
     assert f_med == want and f_cell == 9.0, (f_med, want)
+
+
+@pytest.mark.parametrize("precision,kernel", [("fp64", "auto"), ("fp64", "jit"), ("fp32", "auto"),
+                                              ("fp32", "register")])
+def test_torch_kernel_between_steps_is_ordered(precision, kernel):
+    """The step kernels are launched with a programmatic dependency on the
+    kernel before them in the stream and wait for that grid before they touch
+    the fields: a torch kernel that halves E on the context's stream between
+    two mln_step calls acts before the second call, exactly as the same halved
+    field copied in from the host does."""
+    p = W.three_level_ring(n_cells=2000, n_steps=78)
+    a = make_solver(p, precision, "merged", kernel=kernel)
+    b = make_solver(p, precision, "merged", kernel=kernel)
+    for s in (a, b):
+        s.step(37)
+    a.E.mul_(0.5)  # on the context's stream, right behind the step kernels
+    b.sync()
+    b.E.copy_(b.E.cpu() * 0.5)
+    for s in (a, b):
+        s.step(41)
+        s.sync()
+    Ea, Ha = a.fields()
+    Eb, Hb = b.fields()
+    assert np.abs(Ea).max() > 0
+    assert np.array_equal(Ea, Eb) and np.array_equal(Ha, Hb) and np.array_equal(a.rho(), b.rho())
+    a.close()
+    b.close()
