@@ -110,13 +110,15 @@ bool pack_consts_t(const Setup &s, int form, double dt, std::vector<unsigned cha
     }
 }
 
-// A step kernel launch with a programmatic dependency on the kernel before it
-// in the stream (mln_block_kernel waits for that grid before it touches the
-// fields): the launch is prepared while the previous grid runs and its blocks
-// start as soon as that grid completes.
+// A step kernel launch, with (programmatic) or without a programmatic
+// dependency on the kernel before it in the stream (mln_block_kernel waits for
+// that grid before it touches the fields): with one, the launch is prepared
+// while the previous grid runs and its blocks start as soon as that grid
+// completes. Launches beside concurrent work on another stream go without:
+// blocks placed early hold SM resources that work needs.
 template <typename... P, typename... A>
-cudaError_t launch_dependent(void (*kern)(P...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
-                             const A &...args) {
+cudaError_t launch_dependent(bool programmatic, void (*kern)(P...), dim3 grid, dim3 block, size_t smem,
+                             cudaStream_t st, const A &...args) {
     cudaLaunchConfig_t cfg{};
     cfg.gridDim = grid;
     cfg.blockDim = block;
@@ -126,17 +128,18 @@ cudaError_t launch_dependent(void (*kern)(P...), dim3 grid, dim3 block, size_t s
     attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
-    cfg.numAttrs = 1;
+    cfg.numAttrs = programmatic ? 1 : 0;
     return cudaLaunchKernelEx(&cfg, kern, args...);
 }
 
 template <int N, typename R, typename K>
 cudaError_t launch_one(const BlockArgs<R> &a, const std::vector<unsigned char> &consts, dim3 grid,
-                       dim3 block, size_t smem, cudaStream_t st) {
+                       dim3 block, size_t smem, cudaStream_t st, bool programmatic) {
     K k;
     if (consts.size() != sizeof(K)) return cudaErrorInvalidValue;
     std::memcpy(&k, consts.data(), sizeof(K));
-    return launch_dependent(mln_block_kernel<N, R, RegisterCell<N, R, K>>, grid, block, smem, st, a, k);
+    return launch_dependent(programmatic, mln_block_kernel<N, R, RegisterCell<N, R, K>>, grid, block, smem, st, a,
+                            k);
 }
 
 // The sparse program of the merged FP64 step (see SparseConsts): entries of
@@ -197,17 +200,17 @@ cudaError_t launch_sparse_one(const BlockArgs<double> &a, const std::vector<unsi
     auto kern = mln_block_kernel<N, double, SharedSparseCell<N>>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
     if (e != cudaSuccess) return e;
-    return launch_dependent(kern, grid, block, smem, st, a, k);
+    return launch_dependent(true, kern, grid, block, smem, st, a, k);
 }
 
 template <typename R>
 cudaError_t launch_block_t(int N, int form, const BlockArgs<R> &a, const std::vector<unsigned char> &consts,
-                           dim3 grid, dim3 block, size_t smem, cudaStream_t st) {
+                           dim3 grid, dim3 block, size_t smem, cudaStream_t st, bool programmatic) {
     if (form == MLN_FORM_RODRIGUES) {
         switch (N) {
-        case 2: return launch_one<2, R, RodriguesConsts<2, R>>(a, consts, grid, block, smem, st);
-        case 3: return launch_one<3, R, RodriguesConsts<3, R>>(a, consts, grid, block, smem, st);
-        case 4: return launch_one<4, R, RodriguesConsts<4, R>>(a, consts, grid, block, smem, st);
+        case 2: return launch_one<2, R, RodriguesConsts<2, R>>(a, consts, grid, block, smem, st, programmatic);
+        case 3: return launch_one<3, R, RodriguesConsts<3, R>>(a, consts, grid, block, smem, st, programmatic);
+        case 4: return launch_one<4, R, RodriguesConsts<4, R>>(a, consts, grid, block, smem, st, programmatic);
         default: return cudaErrorInvalidValue;
         }
     }
@@ -215,8 +218,8 @@ cudaError_t launch_block_t(int N, int form, const BlockArgs<R> &a, const std::ve
 #define MLN_LAUNCH_CASE(NN)                                                                     \
     case NN:                                                                                    \
         if (form == MLN_FORM_STRANG)                                                            \
-            return launch_one<NN, R, StrangConsts<NN, R>>(a, consts, grid, block, smem, st);    \
-        return launch_one<NN, R, MergedConsts<NN, R>>(a, consts, grid, block, smem, st);
+            return launch_one<NN, R, StrangConsts<NN, R>>(a, consts, grid, block, smem, st, programmatic);    \
+        return launch_one<NN, R, MergedConsts<NN, R>>(a, consts, grid, block, smem, st, programmatic);
         MLN_LAUNCH_CASE(2)
         MLN_LAUNCH_CASE(3)
         MLN_LAUNCH_CASE(4)
@@ -231,10 +234,11 @@ cudaError_t launch_block_t(int N, int form, const BlockArgs<R> &a, const std::ve
 // Entry points defined once per precision.
 bool pack_consts(const Setup &s, int form, double dt, double tag, std::vector<unsigned char> &out);
 bool pack_consts(const Setup &s, int form, double dt, float tag, std::vector<unsigned char> &out);
+// programmatic: launch with a programmatic dependency on the kernel before it
 cudaError_t launch_block(int N, int form, const BlockArgs<double> &a, const std::vector<unsigned char> &consts,
-                         dim3 grid, dim3 block, size_t smem, cudaStream_t st);
+                         dim3 grid, dim3 block, size_t smem, cudaStream_t st, bool programmatic = true);
 cudaError_t launch_block(int N, int form, const BlockArgs<float> &a, const std::vector<unsigned char> &consts,
-                         dim3 grid, dim3 block, size_t smem, cudaStream_t st);
+                         dim3 grid, dim3 block, size_t smem, cudaStream_t st, bool programmatic = true);
 cudaError_t launch_sin_cosm1(int precision, const double *x, int64_t n, double *s, double *c1, cudaStream_t st);
 bool pack_sparse_consts(const Setup &s, double dt, const int32_t *rowptr, const int32_t *cols, const double *vals,
                         int nnz, int nrowptr, std::vector<unsigned char> &out);

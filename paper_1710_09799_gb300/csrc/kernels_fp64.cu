@@ -8,8 +8,8 @@ bool pack_consts(const Setup &s, int form, double dt, double, std::vector<unsign
 }
 
 cudaError_t launch_block(int N, int form, const BlockArgs<double> &a, const std::vector<unsigned char> &consts,
-                         dim3 grid, dim3 block, size_t smem, cudaStream_t st) {
-    return launch_block_t<double>(N, form, a, consts, grid, block, smem, st);
+                         dim3 grid, dim3 block, size_t smem, cudaStream_t st, bool programmatic) {
+    return launch_block_t<double>(N, form, a, consts, grid, block, smem, st, programmatic);
 }
 
 cudaError_t launch_sin_cosm1(int precision, const double *x, int64_t n, double *s, double *c1, cudaStream_t st) {
