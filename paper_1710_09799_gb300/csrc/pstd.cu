@@ -480,9 +480,10 @@ FsArgs<R> fs_base(const mln_ctx *c, const Layout<R> &L) {
 // kernel before it in the stream (captured as a programmatic graph edge).
 // FP32 transforms are latency-bound, and starting each while the previous
 // one drains shortens the step (28.6 -> 20.8 us at 65536 cells). The FP64
-// transforms are bound by the FP64 pipe; blocks placed early leave SMs
-// unevenly loaded beside the overlapping medium kernel, and the FP64 step
-// took longer (76 -> 87 us), so FP64 launches carry no such dependency.
+// transforms run about one warp per SM sub-partition, limited by the latency
+// of dependent FP64 operations; blocks placed early leave SMs unevenly loaded
+// beside the overlapping medium kernel, and the FP64 step took longer
+// (76 -> 87 us), so FP64 launches carry no such dependency.
 template <typename R>
 cudaError_t launch_fs(void (*kernel)(FsArgs<R>), const FsArgs<R> &a, int blocks, int L, cudaStream_t st) {
     cudaLaunchConfig_t cfg{};
