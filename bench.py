@@ -540,7 +540,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="mine", choices=["mine", "reference"])
     ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32"])
-    ap.add_argument("--form", default="merged", choices=["strang", "merged", "rodrigues"])
+    ap.add_argument("--form", default="merged", choices=["strang", "merged", "rodrigues", "rotated"])
     ap.add_argument("--seg", type=int, default=1000, help="time steps per benchmark step")
     ap.add_argument("--block-steps", type=int, default=0, help="0: autotuned")
     ap.add_argument("--tile", type=int, default=0)

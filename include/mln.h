@@ -67,7 +67,18 @@ enum { MLN_FP64 = 0, MLN_FP32 = 1 };
  * exponential evaluated by the generalised Rodrigues formula of Eq. 27,
  * I + sum_k sin(a_k) S_k + (1 - cos a_k) S_k^2, with the rank-2 matrices
  * S_k = T Theta_k T^T (and S_k^2) stored in full: the paper's "rodr" method. */
-enum { MLN_FORM_STRANG = 0, MLN_FORM_MERGED = 1, MLN_FORM_RODRIGUES = 2 };
+/* MLN_FORM_ROTATED is the merged form with the state held in the basis of
+ * the rotation planes, z = T^T y: a step rotates the plane pairs of z by the
+ * angles of Eq. 24 and applies one affine map C z'' + c' with
+ * C = T^T A0^2 T and c' = T^T (A0 b + b), and dP/dt = (T^T A0^T w) . z'' +
+ * w . b + c. One dense D x D product per step instead of the merged form's
+ * three (T^T, T and A0^2 - I): fewer operations where T is dense (N >= 5;
+ * the six-level model: 2750 against 6919 flops per cell update), more where
+ * T is sparse and C is not (the three-level ring: 199 against 179). Same
+ * result up to rounding. Runs on the run-time compiled kernel only
+ * (MLN_KERNEL_AUTO or MLN_KERNEL_JIT) with the FDTD field solver, single
+ * grids (no batches, adjoint or allocation-free step). */
+enum { MLN_FORM_STRANG = 0, MLN_FORM_MERGED = 1, MLN_FORM_RODRIGUES = 2, MLN_FORM_ROTATED = 3 };
 /* Cell model of the step kernel. MLN_KERNEL_REGISTER keeps each cell's
  * vector in registers and multiplies by the full D x D constant matrices.
  * MLN_KERNEL_SPARSE (FP64, merged form only) keeps the vectors in shared
@@ -125,7 +136,8 @@ enum {
  *   N             number of levels, MLN_MIN_N..MLN_MAX_N; adjoint dimension D = N*N-1.
  *   precision     MLN_FP64 or MLN_FP32: type of the device state, fields and
  *                 propagator arithmetic. Set-up is always FP64.
- *   form          MLN_FORM_STRANG, MLN_FORM_MERGED or MLN_FORM_RODRIGUES (N <= 4).
+ *   form          MLN_FORM_STRANG, MLN_FORM_MERGED, MLN_FORM_RODRIGUES (N <= 4)
+ *                 or MLN_FORM_ROTATED (run-time compiled kernel, FDTD).
  *   H0            N x N complex Hermitian, J (Eq. 2, H = H0 - mu E_z).
  *   mu            N x N complex Hermitian dipole operator, C m.
  *   G             (N*N) x (N*N) complex relaxation superoperator, 1/s; it must

@@ -341,7 +341,8 @@ mln_status mln_kernel_source(const mln_params *p, char *buf, size_t cap, size_t 
         mln::create_error() = err;
         return st;
     }
-    const std::string src = mln::jit_merged_source(s, p->dt, p->precision == MLN_FP32);
+    const std::string src =
+        mln::jit_merged_source(s, p->dt, p->precision == MLN_FP32, p->form == MLN_FORM_ROTATED);
     if (len) *len = src.size();
     if (buf && cap > 0) {
         const size_t k = std::min(cap - 1, src.size());
@@ -638,19 +639,22 @@ mln_status mln_create(const mln_params *p, void *d_state, void *Ez, void *Hy, vo
     } else {
         ok = p->precision == MLN_FP64 ? mln::pack_consts(c->s, p->form, p->dt, 0.0, c->consts)
                                       : mln::pack_consts(c->s, p->form, p->dt, 0.0f, c->consts);
-        const bool want_jit = p->kernel == MLN_KERNEL_JIT ||
+        // the rotated form exists only as a run-time compiled kernel
+        const bool rotated = p->form == MLN_FORM_ROTATED;
+        const bool want_jit = p->kernel == MLN_KERNEL_JIT || rotated ||
                               (p->kernel == MLN_KERNEL_AUTO && p->precision == MLN_FP32 && p->form == MLN_FORM_MERGED &&
                                p->maxwell == MLN_MAXWELL_FDTD);
         if (ok && want_jit) {
             std::string why, log;
             cudaError_t e = cudaErrorNotSupported;
             if (mln::jit_available(&why))
-                e = mln::jit_compile(mln::jit_merged_source(c->s, p->dt, p->precision == MLN_FP32), &c->jit_fn, log);
+                e = mln::jit_compile(mln::jit_merged_source(c->s, p->dt, p->precision == MLN_FP32, rotated),
+                                     &c->jit_fn, log);
             else
                 log = why;
             if (e != cudaSuccess) {
                 c->jit_fn = nullptr;
-                if (p->kernel == MLN_KERNEL_JIT) {
+                if (p->kernel == MLN_KERNEL_JIT || rotated) {
                     c->err = "run-time compiled kernel unavailable: " + log;
                     return fail(MLN_EUNSUPPORTED);
                 }
@@ -803,6 +807,10 @@ mln_status mln_work_per_step(const mln_ctx *c, double *flops_medium, double *flo
     if (c->p.form == MLN_FORM_MERGED) {
         // y'' = y + T dz; dP/dt = c' + wm . y''; y = (y'' + b2) + C1 y''
         f = tt + rot + 2 * nT + dot(s.wm, s.cm) + 2 * nz(s.C1, D, D, D, 0.0) + nz(s.b2, 1, D, D, 0.0);
+    } else if (c->p.form == MLN_FORM_ROTATED) {
+        // z'' = z + dz on the P plane coordinates; dP/dt = cm + wz . z'';
+        // z = (z'' + cz) + C1z z''
+        f = P + rot + dot(s.wz, s.cm) + 2 * nz(s.C1z, D, D, D, 0.0) + nz(s.cz, 1, D, D, 0.0);
     } else {
         // d' = d + ((A0 - I) d + b), twice per step
         const double half = 2 * nz(s.A0, D, D, D, 1.0) + nz(s.b, 1, D, D, 0.0);

@@ -133,7 +133,7 @@ std::string row_sum(const std::vector<double> &A, int ld, int i, int ncols, cons
 
 }  // namespace
 
-std::string jit_merged_source(const Setup &s, double dt, bool fp32) {
+std::string jit_merged_source(const Setup &s, double dt, bool fp32, bool rotated) {
     const int N = s.N, D = s.D, Q = s.q, P = 2 * Q;
     const char *R = fp32 ? "float" : "double";
     std::ostringstream o;
@@ -151,12 +151,13 @@ std::string jit_merged_source(const Setup &s, double dt, bool fp32) {
       << "  __device__ __forceinline__ void end_step() {}\n"
       << "  __device__ __forceinline__ " << R << " step(" << R << " e, const Consts &) {\n"
       << "    " << R << " z[D], y[D];\n";
-    // z = T^T y on the plane rows (T^T row k = T column k)
+    // z = T^T y on the plane rows (T^T row k = T column k); in the rotated
+    // form the state already is z
     std::vector<double> Tt((size_t)D * D);
     for (int i = 0; i < D; ++i)
         for (int k = 0; k < D; ++k) Tt[k * D + i] = s.T[i * D + k];
     for (int k = 0; k < P; ++k) {
-        std::string e = row_sum(Tt, D, k, D, "s", fp32);
+        std::string e = rotated ? "s[" + std::to_string(k) + "]" : row_sum(Tt, D, k, D, "s", fp32);
         o << "    z[" << k << "] = " << (e.empty() ? std::string(fp32 ? "0.0f" : "0.0") : e) << ";\n";
     }
     for (int k = P; k < D; ++k) o << "    z[" << k << "] = " << (fp32 ? "0.0f" : "0.0") << ";\n";
@@ -167,18 +168,23 @@ std::string jit_merged_source(const Setup &s, double dt, bool fp32) {
     // the increment summed first in FP32 (as the register model)
     for (int i = 0; i < D; ++i) {
         const std::string si = "s[" + std::to_string(i) + "]";
-        if (fp32) {
+        if (rotated) {  // z'' = z + (R - I) z on the plane pairs, the rest unchanged
+            o << "    y[" << i << "] = " << (i < P ? si + " + z[" + std::to_string(i) + "]" : si) << ";\n";
+        } else if (fp32) {
             std::string e = row_sum(s.T, D, i, P, "z", fp32);
             o << "    y[" << i << "] = " << (e.empty() ? si : si + " + (" + e + ")") << ";\n";
         } else {
             o << "    y[" << i << "] = " << row_sum(s.T, D, i, P, "z", fp32, si) << ";\n";
         }
     }
-    // dP/dt = wm . y'' + cm
+    // dP/dt = wm . y'' + cm (rotated: wz . z'' + cm)
+    const std::vector<double> &wv = rotated ? s.wz : s.wm;
+    const std::vector<double> &Cm = rotated ? s.C1z : s.C1;
+    const std::vector<double> &bv = rotated ? s.cz : s.b2;
     {
         std::string acc = lit(s.cm, fp32);
         for (int i = 0; i < D; ++i)
-            if (nz(s.wm[i], fp32)) acc = "fma(" + lit(s.wm[i], fp32) + ", y[" + std::to_string(i) + "], " + acc + ")";
+            if (nz(wv[i], fp32)) acc = "fma(" + lit(wv[i], fp32) + ", y[" + std::to_string(i) + "], " + acc + ")";
         o << "    const " << R << " dpdt = " << acc << ";\n";
     }
     // y = (y'' + b2) + C1 y'' accumulated onto y'' + b2 (no add where b2 is
@@ -186,11 +192,11 @@ std::string jit_merged_source(const Setup &s, double dt, bool fp32) {
     for (int i = 0; i < D; ++i) {
         const std::string yi = "y[" + std::to_string(i) + "]";
         if (fp32) {
-            std::string e = row_sum(s.C1, D, i, D, "y", fp32, lit(s.b2[i], fp32));
+            std::string e = row_sum(Cm, D, i, D, "y", fp32, lit(bv[i], fp32));
             o << "    s[" << i << "] = " << yi << " + (" << e << ");\n";
         } else {
-            const std::string init = nz(s.b2[i], fp32) ? "(" + yi + " + " + lit(s.b2[i], fp32) + ")" : yi;
-            o << "    s[" << i << "] = " << row_sum(s.C1, D, i, D, "y", fp32, init) << ";\n";
+            const std::string init = nz(bv[i], fp32) ? "(" + yi + " + " + lit(bv[i], fp32) + ")" : yi;
+            o << "    s[" << i << "] = " << row_sum(Cm, D, i, D, "y", fp32, init) << ";\n";
         }
     }
     o << "    return dpdt;\n  }\n};\n"

@@ -13,7 +13,8 @@ namespace mln {
 
 // CUDA source of the merged-form step kernel of one context (constants inlined,
 // exact zeros left out), kernel name mln_jit_step.
-std::string jit_merged_source(const Setup &s, double dt, bool fp32);
+// rotated: the state is z = T^T y (MLN_FORM_ROTATED), else y (MLN_FORM_MERGED)
+std::string jit_merged_source(const Setup &s, double dt, bool fp32, bool rotated = false);
 
 // Whether NVRTC and the driver entry points could be loaded (reason if not).
 bool jit_available(std::string *why);

@@ -383,8 +383,15 @@ mln_status validate(const mln_params &p, std::string &err) {
         err = "precision must be MLN_FP64 or MLN_FP32";
         return MLN_EINVAL;
     }
-    if (p.form != MLN_FORM_STRANG && p.form != MLN_FORM_MERGED && p.form != MLN_FORM_RODRIGUES) {
-        err = "form must be MLN_FORM_STRANG, MLN_FORM_MERGED or MLN_FORM_RODRIGUES";
+    if (p.form != MLN_FORM_STRANG && p.form != MLN_FORM_MERGED && p.form != MLN_FORM_RODRIGUES &&
+        p.form != MLN_FORM_ROTATED) {
+        err = "form must be MLN_FORM_STRANG, MLN_FORM_MERGED, MLN_FORM_RODRIGUES or MLN_FORM_ROTATED";
+        return MLN_EINVAL;
+    }
+    if (p.form == MLN_FORM_ROTATED &&
+        ((p.kernel != MLN_KERNEL_AUTO && p.kernel != MLN_KERNEL_JIT) || p.maxwell != MLN_MAXWELL_FDTD)) {
+        err = "MLN_FORM_ROTATED runs on the run-time compiled kernel (MLN_KERNEL_AUTO or MLN_KERNEL_JIT) with "
+              "MLN_MAXWELL_FDTD";
         return MLN_EINVAL;
     }
     if (p.form == MLN_FORM_RODRIGUES && p.N > 4) {
@@ -458,8 +465,8 @@ mln_status validate(const mln_params &p, std::string &err) {
         err = "MLN_KERNEL_TENSOR fuses at most 32 steps per launch";
         return MLN_EINVAL;
     }
-    if (p.kernel == MLN_KERNEL_JIT && p.form != MLN_FORM_MERGED) {
-        err = "MLN_KERNEL_JIT needs MLN_FORM_MERGED";
+    if (p.kernel == MLN_KERNEL_JIT && p.form != MLN_FORM_MERGED && p.form != MLN_FORM_ROTATED) {
+        err = "MLN_KERNEL_JIT needs MLN_FORM_MERGED or MLN_FORM_ROTATED";
         return MLN_EINVAL;
     }
     if (p.kernel == MLN_KERNEL_SPARSE && (p.precision != MLN_FP64 || p.form != MLN_FORM_MERGED)) {
@@ -694,19 +701,32 @@ mln_status build_setup(const mln_params &p, Setup &s, std::string &err) {
     s.cm = s.c;
     for (int i = 0; i < D; ++i) s.cm += s.w[i] * s.b[i];
 
+    // Rotated form (state z = T^T y, T orthogonal): z'' = R(E) z on the plane
+    // pairs; dP/dt = (T^T wm) . z'' + cm; the next state is
+    // T^T (y'' + C1 y'' + b2) = z'' + (T^T C1 T) z'' + T^T b2.
+    s.C1z = rmul(Tt, rmul(s.C1, s.T, D), D);
+    s.cz = rmatvec(Tt, s.b2, D);
+    s.wz = rmatvec(Tt, s.wm, D);
+
     // State <-> adjoint vector maps.
     s.Sd.assign((size_t)D * D, 0.0);
     s.sd0.assign(D, 0.0);
     s.Sp.assign((size_t)D * D, 0.0);
     s.sp0.assign(D, 0.0);
-    if (p.form != MLN_FORM_MERGED) {
-        for (int i = 0; i < D; ++i) s.Sd[i * D + i] = s.Sp[i * D + i] = 1.0;
-    } else {
+    if (p.form == MLN_FORM_MERGED) {
         // d = A0^-1 (y - b) = A0inv y + binv;  y = A0 d + b
         s.Sd = s.A0inv;
         s.sd0 = s.binv;
         s.Sp = s.A0;
         s.sp0 = s.b;
+    } else if (p.form == MLN_FORM_ROTATED) {
+        // d = A0inv T z + binv;  z = T^T A0 d + T^T b
+        s.Sd = rmul(s.A0inv, s.T, D);
+        s.sd0 = s.binv;
+        s.Sp = rmul(Tt, s.A0, D);
+        s.sp0 = rmatvec(Tt, s.b, D);
+    } else {
+        for (int i = 0; i < D; ++i) s.Sd[i * D + i] = s.Sp[i * D + i] = 1.0;
     }
 
     // rho = I/N + 1/2 sum_j d_j s_j (Eq. 6) as rho_c + Z d over interleaved re/im.

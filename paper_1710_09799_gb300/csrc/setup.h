@@ -32,6 +32,8 @@ struct Setup {
     // merged form: state y = A0 d + b; C1 = A0^2 - I, b2 = A0 b + b, wm = A0^T w, cm = w . b + c
     std::vector<double> C1, b2, wm;
     double cm = 0;
+    // rotated form: state z = T^T y; C1z = T^T C1 T, cz = T^T b2, wz = T^T wm
+    std::vector<double> C1z, cz, wz;
     // device state -> adjoint vector d = sd0 + Sd state, and back state = sp0 + Sp d
     std::vector<double> Sd, sd0, Sp, sp0;
     // rho (2 N^2 reals, interleaved re/im) = rho_c + Z d   (Eq. 6)

@@ -208,8 +208,9 @@ mln_status mln_step_noalloc(const mln_params *p, void *d_state, void *Ez, void *
         mln::create_error() = err;
         return st;
     }
-    if (p->kernel == MLN_KERNEL_SPARSE || p->maxwell != MLN_MAXWELL_FDTD) {
-        mln::create_error() = "mln_step_noalloc runs the register cell model with the FDTD field solver only";
+    if (p->kernel == MLN_KERNEL_SPARSE || p->maxwell != MLN_MAXWELL_FDTD || p->form == MLN_FORM_ROTATED) {
+        mln::create_error() = "mln_step_noalloc runs the register cell model (not the rotated form) with the FDTD "
+                              "field solver only";
         return MLN_EINVAL;
     }
     const size_t need = scratch_bytes_for(p);

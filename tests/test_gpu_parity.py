@@ -40,7 +40,7 @@ def pops(rho):
     return np.einsum("cii->ci", rho).real
 
 
-@pytest.mark.parametrize("form", ["strang", "merged", "rodrigues"])
+@pytest.mark.parametrize("form", ["strang", "merged", "rodrigues", "rotated"])
 def test_two_level_sit_full_fp64(orc, form):
     """The two-level workload at full size: 2000 cells, medium [500, 1500),
     sech pulse of area 2 pi, hard source + Mur, 20000 steps."""
@@ -54,7 +54,7 @@ def test_two_level_sit_full_fp64(orc, form):
     assert pops(ref.rho)[:, 1].max() > 1e-3  # the pulse reached and excited the medium
 
 
-@pytest.mark.parametrize("form", ["strang", "merged", "rodrigues"])
+@pytest.mark.parametrize("form", ["strang", "merged", "rodrigues", "rotated"])
 def test_three_level_ring_small_fp64(orc, form):
     """Three-level ring, 4096 cells (several tiles, ragged last tile), 1500 steps."""
     p = W.three_level_ring(n_cells=4096, n_steps=1500)
@@ -66,7 +66,7 @@ def test_three_level_ring_small_fp64(orc, form):
     assert np.abs(rho - ref.rho).max() < FP64_POP
 
 
-@pytest.mark.parametrize("form", ["strang", "merged"])
+@pytest.mark.parametrize("form", ["strang", "merged", "rotated"])
 def test_six_level_small_fp64(orc, form):
     """Six-level manifold (D = 35), 700 cells (medium up to the cell before the
     Mur cell), Gaussian source, 400 steps."""
@@ -89,7 +89,7 @@ def test_other_N_fp64(orc, N):
                   medium_end=650, boundary="periodic", n_steps=300,
                   E_init=rng.normal(0, 1e8, size=777))
     ref = oracle_ref(orc, p, p.n_steps)
-    for form in ("strang", "merged") + (("rodrigues",) if N <= 4 else ()):
+    for form in ("strang", "merged", "rotated") + (("rodrigues",) if N <= 4 else ()):
         E, H, rho, _ = gpu_run(p, p.n_steps, "fp64", form)
         assert rel_inf(E, ref.E) < FP64_E
         assert np.abs(rho - ref.rho).max() < FP64_POP
@@ -114,7 +114,7 @@ def test_fp32_error_bounds(orc):
     p = W.three_level_ring(n_cells=4096, n_steps=2000)
     ref = oracle_ref(orc, p, p.n_steps)
     k = p.n_steps / 1000
-    for form in ("strang", "merged", "rodrigues"):
+    for form in ("strang", "merged", "rodrigues", "rotated"):
         E, H, rho, _ = gpu_run(p, p.n_steps, "fp32", form)
         e_err = rel_inf(E, ref.E)
         p_err = np.abs(pops(rho) - pops(ref.rho)).max()
@@ -234,7 +234,7 @@ def test_edge_cases(orc, case):
 def test_zero_steps_and_state_round_trip(orc):
     p = W.three_level_ring(n_cells=500, n_steps=100)
     for prec in ("fp64", "fp32"):
-        for form in ("strang", "merged"):
+        for form in ("strang", "merged", "rotated"):
             s = make_solver(p, prec, form)
             s.step(0)
             s.sync()
@@ -343,7 +343,7 @@ def test_six_level_fp32_error_4096_cells(orc):
     p = W.six_level_pulse(n_cells=4096, n_steps=1000)
     ref = oracle_ref(orc, p, p.n_steps)
     k = p.n_steps / 1000
-    for form in ("merged",):
+    for form in ("merged", "rotated"):
         E, H, rho, _ = gpu_run(p, p.n_steps, "fp32", form)
         e_err = rel_inf(E, ref.E)
         p_err = np.abs(pops(rho) - pops(ref.rho)).max()
@@ -352,7 +352,7 @@ def test_six_level_fp32_error_4096_cells(orc):
         assert p_err < FP32_POP_PER_KSTEP * k
 
 
-@pytest.mark.parametrize("form", ["merged", "strang"])
+@pytest.mark.parametrize("form", ["merged", "strang", "rotated"])
 @pytest.mark.parametrize("make", [lambda: W.three_level_ring(n_cells=256, n_steps=1),
                                   lambda: W.multi_level_ring(4, n_cells=256, n_steps=1, seed=2),
                                   lambda: W.two_level_sit(n_cells=200, medium=(50, 150), n_steps=1)])
@@ -361,7 +361,8 @@ def test_work_count_is_the_exact_operation_count(make, form):
     the set-up matrices: a product row of k non-zero entries is k
     multiplications and k - 1 additions, k additions when added onto a vector,
     one more for a non-zero offset; the N - 1 angle series (8), the other
-    planes by the subtraction formulas (10) and 6 per plane increment."""
+    planes by the subtraction formulas (10) and 6 per plane increment; in the
+    rotated basis one addition per plane coordinate for z'' = z + dz."""
     from paper_1710_09799_gb300 import mln
     from helpers import params_of
     p = make()
@@ -378,6 +379,9 @@ def test_work_count_is_the_exact_operation_count(make, form):
     if form == "merged":
         b2, wm, cm = A0 @ b + b, A0.T @ w, w @ b + c
         want = tt + rot + 2 * nT + dot(wm, cm) + 2 * nz(C1) + nz(b2)
+    elif form == "rotated":
+        b2, wm, cm = A0 @ b + b, A0.T @ w, w @ b + c
+        want = P + rot + dot(T.T @ wm, cm) + 2 * nz(T.T @ C1 @ T) + nz(T.T @ b2)
     else:
         half = 2 * nz(A0 - np.eye(D)) + nz(b)
         want = 2 * half + tt + rot + 2 * nT + dot(w, c)
@@ -412,3 +416,21 @@ def test_torch_kernel_between_steps_is_ordered(precision, kernel):
     assert np.array_equal(Ea, Eb) and np.array_equal(Ha, Hb) and np.array_equal(a.rho(), b.rho())
     a.close()
     b.close()
+
+
+def test_rotated_form_six_level_costs_fewer_flops_and_agrees_with_merged():
+    """The rotated basis replaces the merged form's three products (T^T, T and
+    A0^2 - I) by one dense C z: 2750 against 6919 flops per medium cell update
+    on the six-level model. The two forms compute the same step: FP64 results
+    agree to rounding after 300 steps."""
+    p = W.six_level_pulse(n_cells=600, n_steps=300, t0=15e-15, fwhm=10e-15)
+    a = gpu_run(p, p.n_steps, "fp64", "merged", kernel="jit")
+    b = gpu_run(p, p.n_steps, "fp64", "rotated")
+    fa, fb = a[3].work_per_step[0], b[3].work_per_step[0]
+    assert b[3].kernel_in_use == "jit"
+    a[3].close()
+    b[3].close()
+    assert fb < 0.45 * fa, (fa, fb)
+    assert rel_inf(b[0], a[0]) < 1e-11
+    assert np.abs(b[2] - a[2]).max() < 1e-11
+

@@ -80,3 +80,31 @@ def test_batch_source_compiles_and_follows_the_union_pattern(lib, tmp_path, prec
     r = subprocess.run([nvcc, "-gencode", "arch=compute_103a,code=sm_103a", "-std=c++17", "-c", str(f),
                         "-o", str(tmp_path / "b.o")], capture_output=True, text=True)
     assert r.returncode == 0, r.stderr[-3000:]
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_rotated_form_source_has_one_product(lib, tmp_path, prec):
+    """MLN_FORM_ROTATED: the state is z = T^T y, so the generated step takes the
+    plane coordinates from the state itself and has no T or T^T product: its
+    terms are those of C = T^T (A0^2 - I) T and of T^T A0^T w only."""
+    nvcc = shutil.which("nvcc") or "/usr/local/cuda/bin/nvcc"
+    if not os.path.exists(nvcc):
+        pytest.skip("nvcc not found")
+    p = W.three_level_ring(n_cells=1000)
+    par = params_of(p, precision=prec, form="rotated")
+    src = mln.mln_kernel_source(par)
+    s = mln.mln_setup_host(par)
+    D, q = s["D"], s["q"]
+    cast = (lambda x: np.float32(x)) if prec == "fp32" else (lambda x: x)
+    T, C1 = s["T"], s["C1"]
+    nnz_C = int(np.count_nonzero(cast(T.T @ C1 @ T)))
+    body = src[src.index("struct JitCell"):]
+    n_terms = body.count("fma(") + body.count("mul_rn(")
+    assert nnz_C <= n_terms <= nnz_C + D
+    for k in range(2 * q):
+        assert f"z[{k}] = s[{k}];" in body
+    f = tmp_path / "r.cu"
+    f.write_text(src)
+    r = subprocess.run([nvcc, "-gencode", "arch=compute_103a,code=sm_103a", "-std=c++17", "-c", str(f),
+                        "-o", str(tmp_path / "r.o")], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr[-3000:]

@@ -216,6 +216,12 @@ def test_validation(lib):
     assert okr(kernel="jit", form="merged") == mln.MLN_EINVAL
     assert okr(kernel="tensor", form="merged", precision="fp32") == mln.MLN_EINVAL
     assert ok(maxwell="pstd") == mln.MLN_EINVAL                   # open grid
+    # the rotated form: the run-time compiled kernel with the FDTD field solver only
+    assert ok(form="rotated") == mln.MLN_OK and ok(form="rotated", kernel="jit") == mln.MLN_OK
+    for k in ("register", "sparse", "tensor"):
+        assert ok(form="rotated", kernel=k) == mln.MLN_EINVAL
+    assert okr(form="rotated") == mln.MLN_EINVAL
+    assert ok(form=4) == mln.MLN_EINVAL
     assert ok(maxwell=2) == mln.MLN_EINVAL
     q = random_problem(7, 1, G=False)
     assert _status_of(lambda: mln.mln_query_buffers(params_of(q))) == mln.MLN_EUNSUPPORTED
