@@ -1,9 +1,11 @@
-// Per-problem kernels: the merged-form step of one context written out as
+// Per-problem kernels: the merged-form step of one context (state y, or the
+// rotated basis z = T^T y of MLN_FORM_ROTATED) written out as
 // straight-line code with the constants as literals and the exactly-zero
 // entries of the set-up matrices left out, compiled at run time for sm_103a
-// (NVRTC) and launched through the driver API. The arithmetic and its order
-// are those of the register cell model, so the results are bit-identical; the
-// kernel just skips multiplications by zero and needs no constant-bank loads.
+// (NVRTC) and launched through the driver API. In the merged form the
+// arithmetic and its order are those of the register cell model, so the
+// results are bit-identical; the kernel just skips multiplications by zero and
+// needs no constant-bank loads. The rotated form exists only here.
 //
 // NVRTC and the driver entry points are looked up at run time (dlopen and
 // cudaGetDriverEntryPointByVersion): without them the JIT model is reported
