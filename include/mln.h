@@ -510,7 +510,8 @@ mln_status mln_tc_wait_selftest(void);
  * file-scope device array of MLN_STATIC_SCRATCH_BYTES (32 MiB), which every
  * GPU that loads this library holds until the process exits.
  *
- *   p           problem (as for mln_create; kernel must not be MLN_KERNEL_SPARSE).
+ *   p           problem (as for mln_create; kernel must not be MLN_KERNEL_SPARSE,
+ *               form not MLN_FORM_ROTATED, field solver MLN_MAXWELL_FDTD).
  *   d_state, Ez, Hy  caller-owned device buffers with the sizes and layout of
  *               mln_query_buffers: the state in, the state after n_steps out.
  *   init_state  non-zero: first write the initial medium state built from
@@ -535,8 +536,9 @@ mln_status mln_step_noalloc(const mln_params *p, void *d_state, void *Ez, void *
                             int64_t n_steps, const double *src, void *stream);
 
 /*
- * Diagnostic: the CUDA source that MLN_KERNEL_JIT would compile for p (merged
- * form), written to buf (capacity cap bytes, NUL-terminated when it fits);
+ * Diagnostic: the CUDA source that MLN_KERNEL_JIT would compile for p (the
+ * merged form; the rotated basis when p->form is MLN_FORM_ROTATED), written to
+ * buf (capacity cap bytes, NUL-terminated when it fits);
  * *len receives the length without the NUL. Host only.
  */
 mln_status mln_kernel_source(const mln_params *p, char *buf, size_t cap, size_t *len);
