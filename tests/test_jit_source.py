@@ -108,3 +108,52 @@ def test_rotated_form_source_has_one_product(lib, tmp_path, prec):
     r = subprocess.run([nvcc, "-gencode", "arch=compute_103a,code=sm_103a", "-std=c++17", "-c", str(f),
                         "-o", str(tmp_path / "r.o")], capture_output=True, text=True)
     assert r.returncode == 0, r.stderr[-3000:]
+
+
+def _hex(x):
+    """A C hexadecimal floating literal (an FP32 'f' suffix follows the decimal exponent)."""
+    return float.fromhex(x[:-1] if x.endswith("f") else x)
+
+
+@pytest.mark.parametrize("make", [lambda: W.three_level_ring(n_cells=1000),
+                                  lambda: W.multi_level_ring(4, n_cells=256, n_steps=1, seed=2)])
+def test_rotated_form_constants_are_the_rotated_matrices(lib, make):
+    """The literals of the generated rotated-basis step (FP64) are T^T C1 T with
+    C1 = A0^2 - I of the set-up (row i of the next state), T^T (A0 b + b) (its offset) and T^T A0^T w (the
+    dP/dt weights), recomputed here with numpy from the set-up's T, A0, b and w:
+    a transposed or mis-indexed matrix in the generator fails here."""
+    import re
+    p = make()
+    par = params_of(p, precision="fp64", form="rotated")
+    s = mln.mln_setup_host(par)
+    D = s["D"]
+    T, A0, b, w, C1 = s["T"], s["A0"], s["b"], s["w"], s["C1"]  # C1 = A0^2 - I (set-up, FP64)
+    C = T.T @ C1 @ T
+    cz = T.T @ (A0 @ b + b)
+    wz = T.T @ (A0.T @ w)
+    body = mln.mln_kernel_source(par)
+    body = body[body.index("struct JitCell"):]
+    lit = r"(-?0x[0-9a-fA-Fp.+-]+)"
+    got_C = np.zeros((D, D))
+    got_c = np.zeros(D)
+    for line in body.splitlines():
+        m = re.match(r"\s*s\[(\d+)\] = (.*);$", line)
+        if m:
+            i = int(m.group(1))
+            for a, j in re.findall(lit + r", y\[(\d+)\]", m.group(2)):
+                got_C[i, int(j)] = _hex(a)
+            off = re.search(r"\(y\[\d+\] \+ " + lit + r"\)", m.group(2))
+            if off:
+                got_c[i] = _hex(off.group(1))
+        m = re.match(r"\s*const double dpdt = (.*);$", line)
+        if m:
+            got_w = np.zeros(D)
+            for a, j in re.findall(lit + r", y\[(\d+)\]", m.group(1)):
+                got_w[int(j)] = _hex(a)
+    # rounding bound of a product of three D x D matrices, entry by entry
+    u = np.finfo(float).eps
+    aT = np.abs(T)
+    assert np.all(np.abs(got_C - C) <= 8 * D * u * (aT.T @ np.abs(C1) @ aT) + 1e-300)
+    assert np.all(np.abs(got_c - cz) <= 8 * D * u * (aT.T @ np.abs(A0 @ b + b)) + 1e-300)
+    assert np.all(np.abs(got_w - wz) <= 8 * D * u * (aT.T @ np.abs(A0.T @ w)) + 1e-300)
+    assert np.count_nonzero(got_C) >= np.count_nonzero(np.abs(C) > 1e-12 * np.abs(C).max())
