@@ -252,6 +252,29 @@ def make_params(p, precision, form, block_steps=0, tile_cells=0, kernel="auto"):
                       tile_cells=tile_cells, kernel=kernel, maxwell=p.maxwell)
 
 
+def fp32_error_vs_fp64(n_cells=4096, n_steps=2000):
+    """The error the FP32 rates come with: E_z (relative, infinity norm) and
+    populations (absolute) of the FP32 path against the FP64 path (which
+    matches the FP64 oracle to 1e-10), merged form, on a 4096-cell ring with
+    the parameters of the benchmark ring, after 2000 steps."""
+    import numpy as np
+    from paper_1710_09799_gb300 import mln
+    q = W.three_level_ring(n_cells=n_cells, n_steps=n_steps)
+    out = {}
+    for prec in ("fp64", "fp32"):
+        s = mln.Solver(make_params(q, prec, "merged"), E0=q.e_init())
+        s.step(n_steps)
+        s.sync()
+        out[prec] = (s.fields()[0], s.populations())
+        s.close()
+    e64, p64 = out["fp64"]
+    e32, p32 = out["fp32"]
+    return {"E_rel": float(np.abs(e32 - e64).max() / np.abs(e64).max()),
+            "pop_abs": float(np.abs(p32 - p64).max()),
+            "case": f"three-level ring, {n_cells} cells x {n_steps} steps, merged form",
+            "bound": "2e-3 (E) and 2e-5 (populations) per 1000 steps, the tests' FP32 tolerance"}
+
+
 def time_device(p, precision, form, seg, steps, warmup, block_steps, tile_cells, ws, flush=True,
                 sampler=None, kernel="auto", autotune=True):
     """Device-timed run: returns dict with total ms (max over ranks), launches, shape."""
@@ -633,6 +656,10 @@ def main():
             variants[f"{prec}_{form}_{kern}"] = {"value": p.n_cells * args.seg * 10 / (r["ms"] / 1e3), "unit": UNIT,
                                                  "ms_per_step": r["ms"] / 10}
         line["variants"] = variants
+        try:
+            line["fp32_error_vs_fp64"] = fp32_error_vs_fp64()
+        except Exception as ex:  # an auxiliary report: keep the benchmark line
+            line["fp32_error_vs_fp64"] = {"error": f"{type(ex).__name__}: {ex}"}
         line["e2e"] = time_e2e(p, args.precision, args.form, args.seg, min(10, args.steps))
         if ws == 1:
             threads = os.cpu_count() or 1
