@@ -40,3 +40,38 @@ def test_max_over_ranks_gloo_two_ranks():
         p.join(timeout=60)
         assert p.exitcode == 0
     assert res == {0: 11.0, 1: 11.0}
+
+
+def test_fp32_error_report_arithmetic(monkeypatch):
+    """The benchmark's fp32_error_vs_fp64 key: relative infinity-norm E_z and
+    absolute population differences of the FP32 run from the FP64 run, with a
+    stand-in solver that returns known perturbations (no GPU)."""
+    import numpy as np
+
+    import bench
+    from paper_1710_09799_gb300 import mln
+
+    class Stand:
+        def __init__(self, params, E0=None):
+            self.fp32 = params.s.precision == mln.MLN_FP32
+            self.E = 2.0 * np.asarray(E0)
+
+        def step(self, n):
+            pass
+
+        def sync(self):
+            pass
+
+        def fields(self):
+            return self.E * (1 + 3e-6 if self.fp32 else 1.0), 0 * self.E
+
+        def populations(self):
+            return np.full((7, 3), 0.25) + (4e-9 if self.fp32 else 0.0)
+
+        def close(self):
+            pass
+
+    monkeypatch.setattr(mln, "Solver", Stand)
+    r = bench.fp32_error_vs_fp64(n_cells=128, n_steps=5)
+    assert abs(r["E_rel"] - 3e-6) < 1e-12 and abs(r["pop_abs"] - 4e-9) < 1e-15
+    assert "128 cells x 5 steps" in r["case"]
