@@ -30,7 +30,7 @@
  *   - The polarisation source dP/dt = N_a Tr{mu (L0(rho) + G(rho))}
  *     (Sec. 2, Eqs. 3-5), evaluated on rho^{n+1/2}.
  *
- * Readings of points the paper leaves open (all stated in the design notes):
+ * Readings of points the paper leaves open (the paper is silent on each):
  *   - order in a step: H^{n+1/2} from E^n; rho^{n-1/2} -> rho^{n+1/2} with E^n;
  *     dP/dt^{n+1/2} from rho^{n+1/2}; E^{n+1} from H^{n+1/2} and dP/dt^{n+1/2};
  *   - conductivity is averaged semi-implicitly:

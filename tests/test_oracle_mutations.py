@@ -1,7 +1,8 @@
 """The oracle's pins catch plausible mistakes.
 
-Each case plants one mistake in a copy of the oracle's C source (a sign, an
-index, a dropped term, a transposed operand, a wrong constant) and runs the
+Each case plants one mistake in a copy of the oracle's C source or of its
+Python helpers (a sign, an index, a dropped term, a transposed operand, a
+wrong constant, a too narrow light-cone window) and runs the
 oracle pin tests against the mutated copy in a subprocess: at least one pin
 must fail. This shows that the pins constrain every part of the oracle, not
 only that the oracle passes them.
@@ -37,22 +38,26 @@ MUTATIONS = [
     ("PSTD wavenumber not folded", "(m <= n / 2) ? m : m - n;", "m;"),
     ("PSTD dP/dt sign", "cb * (dv[i] - dP[i]);", "cb * (dv[i] + dP[i]);"),
     ("PSTD H coefficient", "H[i] += (p->dt / muu) * dv[i];", "H[i] += (p->dt / muu) * 1.0000001 * dv[i];"),
+    # the light-cone window of run_window: one cell inside the light cone on each side
+    ("window inside the light cone", "half = n_steps + 1", "half = n_steps - 1", "__init__.py"),
 ]
 
 
 @pytest.mark.slow
-@pytest.mark.parametrize("name,old,new", MUTATIONS, ids=[m[0] for m in MUTATIONS])
-def test_mutation_is_caught(tmp_path, name, old, new):
+@pytest.mark.parametrize("mutation", MUTATIONS, ids=[m[0] for m in MUTATIONS])
+def test_mutation_is_caught(tmp_path, mutation):
+    name, old, new = mutation[:3]
+    target = mutation[3] if len(mutation) > 3 else "mln_oracle.c"
     for d in ("oracle", "workloads", "tests"):
         shutil.copytree(os.path.join(ROOT, d), tmp_path / d,
                         ignore=shutil.ignore_patterns("_build", "__pycache__"))
     shutil.copy(os.path.join(ROOT, "pytest.ini"), tmp_path / "pytest.ini")
-    src = tmp_path / "oracle" / "mln_oracle.c"
+    src = tmp_path / "oracle" / target
     text = src.read_text()
     assert text.count(old) == 1, name
     src.write_text(text.replace(old, new))
     files = [f"tests/{f}" for f in ("test_oracle_expm.py", "test_oracle_liouville.py", "test_oracle_fdtd.py",
-                                            "test_oracle_pstd.py")]
+                                            "test_oracle_pstd.py", "test_oracle_window.py")]
     r = subprocess.run([sys.executable, "-m", "pytest", "-q", "-x", "-m", "not gpu", *files],
                        cwd=tmp_path, capture_output=True, text=True, timeout=600)
     assert r.returncode != 0, f"mutation '{name}' was not caught:\n{r.stdout[-2000:]}"
