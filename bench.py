@@ -252,27 +252,22 @@ def make_params(p, precision, form, block_steps=0, tile_cells=0, kernel="auto"):
                       tile_cells=tile_cells, kernel=kernel, maxwell=p.maxwell)
 
 
-def fp32_error_vs_fp64(n_cells=4096, n_steps=2000):
+def fp32_error_vs_oracle(ref, n_cells=4096, n_steps=2000):
     """The error the FP32 rates come with: E_z (relative, infinity norm) and
-    populations (absolute) of the FP32 path against the FP64 path (which
-    matches the FP64 oracle to 1e-10), merged form, on a 4096-cell ring with
-    the parameters of the benchmark ring, after 2000 steps."""
-    import numpy as np
+    populations (absolute) of the FP32 and FP64 paths (merged form) against the
+    FP64 oracle's result `ref` for a 4096-cell ring with the parameters of the
+    benchmark ring, after 2000 steps."""
     from paper_1710_09799_gb300 import mln
     q = W.three_level_ring(n_cells=n_cells, n_steps=n_steps)
-    out = {}
-    for prec in ("fp64", "fp32"):
+    out = {"case": f"three-level ring, {n_cells} cells x {n_steps} steps, merged form, against the FP64 oracle"}
+    for prec in ("fp32", "fp64"):
         s = mln.Solver(make_params(q, prec, "merged"), E0=q.e_init())
         s.step(n_steps)
         s.sync()
-        out[prec] = (s.fields()[0], s.populations())
+        E, pops = s.fields()[0], s.populations()
         s.close()
-    e64, p64 = out["fp64"]
-    e32, p32 = out["fp32"]
-    return {"E_rel": float(np.abs(e32 - e64).max() / np.abs(e64).max()),
-            "pop_abs": float(np.abs(p32 - p64).max()),
-            "case": f"three-level ring, {n_cells} cells x {n_steps} steps, merged form",
-            "bound": "2e-3 (E) and 2e-5 (populations) per 1000 steps, the tests' FP32 tolerance"}
+        out[prec] = _oracle_error(E, pops, ref)
+    return out
 
 
 def time_device(p, precision, form, seg, steps, warmup, block_steps, tile_cells, ws, flush=True,
@@ -442,6 +437,256 @@ def oracle_rate(p, target_s: float, threads: int, max_steps: int = 100000):
     return p.n_cells * n / dt, n, dt
 
 
+def _oracle_error(E, pops, ref, n_cells=None):
+    """E_z (relative, infinity norm) and populations (absolute) against an oracle state."""
+    E_ref = ref.E if n_cells is None else ref.E[:n_cells]
+    p_ref = np.einsum("cii->ci", ref.rho).real
+    return {"E_rel": float(np.abs(E - E_ref).max() / max(np.abs(E_ref).max(), 1e-300)),
+            "pop_abs": float(np.abs(pops - p_ref[:len(pops)]).max()) if len(pops) else 0.0}
+
+
+def _fresh_run(p, precision, form, n_steps, kernel="auto"):
+    """A fresh solver advanced n_steps from the problem's initial state, in the
+    launch shape the autotuner picks (as timed); returns (E, populations)."""
+    import torch
+    from paper_1710_09799_gb300 import mln
+    s = mln.Solver(make_params(p, precision, form, kernel=kernel), E0=p.e_init())
+    s.autotune(2)
+    smp = p.source_samples(0, n_steps)
+    s.step(n_steps, None if smp is None else torch.as_tensor(smp, dtype=torch.float64, device="cuda"))
+    s.sync()
+    E, _ = s.fields()
+    pops = s.populations() if p.n_medium > 0 else np.zeros((0, p.N))
+    s.close()
+    return E, pops
+
+
+def _alu_roofline(run, p, seg, steps, precision, kernel_name):
+    per_launch_s = run["ms_local"] / 1e3 / max(run["launches"], 1)
+    f_med, f_cell, _, _ = run["work"]
+    flops = p.n_medium * f_med + p.n_cells * f_cell
+    achieved = flops * (seg * steps / max(run["launches"], 1)) / per_launch_s / 1e12
+    peak = alu_peak_tflops(precision)
+    out = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+           "traffic": None, "kernel": kernel_name, "flops_per_medium_cell_update": f_med,
+           "flops_per_grid_cell": f_cell,
+           "peak_source": f"derived: {SMS} SMs x {FP64_FLOP_PER_CLK_SM if precision == 'fp64' else FP32_FLOP_PER_CLK_SM} "
+                          f"flop/clk x {SM_MAX_MHZ:.0f} MHz"}
+    return out
+
+
+def _kernel_name(kern):
+    return "mln_jit_step" if kern == "jit" else ("mln_tc_kernel" if kern == "tensor"
+                                                 else f"mln_block_kernel ({kern} cell model)")
+
+
+def _device_record(p, precision, form, seg, steps, warmup, kernel="auto", note=None, shape=(0, 0)):
+    r = time_device(p, precision, form, seg, steps, warmup, shape[0], shape[1], 1, kernel=kernel)
+    rec = {"value": p.n_cells * seg * steps / (r["ms"] / 1e3), "unit": UNIT, "ms_per_1000_steps": r["ms"] / (seg * steps) * 1e3,
+           "precision": precision, "form": form, "kernel": r["kernel"], "launch_shape": list(r["shape"]),
+           "timed": f"{steps} x {seg} time steps after {warmup} x {seg} warm-up, L2 flushed between them"}
+    if r["kernel"] == "tensor":
+        class _A:  # the arguments tensor_roofline reads
+            pass
+        a = _A()
+        a.seg, a.steps = seg, steps
+        per_launch_s = r["ms_local"] / 1e3 / max(r["launches"], 1)
+        rec["roofline"] = tensor_roofline(p, a, r, r["launches"], per_launch_s, r["clocks"] or {})
+    else:
+        rec["roofline"] = _alu_roofline(r, p, seg, steps, precision, _kernel_name(r["kernel"]))
+    if note:
+        rec["roofline"]["note"] = note
+    return rec
+
+
+def oracle_references(threads: int) -> dict:
+    """Part of the CPU-baseline leg: the FP64 oracle's results on the host
+    cores for the inputs the GPU records below are compared with (each with
+    its run time)."""
+    import oracle
+    oracle.build()
+    refs = {}
+
+    def run(key, p, n, **kw):
+        t = time.perf_counter()
+        refs[key] = oracle.run(p, n_steps=n, threads=threads, **kw) + (time.perf_counter() - t,)
+
+    run("ring_4096", W.three_level_ring(n_cells=4096, n_steps=2000), 2000)
+    run("two_level_sit", W.two_level_sit(), 20000)
+    run("six_level_4096", W.six_level_pulse(n_cells=4096, n_steps=1000), 1000)
+    devs = W.batched_devices(n_steps=1000)
+    by_size = sorted(range(len(devs)), key=lambda i: devs[i].n_cells)
+    for N in (2, 3, 4):
+        i = next(i for i in by_size if devs[i].N == N)
+        run(f"batch_device_{i}", devs[i], 1000)
+    p = W.adjoint_ring()
+    run("adjoint_ring", p, p.n_steps, probe_cell=p.meta["probe_cell"])
+    return refs
+
+
+def workload_records(refs: dict):
+    """The other workloads of the benchmark suite, each timed on the device
+    (CUDA events, L2 flushed between timed segments) and each with its error
+    against the FP64 CPU oracle's results on the same inputs."""
+    out = {}
+    for section in (_rec_two_level, _rec_six_level, _rec_batched, _rec_adjoint):
+        try:
+            section(out, refs)
+        except Exception as ex:  # keep the benchmark line and the other records
+            out[section.__name__[5:]] = {"error": f"{type(ex).__name__}: {ex}"}
+    return out
+
+
+def _rec_two_level(out, refs):
+    """two-level SIT (2000 cells x 20000 steps): latency-bound, a parity configuration"""
+    p = W.two_level_sit()
+    ref, _, t_orc = refs["two_level_sit"]
+    for prec in ("fp64", "fp32"):
+        rec = _device_record(p, prec, "merged", 2000, 10, 3,
+                             note="2000-cell grid: latency-bound; frac_of_one_sm_peak compares with one SM's ALU peak")
+        rec["roofline"]["frac_of_one_sm_peak"] = rec["roofline"]["achieved"] / (rec["roofline"]["peak"] / SMS)
+        E, pops = _fresh_run(p, prec, "merged", p.n_steps)
+        rec["error_vs_oracle"] = dict(_oracle_error(E, pops, ref), case=f"full workload, {p.n_steps} steps",
+                                      oracle_s=t_orc)
+        out[f"two_level_sit_{prec}"] = rec
+
+
+def _rec_six_level(out, refs):
+    """six-level pulse (1048576 cells): FP32 in its fastest form, FP64 beside it;
+    error on a separate 4096-cell x 1000-step run with the same parameters"""
+    p = W.six_level_pulse()
+    q = W.six_level_pulse(n_cells=4096, n_steps=1000)
+    ref, _, t_orc = refs["six_level_4096"]
+    # FP64 at a fixed launch shape (autotuning it would take seconds per shape)
+    for prec, seg, steps, shape in (("fp32", 500, 5, (0, 0)), ("fp64", 40, 3, (16, 480))):
+        rec = _device_record(p, prec, "rotated", seg, steps, 3, shape=shape)
+        E, pops = _fresh_run(q, prec, "rotated", q.n_steps)
+        rec["error_vs_oracle"] = dict(_oracle_error(E, pops, ref), case="4096 cells x 1000 steps, same parameters",
+                                      oracle_s=t_orc)
+        out[f"six_level_pulse_{prec}"] = rec
+
+
+def _rec_batched(out, refs):
+    """batched devices (256 grids, N in {2, 3, 4}, 1k-64k cells): the smallest
+    grid of each N compared with the oracle after the first 1000 steps"""
+    import torch
+    from paper_1710_09799_gb300 import mln
+    for prec, seg, steps in (("fp32", 1000, 3), ("fp64", 100, 3)):
+        total = 1000 + (3 + steps) * seg
+        devs = W.batched_devices(n_steps=total)
+        pars = [make_params(d, prec, "merged") for d in devs]
+        srcs = [d.source_samples(0, total) for d in devs]
+        b = mln.Batch(pars, [d.e_init() for d in devs], srcs, total)
+        b.autotune(2)
+        b.step(1000)
+        b.sync()
+        by_size = sorted(range(len(devs)), key=lambda i: devs[i].n_cells)
+        errs = {}
+        t_orc = 0.0
+        for N in (2, 3, 4):
+            i = next(i for i in by_size if devs[i].N == N)
+            r, _, t = refs[f"batch_device_{i}"]
+            t_orc += t
+            E, _ = b.fields(i)
+            pops = np.einsum("cii->ci", b.rho(i)).real
+            errs[f"device{i}_N{N}_{devs[i].n_cells}_cells"] = _oracle_error(E, pops, r)
+        for _ in range(3):
+            b.step(seg)
+        b.sync()
+        flush_buf = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        l0 = b.shape[3]
+        torch.cuda.synchronize()
+        with torch.cuda.stream(b.stream):
+            for i in range(steps):
+                flush_buf.fill_(i & 0xFF)
+                evs[i][0].record(b.stream)
+                b.step(seg)
+                evs[i][1].record(b.stream)
+        torch.cuda.synchronize()
+        ms = sum(x.elapsed_time(y) for x, y in evs)
+        launches = b.shape[3] - l0
+        flops = 0.0
+        for i, d in enumerate(devs):
+            f_med, f_cell, _, _ = mln.mln_work_per_step(mln.mln_batch_context(b.b, i))
+            flops += d.n_medium * f_med + d.n_cells * f_cell
+        cells = sum(d.n_cells for d in devs)
+        kernels = {N: b.kernel_in_use(N) for N in (2, 3, 4)}
+        b.close()
+        achieved = flops * seg * steps / (ms / 1e3) / 1e12
+        peak = alu_peak_tflops(prec)
+        out[f"batched_{prec}"] = {
+            "value": cells * seg * steps / (ms / 1e3), "unit": UNIT, "ms_per_1000_steps": ms / (seg * steps) * 1e3,
+            "precision": prec, "devices": len(devs), "cells": cells, "cell_model_by_N": kernels,
+            "gpu_launches": launches,
+            "timed": f"{steps} x {seg} time steps (one graph replay each) after warm-up, L2 flushed between them",
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                         "traffic": None, "kernel": "mln_jit_batch (one launch per N per K steps)"},
+            "error_vs_oracle": {"after": "1000 steps", "devices": errs, "oracle_s": t_orc},
+        }
+
+
+def _rec_adjoint(out, refs):
+    """gradient workload (8192-cell ring, 5000 steps, checkpoints every 256)"""
+    import torch
+    from paper_1710_09799_gb300 import mln
+    p = W.adjoint_ring()
+    src_np = p.source_samples(0, p.n_steps)
+    src = torch.as_tensor(src_np, dtype=torch.float64, device="cuda")
+    _, probe, t_orc = refs["adjoint_ring"]
+    J_orc = p.dt * float(np.sum(probe ** 2))
+    rng = np.random.default_rng(0)
+    direction = np.zeros(p.n_steps)
+    direction[:p.meta["n_src"]] = rng.normal(size=p.meta["n_src"])
+    for prec in ("fp64", "fp32"):
+        par = make_params(p, prec, "strang")
+        times = []
+        for i in range(3 + 3):
+            s = mln.Solver(par, E0=p.e_init())
+            torch.cuda.synchronize()
+            t = time.perf_counter()
+            J, dsrc, dmu, dG = mln.mln_adjoint(s.ctx, p.N, p.n_steps, src.data_ptr(), p.meta["probe_cell"], 256)
+            torch.cuda.synchronize()
+            if i >= 3:
+                times.append(time.perf_counter() - t)
+            work = s.work_per_step
+            s.close()
+        t_grad = float(np.mean(times))
+        # the plain forward of the same problem, same precision and form, for the cost ratio
+        fwd = time_device(p, prec, "strang", 1000, 3, 2, 0, 0, 1)
+        t_fwd = fwd["ms"] / 3e3 * p.n_steps / 1000
+        # central difference of the GPU J along one seeded source direction
+        h = 1e-6 * np.abs(src_np).max()
+        Jpm = []
+        for sgn in (1, -1):
+            s = mln.Solver(make_params(p, "fp64", "strang"), E0=p.e_init())
+            tt = torch.as_tensor(src_np + sgn * h * direction, dtype=torch.float64, device="cuda")
+            Jpm.append(mln.mln_adjoint(s.ctx, p.N, p.n_steps, tt.data_ptr(), p.meta["probe_cell"], 10 ** 6)[0])
+            s.close()
+        fd = (Jpm[0] - Jpm[1]) / (2 * h)
+        ad = float(dsrc @ direction)
+        f_fwd = p.n_medium * work[0] + p.n_cells * work[1]
+        D, Q = p.D, p.N * (p.N - 1) // 2
+        rot = 6 * Q + 10 * (Q - (p.N - 1)) + 8 * (p.N - 1)
+        f_rev = p.n_medium * (20 * D * D + 8 * D * Q + 6 * D + 24 * Q + rot) + p.n_cells * 12
+        flops = (2 * f_fwd + f_rev) * p.n_steps
+        peak = alu_peak_tflops(prec)
+        out[f"adjoint_{prec}"] = {
+            "value": p.n_cells * p.n_steps / t_grad, "unit": UNIT + " (forward cell-updates per second of a J + gradient evaluation)",
+            "ms_per_gradient": t_grad * 1e3, "gradient_cost_over_forward": t_grad / t_fwd,
+            "forward_cell_updates_per_s": p.n_cells * p.n_steps / t_fwd,
+            "timed": "3 evaluations after 3 warm-up (host clock around synchronised calls)",
+            "roofline": {"bound": "alu", "achieved": flops / t_grad / 1e12, "peak": peak, "unit": "TFLOP/s",
+                         "frac": flops / t_grad / 1e12 / peak, "traffic": None,
+                         "kernel": "whole gradient: forward with checkpoints, recomputation, mln_adjoint_step_rows",
+                         "counted": "forward and recomputation (mln_work_per_step) + the reverse step's dense products "
+                                    "and accumulations"},
+            "error_vs_oracle": {"J_rel": abs(J - J_orc) / abs(J_orc), "oracle_s": t_orc,
+                                "directional_derivative_vs_central_difference": abs(ad - fd) / max(abs(fd), 1e-300),
+                                "direction": "seeded normal over the 512 free source samples, h = 1e-6 max|src| (FP64 forward)"},
+        }
+
+
 def run_reference(args):
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -562,8 +807,10 @@ def main():
     ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="mine", choices=["mine", "reference"])
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32"])
-    ap.add_argument("--form", default="merged", choices=["strang", "merged", "rodrigues", "rotated"])
+    ap.add_argument("--precision", default=None, choices=["fp64", "fp32"],
+                    help="default: fp32 for six_level_pulse and batched, fp64 otherwise")
+    ap.add_argument("--form", default=None, choices=["strang", "merged", "rodrigues", "rotated"],
+                    help="default: rotated for six_level_pulse (its fastest form), merged otherwise")
     ap.add_argument("--seg", type=int, default=1000, help="time steps per benchmark step")
     ap.add_argument("--block-steps", type=int, default=0, help="0: autotuned")
     ap.add_argument("--tile", type=int, default=0)
@@ -571,6 +818,10 @@ def main():
     ap.add_argument("--workload", default="three_level_ring", choices=sorted(WORKLOADS))
     ap.add_argument("--quick", action="store_true", help="skip variants, e2e and the CPU baseline")
     args = ap.parse_args()
+    if args.precision is None:
+        args.precision = "fp32" if args.workload in ("six_level_pulse", "batched") else "fp64"
+    if args.form is None:
+        args.form = "rotated" if args.workload == "six_level_pulse" else "merged"
     if args.impl == "reference":
         return run_reference(args)
 
@@ -656,10 +907,6 @@ def main():
             variants[f"{prec}_{form}_{kern}"] = {"value": p.n_cells * args.seg * 10 / (r["ms"] / 1e3), "unit": UNIT,
                                                  "ms_per_step": r["ms"] / 10}
         line["variants"] = variants
-        try:
-            line["fp32_error_vs_fp64"] = fp32_error_vs_fp64()
-        except Exception as ex:  # an auxiliary report: keep the benchmark line
-            line["fp32_error_vs_fp64"] = {"error": f"{type(ex).__name__}: {ex}"}
         line["e2e"] = time_e2e(p, args.precision, args.form, args.seg, min(10, args.steps))
         if ws == 1:
             threads = os.cpu_count() or 1
@@ -671,6 +918,14 @@ def main():
                                     "single_thread": {"value": rate1, "unit": UNIT, "cores": 1,
                                                       "sample": f"{n1} time steps ({secs1:.1f} s)"}}
             line["vs_oracle"] = value / rate
+            # the rest of the CPU-baseline leg: the oracle's results for the
+            # error reports of the FP32 variants and of the other workloads
+            refs = oracle_references(threads)
+            try:
+                line["fp32_error_vs_oracle"] = fp32_error_vs_oracle(refs["ring_4096"][0])
+            except Exception as ex:  # an auxiliary report: keep the benchmark line
+                line["fp32_error_vs_oracle"] = {"error": f"{type(ex).__name__}: {ex}"}
+            line["workloads"] = workload_records(refs)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if ws > 1:

@@ -43,18 +43,25 @@ def test_max_over_ranks_gloo_two_ranks():
 
 
 def test_fp32_error_report_arithmetic(monkeypatch):
-    """The benchmark's fp32_error_vs_fp64 key: relative infinity-norm E_z and
-    absolute population differences of the FP32 run from the FP64 run, with a
-    stand-in solver that returns known perturbations (no GPU)."""
+    """The benchmark's fp32_error_vs_oracle key: relative infinity-norm E_z and
+    absolute population differences of the FP32 and FP64 runs from the
+    oracle's result, with a stand-in solver that returns known perturbations
+    of that result (no GPU)."""
     import numpy as np
 
     import bench
     from paper_1710_09799_gb300 import mln
 
+    E_ref = np.linspace(-3.0, 5.0, 128)
+    rho_ref = np.zeros((7, 3, 3), complex)
+    rho_ref[:, 0, 0], rho_ref[:, 1, 1], rho_ref[:, 2, 2] = 0.25, 0.5, 0.25
+
+    class Ref:
+        E, rho = E_ref, rho_ref
+
     class Stand:
         def __init__(self, params, E0=None):
             self.fp32 = params.s.precision == mln.MLN_FP32
-            self.E = 2.0 * np.asarray(E0)
 
         def step(self, n):
             pass
@@ -63,15 +70,16 @@ def test_fp32_error_report_arithmetic(monkeypatch):
             pass
 
         def fields(self):
-            return self.E * (1 + 3e-6 if self.fp32 else 1.0), 0 * self.E
+            return E_ref * (1 + (3e-6 if self.fp32 else 2e-13)), 0 * E_ref
 
         def populations(self):
-            return np.full((7, 3), 0.25) + (4e-9 if self.fp32 else 0.0)
+            return np.einsum("cii->ci", rho_ref).real + (4e-9 if self.fp32 else 1e-14)
 
         def close(self):
             pass
 
     monkeypatch.setattr(mln, "Solver", Stand)
-    r = bench.fp32_error_vs_fp64(n_cells=128, n_steps=5)
-    assert abs(r["E_rel"] - 3e-6) < 1e-12 and abs(r["pop_abs"] - 4e-9) < 1e-15
+    r = bench.fp32_error_vs_oracle(Ref, n_cells=128, n_steps=5)
+    assert abs(r["fp32"]["E_rel"] - 3e-6) < 1e-12 and abs(r["fp32"]["pop_abs"] - 4e-9) < 1e-15
+    assert abs(r["fp64"]["E_rel"] - 2e-13) < 1e-15 and abs(r["fp64"]["pop_abs"] - 1e-14) < 1e-16
     assert "128 cells x 5 steps" in r["case"]

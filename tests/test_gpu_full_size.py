@@ -12,13 +12,11 @@ import numpy as np
 import pytest
 
 import workloads as W
-from helpers import make_solver, params_of, rel_inf, src_tensor
+from helpers import assert_fp32, make_solver, params_of, rel_inf, src_tensor
 
 pytestmark = pytest.mark.gpu
 
 FP64_E = 1e-10
-FP32_E_PER_KSTEP = 2e-3
-FP32_POP_PER_KSTEP = 2e-5
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -55,7 +53,7 @@ def test_six_level_full_size_sampled(six_level_reference, precision, kernel):
     if precision == "fp64":
         assert e_err < FP64_E and p_err < FP64_E
     else:
-        assert e_err < FP32_E_PER_KSTEP * S / 1000 and p_err < FP32_POP_PER_KSTEP * S / 1000
+        assert_fp32("six_level", S, e_err, p_err)
     s.close()
 
 

@@ -11,7 +11,7 @@ import numpy as np
 import pytest
 
 import workloads as W
-from helpers import make_solver, params_of
+from helpers import assert_fp32, make_solver, params_of
 
 pytestmark = pytest.mark.gpu
 
@@ -122,5 +122,5 @@ def test_fp32_run_with_periodic_projection(orc):
     p_err = float(np.abs(np.einsum("cii->ci", rho - st.rho).real).max())
     print(f"fp32 three-level ring with projection every 100 steps: {projected} cell projections, "
           f"E rel {e_err:.3e}, pop abs {p_err:.3e}")
-    assert e_err < 2e-3 and p_err < 2e-5
+    assert_fp32("ring", p.n_steps, e_err, p_err)
     s.close()

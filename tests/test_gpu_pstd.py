@@ -13,14 +13,12 @@ import numpy as np
 import pytest
 
 import workloads as W
-from helpers import gpu_run, make_solver, rel_inf
+from helpers import assert_fp32, gpu_run, make_solver, rel_inf
 from workloads import EPS0, MU0
 
 pytestmark = pytest.mark.gpu
 
 FP64_TOL = 1e-10
-FP32_E_PER_KSTEP = 2e-3
-FP32_POP_PER_KSTEP = 2e-5
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -68,10 +66,9 @@ def test_pulse_through_partial_medium(orc, source):
     assert np.abs(pops(rho) - pops(ref.rho)).max() < FP64_TOL
     E32, _, rho32, s = gpu_run(p, p.n_steps, "fp32", "merged")
     s.close()
-    k = p.n_steps / 1000
     e_err, p_err = rel_inf(E32, ref.E), np.abs(pops(rho32) - pops(ref.rho)).max()
     print(f"pstd fp32 {source}: E rel {e_err:.3e}  pop abs {p_err:.3e}")
-    assert e_err < FP32_E_PER_KSTEP * k and p_err < FP32_POP_PER_KSTEP * k
+    assert_fp32("pstd", p.n_steps, e_err, p_err)
 
 
 def test_4096_cells_against_oracle(orc):

@@ -18,12 +18,10 @@ import numpy as np
 import pytest
 
 import workloads as W
-from helpers import gpu_run, params_of, rel_inf
+from helpers import assert_fp32, gpu_run, params_of, rel_inf
 
 pytestmark = pytest.mark.gpu
 
-FP32_E_PER_KSTEP = 2e-3
-FP32_POP_PER_KSTEP = 2e-5
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -72,7 +70,7 @@ def test_six_level_against_oracle(orc):
     e_err = rel_inf(E, st.E)
     p_err = np.abs(pops(rho) - pops(st.rho)).max()
     print(f"tensor ({kernel}) six-level: E rel {e_err:.3e}  pop abs {p_err:.3e}")
-    assert e_err < FP32_E_PER_KSTEP and p_err < FP32_POP_PER_KSTEP
+    assert_fp32("six_level", p.n_steps, e_err, p_err)
 
 
 def test_six_level_close_to_fp32_register_model():
@@ -91,7 +89,7 @@ def test_five_level_ring_against_oracle(orc):
     e_err = rel_inf(E, st.E)
     p_err = np.abs(pops(rho) - pops(st.rho)).max()
     print(f"tensor ({kernel}) five-level ring: E rel {e_err:.3e}  pop abs {p_err:.3e}")
-    assert e_err < FP32_E_PER_KSTEP * 0.5 and p_err < FP32_POP_PER_KSTEP * 0.5
+    assert_fp32("five_level_ring", p.n_steps, e_err, p_err)
 
 
 def test_launch_shape_does_not_change_the_bits():
