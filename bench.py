@@ -248,8 +248,9 @@ def make_params(p, precision, form, block_steps=0, tile_cells=0, kernel="auto"):
     from paper_1710_09799_gb300 import mln
     return mln.Params(N=p.N, H0=p.H0, mu=p.mu, G=p.G, rho0=p.rho0, N_a=p.N_a, n_cells=p.n_cells,
                       medium_begin=p.medium_begin, medium_end=p.medium_end, dx=p.dx, dt=p.dt,
-                      boundary=p.boundary, precision=precision, form=form, block_steps=block_steps,
-                      tile_cells=tile_cells, kernel=kernel, maxwell=p.maxwell)
+                      eps_r=p.eps_r, mu_r=p.mu_r, sigma=p.sigma, boundary=p.boundary,
+                      source_kind=p.source_kind, source_cell=p.source_cell, precision=precision, form=form,
+                      block_steps=block_steps, tile_cells=tile_cells, kernel=kernel, maxwell=p.maxwell)
 
 
 def fp32_error_vs_oracle(ref, n_cells=4096, n_steps=2000):

@@ -75,9 +75,10 @@ enum { MLN_FP64 = 0, MLN_FP32 = 1 };
  * three (T^T, T and A0^2 - I): fewer operations where T is dense (N >= 5;
  * the six-level model: 2750 against 6919 flops per cell update), more where
  * T is sparse and C is not (the three-level ring: 199 against 179). Same
- * result up to rounding. Runs on the run-time compiled kernel only
- * (MLN_KERNEL_AUTO or MLN_KERNEL_JIT) with the FDTD field solver, single
- * grids (no batches, adjoint or allocation-free step). */
+ * result up to rounding. Runs on the run-time compiled kernel
+ * (MLN_KERNEL_JIT) or, in FP32 with N = 5 or 6, on the tensor cores
+ * (MLN_KERNEL_TENSOR, which MLN_KERNEL_AUTO picks there), with the FDTD field
+ * solver, single grids (no batches, adjoint or allocation-free step). */
 enum { MLN_FORM_STRANG = 0, MLN_FORM_MERGED = 1, MLN_FORM_RODRIGUES = 2, MLN_FORM_ROTATED = 3 };
 /* Cell model of the step kernel. MLN_KERNEL_REGISTER keeps each cell's
  * vector in registers and multiplies by the full D x D constant matrices.
@@ -85,21 +86,25 @@ enum { MLN_FORM_STRANG = 0, MLN_FORM_MERGED = 1, MLN_FORM_RODRIGUES = 2, MLN_FOR
  * memory and multiplies only by the entries of the constant matrices that
  * are not exactly zero; the sums run in the same order, so both give the
  * same result. MLN_KERNEL_AUTO picks SPARSE for FP64 merged, TENSOR for FP32
- * merged with N = 5 or 6 (the dense case), JIT for the other FP32 merged
- * problems when NVRTC is available, REGISTER otherwise. */
+ * merged or rotated with N = 5 or 6 (the dense case), JIT for the other FP32
+ * merged problems when NVRTC is available and for the other rotated-basis
+ * problems, REGISTER otherwise. */
 /* MLN_KERNEL_JIT (merged form) generates, at mln_create, this problem's step
  * as straight-line CUDA with the constants as literals and the exactly-zero
  * entries left out, compiles it for sm_103a at run time (NVRTC) and launches
  * it; same arithmetic and order as MLN_KERNEL_REGISTER, so the same bits.
  * It needs libnvrtc at run time (MLN_EUNSUPPORTED otherwise). */
-/* MLN_KERNEL_TENSOR (FP32, merged form, N = 5 or 6) runs the dense products
- * of a step on the fifth-generation tensor cores (tcgen05.mma kind::tf32, 128
- * cells per MMA, accumulators in tensor memory), regrouped into two per step
- * (the plane coordinates T^T y, then the increment of y and dP/dt from
- * [y ; dz] in one product), each FP32 operand split into a high and a low
- * TF32 part (three MMAs per K block: FP32-level accuracy, not the FP32
- * register model's bits). Up to 32 steps per launch (block_steps; larger
- * values are an error with MLN_KERNEL_TENSOR and are capped at 32 when
+/* MLN_KERNEL_TENSOR (FP32, merged or rotated form, N = 5 or 6) runs the
+ * dense products of a step on the fifth-generation tensor cores (tcgen05.mma,
+ * 128 cells per MMA, accumulators in tensor memory). Merged form
+ * (kind::tf32): two products per step (the plane coordinates T^T y, then the
+ * increment of y and dP/dt from [y ; dz] in one product), each FP32 operand
+ * split into a high and a low TF32 part. Rotated form (kind::f16): one
+ * product per step (the increment of z and dP/dt from [z'' ; 1]), each
+ * operand scaled by powers of two and split into a high and a low FP16 part.
+ * Three MMAs per K block in both (hi*hi, hi*lo, lo*hi): FP32-level accuracy,
+ * not the FP32 register model's bits. Up to 32 steps per launch (block_steps;
+ * larger values are an error with MLN_KERNEL_TENSOR and are capped at 32 when
  * MLN_KERNEL_AUTO picks it), tiles of 128 - 2 block_steps cells; tile_cells is
  * ignored. */
 enum {
@@ -483,6 +488,22 @@ mln_status mln_rotation_terms(int32_t precision, const double *x, int64_t n, dou
  * MLN_ETIMEOUT if the completion wait gave up.
  */
 mln_status mln_tc_product(int32_t nc, int32_t kc, int32_t a_in_tmem, const float *A, const double *B, float *C);
+
+/*
+ * Diagnostic: C = A B^T computed by the product path of MLN_KERNEL_TENSOR in
+ * the rotated basis (MLN_FORM_ROTATED): A scaled by a power of two (largest
+ * magnitude into (2^12, 2^13]) and split into FP16 high and low parts on the
+ * device, staged in tensor memory; each row of B (given in FP64) scaled by its
+ * own power of two and split into FP16 parts on the host; three tcgen05.mma
+ * kind::f16 per K block of 16 (hi*hi, hi*lo, lo*hi), FP32 accumulation, the
+ * scales undone on the result. Shapes: M = 128 and (nc, kc) one of (48, 48),
+ * (32, 32), (16, 16) (MLN_EINVAL otherwise).
+ *   A  host, 128 x kc row-major floats;  B  host, nc x kc row-major doubles;
+ *   C  host, 128 x nc row-major floats (out).
+ * Synchronous, allocates temporary device memory, legacy default stream.
+ * MLN_ETIMEOUT if the completion wait gave up.
+ */
+mln_status mln_tc_product_f16(int32_t nc, int32_t kc, const float *A, const double *B, float *C);
 
 /*
  * Failure-detection self-test: runs the product kernel above with its MMA and

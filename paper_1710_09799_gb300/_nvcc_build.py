@@ -17,7 +17,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libmln.so")
 
-SOURCES = ["api.cu", "kernels_fp64.cu", "kernels_fp32.cu", "kernels_tc.cu", "setup.cpp", "static_scratch.cu", "batch.cu",
+SOURCES = ["api.cu", "kernels_fp64.cu", "kernels_fp32.cu", "kernels_tc.cu", "kernels_tcr.cu", "setup.cpp", "static_scratch.cu", "batch.cu",
            "adjoint.cu", "jit.cu", "project.cu", "pstd.cu"]
 HEADERS = ["kernels.cuh", "dispatch.cuh", "setup.h", "ctx.h", "adjoint.cuh", "jit.h", "tc.cuh", "tc_kernel.h",
            "pstd.h"]

@@ -62,6 +62,8 @@ struct Set {
 template <int N, typename R>
 mln_status adjoint_t(mln_ctx *c, int64_t n_steps, const double *src, int64_t probe, int every, mln_adjoint_out *out) {
     using L = mln::AccLayout<N>;
+    // a segment never spans more than the run (the slots are sized by it)
+    if (every > n_steps) every = static_cast<int>(n_steps);
     mln_status st = MLN_OK;
     const int64_t n = c->p.n_cells;
     const size_t sb = c->state_bytes, fb = c->field_bytes;

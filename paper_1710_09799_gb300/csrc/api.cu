@@ -135,6 +135,7 @@ cudaError_t launch(mln_ctx *c, const mln::BlockArgs<double> &a, dim3 g, dim3 b, 
 }
 
 cudaError_t launch(mln_ctx *c, const mln::BlockArgs<float> &a, dim3 g, dim3 b, size_t smem) {
+    if (c->tc && c->tcr) return mln::launch_tcr(c->p.N, a, c->tc_scal, c->tc_img, c->sms, c->stream);
     if (c->tc) return mln::launch_tc(c->p.N, a, c->tc_scal, c->tc_img, c->sms, c->stream);
     if (c->jit_fn) return mln::jit_launch(c->jit_fn, a, g, b, smem, c->stream);
     return mln::launch_block(c->p.N, c->p.form, a, c->consts, g, b, smem, c->stream);
@@ -393,6 +394,28 @@ mln_status mln_tc_product(int32_t nc, int32_t kc, int32_t a_in_tmem, const float
     return MLN_OK;
 }
 
+mln_status mln_tc_product_f16(int32_t nc, int32_t kc, const float *A, const double *B, float *C) {
+    if (!A || !B || !C) {
+        mln::create_error() = "NULL argument";
+        return MLN_EINVAL;
+    }
+    std::string err;
+    cudaError_t e = mln::tcr_product(nc, kc, A, B, C, err);
+    if (e == cudaErrorInvalidValue) {
+        mln::create_error() = "unsupported (nc, kc)";
+        return MLN_EINVAL;
+    }
+    if (e != cudaSuccess) {
+        mln::create_error() = std::string("tensor-core product: ") + cudaGetErrorString(e);
+        return MLN_ECUDA;
+    }
+    if (!err.empty()) {
+        mln::create_error() = err;
+        return MLN_ETIMEOUT;
+    }
+    return MLN_OK;
+}
+
 mln_status mln_tc_wait_selftest(void) {
     int dev = 0, major = 0;
     if (cudaGetDevice(&dev) != cudaSuccess ||
@@ -623,10 +646,13 @@ mln_status mln_create(const mln_params *p, void *d_state, void *Ez, void *Hy, vo
             return fail(MLN_EUNSUPPORTED);
         }
     } else if (p->kernel == MLN_KERNEL_TENSOR ||
-               (p->kernel == MLN_KERNEL_AUTO && p->precision == MLN_FP32 && p->form == MLN_FORM_MERGED &&
-                p->maxwell == MLN_MAXWELL_FDTD && mln::tc_supported(p->N))) {
+               (p->kernel == MLN_KERNEL_AUTO && p->precision == MLN_FP32 &&
+                (p->form == MLN_FORM_MERGED || p->form == MLN_FORM_ROTATED) && p->maxwell == MLN_MAXWELL_FDTD &&
+                mln::tc_supported(p->N))) {
         std::vector<unsigned char> img;
-        ok = mln::tc_supported(p->N) && mln::pack_tc(c->s, p->dt, img, c->tc_scal);
+        c->tcr = p->form == MLN_FORM_ROTATED;
+        ok = mln::tc_supported(p->N) && (c->tcr ? mln::pack_tcr(c->s, p->dt, img, c->tc_scal)
+                                                 : mln::pack_tc(c->s, p->dt, img, c->tc_scal));
         if (ok) {
             if (cudaMalloc(&c->tc_img, img.size()) != cudaSuccess ||
                 cudaMemcpy(c->tc_img, img.data(), img.size(), cudaMemcpyHostToDevice) != cudaSuccess) {

@@ -389,9 +389,10 @@ mln_status validate(const mln_params &p, std::string &err) {
         return MLN_EINVAL;
     }
     if (p.form == MLN_FORM_ROTATED &&
-        ((p.kernel != MLN_KERNEL_AUTO && p.kernel != MLN_KERNEL_JIT) || p.maxwell != MLN_MAXWELL_FDTD)) {
-        err = "MLN_FORM_ROTATED runs on the run-time compiled kernel (MLN_KERNEL_AUTO or MLN_KERNEL_JIT) with "
-              "MLN_MAXWELL_FDTD";
+        ((p.kernel != MLN_KERNEL_AUTO && p.kernel != MLN_KERNEL_JIT && p.kernel != MLN_KERNEL_TENSOR) ||
+         p.maxwell != MLN_MAXWELL_FDTD)) {
+        err = "MLN_FORM_ROTATED runs on the run-time compiled or the tensor-core kernel (MLN_KERNEL_AUTO, "
+              "MLN_KERNEL_JIT or MLN_KERNEL_TENSOR) with MLN_MAXWELL_FDTD";
         return MLN_EINVAL;
     }
     if (p.form == MLN_FORM_RODRIGUES && p.N > 4) {
@@ -457,8 +458,9 @@ mln_status validate(const mln_params &p, std::string &err) {
               "MLN_KERNEL_TENSOR";
         return MLN_EINVAL;
     }
-    if (p.kernel == MLN_KERNEL_TENSOR && (p.precision != MLN_FP32 || p.form != MLN_FORM_MERGED || p.N < 5)) {
-        err = "MLN_KERNEL_TENSOR needs MLN_FP32, MLN_FORM_MERGED and N = 5 or 6";
+    if (p.kernel == MLN_KERNEL_TENSOR &&
+        (p.precision != MLN_FP32 || (p.form != MLN_FORM_MERGED && p.form != MLN_FORM_ROTATED) || p.N < 5)) {
+        err = "MLN_KERNEL_TENSOR needs MLN_FP32, MLN_FORM_MERGED or MLN_FORM_ROTATED, and N = 5 or 6";
         return MLN_EINVAL;
     }
     if (p.kernel == MLN_KERNEL_TENSOR && p.block_steps > 32) {

@@ -36,6 +36,25 @@ __host__ __device__ constexpr uint32_t idesc_tf32(int n) {
            | (static_cast<uint32_t>(128 >> 4) << 24); // M / 16
 }
 
+// Byte offset of element (r, k) of a 2-byte K-major operand with K columns (a
+// multiple of 8): 8-row x 16-byte core matrices of 8 elements along K, core
+// matrices adjacent along K 128 bytes apart, 8-row groups K * 16 bytes apart;
+// one kind::f16 MMA consumes K = 16 (two core matrices), the k-th block of 16
+// starting k * 256 bytes after the base.
+__host__ __device__ constexpr int core_offset16(int r, int k, int K) {
+    return (r / 8) * (K * 16) + (k / 8) * 128 + (r % 8) * 16 + (k % 8) * 2;
+}
+
+// Instruction descriptor of tcgen05.mma kind::f16 with FP16 A and B, FP32
+// accumulator, both K-major, M = 128, N given (multiple of 16, 16 .. 256).
+__host__ __device__ constexpr uint32_t idesc_f16(int n) {
+    return (1u << 4)                                  // D format: F32
+           | (0u << 7)                                // A format: F16
+           | (0u << 10)                               // B format: F16
+           | (static_cast<uint32_t>(n >> 3) << 17)    // N / 8
+           | (static_cast<uint32_t>(128 >> 4) << 24); // M / 16
+}
+
 // Shared-memory matrix descriptor (no swizzle): start address, leading and
 // stride byte offsets (all >> 4), descriptor version 1 at bit 46.
 __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
@@ -94,6 +113,27 @@ __device__ __forceinline__ void mma_tf32_ts(uint32_t d_tmem, uint32_t a_tmem, ui
         "tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n\t}" ::"r"(d_tmem),
         "r"(a_tmem), "l"(b_desc), "r"(idesc), "r"(accumulate)
         : "memory");
+}
+
+// D[tmem] (+)= A[tmem] * B[smem]^T, M = 128, kind::f16 (FP16 A and B, FP32
+// D): row i of A is TMEM lane i, its K elements packed two per 32-bit column
+// (element 2c in the low half of column c, 2c + 1 in the high half).
+__device__ __forceinline__ void mma_f16_ts(uint32_t d_tmem, uint32_t a_tmem, uint64_t b_desc, uint32_t idesc,
+                                           uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "r"(a_tmem), "l"(b_desc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+// Two FP32 values to a packed FP16 pair, round to nearest even: lo in the low
+// half, hi in the high half.
+__device__ __forceinline__ uint32_t pack_f16x2(float lo, float hi) {
+    uint32_t d;
+    asm("cvt.rn.f16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(hi), "f"(lo));
+    return d;
 }
 
 // Arrive once on the mbarrier when every MMA issued so far by this thread is complete.

@@ -119,6 +119,7 @@ _SIGS = {
     "mln_rotation_terms": (C.c_int, [C.c_int32, _dp, C.c_int64, _dp, _dp]),
     "mln_tc_product": (C.c_int, [C.c_int32, C.c_int32, C.c_int32, C.POINTER(C.c_float), _dp,
                                  C.POINTER(C.c_float)]),
+    "mln_tc_product_f16": (C.c_int, [C.c_int32, C.c_int32, C.POINTER(C.c_float), _dp, C.POINTER(C.c_float)]),
     "mln_step_noalloc": (C.c_int, [_P, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_int64, C.c_void_p,
                                    C.c_void_p]),
 }
@@ -322,6 +323,19 @@ def mln_tc_product(A, B, a_in_tmem: bool = True) -> np.ndarray:
     fp = C.POINTER(C.c_float)
     _check(lib().mln_tc_product(nc, kc, int(a_in_tmem), A.ctypes.data_as(fp), B.ctypes.data_as(_dp),
                                 C_.ctypes.data_as(fp)))
+    return C_
+
+
+def mln_tc_product_f16(A, B) -> np.ndarray:
+    """C = A B^T through the rotated-basis tensor-core product path (FP16
+    hi/lo operands with power-of-two scales; A: 128 x kc float32, B: nc x kc
+    float64); returns C (128 x nc, float32)."""
+    A = np.ascontiguousarray(A, dtype=np.float32)
+    B = np.ascontiguousarray(B, dtype=np.float64)
+    nc, kc = B.shape
+    C_ = np.zeros((A.shape[0], nc), dtype=np.float32)
+    fp = C.POINTER(C.c_float)
+    _check(lib().mln_tc_product_f16(nc, kc, A.ctypes.data_as(fp), B.ctypes.data_as(_dp), C_.ctypes.data_as(fp)))
     return C_
 
 

@@ -66,6 +66,7 @@ FP32_KAPPA = {
     "two_level": (0.022, 0.2),      # two-level SIT grid (sech pulse through the medium)
     "six_level": (0.25, 0.12),      # six-level pulse (D = 35), every cell model and form
     "five_level_ring": (0.45, 3e-3),
+    "five_level_ring_rotated": (5.5, 0.05),  # rotated basis on a ring (as ring_rotated), both kernels
     "pstd": (1.0, 0.11),            # two-level medium on a PSTD ring
 }
 
@@ -82,6 +83,10 @@ FP32_MEASURED = [
     ("six_level", 1000, 2.294e-6, 9.176e-7),     # rotated
     ("six_level", 400, 1.266e-6, 5.628e-7),      # full 1048576-cell grid, first 200 cells
     ("five_level_ring", 500, 2.589e-6, 1.781e-8),
+    ("five_level_ring_rotated", 500, 3.191e-5, 2.895e-7),  # tensor cores
+    ("five_level_ring_rotated", 500, 3.134e-5, 2.893e-7),  # run-time compiled kernel
+    ("six_level", 1000, 2.050e-6, 9.186e-7),     # rotated, tensor cores
+    ("six_level", 400, 1.263e-6, 3.343e-7),      # rotated, tensor cores, full grid
     ("pstd", 1000, 9.774e-6, 1.218e-6),          # soft source
     ("pstd", 1000, 1.159e-5, 1.238e-6),          # hard source
 ]

@@ -37,10 +37,11 @@ def six_level_reference(orc):
     return p, S, keep, st
 
 
-@pytest.mark.parametrize("precision,kernel", [("fp64", "auto"), ("fp32", "auto"), ("fp32", "tensor")])
-def test_six_level_full_size_sampled(six_level_reference, precision, kernel):
+@pytest.mark.parametrize("precision,kernel,form", [("fp64", "auto", "merged"), ("fp32", "auto", "merged"),
+                                                   ("fp32", "tensor", "merged"), ("fp32", "auto", "rotated")])
+def test_six_level_full_size_sampled(six_level_reference, precision, kernel, form):
     p, S, keep, ref = six_level_reference
-    s = make_solver(p, precision, "merged", kernel=kernel)
+    s = make_solver(p, precision, form, kernel=kernel)
     s.autotune(2)
     s.step(S, src_tensor(p, 0, S))
     s.sync()
@@ -48,7 +49,7 @@ def test_six_level_full_size_sampled(six_level_reference, precision, kernel):
     rho = s.rho(0, keep)
     e_err = rel_inf(E[:keep], ref.E[:keep])
     p_err = np.abs(np.einsum("cii->ci", rho - ref.rho[:keep]).real).max()
-    print(f"six-level full size {precision}/{s.kernel_in_use}: E rel {e_err:.3e}  pop abs {p_err:.3e}")
+    print(f"six-level full size {precision}/{form}/{s.kernel_in_use}: E rel {e_err:.3e}  pop abs {p_err:.3e}")
     assert np.abs(ref.E[:keep]).max() > 1e5  # the pulse has entered the compared cells
     if precision == "fp64":
         assert e_err < FP64_E and p_err < FP64_E

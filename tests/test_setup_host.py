@@ -53,7 +53,7 @@ def random_problem(N, seed, G=True):
 
 def test_exports_every_declared_symbol(lib):
     hdr = open(os.path.join(os.path.dirname(__file__), "..", "include", "mln.h")).read()
-    names = set(re.findall(r"\b(mln_[a-z_]+)\s*\(", hdr))
+    names = set(re.findall(r"\b(mln_[a-z0-9_]+)\s*\(", hdr))
     assert len(names) >= 15
     for n in sorted(names):
         assert hasattr(lib, n), n
