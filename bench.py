@@ -152,6 +152,36 @@ def tensor_roofline(p, args, run, launches, per_launch_s, clk):
                        "split, padding and halo rows"}
 
 
+def tensor_rotated_roofline(p, args, run, launches, per_launch_s, clk):
+    """Roofline of the rotated-basis tensor-core kernel against the FP16 dense
+    tensor peak (the measured sustained bf16 GEMM rate: FP16 and bf16 run at
+    the same rate). achieved counts the method's one dense product per medium
+    cell update, [C1z, cz; wz, cm] [z''; 1]: 2 (D + 1)^2 - (D + 1) flops;
+    issued counts what the MMAs execute (hi*hi + hi*lo + lo*hi, K and N padded
+    to 16, halo rows of every tile)."""
+    D = p.D
+    up = lambda x, m: (x + m - 1) // m * m
+    KA = NB = up(D + 1, 16)
+    K, tile = run["shape"][0], run["shape"][1]
+    algo_per_cell = 2 * (D + 1) ** 2 - (D + 1)
+    issued_per_row = 3 * 2 * NB * KA
+    steps_per_launch = args.seg * args.steps / max(launches, 1)
+    ntiles = -(-p.n_cells // tile)
+    algo = p.n_medium * algo_per_cell * steps_per_launch / per_launch_s / 1e12
+    issued = ntiles * 128 * issued_per_row * steps_per_launch / per_launch_s / 1e12
+    peaks = load_peaks()
+    fp16 = peaks.get("bf16_tflops_sustained") or peaks.get("bf16_tflops")
+    src = "measured bf16_tflops_sustained (FP16 dense runs at the bf16 rate)"
+    if not fp16:
+        fp16, src = 1700.0, "fallback 1.7 PFLOP/s bf16 sustained"
+    return {"bound": "tensor", "achieved": algo, "peak": fp16, "unit": "TFLOP/s", "frac": algo / fp16,
+            "kernel": "mln_tcr_kernel (tcgen05.mma kind::f16, FP16 hi/lo)", "traffic": None, "peak_source": src,
+            "issued": issued, "frac_issued": issued / fp16, "flops_per_medium_cell_update": algo_per_cell,
+            "issued_per_tile_row_step": issued_per_row,
+            "counted": "achieved: the one dense product per medium cell update; issued: MMA work incl. the "
+                       "three-part split, padding and halo rows"}
+
+
 def load_peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -487,12 +517,17 @@ def _device_record(p, precision, form, seg, steps, warmup, kernel="auto", note=N
            "precision": precision, "form": form, "kernel": r["kernel"], "launch_shape": list(r["shape"]),
            "timed": f"{steps} x {seg} time steps after {warmup} x {seg} warm-up, L2 flushed between them"}
     if r["kernel"] == "tensor":
-        class _A:  # the arguments tensor_roofline reads
+        class _A:  # the arguments the tensor rooflines read
             pass
         a = _A()
         a.seg, a.steps = seg, steps
         per_launch_s = r["ms_local"] / 1e3 / max(r["launches"], 1)
-        rec["roofline"] = tensor_roofline(p, a, r, r["launches"], per_launch_s, r["clocks"] or {})
+        roof = tensor_rotated_roofline if form == "rotated" else tensor_roofline
+        rec["roofline"] = roof(p, a, r, r["launches"], per_launch_s, r["clocks"] or {})
+        # the same step's flops (mln_work_per_step) against the FP32 ALU peak, for
+        # comparison with the CUDA-core kernels of the same form
+        alu = _alu_roofline(r, p, seg, steps, precision, "")
+        rec["roofline"]["fp32_alu_equivalent_frac"] = alu["frac"]
     else:
         rec["roofline"] = _alu_roofline(r, p, seg, steps, precision, _kernel_name(r["kernel"]))
     if note:
@@ -868,7 +903,8 @@ def main():
     if clk.get("sm_mhz"):
         roofline["frac_at_measured_clock"] = achieved / alu_peak_tflops(args.precision, clk["sm_mhz"])
     if main_run["kernel"] == "tensor":
-        roofline = tensor_roofline(p, args, main_run, launches, per_launch_s, clk)
+        roof = tensor_rotated_roofline if args.form == "rotated" else tensor_roofline
+        roofline = roof(p, args, main_run, launches, per_launch_s, clk)
     if p.maxwell == "pstd":
         roofline = pstd_roofline(p, args, main_run, f_med, clk)
     if args.workload == "two_level_sit":

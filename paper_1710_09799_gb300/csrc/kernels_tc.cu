@@ -203,41 +203,46 @@ __global__ void __launch_bounds__(512, 1)
     const uint32_t id1 = tc::idesc_tf32(S::N1), id3 = tc::idesc_tf32(S::N3);
     const int bar_id = 1 + g;
     uint32_t phase = 0;
+    // descriptors of the first K block of each shared-memory operand (block kb
+    // starts kb * 256 bytes later: 16 units further in the address field)
+    const uint64_t d1h = tc::smem_desc(b1h, 128, S::KA * 32), d1l = tc::smem_desc(b1l, 128, S::KA * 32);
+    const uint64_t dyh = tc::smem_desc(byh, 128, S::KA * 32), dyl = tc::smem_desc(byl, 128, S::KA * 32);
+    const uint64_t dzh = tc::smem_desc(bzh, 128, S::KP * 32), dzl = tc::smem_desc(bzl, 128, S::KP * 32);
+    const uint64_t dah = tc::smem_desc(z_hi, 128, S::KP * 32), dal = tc::smem_desc(z_lo, 128, S::KP * 32);
 
     // z = T^T y: A = y from tensor memory (one thread)
     auto issue_z = [&] {
 #pragma unroll
-        for (int kb = 0; kb < S::KA / 8; ++kb)
-            tc::mma_tf32_ts(acc, y_lo + kb * 8, tc::smem_desc(b1h + kb * 256, 128, S::KA * 32), id1, kb > 0);
+        for (int kb = 0; kb < S::KA / 8; ++kb) tc::mma_tf32_ts(acc, y_lo + kb * 8, d1h + 16 * kb, id1, kb > 0);
 #pragma unroll
-        for (int kb = 0; kb < S::KA / 8; ++kb)
-            tc::mma_tf32_ts(acc, y_hi + kb * 8, tc::smem_desc(b1l + kb * 256, 128, S::KA * 32), id1, 1u);
+        for (int kb = 0; kb < S::KA / 8; ++kb) tc::mma_tf32_ts(acc, y_hi + kb * 8, d1l + 16 * kb, id1, 1u);
 #pragma unroll
-        for (int kb = 0; kb < S::KA / 8; ++kb)
-            tc::mma_tf32_ts(acc, y_hi + kb * 8, tc::smem_desc(b1h + kb * 256, 128, S::KA * 32), id1, 1u);
+        for (int kb = 0; kb < S::KA / 8; ++kb) tc::mma_tf32_ts(acc, y_hi + kb * 8, d1h + 16 * kb, id1, 1u);
     };
     // [increment ; dP/dt - c'] = [C1, A0^2 T ; wm^T, wm^T T] [y ; dz]: y from
     // tensor memory, dz from shared memory (one thread)
     auto issue_inc = [&] {
-        auto part = [&](uint32_t ya, uint32_t yb, uint32_t za, uint32_t zb, bool first) {
+        auto part = [&](uint32_t ya, uint64_t yb, uint64_t za, uint64_t zb, bool first) {
 #pragma unroll
             for (int kb = 0; kb < S::KA / 8; ++kb)
-                tc::mma_tf32_ts(acc, ya + kb * 8, tc::smem_desc(yb + kb * 256, 128, S::KA * 32), id3,
-                                (first && kb == 0) ? 0u : 1u);
+                tc::mma_tf32_ts(acc, ya + kb * 8, yb + 16 * kb, id3, (first && kb == 0) ? 0u : 1u);
 #pragma unroll
-            for (int kb = 0; kb < S::KP / 8; ++kb)
-                tc::mma_tf32(acc, tc::smem_desc(za + kb * 256, 128, S::KP * 32),
-                             tc::smem_desc(zb + kb * 256, 128, S::KP * 32), id3, 1u);
+            for (int kb = 0; kb < S::KP / 8; ++kb) tc::mma_tf32(acc, za + 16 * kb, zb + 16 * kb, id3, 1u);
         };
-        part(y_lo, byh, z_lo, bzh, true);
-        part(y_hi, byl, z_hi, bzl, false);
-        part(y_hi, byh, z_hi, bzh, false);
+        part(y_lo, dyh, dal, dzh, true);
+        part(y_hi, dyl, dah, dzl, false);
+        part(y_hi, dyh, dah, dzh, false);
     };
+    // one elected lane of the group's first warp issues, from a converged warp
+    const bool mma_warp = warp % 4 == 0;
     auto issue = [&](auto f) {
-        if (j == 0) {
-            tc::fence_after_sync();
-            f();
-            tc::mma_commit(bar);
+        if (mma_warp) {
+            if (tc::elect_one()) {
+                tc::fence_after_sync();
+                f();
+                tc::mma_commit(bar);
+            }
+            __syncwarp();
         }
     };
     auto wait = [&] {

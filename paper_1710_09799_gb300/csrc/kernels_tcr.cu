@@ -72,13 +72,15 @@ struct TcrScalars {
 
 namespace {
 
-// x = hi + lo: hi is x rounded to 11 significant bits (exactly an FP16 value
-// for 2^-14 <= |x| < 65504; integer add and mask, ties away from zero), lo =
-// x - hi exactly in FP32, then both converted to FP16 in pairs.
+// x = hi + lo for a pair: hi is x rounded to FP16 (one packed conversion),
+// read back as FP32; lo = x - hi is exact in FP32 and rounded to FP16 in turn,
+// so hi + lo = x to about 2^-22 relative (|x| < 65504).
 __device__ __forceinline__ void split_f16x2(float x0, float x1, uint32_t &hi, uint32_t &lo) {
-    const float h0 = __uint_as_float(tc::tf32_bits(__float_as_uint(x0)));
-    const float h1 = __uint_as_float(tc::tf32_bits(__float_as_uint(x1)));
-    hi = tc::pack_f16x2(h0, h1);
+    hi = tc::pack_f16x2(x0, x1);
+    float h0, h1;
+    asm("{\n\t.reg .f16 l, h;\n\tmov.b32 {l, h}, %2;\n\tcvt.f32.f16 %0, l;\n\tcvt.f32.f16 %1, h;\n\t}"
+        : "=f"(h0), "=f"(h1)
+        : "r"(hi));
     lo = tc::pack_f16x2(x0 - h0, x1 - h1);
 }
 
@@ -94,7 +96,11 @@ __device__ __forceinline__ void stage_row_f16(uint32_t t_hi, uint32_t t_lo, cons
 #pragma unroll
         for (int e = 0; e < 8; ++e) {
             const int k0 = c + 2 * e, k1 = k0 + 1;
-            const float x0 = k0 < n ? v[k0] : (k0 == n ? 1.0f : 0.0f);
+            if (k0 > n) {  // padding: zero in both parts, no conversion
+                h[e] = l[e] = 0u;
+                continue;
+            }
+            const float x0 = k0 < n ? v[k0] : 1.0f;
             const float x1 = k1 < n ? v[k1] : (k1 == n ? 1.0f : 0.0f);
             split_f16x2(x0, x1, h[e], l[e]);
         }
@@ -104,20 +110,18 @@ __device__ __forceinline__ void stage_row_f16(uint32_t t_hi, uint32_t t_lo, cons
 }
 
 // D = A B^T over K = KA: hi*hi + hi*lo + lo*hi, A in tensor memory (two FP16
-// per column), B images in shared memory (K-major, no swizzle), one thread.
+// per column), B images in shared memory (K-major, no swizzle) given by the
+// descriptors of their first K block (block kb starts kb * 256 bytes later,
+// i.e. 16 units further in the descriptor's address field). One thread.
 template <int KA>
-__device__ __forceinline__ void issue_f16(uint32_t d, uint32_t a_hi, uint32_t a_lo, uint32_t b_hi, uint32_t b_lo,
+__device__ __forceinline__ void issue_f16(uint32_t d, uint32_t a_hi, uint32_t a_lo, uint64_t db_hi, uint64_t db_lo,
                                           uint32_t idesc) {
-    constexpr uint32_t sbo = KA * 16;
 #pragma unroll
-    for (int kb = 0; kb < KA / 16; ++kb)
-        tc::mma_f16_ts(d, a_hi + kb * 8, tc::smem_desc(b_hi + kb * 256, 128, sbo), idesc, kb > 0 ? 1u : 0u);
+    for (int kb = 0; kb < KA / 16; ++kb) tc::mma_f16_ts(d, a_hi + kb * 8, db_hi + 16 * kb, idesc, kb > 0 ? 1u : 0u);
 #pragma unroll
-    for (int kb = 0; kb < KA / 16; ++kb)
-        tc::mma_f16_ts(d, a_hi + kb * 8, tc::smem_desc(b_lo + kb * 256, 128, sbo), idesc, 1u);
+    for (int kb = 0; kb < KA / 16; ++kb) tc::mma_f16_ts(d, a_hi + kb * 8, db_lo + 16 * kb, idesc, 1u);
 #pragma unroll
-    for (int kb = 0; kb < KA / 16; ++kb)
-        tc::mma_f16_ts(d, a_lo + kb * 8, tc::smem_desc(b_hi + kb * 256, 128, sbo), idesc, 1u);
+    for (int kb = 0; kb < KA / 16; ++kb) tc::mma_f16_ts(d, a_lo + kb * 8, db_hi + 16 * kb, idesc, 1u);
 }
 
 template <int cols>
@@ -182,7 +186,10 @@ __global__ void __launch_bounds__(512, 1)
     const uint32_t a_hi = tg + S::A_HI, a_lo = tg + S::A_LO, acc = tg + S::ACC;
     const uint32_t b_hi = tc::smem_addr(smem), b_lo = b_hi + S::BB;
     const uint32_t idesc = tc::idesc_f16(S::NB);
+    // descriptors of the constant operand's images (K-major, 8-row groups KA * 16 bytes apart)
+    const uint64_t db_hi = tc::smem_desc(b_hi, 128, S::KA * 16), db_lo = tc::smem_desc(b_lo, 128, S::KA * 16);
     const int bar_id = 1 + g;
+    const bool mma_warp = warp % 4 == 0;  // the group's first warp issues its MMAs
     uint32_t phase = 0;
 
     const int64_t n = a.n_cells;
@@ -238,12 +245,19 @@ __global__ void __launch_bounds__(512, 1)
             tc::st_wait();
             tc::fence_before_sync();
             tc::bar_sync(bar_id, ROWS);  // A staged, H^{n+1/2} published
-            if (j == 0) {
-                tc::fence_after_sync();
-                issue_f16<S::KA>(acc, a_hi, a_lo, b_hi, b_lo, idesc);
-                tc::mma_commit(bar);
+            // one elected lane of the group's first warp issues, from a converged
+            // warp: about three times faster than issuing from a branch on the lane
+            if (mma_warp) {
+                if (tc::elect_one()) {
+                    tc::fence_after_sync();
+                    issue_f16<S::KA>(acc, a_hi, a_lo, db_hi, db_lo, idesc);
+                    tc::mma_commit(bar);
+                }
+                __syncwarp();
             }
-            ok = tc::mbar_wait(bar, phase) && ok;
+            // one MMA round trip is a few hundred cycles: suspend rather than spin
+            // (at most 2^15 polls of 100 us each)
+            ok = tc::mbar_wait_hint(bar, phase, 100000u, 1 << 15) && ok;
             phase ^= 1;
             tc::fence_after_sync();
             float v[S::LR];
@@ -343,7 +357,8 @@ __global__ void __launch_bounds__(128, 1)
     if (j == 0) {
         tc::fence_after_sync();
         const uint32_t bh = tc::smem_addr(smem);
-        issue_f16<KC>(acc, tmem, tmem + 64, bh, bh + BB, tc::idesc_f16(NC));
+        issue_f16<KC>(acc, tmem, tmem + 64, tc::smem_desc(bh, 128, KC * 16), tc::smem_desc(bh + BB, 128, KC * 16),
+                      tc::idesc_f16(NC));
         tc::mma_commit(tc::smem_addr(bar));
     }
     const bool ok = tc::mbar_wait(tc::smem_addr(bar), 0);

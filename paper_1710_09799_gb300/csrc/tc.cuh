@@ -128,6 +128,17 @@ __device__ __forceinline__ void mma_f16_ts(uint32_t d_tmem, uint32_t a_tmem, uin
         : "memory");
 }
 
+// One lane of the (converged) warp: true for the elected leader.
+__device__ __forceinline__ bool elect_one() {
+    uint32_t e;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "elect.sync _|p, 0xffffffff;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(e));
+    return e != 0;
+}
+
 // Two FP32 values to a packed FP16 pair, round to nearest even: lo in the low
 // half, hi in the high half.
 __device__ __forceinline__ uint32_t pack_f16x2(float lo, float hi) {
@@ -161,6 +172,24 @@ __device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
             "selp.u32 %0, 1, 0, p;\n\t}"
             : "=r"(ok)
             : "r"(mbar), "r"(parity)
+            : "memory");
+        if (ok) return true;
+    }
+    return false;
+}
+
+// As mbar_wait, but each poll suspends the thread until the phase completes
+// or `hint_ns` nanoseconds pass, so a waiting warp issues a few polls instead
+// of spinning; gives up after `polls` polls (bounded: polls x hint_ns at most).
+__device__ __forceinline__ bool mbar_wait_hint(uint32_t mbar, uint32_t parity, uint32_t hint_ns, int polls) {
+    for (int i = 0; i < polls; ++i) {
+        uint32_t ok;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(ok)
+            : "r"(mbar), "r"(parity), "r"(hint_ns)
             : "memory");
         if (ok) return true;
     }
