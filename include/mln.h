@@ -321,11 +321,17 @@ mln_status mln_load_state(mln_ctx *ctx, const double *d_host, const double *Ez_h
                           const double *Hy_host);
 
 /*
- * Adjoint gradients (reverse-time, discrete adjoint of the step as computed).
+ * Adjoint gradients (reverse-time, discrete adjoint of the literal Strang
+ * step of Eq. 23 with the FDTD update of Eq. 1, boundaries and source included).
  * Objective J = dt * sum_{n=1..n_steps} (E_z^n at probe_cell)^2, the field
  * energy density at an output cell integrated over the run, starting from the
- * context's current state; the context ends advanced by n_steps. Needs
- * MLN_FORM_STRANG, MLN_BC_PERIODIC and N <= 4.
+ * context's current state; the context ends advanced by n_steps (by its own
+ * form and cell model). Any form: the forward pass runs the context's step and
+ * checkpoints its state; each segment is recomputed, from the checkpoint
+ * mapped to the adjoint vector d, in the Strang form, which all forms equal up
+ * to rounding, and differentiated there. Periodic rings and open grids (held
+ * cell 0 with a hard or soft source, Mur at the right end). Needs N <= 4 and
+ * MLN_MAXWELL_FDTD (MLN_EUNSUPPORTED otherwise).
  *   src         as for mln_step (device, n_steps samples) or NULL.
  *   every       checkpoint interval: the forward pass saves the state every
  *               `every` steps; the backward pass recomputes each segment from

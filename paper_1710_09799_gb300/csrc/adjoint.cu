@@ -1,14 +1,17 @@
 // mln_adjoint: gradients of a probe-field objective by the discrete adjoint
 // (reverse-time) method with checkpointing and recomputation.
 //
-// Forward: the fused step kernel advances the context, saving the state at
-// the start of every segment of `every` steps. Backward: for the segments in
-// reverse order, the segment is recomputed from its checkpoint by the fused
-// step kernel with every step's state recorded (all its states kept), then
-// the reverse step kernel runs from the segment's last step to its first, carrying the adjoint of (E, H, d) and
-// accumulating the gradients of the step's constants. The host then maps
-// those to the dipole operator and the relaxation superoperator (exact
-// Frechet derivatives, see adjoint_chain).
+// Forward: the context's own step (any form and cell model) advances it,
+// saving the state at the start of every segment of `every` steps.
+// Backward: for the segments in reverse order, the segment is recomputed from
+// its checkpoint in the literal Strang form by the fused step kernel with
+// every step's state recorded (all its states kept; a checkpoint of another
+// form is first mapped to the adjoint vector d, which these forms share up to
+// rounding: the merged and rotated forms hold an affine image of d), then the
+// reverse step kernel runs from the segment's last step to its first,
+// carrying the adjoint of (E, H, d) and accumulating the gradients of the
+// step's constants. The host then maps those to the dipole operator and the
+// relaxation superoperator (exact Frechet derivatives, see adjoint_chain).
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -53,6 +56,19 @@ mln::AdjConsts<N, R> adj_consts(const mln::Setup &s, double dt) {
     return k;
 }
 
+// d = sd0 + Sd s for every medium cell, SoA in and out (tab = [Sd | sd0] in FP64).
+template <typename R>
+__global__ void state_to_d(const R *__restrict__ s, R *__restrict__ d, int64_t stride, int64_t count, int D,
+                           const double *__restrict__ tab) {
+    const int64_t c = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+    if (c >= count) return;
+    for (int k = 0; k < D; ++k) {
+        double acc = tab[D * D + k];
+        for (int j = 0; j < D; ++j) acc += tab[k * D + j] * static_cast<double>(s[j * stride + c]);
+        d[k * stride + c] = static_cast<R>(acc);
+    }
+}
+
 // Buffers of one (state, E, H) set inside a larger allocation.
 template <typename R>
 struct Set {
@@ -85,6 +101,10 @@ mln_status adjoint_t(mln_ctx *c, int64_t n_steps, const double *src, int64_t pro
     };
     const Set<R> user{static_cast<R *>(c->E[0]), static_cast<R *>(c->H[0]), static_cast<R *>(c->st[0])};
     mln::BlockArgs<R> fa = mln::base_args<R>(c);
+    // the recompute runs the literal Strang form whatever the context's form
+    std::vector<unsigned char> strang;
+    const bool convert = c->p.form != MLN_FORM_STRANG;  // checkpoints hold another form's state
+    if (!mln::pack_consts(c->s, MLN_FORM_STRANG, c->p.dt, static_cast<R>(0), strang)) return MLN_EUNSUPPORTED;
     // Reverse step: AdjLanes<N> lanes per cell, blocks of 64 threads (all resident
     // at once for rings of this size; small blocks spread evenly over the SMs).
     const unsigned rblocks = static_cast<unsigned>((n * mln::AdjLanes<N>::value + 63) / 64);
@@ -106,6 +126,11 @@ mln_status adjoint_t(mln_ctx *c, int64_t n_steps, const double *src, int64_t pro
     auto recompute = [&](int64_t sg, unsigned char *sl, cudaStream_t strm) -> cudaError_t {
         const int64_t g0 = sg * every, glen = std::min<int64_t>(every, n_steps - g0);
         cudaError_t e = copy_set(set_at(sl, 0), set_at(ckpt, sg), strm);
+        if (e == cudaSuccess && convert && c->n_med > 0) {
+            state_to_d<R><<<static_cast<unsigned>((c->n_med + 127) / 128), 128, 0, strm>>>(
+                set_at(ckpt, sg).S, set_at(sl, 0).S, c->stride, c->n_med, c->D, c->tab_d);
+            e = cudaGetLastError();
+        }
         for (int64_t j = 0; e == cudaSuccess && j < glen; j += rK) {
             const int ns = static_cast<int>(std::min<int64_t>(rK, glen - j));
             const Set<R> in = set_at(sl, j), o = set_at(sl, j + ns), r1 = set_at(sl, j + 1);
@@ -124,7 +149,7 @@ mln_status adjoint_t(mln_ctx *c, int64_t n_steps, const double *src, int64_t pro
             // plain launches: the recompute runs beside the reverse sweep, and
             // blocks placed early by programmatic launches took SM resources
             // from it (FP64 gradient 1.77e8 -> 1.56e8 cell-updates/s)
-            e = mln::launch_block(c->p.N, MLN_FORM_STRANG, fa, c->consts,
+            e = mln::launch_block(c->p.N, MLN_FORM_STRANG, fa, strang,
                                   dim3(static_cast<unsigned>((n + c->tile - 1) / c->tile)), dim3(rthreads),
                                   mln::field_smem<R>(rthreads), strm, false);
         }
@@ -169,6 +194,8 @@ mln_status adjoint_t(mln_ctx *c, int64_t n_steps, const double *src, int64_t pro
     aa.source_cell = c->p.source_cell;
     aa.probe_cell = probe;
     aa.source_kind = c->p.source_kind;
+    aa.boundary = c->p.boundary;
+    aa.kappa = fa.kappa;
     aa.dt = c->p.dt;
     aa.ch = fa.ch;
     aa.ca = fa.ca;
@@ -253,9 +280,8 @@ mln_status mln_adjoint(mln_ctx *c, int64_t n_steps, const double *src, int64_t p
         if (c) c->err = "invalid adjoint arguments";
         return MLN_EINVAL;
     }
-    if (c->p.form != MLN_FORM_STRANG || c->p.boundary != MLN_BC_PERIODIC || c->p.N > 4 || c->sparse ||
-        c->p.maxwell != MLN_MAXWELL_FDTD) {
-        c->err = "mln_adjoint needs MLN_FORM_STRANG, MLN_BC_PERIODIC, MLN_MAXWELL_FDTD and N <= 4";
+    if (c->p.N > 4 || c->p.maxwell != MLN_MAXWELL_FDTD || c->pstd) {
+        c->err = "mln_adjoint needs MLN_MAXWELL_FDTD and N <= 4";
         return MLN_EUNSUPPORTED;
     }
     switch (c->p.N) {

@@ -1,7 +1,8 @@
-// Reverse-time (adjoint) step of the literal Strang form on a periodic ring
-// (internal header). A step's adjoint reads only the adjoints after the step
-// and the forward state before it, so no block-level synchronisation is
-// needed and one launch handles one step.
+// Reverse-time (adjoint) step of the literal Strang form, on a periodic ring
+// or an open grid (held cell 0 with a hard or soft source, first-order Mur at
+// the right end) (internal header). A step's adjoint reads only the adjoints
+// after the step and the forward state before it, so no block-level
+// synchronisation is needed and one launch handles one step.
 #pragma once
 
 #include "kernels.cuh"
@@ -26,9 +27,9 @@ struct AdjArgs {
     double *dsrc;                 // adjoint of this step's source sample (one double), or nullptr
     double *acc;                  // per-cell accumulators: entry k of cell i at k * n_cells + i (AccLayout)
     int64_t n_cells, mb, me, stride, source_cell, probe_cell;
-    int32_t source_kind, pad_;
+    int32_t source_kind, boundary;  // boundary: 0 ring, 1 open (held cell 0, Mur at n - 1)
     double dt, E_step;            // dt; unused
-    R ch, ca, cb, inv_dx;
+    R ch, ca, cb, inv_dx, kappa;
 };
 
 // Accumulator layout (FP64): Dl_bar (D x D) | b_bar (D) | w_bar (D) | c_bar |
@@ -77,13 +78,27 @@ struct AdjLanes {
 // split changes no bits; small rings keep all SMs busy and each lane's
 // dependency chains are D times shorter.
 //
-// Forward step being differentiated (periodic, sigma general):
-//   H'_i = H_i + ch (E_{i+1} - E_i)
+// Forward step being differentiated (sigma general):
+//   H'_i = H_i + ch (E_{i+1} - E_i)                     i in the H range
 //   d'   = d + (Dl d + b);  z = T^T d';  d'' = d' + T (R(phi) - I) z,  phi_k = theta_k dt E_i
 //   dn   = d'' + (Dl d'' + b);  p = w . dn + c
-//   E'_i = ca E_i + cb ((H'_i - H'_{i-1}) / dx - p_i);  source at source_cell
+//   E'_i = ca E_i + cb ((H'_i - H'_{i-1}) / dx - p_i)   i in the E range
+//   open grid: E'_0 = E_0 (held); E'_{n-1} = E_{n-2} + kappa (E'_{n-2} - E_{n-1}) (Mur,
+//   from E'_{n-2} before any source); then the source at source_cell (hard:
+//   replace, soft: add). Ring: every cell in both ranges, indices modulo n;
+//   open grid: H range 0..n-2, E range 1..n-2.
 // Objective J = dt sum_n (E^{n+1}_probe)^2: the reverse of step n adds
 // 2 dt E^{n+1}_probe to the adjoint of E^{n+1}_probe.
+//
+// Reverse of the field part, per cell i, with Ebar' the adjoint of E^{n+1}:
+//   m      = adjoint of the Mur cell's new value (0 under a hard source there)
+//   epre_i = adjoint of cell i's E update before source and Mur: Ebar'_i (0
+//            under a hard source at i), plus kappa m at i = n - 2; 0 outside the E range
+//   Hbar_i = Hbar'_i + cb/dx (epre_i - epre_{i+1})           i in the H range
+//   Ebar_i = ca epre_i + ch (Hbar_{i-1} - Hbar_i)  (terms in the H range only)
+//            + Ebar'_0 at the held cell 0 (not under a hard source),
+//            + m at n - 2, - kappa m at n - 1, + the medium's term
+//   pbar_i = -cb epre_i
 template <int N, typename R>
 __global__ void __launch_bounds__(128) mln_adjoint_step_rows(const __grid_constant__ AdjArgs<R> a,
                                                              const __grid_constant__ AdjConsts<N, R> k) {
@@ -96,6 +111,7 @@ __global__ void __launch_bounds__(128) mln_adjoint_step_rows(const __grid_consta
     const bool live = i < n;
     const bool row = live && r < D;
     const int64_t ii = live ? i : 0;
+    const bool periodic = a.boundary == 0;
     const int64_t ip = ii + 1 == n ? 0 : ii + 1, im = ii == 0 ? n - 1 : ii - 1;
     const R jdt = static_cast<R>(2.0 * a.dt);
     const unsigned full = 0xffffffffu;
@@ -113,17 +129,25 @@ __global__ void __launch_bounds__(128) mln_adjoint_step_rows(const __grid_consta
     const R b_r = k.b[rr], w_r = k.w[rr];
 
     // scalars of the cell (every lane; lane 0 writes)
-    auto ebar_out = [&](int64_t c) -> R {
+    auto ebar_new = [&](int64_t c) -> R {  // adjoint of E^{n+1}_c, with the objective's term
         R v = a.Ea[c];
         if (c == a.probe_cell) v += jdt * a.E1[c];
-        if (a.dsrc != nullptr && a.source_kind == 1 && c == a.source_cell) v = R(0);
         return v;
     };
+    auto hard = [&](int64_t c) { return a.dsrc != nullptr && a.source_kind == 1 && c == a.source_cell; };
+    const R mbar = (!periodic && live && !hard(n - 1)) ? ebar_new(n - 1) : R(0);
+    auto epre = [&](int64_t c) -> R {
+        if (!periodic && (c <= 0 || c >= n - 1)) return R(0);
+        R v = hard(c) ? R(0) : ebar_new(c);
+        if (!periodic && c == n - 2) v += a.kappa * mbar;
+        return v;
+    };
+    auto in_h = [&](int64_t c) { return periodic || c <= n - 2; };
     R ep_i = R(0), ep_p = R(0), ep_m = R(0);
     if (live) {
-        ep_i = ebar_out(ii);
-        ep_p = ebar_out(ip);
-        ep_m = ebar_out(im);
+        ep_i = epre(ii);
+        if (periodic || ii + 1 < n) ep_p = epre(ip);
+        if (periodic || ii >= 1) ep_m = epre(im);
     }
     if (live && r == 0 && a.dsrc != nullptr && ii == a.source_cell) {
         R v = a.Ea[ii];
@@ -135,12 +159,18 @@ __global__ void __launch_bounds__(128) mln_adjoint_step_rows(const __grid_consta
         a.acc[L::J * n + ii] += a.dt * e1 * e1;
     }
     R hh_i = R(0), hh_m = R(0);
+    const bool has_m = periodic || ii >= 1;  // H_{i-1/2} exists
     if (live) {
-        hh_i = a.Ha[ii] + a.cb * a.inv_dx * (ep_i - ep_p);
-        hh_m = a.Ha[im] + a.cb * a.inv_dx * (ep_m - ep_i);
+        hh_i = a.Ha[ii] + (in_h(ii) ? a.cb * a.inv_dx * (ep_i - ep_p) : R(0));
+        if (has_m) hh_m = a.Ha[im] + (in_h(im) ? a.cb * a.inv_dx * (ep_m - ep_i) : R(0));
         if (r == 0) a.Hb[ii] = hh_i;
     }
-    R eb = live ? a.ca * ep_i + a.ch * (hh_m - hh_i) : R(0);
+    R eb = live ? a.ca * ep_i + a.ch * ((has_m ? hh_m : R(0)) - (in_h(ii) ? hh_i : R(0))) : R(0);
+    if (live && !periodic) {
+        if (ii == 0 && !hard(0)) eb += ebar_new(0);  // held: E^{n+1}_0 = E^n_0
+        if (ii == n - 2) eb += mbar;                 // E^n_{n-2} in the Mur rule
+        if (ii == n - 1) eb -= a.kappa * mbar;       // E^n_{n-1} in the Mur rule
+    }
 
     const bool medium = live && ii >= a.mb && ii < a.me;
     const bool mrow = medium && r < D;
