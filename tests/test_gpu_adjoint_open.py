@@ -32,10 +32,10 @@ def _built():
     build()
 
 
-def open_grid(kind="hard", n_cells=240, n_steps=600, probe=None, T=1e-12):
+def open_grid(kind="hard", n_cells=240, n_steps=600, probe=None, T=1e-12, N_a=1e24):
     """Two-level grid, medium [60, 180), Mur at the right; the source carries a
     Gaussian-envelope carrier (period ~40 steps) over its first 200 steps."""
-    p = W.two_level_sit(n_cells=n_cells, medium=(60, 180), n_steps=n_steps, T1=T, T2=T)
+    p = W.two_level_sit(n_cells=n_cells, medium=(60, 180), n_steps=n_steps, T1=T, T2=T, N_a=N_a)
     k = np.arange(n_steps, dtype=np.float64)
     src = np.zeros(n_steps)
     src[:200] = 3e8 * np.exp(-((k[:200] - 100) / 35) ** 2) * np.sin(2 * np.pi * k[:200] / 40)
@@ -103,15 +103,17 @@ def test_open_grid_probe_on_the_mur_cell():
 
 
 def test_open_grid_dipole_and_relaxation_gradients(orc):
-    """Strong relaxation (T1 = T2 = 20 fs) so that the rate's effect on J over
-    600 steps is resolved by a central difference; the dipole element mu_12."""
+    """Strong relaxation (T1 = T2 = 20 fs) and a dense medium (N_a = 1e27 m^-3:
+    its polarisation changes the probe field by ~1e-3 instead of ~1e-6), so
+    that the effects of the rate and of the dipole element on J are resolved
+    by central differences well above J's rounding."""
     from paper_1710_09799_gb300 import mln
-    p = open_grid("hard", T=2e-14)
+    p = open_grid("hard", T=2e-14, N_a=1e27)
     src = p.source_samples(0, p.n_steps)
     J, _, dmu, dG = J_and_grads(p, src)
     x0 = mln.mu_to_params(p.mu)
     i = p.N  # Re mu_12
-    h = 1e-6 * abs(x0[i])
+    h = 1e-5 * abs(x0[i])
     xp, xm = x0.copy(), x0.copy()
     xp[i] += h
     xm[i] -= h
