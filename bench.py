@@ -771,7 +771,7 @@ def run_adjoint(args, ws, rank, local):
     from paper_1710_09799_gb300 import mln
     p = W.adjoint_ring()
     src = torch.as_tensor(p.source_samples(0, p.n_steps), dtype=torch.float64, device="cuda")
-    par = make_params(p, args.precision, "strang")
+    par = make_params(p, args.precision, args.form)
     times = []
     for i in range(args.warmup + args.steps):
         s = mln.Solver(par, E0=p.e_init())
@@ -782,7 +782,7 @@ def run_adjoint(args, ws, rank, local):
         if i >= args.warmup:
             times.append(time.perf_counter() - t)
         s.close()
-    # the plain forward of the same workload, for comparison
+    # the plain forward of the same workload (same form and cell model), for comparison
     s = mln.Solver(par, E0=p.e_init())
     s.autotune(3)
     torch.cuda.synchronize()
@@ -846,7 +846,8 @@ def main():
     ap.add_argument("--precision", default=None, choices=["fp64", "fp32"],
                     help="default: fp32 for six_level_pulse and batched, fp64 otherwise")
     ap.add_argument("--form", default=None, choices=["strang", "merged", "rodrigues", "rotated"],
-                    help="default: rotated for six_level_pulse (its fastest form), merged otherwise")
+                    help="default: rotated for six_level_pulse (its fastest form), strang for adjoint (the "
+                         "form the gradient differentiates), merged otherwise")
     ap.add_argument("--seg", type=int, default=1000, help="time steps per benchmark step")
     ap.add_argument("--block-steps", type=int, default=0, help="0: autotuned")
     ap.add_argument("--tile", type=int, default=0)
@@ -857,7 +858,7 @@ def main():
     if args.precision is None:
         args.precision = "fp32" if args.workload in ("six_level_pulse", "batched") else "fp64"
     if args.form is None:
-        args.form = "rotated" if args.workload == "six_level_pulse" else "merged"
+        args.form = {"six_level_pulse": "rotated", "adjoint": "strang"}.get(args.workload, "merged")
     if args.impl == "reference":
         return run_reference(args)
 
