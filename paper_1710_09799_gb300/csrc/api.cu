@@ -343,7 +343,7 @@ mln_status mln_kernel_source(const mln_params *p, char *buf, size_t cap, size_t 
         return st;
     }
     const std::string src =
-        mln::jit_merged_source(s, p->dt, p->precision == MLN_FP32, p->form == MLN_FORM_ROTATED);
+        mln::jit_merged_source(s, p->dt, p->precision == MLN_FP32, p->form == MLN_FORM_ROTATED, mln::jit_body_flags(*p));
     if (len) *len = src.size();
     if (buf && cap > 0) {
         const size_t k = std::min(cap - 1, src.size());
@@ -674,7 +674,8 @@ mln_status mln_create(const mln_params *p, void *d_state, void *Ez, void *Hy, vo
             std::string why, log;
             cudaError_t e = cudaErrorNotSupported;
             if (mln::jit_available(&why))
-                e = mln::jit_compile(mln::jit_merged_source(c->s, p->dt, p->precision == MLN_FP32, rotated),
+                e = mln::jit_compile(mln::jit_merged_source(c->s, p->dt, p->precision == MLN_FP32, rotated,
+                                                            mln::jit_body_flags(*p)),
                                      &c->jit_fn, log);
             else
                 log = why;

@@ -460,7 +460,7 @@ mln_status mln_batch_create(int32_t count, const mln_params *params, void *const
     std::string why;
     if (want_jit && mln::jit_available(&why)) {
         const bool fp32 = b->precision == MLN_FP32;
-        for (mln_ctx *c : b->ctx) mln::batch_pattern_add(b->pat[c->p.N], c->s, fp32);
+        for (mln_ctx *c : b->ctx) mln::batch_pattern_add(b->pat[c->p.N], c->s, c->p, fp32);
         for (int N = 2; N <= mln::kBatchMaxN; ++N) {
             if (b->pat[N].N == 0) continue;
             std::string log;
@@ -607,7 +607,7 @@ mln_status mln_batch_kernel_source(int32_t count, const mln_params *params, int3
             mln::create_error() = "grid " + std::to_string(i) + ": " + err;
             return st;
         }
-        mln::batch_pattern_add(pat, s, fp32);
+        mln::batch_pattern_add(pat, s, params[i], fp32);
     }
     if (pat.N == 0) {
         mln::create_error() = "no grid with this N";

@@ -135,7 +135,12 @@ std::string row_sum(const std::vector<double> &A, int ld, int i, int ncols, cons
 
 }  // namespace
 
-std::string jit_merged_source(const Setup &s, double dt, bool fp32, bool rotated) {
+unsigned jit_body_flags(const mln_params &p) {
+    return (p.boundary == MLN_BC_PERIODIC ? kBodyRing : kBodyOpen) |
+           (p.source_kind == MLN_SRC_NONE ? kBodyNoSrc : 0u) | kBodyNoRec;
+}
+
+std::string jit_merged_source(const Setup &s, double dt, bool fp32, bool rotated, unsigned body_flags) {
     const int N = s.N, D = s.D, Q = s.q, P = 2 * Q;
     const char *R = fp32 ? "float" : "double";
     std::ostringstream o;
@@ -210,13 +215,15 @@ std::string jit_merged_source(const Setup &s, double dt, bool fp32, bool rotated
       // any read or write, then let the next launch be placed
       << "  asm volatile(\"griddepcontrol.wait;\" ::: \"memory\");\n"
       << "  asm volatile(\"griddepcontrol.launch_dependents;\" ::: \"memory\");\n"
-      << "  block_body<" << N << ", " << R << ", JitCell>(a, k, static_cast<int64_t>(blockIdx.x), smem_raw);\n}\n"
+      << "  block_body<" << N << ", " << R << ", JitCell, " << body_flags
+      << "u>(a, k, static_cast<int64_t>(blockIdx.x), smem_raw);\n}\n"
       << "}  // namespace mln\n";
     return o.str();
 }
 
-void batch_pattern_add(BatchPattern &pat, const Setup &s, bool fp32) {
+void batch_pattern_add(BatchPattern &pat, const Setup &s, const mln_params &p, bool fp32) {
     const int D = s.D, P = 2 * s.q;
+    pat.flags &= jit_body_flags(p);
     if (pat.N == 0) {
         pat.N = s.N;
         pat.tt.assign(static_cast<size_t>(P) * D, 0);
@@ -366,8 +373,8 @@ std::string jit_batch_source(const BatchPattern &pat, bool fp32) {
       << "> *grids, const BatchItem *items, const unsigned char *consts, int parity, int nsteps, int halo, int tile, "
          "int64_t step_offset) {\n"
       << "  extern __shared__ __align__(16) unsigned char smem_raw[];\n"
-      << "  batch_body<" << N << ", " << R
-      << ", JitBatchCell>(grids, items, consts, parity, nsteps, halo, tile, step_offset, smem_raw);\n}\n"
+      << "  batch_body<" << N << ", " << R << ", JitBatchCell, " << (pat.flags == ~0u ? 0u : pat.flags)
+      << "u>(grids, items, consts, parity, nsteps, halo, tile, step_offset, smem_raw);\n}\n"
       << "}  // namespace mln\n";
     return o.str();
 }

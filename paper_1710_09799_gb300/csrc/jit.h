@@ -14,7 +14,10 @@ namespace mln {
 // CUDA source of the merged-form step kernel of one context (constants inlined,
 // exact zeros left out), kernel name mln_jit_step.
 // rotated: the state is z = T^T y (MLN_FORM_ROTATED), else y (MLN_FORM_MERGED)
-std::string jit_merged_source(const Setup &s, double dt, bool fp32, bool rotated = false);
+std::string jit_merged_source(const Setup &s, double dt, bool fp32, bool rotated = false, unsigned body_flags = 0u);
+// Flags of the fused step's block body (kBody* of kernels.cuh) for a problem:
+// its boundary, whether it has a source; the compiled kernels never record.
+unsigned jit_body_flags(const mln_params &p);
 
 // Whether NVRTC and the driver entry points could be loaded (reason if not).
 bool jit_available(std::string *why);
@@ -32,8 +35,9 @@ struct BatchPattern {
     std::vector<char> t;   // D x 2q: T plane columns
     std::vector<char> wm;  // D
     std::vector<char> c1;  // D x D
+    unsigned flags = ~0u;  // block-body flags that hold for every grid of the pattern
 };
-void batch_pattern_add(BatchPattern &pat, const Setup &s, bool fp32);
+void batch_pattern_add(BatchPattern &pat, const Setup &s, const mln_params &p, bool fp32);
 // Number of constants of one grid in the pattern's compacted order.
 int batch_consts_count(const BatchPattern &pat);
 // One grid's constants in that order (precision's reals, padded to 16 bytes).

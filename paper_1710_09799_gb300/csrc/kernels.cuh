@@ -520,22 +520,34 @@ struct SharedSparseCell {
     }
 };
 
+// Problem properties known when a kernel is compiled (the run-time compiled
+// kernels know their grid): the code for the other cases is left out.
+enum : unsigned {
+    kBodyRing = 1u,   // every grid is a ring (no held cell, no Mur rule)
+    kBodyOpen = 2u,   // every grid is open
+    kBodyNoSrc = 4u,  // no source samples
+    kBodyNoRec = 8u,  // no recording of the steps
+    kBodyUnroll = 16u,  // two steps per loop iteration (buffers at fixed addresses; more registers)
+};
+
 // One thread block advances tile `tile_index` of one grid by a.nsteps steps.
 // smem: 2 * blockDim.x reals for E and H, then the cell model's extra space.
-template <int N, typename R, typename Cell>
+template <int N, typename R, typename Cell, unsigned kFlags = 0u>
 __device__ __forceinline__ void block_body(const BlockArgs<R> &a, const typename Cell::Consts &k, int64_t tile_index,
                                            unsigned char *smem) {
+    constexpr bool kRingOnly = (kFlags & kBodyRing) != 0, kOpenOnly = (kFlags & kBodyOpen) != 0;
+    constexpr bool kNoSrc = (kFlags & kBodyNoSrc) != 0, kNoRec = (kFlags & kBodyNoRec) != 0;
     // E and H of the block, two buffers each: step st reads one and writes the other
-    R *cE = reinterpret_cast<R *>(smem);
-    R *cH = cE + blockDim.x;
-    R *nE = cH + blockDim.x;
-    R *nH = nE + blockDim.x;
+    R *const bufE0 = reinterpret_cast<R *>(smem);
+    R *const bufH0 = bufE0 + blockDim.x;
+    R *const bufE1 = bufH0 + blockDim.x;
+    R *const bufH1 = bufE1 + blockDim.x;
 
     const int j = threadIdx.x;
     const int64_t n = a.n_cells;
     const int64_t t0 = tile_index * a.tile;
     const int64_t t1 = min(t0 + a.tile, n);
-    const bool periodic = a.boundary == 0;
+    const bool periodic = kRingOnly ? true : (kOpenOnly ? false : a.boundary == 0);
     // The Mur cell's value comes from its left neighbour's thread in the same
     // step, so its dependence reaches one cell further left than a step's:
     // a tile that starts at the Mur cell loads one more cell on the left
@@ -558,8 +570,8 @@ __device__ __forceinline__ void block_body(const BlockArgs<R> &a, const typename
     cell.setup(smem + field_smem<R>(blockDim.x), k);
     R e = loaded ? a.E_in[gm] : R(0);
     R h = loaded ? a.H_in[gm] : R(0);
-    cE[j] = e;
-    cH[j] = h;
+    bufE0[j] = e;
+    bufH0[j] = h;
     if (medium) cell.load(a.s_in, a.stride, m);
 
     // H_{i+1/2} exists for every cell of a ring and for cells 0..n-2 of an open grid;
@@ -571,10 +583,11 @@ __device__ __forceinline__ void block_body(const BlockArgs<R> &a, const typename
     const bool e_upd = loaded && j >= 1 && (periodic || (gm > 0 && gm < n - 1));
     const bool mur = !periodic && loaded && gm == n - 2 && j + 1 < L;
     const bool mur_cell = !periodic && loaded && gm == n - 1;
-    const bool is_src = a.src != nullptr && loaded && gm == a.source_cell;
+    const bool has_src = !kNoSrc && a.src != nullptr;
+    const bool is_src = has_src && loaded && gm == a.source_cell;
     const int tlen = static_cast<int>(t1 - t0);
     const bool interior = loaded && j >= lh && j < lh + tlen;
-    const bool record = a.rec_E != nullptr && interior;
+    const bool record = !kNoRec && a.rec_E != nullptr && interior;
     // Light cone: the tile's values after nsteps steps depend on the values
     // after step st only within nsteps - 1 - st cells of the tile; one cell
     // more keeps the Mur cell's left neighbour, whose thread computes the Mur
@@ -585,7 +598,8 @@ __device__ __forceinline__ void block_body(const BlockArgs<R> &a, const typename
     const int active = min(w0 + 32 - lh, lh + tlen - w0) + a.nsteps;  // steps this warp computes
     __syncthreads();
 
-    for (int st = 0; st < a.nsteps; ++st) {
+    // one step from buffers (cE, cH) into (nE, nH)
+    auto step = [&](int st, const R *cE, const R *cH, R *nE, R *nH) {
         if (st < active) {  // warp-uniform
             if (h_upd) h = fma(a.ch, cE[j + 1] - e, h);
             // the previous cell's new H, with the operands and operations of its own thread
@@ -603,7 +617,7 @@ __device__ __forceinline__ void block_body(const BlockArgs<R> &a, const typename
                 en = (a.source_kind == 1) ? v : en + v;
             }
             if (mur) {
-                if (a.src != nullptr && a.source_cell == n - 1) {
+                if (has_src && a.source_cell == n - 1) {
                     R v = static_cast<R>(a.src[st]);
                     e_mur = (a.source_kind == 1) ? v : e_mur + v;
                 }
@@ -622,12 +636,26 @@ __device__ __forceinline__ void block_body(const BlockArgs<R> &a, const typename
             reinterpret_cast<R *>(reinterpret_cast<char *>(a.rec_H) + off)[gm] = h;
             if (medium) cell.store(reinterpret_cast<R *>(reinterpret_cast<char *>(a.rec_S) + off), a.stride, m);
         }
-        R *t = cE;
-        cE = nE;
-        nE = t;
-        t = cH;
-        cH = nH;
-        nH = t;
+    };
+    if constexpr ((kFlags & kBodyUnroll) != 0u) {
+        // two steps per iteration: the buffers alternate at fixed addresses
+        int st = 0;
+        for (; st + 1 < a.nsteps; st += 2) {
+            step(st, bufE0, bufH0, bufE1, bufH1);
+            step(st + 1, bufE1, bufH1, bufE0, bufH0);
+        }
+        if (st < a.nsteps) step(st, bufE0, bufH0, bufE1, bufH1);
+    } else {
+        R *cE = bufE0, *cH = bufH0, *nE = bufE1, *nH = bufH1;
+        for (int st = 0; st < a.nsteps; ++st) {
+            step(st, cE, cH, nE, nH);
+            R *t = cE;
+            cE = nE;
+            nE = t;
+            t = cH;
+            cH = nH;
+            nH = t;
+        }
     }
 
     if (interior) {
@@ -665,7 +693,7 @@ struct BatchItem {
 // The block of one work item: stage the grid's constants (consts_bytes at
 // consts + consts_off, a multiple of 16) at the start of shared memory, where
 // the cell model reads them as its Consts, then run the fused steps.
-template <int N, typename R, typename Cell>
+template <int N, typename R, typename Cell, unsigned kFlags = 0u>
 __device__ __forceinline__ void batch_body(const BatchGrid<R> *__restrict__ grids, const BatchItem *__restrict__ items,
                                            const unsigned char *__restrict__ consts, int parity, int nsteps,
                                            int halo, int tile, int64_t step_offset, unsigned char *smem_raw) {
@@ -701,7 +729,7 @@ __device__ __forceinline__ void batch_body(const BatchGrid<R> *__restrict__ grid
     a.cb = g.cb;
     a.inv_dx = g.inv_dx;
     a.kappa = g.kappa;
-    block_body<N, R, Cell>(a, *reinterpret_cast<const typename Cell::Consts *>(smem_raw), it.tile,
+    block_body<N, R, Cell, kFlags>(a, *reinterpret_cast<const typename Cell::Consts *>(smem_raw), it.tile,
                            smem_raw + kBatchConstsMax);
 }
 
