@@ -537,8 +537,10 @@ mln_status mln_tc_wait_selftest(void);
  * file-scope device array of MLN_STATIC_SCRATCH_BYTES (32 MiB), which every
  * GPU that loads this library holds until the process exits.
  *
- *   p           problem (as for mln_create; kernel must not be MLN_KERNEL_SPARSE,
- *               form not MLN_FORM_ROTATED, field solver MLN_MAXWELL_FDTD).
+ *   p           problem (as for mln_create; kernel MLN_KERNEL_AUTO or
+ *               MLN_KERNEL_REGISTER -- both run the register model here -- form
+ *               not MLN_FORM_ROTATED, field solver MLN_MAXWELL_FDTD; otherwise
+ *               MLN_EINVAL).
  *   d_state, Ez, Hy  caller-owned device buffers with the sizes and layout of
  *               mln_query_buffers: the state in, the state after n_steps out.
  *   init_state  non-zero: first write the initial medium state built from
@@ -551,8 +553,10 @@ mln_status mln_tc_wait_selftest(void);
  * real size) <= MLN_STATIC_SCRATCH_BYTES, else MLN_EINVAL with a message
  * (mln_create_error). The FP64 set-up runs on the host at every call (host
  * heap only). The first call on each device looks up the array's device
- * address with that device current (cudaGetSymbolAddress) and keeps it; make
- * that first call before any stream capture. Every call shares the one array
+ * address with that device current (cudaGetSymbolAddress) and keeps it,
+ * looking it up again when the device's context has changed (for instance
+ * after cudaDeviceReset); make that first call, and the first call after such
+ * a change, before any stream capture. Every call shares the one array
  * and leaves its contents behind (the flag word is cleared at each call), so
  * calls whose work overlaps on the GPU -- on different streams, or from
  * different threads -- race and corrupt each other's results: serialise them.

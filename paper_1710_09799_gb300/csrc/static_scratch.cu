@@ -9,6 +9,7 @@
 // flag word live in one file-scope __device__ array of fixed size, instead of
 // in memory that mln_create allocates. The caller passes the state and field
 // buffers; nothing else is allocated on the device.
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -28,9 +29,30 @@ static __device__ __align__(256) unsigned char g_static_scratch[MLN_STATIC_SCRAT
 constexpr int kMaxDevices = 64;
 std::mutex g_mutex;
 void *g_scratch_addr[kMaxDevices] = {nullptr};
+CUcontext g_scratch_ctx[kMaxDevices] = {nullptr};  // the context the address belongs to
 
-// Device address of the array on the current device, looked up once per
-// device (with that device current) and kept.
+// The current driver context (through the runtime's entry-point query, so the
+// library does not link libcuda); nullptr if that query is unavailable.
+CUcontext current_context() {
+    static CUresult (*get)(CUcontext *) = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void *fn = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &fn, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get = reinterpret_cast<CUresult (*)(CUcontext *)>(fn);
+    }
+    CUcontext ctx = nullptr;
+    if (get && get(&ctx) != CUDA_SUCCESS) ctx = nullptr;
+    return ctx;
+}
+
+// Device address of the array on the current device, looked up with that
+// device current at its first use and kept; looked up again when the
+// device's context has changed since (after cudaDeviceReset the module is
+// loaded anew and the array may sit elsewhere).
 mln_status scratch_address(void **out) {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
@@ -38,7 +60,8 @@ mln_status scratch_address(void **out) {
         return MLN_ECUDA;
     }
     std::lock_guard<std::mutex> lock(g_mutex);
-    if (!g_scratch_addr[dev]) {
+    const CUcontext ctx = current_context();  // nullptr before the runtime has made one current
+    if (!g_scratch_addr[dev] || !ctx || ctx != g_scratch_ctx[dev]) {
         void *ptr = nullptr;
         cudaError_t e = cudaGetSymbolAddress(&ptr, g_static_scratch);
         if (e != cudaSuccess || !ptr) {
@@ -46,6 +69,7 @@ mln_status scratch_address(void **out) {
             return MLN_ECUDA;
         }
         g_scratch_addr[dev] = ptr;
+        g_scratch_ctx[dev] = current_context();  // the lookup has made the device's context current
     }
     *out = g_scratch_addr[dev];
     return MLN_OK;
@@ -93,14 +117,13 @@ mln_status run_static(const mln_params &p, const mln::Setup &s, void *d_state, v
         return MLN_ECUDA;
     }
     if (init_state && n_med > 0) {
+        // the state of rho0 by the set-up's d -> state map, state = sp0 + Sp d0
+        // (as mln_create builds it)
         InitVec<R> v{};
-        for (int k = 0; k < D; ++k) v.v[k] = static_cast<R>(s.d0[k]);
-        if (p.form == MLN_FORM_MERGED) {  // state y = A0 d + b
-            for (int k = 0; k < D; ++k) {
-                double acc = s.b[k];
-                for (int j = 0; j < D; ++j) acc += s.A0[k * D + j] * s.d0[j];
-                v.v[k] = static_cast<R>(acc);
-            }
+        for (int k = 0; k < D; ++k) {
+            double acc = s.sp0[k];
+            for (int j = 0; j < D; ++j) acc += s.Sp[k * D + j] * s.d0[j];
+            v.v[k] = static_cast<R>(acc);
         }
         fill_state_static<R><<<static_cast<unsigned>((n_med + 255) / 256), 256, 0, stream>>>(
             static_cast<R *>(d_state), stride, n_med, D, v);
@@ -208,9 +231,10 @@ mln_status mln_step_noalloc(const mln_params *p, void *d_state, void *Ez, void *
         mln::create_error() = err;
         return st;
     }
-    if (p->kernel == MLN_KERNEL_SPARSE || p->maxwell != MLN_MAXWELL_FDTD || p->form == MLN_FORM_ROTATED) {
-        mln::create_error() = "mln_step_noalloc runs the register cell model (not the rotated form) with the FDTD "
-                              "field solver only";
+    if ((p->kernel != MLN_KERNEL_AUTO && p->kernel != MLN_KERNEL_REGISTER) || p->maxwell != MLN_MAXWELL_FDTD ||
+        p->form == MLN_FORM_ROTATED) {
+        mln::create_error() = "mln_step_noalloc runs the register cell model (kernel MLN_KERNEL_AUTO or "
+                              "MLN_KERNEL_REGISTER; not the rotated form) with the FDTD field solver only";
         return MLN_EINVAL;
     }
     const size_t need = scratch_bytes_for(p);
