@@ -358,9 +358,10 @@ def time_device(p, precision, form, seg, steps, warmup, block_steps, tile_cells,
                 kernel=kern)
 
 
-def time_batch(precision, seg, steps, warmup, sampler=None, kernel="auto"):
+def time_batch(precision, seg, steps, warmup, sampler=None, kernel="auto", launch=None):
     """Batched workload: every bench step advances all devices by seg steps (one
-    graph launch); returns the same fields as time_device."""
+    graph launch); launch "chunks" or "persistent" overrides the library's
+    default launch structure. Returns the same fields as time_device."""
     import torch
     from paper_1710_09799_gb300 import mln
     total = (warmup + steps) * seg
@@ -369,6 +370,8 @@ def time_batch(precision, seg, steps, warmup, sampler=None, kernel="auto"):
     srcs = [d.source_samples(0, total) for d in devs]
     b = mln.Batch(pars, [d.e_init() for d in devs], srcs, total)
     shape = b.autotune(3)
+    if launch is not None:
+        b.set_launch(launch)
     for _ in range(warmup):
         b.step(seg)
     b.sync()
@@ -398,9 +401,10 @@ def time_batch(precision, seg, steps, warmup, sampler=None, kernel="auto"):
         flops += d.n_medium * f_med + d.n_cells * f_cell
     kernels = {N: b.kernel_in_use(N) for N in (2, 3, 4)}
     items = b.shape[2]
+    mode = b.launch
     b.close()
     return dict(ms=ms, ms_local=ms, launches=launches, shape=(shape[0], shape[1], items), clocks=clocks,
-                cells=cells, flops_per_step=flops, devices=len(devs), kernels=kernels)
+                cells=cells, flops_per_step=flops, devices=len(devs), kernels=kernels, launch=mode)
 
 
 def time_e2e(p, precision, form, seg, steps):
@@ -813,7 +817,8 @@ def run_batched(args, ws, rank, local):
     smi_index = int(vis.split(",")[local]) if vis and vis.split(",")[local].isdigit() else local
     prec = args.precision
     r = time_batch(prec, args.seg, args.steps, args.warmup, ClockSampler(smi_index),
-                   kernel=args.kernel if args.kernel in ("register", "jit") else "auto")
+                   kernel=args.kernel if args.kernel in ("register", "jit") else "auto",
+                   launch=None if args.batch_launch == "default" else args.batch_launch)
     total_s = max_over_ranks(ws, r["ms"]) / 1e3
     value = ws * r["cells"] * args.seg * args.steps / total_s
     per_launch_s = r["ms"] / 1e3 / max(r["launches"], 1)
@@ -826,6 +831,7 @@ def run_batched(args, ws, rank, local):
         "config": {"workload": WORKLOADS["batched"], "devices": r["devices"], "cells": r["cells"],
                    "time_steps_per_step": args.seg, "block_steps": r["shape"][0], "tile_cells": r["shape"][1],
                    "work_items_per_launch": r["shape"][2], "cell_model_by_N": r["kernels"],
+                   "launch": r["launch"],
                    "l2": "flushed between steps (256 MiB write)"},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                      "traffic": None,
@@ -854,6 +860,8 @@ def main():
     ap.add_argument("--kernel", default="auto", choices=["auto", "register", "sparse", "jit", "tensor"])
     ap.add_argument("--workload", default="three_level_ring", choices=sorted(WORKLOADS))
     ap.add_argument("--quick", action="store_true", help="skip variants, e2e and the CPU baseline")
+    ap.add_argument("--batch-launch", default="default", choices=["default", "chunks", "persistent"],
+                    help="batched workload: the launch structure (default: the library's)")
     args = ap.parse_args()
     if args.precision is None:
         args.precision = "fp32" if args.workload in ("six_level_pulse", "batched") else "fp64"

@@ -379,7 +379,8 @@ mln_status mln_adjoint(mln_ctx *ctx, int64_t n_steps, const double *src, int64_t
  * mln_batch_step: queue n_steps steps of every grid (async, one graph launch
  * on the batch's own stream, ordered after the work already queued on the
  * creation stream, which in turn waits for the graph).
- * mln_batch_sync: wait; report the first grid's device-side problem.
+ * mln_batch_sync: wait; read and clear every grid's device-side flags and report the
+ * first grid's problem.
  * mln_batch_context: the internal context of grid i, for reading results
  * (mln_get_fields, mln_get_rho, mln_save_state, ...); owned by the batch:
  * do not step or destroy it.
@@ -396,6 +397,22 @@ mln_status mln_adjoint(mln_ctx *ctx, int64_t n_steps, const double *src, int64_t
  * bits.
  * mln_batch_kernel_source: host only; the CUDA source that the batch with
  * these params would compile for its N-level grids (as mln_kernel_source).
+ * mln_batch_set_launch: the launch structure of later mln_batch_step calls.
+ * MLN_BATCH_CHUNKS (the default): one launch per K steps and N, as above.
+ * MLN_BATCH_PERSISTENT: one launch per call and N; its blocks take (chunk,
+ * tile) items in chunk-major order from a device counter and, before chunk c
+ * of a tile, wait until the tiles within halo + 1 cells of it have completed
+ * chunk c - 1 (per-tile progress counters). Same arithmetic, same bits as the
+ * chunked launches. Each wait polls at most wait_limit times (100 ns apart);
+ * a wait that gives up sets a flag, the kernel carries on, and the next
+ * mln_batch_sync returns MLN_ETIMEOUT (wait_limit 0 gives up at once: a test
+ * of that path). Needs the run-time compiled batch kernels (every N of the
+ * batch on MLN_KERNEL_JIT) and tiles of at least K + 2 cells (what
+ * mln_batch_autotune chooses); MLN_EUNSUPPORTED otherwise, MLN_EINVAL for an
+ * unknown mode or a negative limit. Synchronises the batch's stream and
+ * drops its captured graphs.
+ * mln_batch_launch: the launch structure of the next mln_batch_step (-1 for
+ * a NULL batch).
  */
 typedef struct mln_batch mln_batch;
 mln_status mln_batch_create(int32_t count, const mln_params *params, void *const *d_state, void *const *Ez,
@@ -411,6 +428,9 @@ const char *mln_batch_error(const mln_batch *b);
 int32_t mln_batch_kernel_in_use(const mln_batch *b, int32_t N);
 mln_status mln_batch_kernel_source(int32_t count, const mln_params *params, int32_t N, char *buf, size_t cap,
                                    size_t *len);
+enum { MLN_BATCH_CHUNKS = 0, MLN_BATCH_PERSISTENT = 1 };
+mln_status mln_batch_set_launch(mln_batch *b, int32_t mode, int32_t wait_limit);
+int32_t mln_batch_launch(const mln_batch *b);
 void mln_batch_destroy(mln_batch *b);
 
 /* Free the context (NULL-safe). Caller buffers are not touched. */

@@ -774,6 +774,11 @@ mln_status mln_sync(mln_ctx *c) {
         MLN_CK(c, cudaMemset(c->flags, 0, sizeof(unsigned int)));
         return MLN_ETIMEOUT;
     }
+    if (f & 4u) {
+        c->err = "a persistent batch kernel gave up waiting for a neighbouring tile";
+        MLN_CK(c, cudaMemset(c->flags, 0, sizeof(unsigned int)));
+        return MLN_ETIMEOUT;
+    }
     if (f & 1u) {
         c->err = "non-finite E_z on the device";
         MLN_CK(c, cudaMemset(c->flags, 0, sizeof(unsigned int)));

@@ -1,8 +1,10 @@
 // Batched solver: many independent grids (any mix of N = 2..4, lengths and
-// boundaries, one precision) advanced together: every K steps, one launch per
-// N present covers every tile of every grid with that N. The sequence of
-// launches of one mln_batch_step call is captured once into a CUDA graph and
-// replayed.
+// boundaries, one precision) advanced together. Two launch structures, each
+// captured once per mln_batch_step call into a CUDA graph and replayed:
+// every K steps one launch per N present covering every tile of every grid
+// with that N (MLN_BATCH_CHUNKS), or one persistent launch per N for all the
+// call's K-step chunks, tiles waiting on their neighbours' progress counters
+// (MLN_BATCH_PERSISTENT, run-time compiled kernels only).
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -146,7 +148,12 @@ struct mln_batch {
     // per N: run-time compiled kernel over the union sparsity pattern (or
     // nullptr: the padded-constant kernel)
     void *jit[mln::kBatchMaxN + 1] = {};
+    void *jitp[mln::kBatchMaxN + 1] = {};  // the persistent kernel of the same module
     mln::BatchPattern pat[mln::kBatchMaxN + 1];
+    int mode = MLN_BATCH_CHUNKS;
+    int wait_limit = 1 << 22;           // polls of a persistent block's wait (about 0.4 s at 100 ns each)
+    void *d_work = nullptr;             // persistent: one work counter per N
+    void *d_progress = nullptr;         // persistent: chunks completed per work item
     // captured launch sequences, by step count
     std::map<int64_t, cudaGraphExec_t> graphs;
     std::string err;
@@ -272,7 +279,10 @@ mln_status build_tables(mln_batch *b) {
     cudaFree(b->d_grids);
     cudaFree(b->d_items);
     cudaFree(b->d_consts);
-    b->d_grids = b->d_items = b->d_consts = nullptr;
+    cudaFree(b->d_progress);
+    b->d_grids = b->d_items = b->d_consts = b->d_progress = nullptr;
+    MLN_BCK(b, cudaMalloc(&b->d_progress, std::max<size_t>(list.size(), 1) * sizeof(int)));
+    if (!b->d_work) MLN_BCK(b, cudaMalloc(&b->d_work, (mln::kBatchMaxN + 1) * sizeof(unsigned long long)));
     MLN_BCK(b, cudaMalloc(&b->d_grids, grids.size() * sizeof(grids[0])));
     MLN_BCK(b, cudaMalloc(&b->d_items, list.size() * sizeof(list[0])));
     MLN_BCK(b, cudaMalloc(&b->d_consts, std::max<size_t>(blob.size(), 16)));
@@ -319,16 +329,50 @@ int batch_kernels(const mln_batch *b) {
     return k;
 }
 
+// One persistent launch of every chunk of n_steps steps for the items of
+// one N: counters reset, then the kernel (blocks beyond what fits on the GPU
+// wait to start and take the remaining items).
+template <int N, typename R>
+cudaError_t launch_persist_n(mln_batch *b, int64_t n_steps) {
+    if (b->item_cnt[N] == 0) return cudaSuccess;
+    int dev = 0, sms = 152;
+    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    mln::BatchPersist p{};
+    p.work = static_cast<unsigned long long *>(b->d_work) + N;
+    p.progress = static_cast<int *>(b->d_progress) + b->item_off[N];
+    p.n_items = b->item_cnt[N];
+    p.n_chunks = static_cast<int32_t>((n_steps + b->K - 1) / b->K);
+    p.K = b->K;
+    p.last_steps = static_cast<int32_t>(n_steps - static_cast<int64_t>(p.n_chunks - 1) * b->K);
+    p.wait_limit = b->wait_limit;
+    cudaError_t e = cudaMemsetAsync(p.work, 0, sizeof(unsigned long long), b->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(p.progress, 0, p.n_items * sizeof(int), b->stream);
+    if (e != cudaSuccess) return e;
+    const int64_t total = static_cast<int64_t>(p.n_chunks) * p.n_items;
+    const unsigned blocks = static_cast<unsigned>(std::min<int64_t>(total, static_cast<int64_t>(sms) * 8));
+    const size_t smem = batch_smem<R>(b->threads);
+    return mln::jit_launch_batch_persist(b->jitp[N], b->d_grids,
+                                         static_cast<const mln::BatchItem *>(b->d_items) + b->item_off[N],
+                                         b->d_consts, b->K, b->tile, b->steps, p, blocks, b->threads, smem, b->stream);
+}
+
 // Queue the launches of n_steps steps from the batch's current step count;
 // the result ends in buffer set 0 of every grid.
 template <typename R>
 mln_status queue_steps(mln_batch *b, int64_t n_steps) {
     int parity = 0;
-    for (int64_t done = 0; done < n_steps;) {
-        int ns = static_cast<int>(std::min<int64_t>(b->K, n_steps - done));
-        MLN_BCK(b, launch_batch<R>(b, parity, ns, b->steps + done));
-        parity ^= 1;
-        done += ns;
+    if (b->mode == MLN_BATCH_PERSISTENT) {
+        MLN_BCK(b, (launch_persist_n<4, R>(b, n_steps)));
+        MLN_BCK(b, (launch_persist_n<3, R>(b, n_steps)));
+        MLN_BCK(b, (launch_persist_n<2, R>(b, n_steps)));
+        parity = static_cast<int>(((n_steps + b->K - 1) / b->K) & 1);
+    } else {
+        for (int64_t done = 0; done < n_steps;) {
+            int ns = static_cast<int>(std::min<int64_t>(b->K, n_steps - done));
+            MLN_BCK(b, launch_batch<R>(b, parity, ns, b->steps + done));
+            parity ^= 1;
+            done += ns;
+        }
     }
     if (parity == 1) {
         for (mln_ctx *c : b->ctx) {
@@ -353,7 +397,9 @@ mln_status autotune_batch(mln_batch *b, int trials) {
     int bestK = b->K, bestTile = b->tile;
     for (int K : Ks)
         for (int tile : tiles) {
-            if (tile + 2 * K > mln::kBatchThreads) continue;
+            // tiles longer than their halo (+ 1 for a tile made of a Mur cell): a tile's
+            // halo covers only its two neighbours (the persistent launch relies on it)
+            if (tile + 2 * K > mln::kBatchThreads || tile < K + 2) continue;
             b->K = K;
             b->tile = tile;
             b->threads = (tile + 2 * K + 31) / 32 * 32;
@@ -397,6 +443,8 @@ void mln_batch_destroy(mln_batch *b) {
     cudaFree(b->d_grids);
     cudaFree(b->d_items);
     cudaFree(b->d_consts);
+    cudaFree(b->d_progress);
+    cudaFree(b->d_work);
     for (mln_ctx *c : b->ctx) mln_destroy(c);
     delete b;
 }
@@ -464,9 +512,10 @@ mln_status mln_batch_create(int32_t count, const mln_params *params, void *const
         for (int N = 2; N <= mln::kBatchMaxN; ++N) {
             if (b->pat[N].N == 0) continue;
             std::string log;
-            if (mln::jit_compile(mln::jit_batch_source(b->pat[N], fp32), &b->jit[N], log, "mln_jit_batch") !=
-                cudaSuccess) {
-                b->jit[N] = nullptr;
+            const std::string src_n = mln::jit_batch_source(b->pat[N], fp32);
+            if (mln::jit_compile(src_n, &b->jit[N], log, "mln_jit_batch") != cudaSuccess ||
+                mln::jit_compile(src_n, &b->jitp[N], log, "mln_jit_batch_persist") != cudaSuccess) {
+                b->jit[N] = b->jitp[N] = nullptr;
                 why = log;
             }
         }
@@ -544,7 +593,7 @@ mln_status mln_batch_step(mln_batch *b, int64_t n_steps) {
     MLN_BCK(b, cudaEventRecord(b->ev_out, b->stream));
     MLN_BCK(b, cudaStreamWaitEvent(b->user, b->ev_out, 0));
     const int64_t per = (n_steps + b->K - 1) / b->K;
-    b->launches += per * batch_kernels(b);
+    b->launches += (b->mode == MLN_BATCH_PERSISTENT ? 1 : per) * batch_kernels(b);
     b->steps += n_steps;
     for (mln_ctx *c : b->ctx) {
         c->steps += n_steps;
@@ -553,18 +602,42 @@ mln_status mln_batch_step(mln_batch *b, int64_t n_steps) {
     return MLN_OK;
 }
 
+mln_status mln_batch_set_launch(mln_batch *b, int32_t mode, int32_t wait_limit) {
+    if (!b || (mode != MLN_BATCH_CHUNKS && mode != MLN_BATCH_PERSISTENT) || wait_limit < 0) return MLN_EINVAL;
+    if (mode == MLN_BATCH_PERSISTENT) {
+        for (mln_ctx *c : b->ctx)
+            if (!b->jitp[c->p.N]) {
+                b->err = "the persistent launch needs the run-time compiled batch kernels";
+                return MLN_EUNSUPPORTED;
+            }
+        if (b->tile < b->K + 2) {
+            b->err = "the persistent launch needs tiles longer than K + 1 cells";
+            return MLN_EUNSUPPORTED;
+        }
+    }
+    MLN_BCK(b, cudaStreamSynchronize(b->stream));
+    drop_graphs(b);
+    b->mode = mode;
+    b->wait_limit = wait_limit;
+    return MLN_OK;
+}
+
+int32_t mln_batch_launch(const mln_batch *b) { return b ? b->mode : -1; }
+
 mln_status mln_batch_sync(mln_batch *b) {
     if (!b) return MLN_EINVAL;
     MLN_BCK(b, cudaStreamSynchronize(b->stream));
     MLN_BCK(b, cudaStreamSynchronize(b->user));
+    // every grid's flag word is read and cleared; the first grid's problem is reported
+    mln_status first = MLN_OK;
     for (size_t i = 0; i < b->ctx.size(); ++i) {
         mln_status st = mln_sync(b->ctx[i]);
-        if (st != MLN_OK) {
+        if (st != MLN_OK && first == MLN_OK) {
             b->err = "grid " + std::to_string(i) + ": " + mln_last_error(b->ctx[i]);
-            return st;
+            first = st;
         }
     }
-    return MLN_OK;
+    return first;
 }
 
 mln_ctx *mln_batch_context(mln_batch *b, int32_t i) {

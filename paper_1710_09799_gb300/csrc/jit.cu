@@ -62,7 +62,7 @@ Nvrtc g_nvrtc;
 Driver g_drv;
 bool g_tried = false;
 std::string g_why;
-std::map<std::pair<int, std::string>, CUfunction> g_cache;  // (device, source) -> kernel
+std::map<std::pair<int, std::string>, CUmodule> g_cache;  // (device, source) -> loaded module
 
 template <typename F>
 bool sym(void *h, const char *name, F &f) {
@@ -320,6 +320,8 @@ std::string jit_batch_source(const BatchPattern &pat, bool fp32) {
     o << " }\n"
       << "  __device__ __forceinline__ void load(const " << R
       << " *src, int64_t stride, int64_t m) { for (int i = 0; i < D; ++i) s[i] = src[i * stride + m]; }\n"
+      << "  __device__ __forceinline__ void load_cg(const " << R
+      << " *src, int64_t stride, int64_t m) { for (int i = 0; i < D; ++i) s[i] = __ldcg(src + i * stride + m); }\n"
       << "  __device__ __forceinline__ void store(" << R
       << " *dst, int64_t stride, int64_t m) const { for (int i = 0; i < D; ++i) dst[i * stride + m] = s[i]; }\n"
       << "  __device__ __forceinline__ void end_step() {}\n"
@@ -375,6 +377,13 @@ std::string jit_batch_source(const BatchPattern &pat, bool fp32) {
       << "  extern __shared__ __align__(16) unsigned char smem_raw[];\n"
       << "  batch_body<" << N << ", " << R << ", JitBatchCell, " << (pat.flags == ~0u ? 0u : pat.flags)
       << "u>(grids, items, consts, parity, nsteps, halo, tile, step_offset, smem_raw);\n}\n"
+      // every chunk of a call in one persistent launch (see batch_persistent)
+      << "extern \"C\" __global__ void __launch_bounds__(kBatchThreads, 1) mln_jit_batch_persist(const BatchGrid<" << R
+      << "> *grids, const BatchItem *items, const unsigned char *consts, int halo, int tile, int64_t step_offset, "
+         "BatchPersist p) {\n"
+      << "  extern __shared__ __align__(16) unsigned char smem_raw[];\n"
+      << "  batch_persistent<" << N << ", " << R << ", JitBatchCell, " << (pat.flags == ~0u ? 0u : pat.flags)
+      << "u>(grids, items, consts, halo, tile, step_offset, p, smem_raw);\n}\n"
       << "}  // namespace mln\n";
     return o.str();
 }
@@ -396,8 +405,13 @@ cudaError_t jit_compile(const std::string &src, void **fn, std::string &log, con
     cudaGetDevice(&dev);
     auto key = std::make_pair(dev, src);
     auto it = g_cache.find(key);
-    if (it != g_cache.end()) {
-        *fn = it->second;
+    if (it != g_cache.end()) {  // compiled before: look the kernel up by name
+        CUfunction f = nullptr;
+        if (g_drv.get(&f, it->second, name) != CUDA_SUCCESS) {
+            log = std::string("no kernel ") + name + " in the compiled module";
+            return cudaErrorUnknown;
+        }
+        *fn = f;
         return cudaSuccess;
     }
     nvrtcProgram_t prog = nullptr;
@@ -427,7 +441,7 @@ cudaError_t jit_compile(const std::string &src, void **fn, std::string &log, con
         log = "loading the compiled kernel failed";
         return cudaErrorUnknown;
     }
-    g_cache[key] = f;  // modules stay loaded until the process exits
+    g_cache[key] = mod;  // modules stay loaded until the process exits
     *fn = f;
     return cudaSuccess;
 }
@@ -470,6 +484,16 @@ cudaError_t jit_launch_batch(void *fn, const void *grids, const void *items, con
                              int nsteps, int halo, int tile, int64_t step_offset, unsigned nblocks, unsigned threads,
                              size_t smem, cudaStream_t st) {
     void *params[] = {&grids, &items, &consts, &parity, &nsteps, &halo, &tile, &step_offset};
+    CUresult r = g_drv.launch(static_cast<CUfunction>(fn), nblocks, 1, 1, threads, 1, 1, static_cast<unsigned>(smem),
+                              static_cast<CUstream>(st), params, nullptr);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorLaunchFailure;
+}
+
+cudaError_t jit_launch_batch_persist(void *fn, const void *grids, const void *items, const void *consts, int halo,
+                                     int tile, int64_t step_offset, const BatchPersist &p, unsigned nblocks,
+                                     unsigned threads, size_t smem, cudaStream_t st) {
+    BatchPersist pp = p;
+    void *params[] = {&grids, &items, &consts, &halo, &tile, &step_offset, &pp};
     CUresult r = g_drv.launch(static_cast<CUfunction>(fn), nblocks, 1, 1, threads, 1, 1, static_cast<unsigned>(smem),
                               static_cast<CUstream>(st), params, nullptr);
     return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorLaunchFailure;

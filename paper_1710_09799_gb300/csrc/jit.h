@@ -51,6 +51,10 @@ cudaError_t jit_launch_batch(void *fn, const void *grids, const void *items, con
                              int nsteps, int halo, int tile, int64_t step_offset, unsigned nblocks, unsigned threads,
                              size_t smem, cudaStream_t st);
 
+// The persistent batch kernel of the same module (compiled as "mln_jit_batch_persist").
+cudaError_t jit_launch_batch_persist(void *fn, const void *grids, const void *items, const void *consts, int halo,
+                                     int tile, int64_t step_offset, const BatchPersist &p, unsigned nblocks,
+                                     unsigned threads, size_t smem, cudaStream_t st);
 cudaError_t jit_launch(void *fn, const BlockArgs<double> &a, dim3 g, dim3 b, size_t smem, cudaStream_t st);
 cudaError_t jit_launch(void *fn, const BlockArgs<float> &a, dim3 g, dim3 b, size_t smem, cudaStream_t st);
 

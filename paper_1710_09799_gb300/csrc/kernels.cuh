@@ -528,6 +528,8 @@ enum : unsigned {
     kBodyNoSrc = 4u,  // no source samples
     kBodyNoRec = 8u,  // no recording of the steps
     kBodyUnroll = 16u,  // two steps per loop iteration (buffers at fixed addresses; more registers)
+    kBodyCg = 32u,      // inputs read through L2 only (ld.global.cg): other blocks of the same
+                        // launch wrote them, and this SM's L1 may hold an older copy
 };
 
 // One thread block advances tile `tile_index` of one grid by a.nsteps steps.
@@ -568,11 +570,22 @@ __device__ __forceinline__ void block_body(const BlockArgs<R> &a, const typename
 
     Cell cell;
     cell.setup(smem + field_smem<R>(blockDim.x), k);
-    R e = loaded ? a.E_in[gm] : R(0);
-    R h = loaded ? a.H_in[gm] : R(0);
+    R e = R(0), h = R(0);
+    if constexpr ((kFlags & kBodyCg) != 0u) {
+        if (loaded) {
+            e = __ldcg(a.E_in + gm);
+            h = __ldcg(a.H_in + gm);
+        }
+        if (medium) cell.load_cg(a.s_in, a.stride, m);
+    } else {
+        if (loaded) {
+            e = a.E_in[gm];
+            h = a.H_in[gm];
+        }
+        if (medium) cell.load(a.s_in, a.stride, m);
+    }
     bufE0[j] = e;
     bufH0[j] = h;
-    if (medium) cell.load(a.s_in, a.stride, m);
 
     // H_{i+1/2} exists for every cell of a ring and for cells 0..n-2 of an open grid;
     // it needs E of the next loaded cell.
@@ -696,8 +709,9 @@ struct BatchItem {
 template <int N, typename R, typename Cell, unsigned kFlags = 0u>
 __device__ __forceinline__ void batch_body(const BatchGrid<R> *__restrict__ grids, const BatchItem *__restrict__ items,
                                            const unsigned char *__restrict__ consts, int parity, int nsteps,
-                                           int halo, int tile, int64_t step_offset, unsigned char *smem_raw) {
-    const BatchItem it = items[blockIdx.x];
+                                           int halo, int tile, int64_t step_offset, unsigned char *smem_raw,
+                                           int64_t item_index = -1) {
+    const BatchItem it = items[item_index >= 0 ? item_index : static_cast<int64_t>(blockIdx.x)];
     const BatchGrid<R> &g = grids[it.grid];
     for (int o = threadIdx.x * 16; o < g.consts_bytes; o += blockDim.x * 16)
         *reinterpret_cast<uint4 *>(smem_raw + o) = *reinterpret_cast<const uint4 *>(consts + g.consts_off + o);
@@ -731,6 +745,100 @@ __device__ __forceinline__ void batch_body(const BatchGrid<R> *__restrict__ grid
     a.kappa = g.kappa;
     block_body<N, R, Cell, kFlags>(a, *reinterpret_cast<const typename Cell::Consts *>(smem_raw), it.tile,
                            smem_raw + kBatchConstsMax);
+}
+
+// One persistent launch for all K-step chunks of a call over the work items
+// of one N. Blocks take items (chunk c, item i) from a counter in
+// chunk-major order; before chunk c of a tile, one thread waits until the
+// tile and every tile of its grid within halo + 1 cells of it (those whose
+// cells it reads, and whose reads cover its cells: the two neighbours, and a
+// tile beyond a neighbour as short as the ragged last one) have completed
+// chunk c - 1, then the block runs the chunk and publishes the tile's
+// progress. An item is only taken by a block that is running, and it
+// waits only for items with smaller indices, which running blocks hold, so
+// the waits end without any guarantee of co-residency; each is still bounded
+// (wait_limit polls; 0 gives up at once, for testing) and a wait that gives up
+// sets bit 2 of the grid's flag word and lets the block go on.
+struct BatchPersist {
+    unsigned long long *work;  // next item index (zero at the launch)
+    int *progress;             // chunks completed, per item of this N (zero at the launch)
+    int64_t n_items;
+    int32_t n_chunks, K, last_steps, wait_limit;
+};
+
+__device__ __forceinline__ int ld_acquire(const int *p) {
+    int v;
+    asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release(int *p, int v) {
+    asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Wait until *progress >= c, for at most `limit` polls; false if it gave up.
+__device__ __forceinline__ bool batch_wait(const int *progress, int c, int limit) {
+    int polls = 0;
+    while (ld_acquire(progress) < c) {
+        if (++polls > limit) return false;
+        __nanosleep(100);
+    }
+    return true;
+}
+
+// The waits before chunk c of item i (tile it.tile of its grid): the item
+// itself, then outwards in each direction every tile of the grid whose cells
+// start within halo + 1 cells of this tile (wrapping on a ring; the grid's
+// tiles are consecutive items). False if a wait gave up.
+template <typename R>
+__device__ bool batch_wait_deps(const BatchGrid<R> &g, const BatchItem &it, const int *progress, int64_t i, int c,
+                                int halo, int tile, int limit) {
+    if (limit <= 0 || !batch_wait(progress + i, c, limit)) return false;
+    const int64_t nt = (g.n_cells + tile - 1) / tile;
+    for (int dir = -1; dir <= 1; dir += 2) {
+        int64_t gap = 0;  // cells strictly between this tile and tile t
+        for (int64_t s = 1; s < nt && gap <= halo; ++s) {
+            int64_t t = it.tile + dir * s;
+            if (t < 0 || t >= nt) {
+                if (g.boundary != 0) break;  // open grid: nothing beyond its ends
+                t = t < 0 ? t + nt : t - nt;
+            }
+            if (!batch_wait(progress + i + (t - it.tile), c, limit)) return false;
+            gap += min(static_cast<int64_t>(tile), g.n_cells - t * tile);
+        }
+    }
+    return true;
+}
+
+template <int N, typename R, typename Cell, unsigned kFlags = 0u>
+__device__ __forceinline__ void batch_persistent(const BatchGrid<R> *__restrict__ grids,
+                                                 const BatchItem *__restrict__ items,
+                                                 const unsigned char *__restrict__ consts, int halo, int tile,
+                                                 int64_t step_offset, const BatchPersist &p, unsigned char *smem_raw) {
+    __shared__ long long q_sh;
+    const int64_t total = static_cast<int64_t>(p.n_chunks) * p.n_items;
+    for (;;) {
+        if (threadIdx.x == 0) q_sh = static_cast<long long>(atomicAdd(p.work, 1ull));
+        __syncthreads();
+        const int64_t q = q_sh;
+        __syncthreads();  // every thread has read q_sh before the next item's fetch
+        if (q >= total) break;
+        const int c = static_cast<int>(q / p.n_items);
+        const int64_t i = q % p.n_items;
+        if (threadIdx.x == 0 && c > 0) {
+            const BatchItem it = items[i];
+            if (!batch_wait_deps(grids[it.grid], it, p.progress, i, c, halo, tile, p.wait_limit))
+                atomicOr(grids[it.grid].flags, 4u);
+        }
+        __syncthreads();
+        const int ns = c == p.n_chunks - 1 ? p.last_steps : p.K;
+        batch_body<N, R, Cell, kFlags | kBodyCg>(grids, items, consts, c & 1, ns, halo, tile,
+                                                 step_offset + static_cast<int64_t>(c) * p.K, smem_raw, i);
+        __syncthreads();  // every thread's writes of the chunk are done
+        if (threadIdx.x == 0) {
+            __threadfence();
+            st_release(p.progress + i, c + 1);
+        }
+    }
 }
 
 template <int N, typename R, typename Cell>

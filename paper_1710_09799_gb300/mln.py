@@ -26,6 +26,7 @@ MLN_FP64, MLN_FP32 = 0, 1
 MLN_FORM_STRANG, MLN_FORM_MERGED, MLN_FORM_RODRIGUES, MLN_FORM_ROTATED = 0, 1, 2, 3
 MLN_KERNEL_AUTO, MLN_KERNEL_REGISTER, MLN_KERNEL_SPARSE, MLN_KERNEL_JIT, MLN_KERNEL_TENSOR = 0, 1, 2, 3, 4
 MLN_MIN_N, MLN_MAX_N = 2, 6
+MLN_BATCH_CHUNKS, MLN_BATCH_PERSISTENT = 0, 1
 _DMAX = MLN_MAX_N * MLN_MAX_N - 1
 
 BOUNDARY = {"periodic": MLN_BC_PERIODIC, "open": MLN_BC_OPEN}
@@ -115,6 +116,8 @@ _SIGS = {
     "mln_batch_error": (C.c_char_p, [C.c_void_p]),
     "mln_batch_kernel_in_use": (C.c_int32, [C.c_void_p, C.c_int32]),
     "mln_batch_kernel_source": (C.c_int, [C.c_int32, _P, C.c_int32, C.c_char_p, C.c_size_t, C.POINTER(C.c_size_t)]),
+    "mln_batch_set_launch": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32]),
+    "mln_batch_launch": (C.c_int32, [C.c_void_p]),
     "mln_batch_destroy": (None, [C.c_void_p]),
     "mln_rotation_terms": (C.c_int, [C.c_int32, _dp, C.c_int64, _dp, _dp]),
     "mln_tc_product": (C.c_int, [C.c_int32, C.c_int32, C.c_int32, C.POINTER(C.c_float), _dp,
@@ -606,6 +609,10 @@ def mln_batch_shape(b):
     return k.value, t.value, it.value, la.value
 
 
+def mln_batch_set_launch(b, mode: int, wait_limit: int = 1 << 22):
+    _bcheck(lib().mln_batch_set_launch(b, mode, wait_limit), b)
+
+
 def mln_batch_destroy(b):
     if b:
         lib().mln_batch_destroy(b)
@@ -646,6 +653,17 @@ class Batch:
         """Cell model of the N-level grids ("jit" or "register"), None if none."""
         k = lib().mln_batch_kernel_in_use(self.b, N)
         return None if k < 0 else {v: n for n, v in KERNEL.items()}[k]
+
+    def set_launch(self, launch: str, wait_limit: int = 1 << 22):
+        """"chunks" (one launch per K steps and N) or "persistent" (one launch
+        per call and N, tiles waiting on their neighbours' progress)."""
+        mode = {"chunks": MLN_BATCH_CHUNKS, "persistent": MLN_BATCH_PERSISTENT}[launch]
+        mln_batch_set_launch(self.b, mode, wait_limit)
+
+    @property
+    def launch(self) -> str:
+        """The launch structure of the next steps: "chunks" or "persistent"."""
+        return {MLN_BATCH_CHUNKS: "chunks", MLN_BATCH_PERSISTENT: "persistent"}[lib().mln_batch_launch(self.b)]
 
     def step(self, n_steps: int):
         mln_batch_step(self.b, n_steps)

@@ -75,6 +75,9 @@ def test_batch_source_compiles_and_follows_the_union_pattern(lib, tmp_path, prec
     # T^T and T once per union entry, C1 once per union entry, at most D terms of wm
     assert n_terms <= 2 * int(union_T.sum()) + int(union_C1.sum()) + D
     assert n_terms >= 2 * int(union_T.sum()) + int(union_C1.sum())
+    # the chunked and the persistent batch kernels come from the same module
+    assert "void __launch_bounds__(kBatchThreads, 1) mln_jit_batch(" in src
+    assert "mln_jit_batch_persist(" in src
     f = tmp_path / "b.cu"
     f.write_text(src)
     r = subprocess.run([nvcc, "-gencode", "arch=compute_103a,code=sm_103a", "-std=c++17", "-c", str(f),
