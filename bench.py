@@ -802,7 +802,8 @@ def run_adjoint(args, ws, rank, local):
         "ms_per_step": 1e3 * tot / len(times), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64" if args.precision == "fp64" else "f32", "data": "synthetic (seeded)",
         "config": {"workload": WORKLOADS["adjoint"], "n_cells": p.n_cells, "time_steps": p.n_steps,
-                   "checkpoint_every": 256, "gradients": "512 source samples, 9 dipole parameters, 81 x 81 G"},
+                   "checkpoint_every": 256, "gradients": "512 source samples, 9 dipole parameters, 81 x 81 G",
+                   "forward_launch_shape": {"block_steps": par.s.block_steps, "tile_cells": par.s.tile_cells}},
         "forward_only_cell_updates_per_s": p.n_cells * p.n_steps / t_fwd,
         "gradient_cost_over_forward": (tot / len(times)) / t_fwd,
         "J": J, "dJ_dmu12": float(dmu[p.N]),

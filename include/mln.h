@@ -335,8 +335,14 @@ mln_status mln_load_state(mln_ctx *ctx, const double *d_host, const double *Ez_h
  *   src         as for mln_step (device, n_steps samples) or NULL.
  *   every       checkpoint interval: the forward pass saves the state every
  *               `every` steps; the backward pass recomputes each segment from
- *               its checkpoint and keeps its every + 1 states (device memory
- *               about (n_steps / every + every) x the state and field bytes).
+ *               its checkpoint, keeping each step's state, fields and traced
+ *               intermediates (a "set", about 3 x the state bytes). When the
+ *               sets of all segments (about n_steps + n_steps / every of them)
+ *               fit the memory limit (mln_set_adjoint_memory), every segment
+ *               is recomputed at once, side by side, after the forward pass;
+ *               otherwise two segments' sets are kept and segment s - 1 is
+ *               recomputed while the reverse sweep of segment s runs. Both
+ *               give the same bits.
  *   out->J      the objective.
  *   out->dJ_dsrc  NULL or n_steps doubles: dJ / d(source sample k).
  *   out->dJ_dmu   NULL or N*N doubles: dJ / d mu_ll (l = 0..N-1), then
@@ -348,6 +354,11 @@ mln_status mln_load_state(mln_ctx *ctx, const double *d_host, const double *Ez_h
  *               superoperator of the parameter set (zero rows and columns included).
  * Device memory for checkpoints and adjoints is allocated inside the call and
  * freed before it returns. Synchronises.
+ *
+ * mln_set_adjoint_memory: the most device memory, in bytes, that mln_adjoint
+ * on this context may take for the recorded sets of all segments at once;
+ * 0 (the default): half the free device memory at the call. MLN_EINVAL for a
+ * negative value.
  */
 typedef struct mln_adjoint_out {
     double J;
@@ -355,6 +366,7 @@ typedef struct mln_adjoint_out {
     double *dJ_dmu;
     double *dJ_dG;
 } mln_adjoint_out;
+mln_status mln_set_adjoint_memory(mln_ctx *ctx, int64_t bytes);
 mln_status mln_adjoint(mln_ctx *ctx, int64_t n_steps, const double *src, int64_t probe_cell, int32_t every,
                        mln_adjoint_out *out);
 

@@ -5,7 +5,7 @@
 // saving the state at the start of every segment of `every` steps.
 // Backward: for the segments in reverse order, the segment is recomputed from
 // its checkpoint in the literal Strang form by the fused step kernel with
-// every step's state recorded (all its states kept; a checkpoint of another
+// every step's state and intermediates recorded (all kept; a checkpoint of another
 // form is first mapped to the adjoint vector d, which these forms share up to
 // rounding: the merged and rotated forms hold an affine image of d), then the
 // reverse step kernel runs from the segment's last step to its first,
@@ -73,6 +73,7 @@ __global__ void state_to_d(const R *__restrict__ s, R *__restrict__ d, int64_t s
 template <typename R>
 struct Set {
     R *E, *H, *S;
+    R *I;  // traced intermediates of the step that starts from this set
 };
 
 template <int N, typename R>
@@ -83,7 +84,11 @@ mln_status adjoint_t(mln_ctx *c, int64_t n_steps, const double *src, int64_t pro
     mln_status st = MLN_OK;
     const int64_t n = c->p.n_cells;
     const size_t sb = c->state_bytes, fb = c->field_bytes;
-    const size_t set_bytes = (sb + 2 * fb + 255) / 256 * 256;
+    // a set: state, E, H, then the intermediates of the step from it
+    // (2 D + 2 q rows of `stride`, see StrangTraceCell)
+    const size_t ib = static_cast<size_t>(2 * mln::Dims<N>::D + 2 * mln::Dims<N>::Q) * c->stride * sizeof(R);
+    const size_t off_I = (sb + 2 * fb + 255) / 256 * 256;
+    const size_t set_bytes = (off_I + ib + 255) / 256 * 256;
     const int64_t nseg = (n_steps + every - 1) / every;
     unsigned char *ckpt = nullptr, *slots = nullptr, *adj = nullptr;
     double *dsrc = nullptr, *acc = nullptr, *accsum = nullptr;
@@ -91,7 +96,8 @@ mln_status adjoint_t(mln_ctx *c, int64_t n_steps, const double *src, int64_t pro
     const mln::AdjConsts<N, R> k = adj_consts<N, R>(c->s, c->p.dt);
     auto set_at = [&](unsigned char *base, int64_t i) {
         unsigned char *p = base + i * set_bytes;
-        return Set<R>{reinterpret_cast<R *>(p + sb), reinterpret_cast<R *>(p + sb + fb), reinterpret_cast<R *>(p)};
+        return Set<R>{reinterpret_cast<R *>(p + sb), reinterpret_cast<R *>(p + sb + fb), reinterpret_cast<R *>(p),
+                      reinterpret_cast<R *>(p + off_I)};
     };
     auto copy_set = [&](Set<R> dst, Set<R> from, cudaStream_t strm) {
         cudaError_t e = cudaMemcpyAsync(dst.S, from.S, sb, cudaMemcpyDeviceToDevice, strm);
@@ -99,7 +105,7 @@ mln_status adjoint_t(mln_ctx *c, int64_t n_steps, const double *src, int64_t pro
         if (e == cudaSuccess) e = cudaMemcpyAsync(dst.H, from.H, fb, cudaMemcpyDeviceToDevice, strm);
         return e;
     };
-    const Set<R> user{static_cast<R *>(c->E[0]), static_cast<R *>(c->H[0]), static_cast<R *>(c->st[0])};
+    const Set<R> user{static_cast<R *>(c->E[0]), static_cast<R *>(c->H[0]), static_cast<R *>(c->st[0]), nullptr};
     mln::BlockArgs<R> fa = mln::base_args<R>(c);
     // Reverse sweep: K steps per launch over tiles with K-cell halos (one more
     // on the right of an open grid), cells of AdjLanes lanes, 512 threads per
@@ -116,29 +122,67 @@ mln_status adjoint_t(mln_ctx *c, int64_t n_steps, const double *src, int64_t pro
     std::vector<unsigned char> strang;
     const bool convert = c->p.form != MLN_FORM_STRANG;  // checkpoints hold another form's state
     if (!mln::pack_consts(c->s, MLN_FORM_STRANG, c->p.dt, static_cast<R>(0), strang)) return MLN_EUNSUPPORTED;
-    // Recompute: the context's launch shape (fused steps per launch, tile,
-    // threads; autotuned if the caller did), every step recorded into its slot.
-    const int rK = c->K, rthreads = c->threads;
+    // Recompute: the context's fused steps per launch (autotuned if the
+    // caller did), at most 256 threads a block (the tracing kernel's bound);
+    // every step recorded into its slot. One segment at a time runs the
+    // context's tile (its latency-bound shape); segments side by side run the
+    // longest tile (least halo: the launch has work for every SM).
+    const int rK = std::min(c->K, 64);
+    const int tile_one = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(c->tile, 256 - 2 * rK)));
+    const int tile_many = std::max(tile_one, 256 - 2 * rK);
     mln::AdjBlockArgs<R> aa{};
     Set<R> A0s, A1s;
-    // Two slot buffers: segment s - 1 is recomputed on a second stream while the
-    // reverse sweep of segment s runs (the two kernels are independent and each
-    // leaves most of the GPU idle on rings of this size); events order the
-    // recompute after the sweep that last used its buffer, and each sweep after
-    // its recompute.
+    // Two ways to schedule the recomputation (segments are independent given
+    // their checkpoints; a ring of a few thousand cells leaves most of the GPU
+    // idle in one segment's launches):
+    // - all at once, when every segment's slot fits in half the free device
+    //   memory: after the forward pass, each launch advances the same steps of
+    //   all full segments side by side (grid y = segment), then the reverse
+    //   sweeps run segment after segment;
+    // - otherwise two slot buffers: segment s - 1 is recomputed on a second
+    //   stream while the reverse sweep of segment s runs; events order the
+    //   recompute after the sweep that last used its buffer, and each sweep
+    //   after its recompute.
     cudaStream_t rs = nullptr;
     cudaEvent_t ev_fwd = nullptr, ev_rec[2] = {nullptr, nullptr}, ev_rev[2] = {nullptr, nullptr};
     unsigned char *slot_buf[2] = {nullptr, nullptr};
     const size_t slot_bytes = static_cast<size_t>(every + 1) * set_bytes;
-    // segment sg from its checkpoint into slots, every step recorded, on stream strm
-    auto recompute = [&](int64_t sg, unsigned char *sl, cudaStream_t strm) -> cudaError_t {
-        const int64_t g0 = sg * every, glen = std::min<int64_t>(every, n_steps - g0);
+    const int64_t nfull = n_steps / every;  // segments of `every` steps
+    int64_t launches = 0;
+    bool all_at_once = false;
+    {
+        size_t free_b = 0, total_b = 0;
+        if (nfull <= 65535 && cudaMemGetInfo(&free_b, &total_b) == cudaSuccess) {
+            const double limit = c->adj_mem > 0 ? static_cast<double>(c->adj_mem) : 0.5 * static_cast<double>(free_b);
+            all_at_once = static_cast<double>(nseg) * static_cast<double>(slot_bytes) <= limit;
+        }
+    }
+    auto slot_of = [&](int64_t sg) { return all_at_once ? slots + sg * slot_bytes : slot_buf[sg & 1]; };
+    // A Strang-form context whose step is the register model (the tracing
+    // kernel's arithmetic) and whose segments all fit: its forward pass can
+    // record the segments itself, so nothing is recomputed.
+    const bool traced_forward = all_at_once && c->p.form == MLN_FORM_STRANG && !c->jit_fn && !c->sparse && !c->tc &&
+                                !c->pstd;
+    // the segment's checkpoint into set 0 of its slot (as d), on stream strm
+    auto prepare = [&](int64_t sg, unsigned char *sl, cudaStream_t strm) -> cudaError_t {
         cudaError_t e = copy_set(set_at(sl, 0), set_at(ckpt, sg), strm);
         if (e == cudaSuccess && convert && c->n_med > 0) {
             state_to_d<R><<<static_cast<unsigned>((c->n_med + 127) / 128), 128, 0, strm>>>(
                 set_at(ckpt, sg).S, set_at(sl, 0).S, c->stride, c->n_med, c->D, c->tab_d);
             e = cudaGetLastError();
         }
+        return e;
+    };
+    // steps of `segs` segments side by side from the slot sl of the first
+    // (the others seg_bytes apart), every step recorded, on stream strm
+    auto run_segments = [&](int64_t sg, int64_t segs, int64_t glen, unsigned char *sl, cudaStream_t strm,
+                            bool programmatic = false) -> cudaError_t {
+        const int64_t g0 = sg * every;
+        const int rtile = segs > 1 ? tile_many : tile_one;
+        const int rthreads = (rtile + 2 * rK + 31) / 32 * 32;
+        cudaError_t e = cudaSuccess;
+        fa.seg_bytes = static_cast<int64_t>(slot_bytes);
+        fa.seg_src = every;
         for (int64_t j = 0; e == cudaSuccess && j < glen; j += rK) {
             const int ns = static_cast<int>(std::min<int64_t>(rK, glen - j));
             const Set<R> in = set_at(sl, j), o = set_at(sl, j + ns), r1 = set_at(sl, j + 1);
@@ -151,21 +195,32 @@ mln_status adjoint_t(mln_ctx *c, int64_t n_steps, const double *src, int64_t pro
             fa.rec_E = r1.E;
             fa.rec_H = r1.H;
             fa.rec_S = r1.S;
+            fa.rec_I = in.I;
             fa.rec_set = static_cast<int64_t>(set_bytes);
             fa.nsteps = ns;
             fa.src = (src && c->p.source_kind != MLN_SRC_NONE) ? src + g0 + j : nullptr;
             // plain launches: the recompute runs beside the reverse sweep, and
             // blocks placed early by programmatic launches took SM resources
             // from it (FP64 gradient 1.77e8 -> 1.56e8 cell-updates/s)
-            e = mln::launch_block(c->p.N, MLN_FORM_STRANG, fa, strang,
-                                  dim3(static_cast<unsigned>((n + c->tile - 1) / c->tile)), dim3(rthreads),
-                                  mln::field_smem<R>(rthreads), strm, false);
+            fa.halo = rK;
+            fa.tile = rtile;
+            e = mln::launch_block_trace(c->p.N, fa, strang,
+                                        dim3(static_cast<unsigned>((n + rtile - 1) / rtile),
+                                             static_cast<unsigned>(segs)),
+                                        dim3(rthreads), mln::field_smem<R>(rthreads), strm, programmatic);
+            ++launches;
         }
+        return e;
+    };
+    // segment sg from its checkpoint into slot sl, on stream strm
+    auto recompute = [&](int64_t sg, unsigned char *sl, cudaStream_t strm) -> cudaError_t {
+        cudaError_t e = prepare(sg, sl, strm);
+        if (e == cudaSuccess) e = run_segments(sg, 1, std::min<int64_t>(every, n_steps - sg * every), sl, strm);
         return e;
     };
 
     MLN_ACK(c, cudaMalloc(&ckpt, nseg * set_bytes));
-    MLN_ACK(c, cudaMalloc(&slots, 2 * slot_bytes));
+    MLN_ACK(c, cudaMalloc(&slots, (all_at_once ? nseg : 2) * slot_bytes));
     slot_buf[0] = slots;
     slot_buf[1] = slots + slot_bytes;
     MLN_ACK(c, cudaStreamCreateWithFlags(&rs, cudaStreamNonBlocking));
@@ -179,14 +234,28 @@ mln_status adjoint_t(mln_ctx *c, int64_t n_steps, const double *src, int64_t pro
     MLN_ACK(c, cudaMalloc(&accsum, L::size * sizeof(double)));
     if (src) MLN_ACK(c, cudaMalloc(&dsrc, n_steps * sizeof(double)));
 
-    // forward with checkpoints
-    for (int64_t s = 0; s < nseg; ++s) {
-        const int64_t len = std::min<int64_t>(every, n_steps - s * every);
-        MLN_ACK(c, copy_set(set_at(ckpt, s), user, c->stream));
-        mln_status r = mln_step(c, len, src ? src + s * every : nullptr);
-        if (r != MLN_OK) {
-            st = r;
-            goto done;
+    if (traced_forward) {
+        // The forward pass is the recomputation: each segment from the end of
+        // the one before, every step traced (the same arithmetic as the
+        // context's own Strang step), then the context takes the last state.
+        for (int64_t s = 0; s < nseg; ++s) {
+            const int64_t len = std::min<int64_t>(every, n_steps - s * every);
+            MLN_ACK(c, copy_set(set_at(slot_of(s), 0), s == 0 ? user : set_at(slot_of(s - 1), every), c->stream));
+            MLN_ACK(c, run_segments(s, 1, len, slot_of(s), c->stream, true));
+        }
+        MLN_ACK(c, copy_set(user, set_at(slot_of(nseg - 1), n_steps - (nseg - 1) * every), c->stream));
+        c->steps += n_steps;
+        c->launches += launches;
+    } else {
+        // forward with checkpoints
+        for (int64_t s = 0; s < nseg; ++s) {
+            const int64_t len = std::min<int64_t>(every, n_steps - s * every);
+            MLN_ACK(c, copy_set(set_at(ckpt, s), user, c->stream));
+            mln_status r = mln_step(c, len, src ? src + s * every : nullptr);
+            if (r != MLN_OK) {
+                st = r;
+                goto done;
+            }
         }
     }
     // backward
@@ -209,15 +278,23 @@ mln_status adjoint_t(mln_ctx *c, int64_t n_steps, const double *src, int64_t pro
     aa.ca = fa.ca;
     aa.cb = fa.cb;
     aa.inv_dx = fa.inv_dx;
-    MLN_ACK(c, cudaEventRecord(ev_fwd, c->stream));
-    MLN_ACK(c, cudaStreamWaitEvent(rs, ev_fwd, 0));
-    MLN_ACK(c, recompute(nseg - 1, slot_buf[(nseg - 1) & 1], rs));
-    MLN_ACK(c, cudaEventRecord(ev_rec[(nseg - 1) & 1], rs));
+    if (traced_forward) {
+        // every segment recorded by the forward pass
+    } else if (all_at_once) {
+        for (int64_t s = 0; s < nseg; ++s) MLN_ACK(c, prepare(s, slot_of(s), c->stream));
+        if (nfull > 0) MLN_ACK(c, run_segments(0, nfull, every, slot_of(0), c->stream));
+        if (nfull < nseg) MLN_ACK(c, run_segments(nfull, 1, n_steps - nfull * every, slot_of(nfull), c->stream));
+    } else {
+        MLN_ACK(c, cudaEventRecord(ev_fwd, c->stream));
+        MLN_ACK(c, cudaStreamWaitEvent(rs, ev_fwd, 0));
+        MLN_ACK(c, recompute(nseg - 1, slot_buf[(nseg - 1) & 1], rs));
+        MLN_ACK(c, cudaEventRecord(ev_rec[(nseg - 1) & 1], rs));
+    }
     for (int64_t s = nseg - 1; s >= 0; --s) {
         const int64_t s0 = s * every, len = std::min<int64_t>(every, n_steps - s0);
-        unsigned char *sl = slot_buf[s & 1];
-        MLN_ACK(c, cudaStreamWaitEvent(c->stream, ev_rec[s & 1], 0));
-        if (s >= 1) {
+        unsigned char *sl = slot_of(s);
+        if (!all_at_once) MLN_ACK(c, cudaStreamWaitEvent(c->stream, ev_rec[s & 1], 0));
+        if (s >= 1 && !all_at_once) {
             // the buffer of segment s - 1 was last read by the sweep of segment s + 1
             MLN_ACK(c, cudaStreamWaitEvent(rs, ev_rev[(s - 1) & 1], 0));
             MLN_ACK(c, recompute(s - 1, slot_buf[(s - 1) & 1], rs));
@@ -227,6 +304,7 @@ mln_status adjoint_t(mln_ctx *c, int64_t n_steps, const double *src, int64_t pro
             aa.rec = sl;
             aa.rec_set = static_cast<int64_t>(set_bytes);
             aa.off_E = static_cast<int64_t>(sb);
+            aa.off_I = static_cast<int64_t>(off_I);
             aa.j_hi = static_cast<int32_t>(j_hi);
             aa.nsteps = static_cast<int32_t>(std::min<int64_t>(bK, j_hi + 1));
             aa.halo = bK;
@@ -242,9 +320,10 @@ mln_status adjoint_t(mln_ctx *c, int64_t n_steps, const double *src, int64_t pro
             MLN_ACK(c, cudaGetLastError());
             std::swap(A0s, A1s);
         }
-        MLN_ACK(c, cudaEventRecord(ev_rev[s & 1], c->stream));
+        if (!all_at_once) MLN_ACK(c, cudaEventRecord(ev_rev[s & 1], c->stream));
     }
-    mln::mln_adjoint_reduce<<<L::size, 256, 0, c->stream>>>(acc, n, accsum);
+    if (sizeof(R) == 8) mln::mln_adjoint_reduce<<<L::size, 256, 0, c->stream>>>(acc, n, accsum);
+    else mln::mln_adjoint_reduce_pairs<<<L::size, 256, 0, c->stream>>>(reinterpret_cast<const float2 *>(acc), n, accsum);
     MLN_ACK(c, cudaGetLastError());
     MLN_ACK(c, cudaMemcpyAsync(hacc.data(), accsum, L::size * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
     if (out->dJ_dsrc) {
@@ -284,6 +363,12 @@ done:
 }  // namespace
 
 extern "C" {
+
+mln_status mln_set_adjoint_memory(mln_ctx *c, int64_t bytes) {
+    if (!c || bytes < 0) return MLN_EINVAL;
+    c->adj_mem = bytes;
+    return MLN_OK;
+}
 
 mln_status mln_adjoint(mln_ctx *c, int64_t n_steps, const double *src, int64_t probe_cell, int32_t every,
                        mln_adjoint_out *out) {

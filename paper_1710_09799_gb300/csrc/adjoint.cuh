@@ -19,7 +19,7 @@ struct AdjConsts {
     R theta_dt[Dims<N>::Q];
 };
 
-// Accumulator layout (FP64): Dl_bar (D x D) | b_bar (D) | w_bar (D) | c_bar |
+// Accumulator layout (entries of 8 bytes): Dl_bar (D x D) | b_bar (D) | w_bar (D) | c_bar |
 // T_bar (D x D) | theta_bar (q) | J
 template <int N>
 struct AccLayout {
@@ -29,9 +29,23 @@ struct AccLayout {
 };
 
 // Each cell owns one column of the accumulators and adds to it at every
-// step (no atomics, no shuffles); mln_adjoint_reduce sums over the cells.
+// launch (no atomics, no shuffles); mln_adjoint_reduce sums over the cells.
+// FP64 contexts: one double per entry.
 __device__ __forceinline__ void acc_add(double *acc, int64_t n, int64_t i, int idx, double v) {
     acc[idx * n + i] += v;
+}
+// FP32 contexts: a pair (hi, lo) of floats per entry in the same 8 bytes,
+// summed by Knuth's two-sum (hi + lo holds the running sum to about twice
+// the FP32 precision), so that the sweep does no FP64 arithmetic (1/64 of
+// the FP32 rate on this GPU).
+__device__ __forceinline__ void acc_add(float2 *acc, int64_t n, int64_t i, int idx, float v) {
+    float2 a = acc[idx * n + i];
+    const float s = a.x + v;
+    const float bv = s - a.x;
+    const float err = (a.x - (s - bv)) + (v - bv);
+    a.x = s;
+    a.y += err;
+    acc[idx * n + i] = a;
 }
 
 // acc_out[k] = sum_i acc[k * n + i], one block per k, fixed summation order.
@@ -41,6 +55,25 @@ __global__ void __launch_bounds__(256) mln_adjoint_reduce(const double *__restri
     const int k = blockIdx.x;
     double s = 0.0;
     for (int64_t i = threadIdx.x; i < n; i += blockDim.x) s += acc[k * n + i];
+    part[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if (threadIdx.x < w) part[threadIdx.x] += part[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[k] = part[0];
+}
+
+// The same sum over (hi, lo) pairs (FP32 contexts), in FP64.
+__global__ void __launch_bounds__(256) mln_adjoint_reduce_pairs(const float2 *__restrict__ acc, int64_t n,
+                                                                double *__restrict__ out) {
+    __shared__ double part[256];
+    const int k = blockIdx.x;
+    double s = 0.0;
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+        const float2 a = acc[k * n + i];
+        s += static_cast<double>(a.x) + static_cast<double>(a.y);
+    }
     part[threadIdx.x] = s;
     __syncthreads();
     for (int w = 128; w > 0; w >>= 1) {
@@ -66,11 +99,13 @@ template <typename R>
 struct AdjBlockArgs {
     const unsigned char *rec;  // recorded forward sets of the segment: set j at rec + j * rec_set
     int64_t rec_set, off_E;    // bytes per set; offset of E within a set (the state S at offset 0)
+    int64_t off_I;             // offset of step j's traced intermediates (StrangTraceCell rows) in set j
     int32_t j_hi, nsteps, halo, tile;
     const R *Ea, *Ha, *Sa;     // adjoints after step j_hi (of E^{n+1}, H^{n+1/2}, d^{n+1/2})
     R *Eb, *Hb, *Sb;           // adjoints before step j_hi - nsteps + 1
     double *dsrc;              // adjoint of the source sample of segment step j at dsrc[j], or nullptr
-    double *acc;               // per-cell accumulators: entry k of cell i at k * n_cells + i (AccLayout)
+    double *acc;               // per-cell accumulators: entry k of cell i at k * n_cells + i (AccLayout;
+                               // FP32 contexts: a float2 two-sum pair in each 8-byte entry)
     int64_t n_cells, mb, me, stride, source_cell, probe_cell;
     int32_t source_kind, boundary;  // boundary: 0 ring, 1 open (held cell 0, Mur at n - 1)
     double dt;
@@ -123,17 +158,50 @@ struct AdjLaneConsts<N, R, false> {
     __device__ __forceinline__ R t_col(int j) const { return t[j * P + rr]; }
 };
 
-// Shared memory of the blocked reverse kernel: the padded constants (FP64)
-// and two field arrays of the block's cells.
+// Vectors of a step that the lanes of a cell exchange through shared memory
+// (one slot each, written once per step).
+enum AdjSlot { kSlotD, kSlotDz, kSlotY2, kSlotDnb, kSlotY2b, kSlotDzb, kSlotYb, kSlotBr, kAdjSlots };
+
+// Shared memory of the blocked reverse kernel: the padded constants (FP64),
+// two field arrays of the block's cells and the exchange slots.
 template <int N, typename R>
 __host__ __device__ constexpr size_t adj_block_smem(int cells) {
-    return (sizeof(R) == 8 ? 2 * Dims<N>::D * (Dims<N>::D + 1) * sizeof(R) : 0) + 2 * static_cast<size_t>(cells) * sizeof(R);
+    return (sizeof(R) == 8 ? 2 * Dims<N>::D * (Dims<N>::D + 1) * sizeof(R) : 0) + 2 * static_cast<size_t>(cells) * sizeof(R) +
+           static_cast<size_t>(kAdjSlots) * cells * AdjLanes<N>::value * sizeof(R);
+}
+
+// The exchange of a vector held one component per lane: lane r of a cell
+// stores its component in the cell's row of a slot, the warp synchronises,
+// and every lane of the cell reads the whole row with 16-byte loads (the
+// cell's lanes lie in one warp; rows are LN components, 16-byte aligned).
+template <int LN>
+__device__ __forceinline__ void adj_row_load(const float *p, float (&v)[LN]) {
+#pragma unroll
+    for (int i = 0; i < LN / 4; ++i) {
+        const float4 t = reinterpret_cast<const float4 *>(p)[i];
+        v[4 * i] = t.x;
+        v[4 * i + 1] = t.y;
+        v[4 * i + 2] = t.z;
+        v[4 * i + 3] = t.w;
+    }
+}
+template <int LN>
+__device__ __forceinline__ void adj_row_load(const double *p, double (&v)[LN]) {
+#pragma unroll
+    for (int i = 0; i < LN / 2; ++i) {
+        const double2 t = reinterpret_cast<const double2 *>(p)[i];
+        v[2 * i] = t.x;
+        v[2 * i + 1] = t.y;
+    }
 }
 
 // The temporally blocked reverse sweep with one lane per component: the
 // AdjLanes lanes of a cell each own one row r < D of every vector and of
-// every product and read the other components of a product's input by
-// shuffles within the cell's lanes; each lane also owns row r of the
+// every product and read the other components of a product's input from
+// the cell's row of an exchange slot in shared memory (each vector stored
+// once, read back whole). The step's forward values d', z and d'' come from
+// the recomputation's trace (StrangTraceCell) and d^{n+1/2} from the next
+// recorded state, so only the transposed products run here; each lane also owns row r of the
 // outer-product gradients, summed in registers over the launch's steps and
 // added to the cell's accumulator column once at the end (interior cells
 // only: halo cells are the neighbouring tiles' interior).
@@ -174,6 +242,7 @@ __global__ void __launch_bounds__(512) mln_adjoint_block(const __grid_constant__
     const int cells = blockDim.x / LN;
     R *sEp = smc + (kRegs ? 0 : 2 * D * (D + 1));  // epre of each cell
     R *sHh = sEp + cells;                            // new Hbar of each cell
+    R *sVec = sHh + cells;                           // exchange slots, [kAdjSlots][cells][LN]
 
     const int64_t n = a.n_cells;
     const bool periodic = a.boundary == 0;
@@ -202,7 +271,13 @@ __global__ void __launch_bounds__(512) mln_adjoint_block(const __grid_constant__
     const bool before_mur = !periodic && loaded && ii == n - 2;
     const R jdt = static_cast<R>(2.0 * a.dt), cbdx = a.cb * a.inv_dx;
     const unsigned full = 0xffffffffu;
-    auto get = [&](R v, int src) { return __shfl_sync(full, v, src, LN); };  // component src of this cell
+    // store this lane's component of a vector in its slot; read a slot's row
+    auto stage = [&](int sl, R v) { sVec[(sl * cells + lc) * LN + r] = v; };
+    auto put = [&](int sl, R v) {
+        stage(sl, v);
+        __syncwarp();
+    };
+    auto row = [&](int sl, R (&v)[LN]) { adj_row_load<LN>(sVec + (sl * cells + lc) * LN, v); };
 
     AdjLaneConsts<N, R, kRegs> cm;
     cm.init(k, rr, smc);
@@ -221,17 +296,45 @@ __global__ void __launch_bounds__(512) mln_adjoint_block(const __grid_constant__
     for (int c = 0; c < 2 * Q; ++c) gT[c] = R(0);
     R gb = R(0), gw = R(0), gc = R(0), gth = R(0);
     double gJ = 0.0;
+    // The recorded forward values of step j: E^j (E^{j+1} at the probe), this
+    // lane's row of d^j, of the traced intermediates y = d', z = T^T d' (plane
+    // rows) and y2 = d'', and of dn = d^{j+1}; loaded one step ahead, so that
+    // the loads' latency is spent under the previous step (dn is the previous
+    // step's d).
+    auto rec_S = [&](int jj) { return reinterpret_cast<const R *>(a.rec + static_cast<int64_t>(jj) * a.rec_set); };
+    auto rec_E = [&](int jj) {
+        return reinterpret_cast<const R *>(a.rec + static_cast<int64_t>(jj) * a.rec_set + a.off_E);
+    };
+    auto rec_I = [&](int jj, int rowi) {
+        return reinterpret_cast<const R *>(a.rec + static_cast<int64_t>(jj) * a.rec_set + a.off_I)[rowi * a.stride + m];
+    };
+    const bool zrow = mrow && r < 2 * Q;
+    R e_nx = loaded ? rec_E(a.j_hi)[ii] : R(0);
+    R d_nx = mrow ? rec_S(a.j_hi)[r * a.stride + m] : R(0);
+    R e1_nx = is_probe ? rec_E(a.j_hi + 1)[ii] : R(0);
+    R y_nx = mrow ? rec_I(a.j_hi, r) : R(0);
+    R z_nx = zrow ? rec_I(a.j_hi, D + r) : R(0);
+    R y2_nx = mrow ? rec_I(a.j_hi, D + 2 * Q + r) : R(0);
+    R dn_nx = mrow ? rec_S(a.j_hi + 1)[r * a.stride + m] : R(0);
     __syncthreads();  // padded constants in place
 
     for (int s = 0; s < a.nsteps; ++s) {
         const int j = a.j_hi - s;
-        const unsigned char *f0 = a.rec + static_cast<int64_t>(j) * a.rec_set, *f1 = f0 + a.rec_set;
-        const R *S0 = reinterpret_cast<const R *>(f0);
-        const R *E0 = reinterpret_cast<const R *>(f0 + a.off_E), *E1 = reinterpret_cast<const R *>(f1 + a.off_E);
+        const R *E1 = rec_E(j + 1);
+        const R e = e_nx, d = d_nx, e1_rec = e1_nx, y = y_nx, z = z_nx, y2 = y2_nx, dn = dn_nx;
+        if (s + 1 < a.nsteps) {
+            e_nx = loaded ? rec_E(j - 1)[ii] : R(0);
+            d_nx = mrow ? rec_S(j - 1)[r * a.stride + m] : R(0);
+            e1_nx = e;  // E^{j} of this cell is E^{(j-1)+1}
+            y_nx = mrow ? rec_I(j - 1, r) : R(0);
+            z_nx = zrow ? rec_I(j - 1, D + r) : R(0);
+            y2_nx = mrow ? rec_I(j - 1, D + 2 * Q + r) : R(0);
+            dn_nx = d;  // d^{j} is the dn of step j - 1
+        }
         // adjoint of E^{n+1} with the objective's term; the source's adjoint
         R ebn = ebar;
         if (is_probe) {
-            const R e1 = E1[ii];
+            const R e1 = e1_rec;
             ebn += jdt * e1;
             if (interior && r == 0) gJ += a.dt * static_cast<double>(e1) * static_cast<double>(e1);
         }
@@ -255,59 +358,46 @@ __global__ void __launch_bounds__(512) mln_adjoint_block(const __grid_constant__
         const R hh = hbar + (in_h ? cbdx * (epre - ep_p) : R(0));
         if (r == 0) sHh[lc] = hh;
 
-        // the medium: forward recompute of the cell, then its reverse
-        const R e = loaded ? E0[ii] : R(0);
-        const R d = mrow ? S0[r * a.stride + m] : R(0);
-        R y;  // y = d + (Dl d + b)
-        {
-            R acc = b_r;
-#pragma unroll
-            for (int c = 0; c < D; ++c) acc = fma(cm.dl_row(c), get(d, c), acc);
-            y = d + acc;
-        }
-        R z;  // z = T^T y
-        {
-            R acc = cm.t_col(0) * get(y, 0);
-#pragma unroll
-            for (int c = 1; c < D; ++c) acc = fma(cm.t_col(c), get(y, c), acc);
-            z = acc;
-        }
+        // the medium: the step's forward values (recorded), then its reverse
+        R v[LN];
         R sn[Q], c1[Q];
         plane_terms<N>(k.psi_dt, e, sn, c1);
-        const int pl = rr / 2;
+        // this lane's plane terms, selected in registers (no indexed array)
+        R c1p = c1[0], snp = sn[0];
+#pragma unroll
+        for (int q = 1; q < Q; ++q)
+            if (rr / 2 == q) {
+                c1p = c1[q];
+                snp = sn[q];
+            }
         const R z_pair = __shfl_xor_sync(full, z, 1, LN);
-        R dz = R(0);
-        if (r < 2 * Q) dz = (r % 2 == 0) ? fma(c1[pl], z, sn[pl] * z_pair) : fma(c1[pl], z, -(sn[pl] * z_pair));
-        R y2;  // y2 = y + T dz
-        {
-            R acc = cm.t_row(0) * get(dz, 0);
-#pragma unroll
-            for (int c = 1; c < D; ++c) acc = fma(cm.t_row(c), get(dz, c), acc);
-            y2 = y + acc;
-        }
-        R dn;  // dn = y2 + (Dl y2 + b)
-        {
-            R acc = b_r;
-#pragma unroll
-            for (int c = 0; c < D; ++c) acc = fma(cm.dl_row(c), get(y2, c), acc);
-            dn = y2 + acc;
-        }
-        R dv = d, yv = y, zv = z, y2v = y2, dnv = dn, dzv = dz;
-        if (!mrow) dv = yv = zv = y2v = dnv = dzv = R(0);
+        R dz = R(0);  // (R - I) z
+        if (r < 2 * Q) dz = (r % 2 == 0) ? fma(c1p, z, snp * z_pair) : fma(c1p, z, -(snp * z_pair));
+        // d, dz and y2 for the gradients' outer products
+        stage(kSlotD, d);
+        stage(kSlotDz, dz);
+        stage(kSlotY2, y2);
+        __syncwarp();
+        R yv = y, zv = z, dnv = dn;
+        if (!mrow) yv = zv = dnv = R(0);
         const R pbar = (medium && in_e) ? -a.cb * epre : R(0);
         const R dnb = sbar + pbar * w_r;
         R y2b;  // y2b = dnb + Dl^T dnb
         {
+            put(kSlotDnb, dnb);
+            row(kSlotDnb, v);
             R acc = dnb;
 #pragma unroll
-            for (int c = 0; c < D; ++c) acc = fma(cm.dl_col(c), get(dnb, c), acc);
+            for (int c = 0; c < D; ++c) acc = fma(cm.dl_col(c), v[c], acc);
             y2b = acc;
         }
         R zb;  // zb = T^T y2b
         {
-            R acc = cm.t_col(0) * get(y2b, 0);
+            put(kSlotY2b, y2b);
+            row(kSlotY2b, v);
+            R acc = cm.t_col(0) * v[0];
 #pragma unroll
-            for (int c = 1; c < D; ++c) acc = fma(cm.t_col(c), get(y2b, c), acc);
+            for (int c = 1; c < D; ++c) acc = fma(cm.t_col(c), v[c], acc);
             zb = acc;
         }
         const R zb_pair = __shfl_xor_sync(full, zb, 1, LN);
@@ -315,39 +405,47 @@ __global__ void __launch_bounds__(512) mln_adjoint_block(const __grid_constant__
         R dzb = R(0), br = R(0);
         if (r < 2 * Q) {
             const bool even = r % 2 == 0;
-            dzb = even ? fma(c1[pl], zb, -(sn[pl] * zb_pair)) : fma(c1[pl], zb, sn[pl] * zb_pair);
+            dzb = even ? fma(c1p, zb, -(snp * zb_pair)) : fma(c1p, zb, snp * zb_pair);
             if (even) {
-                const R zx = zv, zy = zv_pair, bx = zb, by = zb_pair, cs = R(1) + c1[pl];
-                br = bx * fma(-sn[pl], zx, cs * zy) + by * fma(-cs, zx, -(sn[pl] * zy));
+                const R zx = zv, zy = zv_pair, bx = zb, by = zb_pair, cs = R(1) + c1p;
+                br = bx * fma(-snp, zx, cs * zy) + by * fma(-cs, zx, -(snp * zy));
             }
         }
         R e_term = R(0);
+        put(kSlotBr, br);
+        row(kSlotBr, v);
 #pragma unroll
-        for (int p = 0; p < Q; ++p) e_term = fma(k.theta_dt[p], get(br, 2 * p), e_term);
+        for (int p = 0; p < Q; ++p) e_term = fma(k.theta_dt[p], v[2 * p], e_term);
         R yb;  // yb = y2b + T dzb
         {
-            R acc = cm.t_row(0) * get(dzb, 0);
+            put(kSlotDzb, dzb);
+            row(kSlotDzb, v);
+            R acc = cm.t_row(0) * v[0];
 #pragma unroll
-            for (int c = 1; c < D; ++c) acc = fma(cm.t_row(c), get(dzb, c), acc);
+            for (int c = 1; c < D; ++c) acc = fma(cm.t_row(c), v[c], acc);
             yb = y2b + acc;
         }
         R db;  // db = yb + Dl^T yb
         {
+            put(kSlotYb, yb);
+            row(kSlotYb, v);
             R acc = yb;
 #pragma unroll
-            for (int c = 0; c < D; ++c) acc = fma(cm.dl_col(c), get(yb, c), acc);
+            for (int c = 0; c < D; ++c) acc = fma(cm.dl_col(c), v[c], acc);
             db = acc;
         }
-        // this lane's rows of the gradients (shuffles for every lane)
+        // this lane's rows of the gradients, from the slots of y2, d, dz and dzb
+        // (a lane with mrow belongs to a medium cell, whose rows c < D hold them)
+        if (mrow) {
+            R w2[LN];
+            row(kSlotY2, v);
+            row(kSlotD, w2);
 #pragma unroll
-        for (int c = 0; c < D; ++c) {
-            const R y2c = get(y2v, c), dc = get(dv, c);
-            if (mrow) gDl[c] = fma(dnb, y2c, fma(yb, dc, gDl[c]));
-        }
+            for (int c = 0; c < D; ++c) gDl[c] = fma(dnb, v[c], fma(yb, w2[c], gDl[c]));
+            row(kSlotDz, v);
+            row(kSlotDzb, w2);
 #pragma unroll
-        for (int c = 0; c < 2 * Q; ++c) {
-            const R dzc = get(dzv, c), dzbc = get(dzb, c);
-            if (mrow) gT[c] = fma(y2b, dzc, fma(yv, dzbc, gT[c]));
+            for (int c = 0; c < 2 * Q; ++c) gT[c] = fma(y2b, v[c], fma(yv, w2[c], gT[c]));
         }
         if (mrow) {
             gb += dnb + yb;
@@ -386,18 +484,31 @@ __global__ void __launch_bounds__(512) mln_adjoint_block(const __grid_constant__
             a.Eb[ii] = ebar;
             a.Hb[ii] = hbar;
         }
+        // into the cell's accumulator column: doubles (FP64), two-sum pairs (FP32)
+        auto add = [&](int idx, R v) {
+            if constexpr (sizeof(R) == 8) acc_add(a.acc, n, ii, idx, v);
+            else acc_add(reinterpret_cast<float2 *>(a.acc), n, ii, idx, v);
+        };
         if (mrow) {
             a.Sb[r * a.stride + m] = sbar;
 #pragma unroll
-            for (int c = 0; c < D; ++c) acc_add(a.acc, n, ii, L::Dl + r * D + c, static_cast<double>(gDl[c]));
+            for (int c = 0; c < D; ++c) add(L::Dl + r * D + c, gDl[c]);
 #pragma unroll
-            for (int c = 0; c < 2 * Q; ++c) acc_add(a.acc, n, ii, L::T + r * D + c, static_cast<double>(gT[c]));
-            acc_add(a.acc, n, ii, L::b + r, static_cast<double>(gb));
-            acc_add(a.acc, n, ii, L::w + r, static_cast<double>(gw));
+            for (int c = 0; c < 2 * Q; ++c) add(L::T + r * D + c, gT[c]);
+            add(L::b + r, gb);
+            add(L::w + r, gw);
         }
-        if (medium && r == 0) acc_add(a.acc, n, ii, L::c, static_cast<double>(gc));
-        if (medium && r < 2 * Q && r % 2 == 0) acc_add(a.acc, n, ii, L::th + r / 2, static_cast<double>(gth));
-        if (r == 0 && is_probe) acc_add(a.acc, n, ii, L::J, gJ);
+        if (medium && r == 0) add(L::c, gc);
+        if (medium && r < 2 * Q && r % 2 == 0) add(L::th + r / 2, gth);
+        if (r == 0 && is_probe) {
+            if constexpr (sizeof(R) == 8) {
+                acc_add(a.acc, n, ii, L::J, gJ);
+            } else {  // the FP64 partial sum as two floats
+                const float hi = static_cast<float>(gJ);
+                acc_add(reinterpret_cast<float2 *>(a.acc), n, ii, L::J, hi);
+                acc_add(reinterpret_cast<float2 *>(a.acc), n, ii, L::J, static_cast<float>(gJ - static_cast<double>(hi)));
+            }
+        }
     }
 }
 

@@ -31,6 +31,7 @@ struct mln_ctx {
     void *prog = nullptr;              // its program: rowptr | cols | vals
     int tc = 0;                        // tensor-core cell model: 0 none, MLN_KERNEL_TENSOR(_SMEM)
     bool tcr = false;                  // ... for the rotated basis (MLN_FORM_ROTATED)
+    int64_t adj_mem = 0;               // mln_adjoint's limit for the recorded segments (0: half the free memory)
     int sms = 152;                     // SMs of the context's device
     void *tc_img = nullptr;            // its B-operand image (device)
     std::vector<unsigned char> tc_scal;  // and scalar constants

@@ -203,6 +203,29 @@ cudaError_t launch_sparse_one(const BlockArgs<double> &a, const std::vector<unsi
     return launch_dependent(true, kern, grid, block, smem, st, a, k);
 }
 
+// The Strang step with its intermediates traced (mln_trace_kernel), N <= 4,
+// at most 256 threads a block: the adjoint's recomputation.
+template <typename R>
+cudaError_t launch_block_trace_t(int N, const BlockArgs<R> &a, const std::vector<unsigned char> &consts, dim3 grid,
+                                 dim3 block, size_t smem, cudaStream_t st, bool programmatic) {
+    switch (N) {
+#define MLN_TRACE_CASE(NN)                                                                                  \
+    case NN: {                                                                                              \
+        StrangConsts<NN, R> k;                                                                              \
+        if (consts.size() != sizeof(k)) return cudaErrorInvalidValue;                                       \
+        std::memcpy(&k, consts.data(), sizeof(k));                                                          \
+        if (block.x > 256) return cudaErrorInvalidValue;                                                   \
+        return launch_dependent(programmatic, mln_trace_kernel<NN, R>, grid, block, smem, st, a, k);       \
+    }
+        MLN_TRACE_CASE(2)
+        MLN_TRACE_CASE(3)
+        MLN_TRACE_CASE(4)
+#undef MLN_TRACE_CASE
+    default:
+        return cudaErrorInvalidValue;
+    }
+}
+
 template <typename R>
 cudaError_t launch_block_t(int N, int form, const BlockArgs<R> &a, const std::vector<unsigned char> &consts,
                            dim3 grid, dim3 block, size_t smem, cudaStream_t st, bool programmatic) {
@@ -239,6 +262,10 @@ cudaError_t launch_block(int N, int form, const BlockArgs<double> &a, const std:
                          dim3 grid, dim3 block, size_t smem, cudaStream_t st, bool programmatic = true);
 cudaError_t launch_block(int N, int form, const BlockArgs<float> &a, const std::vector<unsigned char> &consts,
                          dim3 grid, dim3 block, size_t smem, cudaStream_t st, bool programmatic = true);
+cudaError_t launch_block_trace(int N, const BlockArgs<double> &a, const std::vector<unsigned char> &consts,
+                               dim3 grid, dim3 block, size_t smem, cudaStream_t st, bool programmatic);
+cudaError_t launch_block_trace(int N, const BlockArgs<float> &a, const std::vector<unsigned char> &consts,
+                               dim3 grid, dim3 block, size_t smem, cudaStream_t st, bool programmatic);
 cudaError_t launch_sin_cosm1(int precision, const double *x, int64_t n, double *s, double *c1, cudaStream_t st);
 bool pack_sparse_consts(const Setup &s, double dt, const int32_t *rowptr, const int32_t *cols, const double *vals,
                         int nnz, int nrowptr, std::vector<unsigned char> &out);

@@ -79,9 +79,16 @@ struct BlockArgs {
     unsigned int *flags;   // bit 0: non-finite E seen
     // optional record of every step (nullptr: none): after step st the
     // interior cells also write E, H and the state to rec_E, rec_H, rec_S
-    // advanced by st * rec_set bytes (the adjoint's recomputed segment)
+    // advanced by st * rec_set bytes (the adjoint's recomputed segment);
+    // a cell model that traces its intermediates (StrangTraceCell) writes
+    // those of step st to rec_I advanced by st * rec_set bytes
     R *rec_E, *rec_H, *rec_S;
     int64_t rec_set;
+    R *rec_I;
+    // mln_trace_kernel only: launches with gridDim.y > 1 run independent
+    // segments side by side, segment y with every buffer pointer advanced by
+    // y * seg_bytes bytes and src by y * seg_src samples
+    int64_t seg_bytes, seg_src;
     int64_t n_cells, mb, me, stride, source_cell;
     int32_t nsteps, halo, tile, boundary, source_kind, pad_;
     R ch, ca, cb, inv_dx, kappa;
@@ -414,6 +421,76 @@ struct RegisterCell {
     __device__ __forceinline__ void end_step() {}
 };
 
+// p advanced by off bytes (nullptr stays nullptr).
+template <typename T>
+__device__ __forceinline__ T *byte_advance(T *p, int64_t off) {
+    return p ? reinterpret_cast<T *>(reinterpret_cast<unsigned long long>(p) + static_cast<unsigned long long>(off))
+             : p;
+}
+
+// Whether a cell model writes its intermediates (Cell::kTrace).
+template <typename...>
+using mln_void_t = void;
+template <typename C, typename = void>
+struct CellTraces {
+    static constexpr bool value = false;
+};
+template <typename C>
+struct CellTraces<C, mln_void_t<decltype(C::kTrace)>> {
+    static constexpr bool value = C::kTrace;
+};
+
+// The Strang step of RegisterCell<N, R, StrangConsts> (same operations, same
+// bits) that also writes the step's intermediates for the reverse sweep of
+// the adjoint: rows 0..D-1 d' = A0 d + b, rows D..D+2q-1 the plane rows of
+// z = T^T d', rows D+2q..2D+2q-1 d'' = d' + T (R - I) z, each row `stride`
+// apart, at the pointer given by trace_to before the step (nullptr: none).
+template <int N, typename R>
+struct StrangTraceCell {
+    static constexpr int D = Dims<N>::D, P = 2 * Dims<N>::Q;
+    static constexpr bool kTrace = true;
+    using Consts = StrangConsts<N, R>;
+    R s[D];
+    R *tp = nullptr;
+    int64_t ts = 0, tm = 0;
+    __device__ __forceinline__ void setup(unsigned char *, const Consts &) {}
+    __device__ __forceinline__ void load(const R *src, int64_t stride, int64_t m) {
+#pragma unroll
+        for (int i = 0; i < D; ++i) s[i] = src[i * stride + m];
+    }
+    __device__ __forceinline__ void store(R *dst, int64_t stride, int64_t m) const {
+#pragma unroll
+        for (int i = 0; i < D; ++i) dst[i * stride + m] = s[i];
+    }
+    __device__ __forceinline__ void trace_to(R *p, int64_t stride, int64_t m) {
+        tp = p;
+        ts = stride;
+        tm = m;
+    }
+    __device__ __forceinline__ R step(R e, const Consts &k) {
+        R y[D];
+        affine_inc<D>(y, k.Dl, s, k.b);  // d' = A0 d + b
+        if (tp) {
+#pragma unroll
+            for (int i = 0; i < D; ++i) tp[i * ts + tm] = y[i];
+        }
+        matTvec<D>(s, k.T, y);  // z = T^T d'
+        if (tp) {
+#pragma unroll
+            for (int i = 0; i < P; ++i) tp[(D + i) * ts + tm] = s[i];
+        }
+        rotation_increment<N>(s, k.psi_dt, e);  // (R - I) z
+        matvec_acc<D>(y, k.T, s);               // d'' = d' + T (R - I) z
+        if (tp) {
+#pragma unroll
+            for (int i = 0; i < D; ++i) tp[(D + P + i) * ts + tm] = y[i];
+        }
+        affine_inc<D>(s, k.Dl, y, k.b);  // d = A0 d'' + b
+        return dot_bias<D>(k.w, s, k.c);
+    }
+    __device__ __forceinline__ void end_step() {}
+};
+
 // Sparse program of the merged FP64 step: the non-zero entries of T^T
 // (restricted to the 2q plane rows), T (restricted to the plane columns),
 // A0^2 - I and A0^T w, row by row in ascending column order (the order of
@@ -619,6 +696,13 @@ __device__ __forceinline__ void block_body(const BlockArgs<R> &a, const typename
             R hl = R(0);
             if (e_upd) hl = fma(a.ch, e - cE[j - 1], cH[j - 1]);
             R dpdt = R(0);
+            if constexpr (CellTraces<Cell>::value) {
+                if (medium)
+                    cell.trace_to(record ? reinterpret_cast<R *>(reinterpret_cast<char *>(a.rec_I) +
+                                                                 static_cast<int64_t>(st) * a.rec_set)
+                                         : nullptr,
+                                  a.stride, m);
+            }
             if (medium) dpdt = cell.step(e, k);
             cell.end_step();
             R en = e;
@@ -725,8 +809,9 @@ __device__ __forceinline__ void batch_body(const BatchGrid<R> *__restrict__ grid
     a.s_out = g.S[parity ^ 1];
     a.src = g.src ? g.src + step_offset : nullptr;
     a.flags = g.flags;
-    a.rec_E = a.rec_H = a.rec_S = nullptr;
+    a.rec_E = a.rec_H = a.rec_S = a.rec_I = nullptr;
     a.rec_set = 0;
+    a.seg_bytes = a.seg_src = 0;
     a.n_cells = g.n_cells;
     a.mb = g.mb;
     a.me = g.me;
@@ -852,6 +937,34 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
     asm volatile("griddepcontrol.wait;" ::: "memory");
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     block_body<N, R, Cell>(a, k, static_cast<int64_t>(blockIdx.x), smem_raw);
+}
+
+// The adjoint's recomputation: the Strang step with its intermediates traced
+// (StrangTraceCell), at most 256 threads a block (the register room the
+// trace needs), segment blockIdx.y of a side-by-side launch (0 when
+// gridDim.y == 1). Programmatic dependency as in mln_block_kernel.
+template <int N, typename R>
+__global__ void __launch_bounds__(256, 1)
+    mln_trace_kernel(const __grid_constant__ BlockArgs<R> a, const __grid_constant__ StrangConsts<N, R> k) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    {
+        const int64_t off = static_cast<int64_t>(blockIdx.y) * a.seg_bytes;
+        BlockArgs<R> b = a;
+        b.E_in = byte_advance(a.E_in, off);
+        b.H_in = byte_advance(a.H_in, off);
+        b.s_in = byte_advance(a.s_in, off);
+        b.E_out = byte_advance(a.E_out, off);
+        b.H_out = byte_advance(a.H_out, off);
+        b.s_out = byte_advance(a.s_out, off);
+        b.rec_E = byte_advance(a.rec_E, off);
+        b.rec_H = byte_advance(a.rec_H, off);
+        b.rec_S = byte_advance(a.rec_S, off);
+        b.rec_I = byte_advance(a.rec_I, off);
+        b.src = a.src ? a.src + static_cast<int64_t>(blockIdx.y) * a.seg_src : nullptr;
+        block_body<N, R, StrangTraceCell<N, R>>(b, k, static_cast<int64_t>(blockIdx.x), smem_raw);
+    }
 }
 
 }  // namespace mln

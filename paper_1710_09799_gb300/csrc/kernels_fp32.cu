@@ -7,6 +7,11 @@ bool pack_consts(const Setup &s, int form, double dt, float, std::vector<unsigne
     return pack_consts_t<float>(s, form, dt, out);
 }
 
+cudaError_t launch_block_trace(int N, const BlockArgs<float> &a, const std::vector<unsigned char> &consts,
+                               dim3 grid, dim3 block, size_t smem, cudaStream_t st, bool programmatic) {
+    return launch_block_trace_t<float>(N, a, consts, grid, block, smem, st, programmatic);
+}
+
 cudaError_t launch_block(int N, int form, const BlockArgs<float> &a, const std::vector<unsigned char> &consts,
                          dim3 grid, dim3 block, size_t smem, cudaStream_t st, bool programmatic) {
     return launch_block_t<float>(N, form, a, consts, grid, block, smem, st, programmatic);

@@ -7,6 +7,11 @@ bool pack_consts(const Setup &s, int form, double dt, double, std::vector<unsign
     return pack_consts_t<double>(s, form, dt, out);
 }
 
+cudaError_t launch_block_trace(int N, const BlockArgs<double> &a, const std::vector<unsigned char> &consts,
+                               dim3 grid, dim3 block, size_t smem, cudaStream_t st, bool programmatic) {
+    return launch_block_trace_t<double>(N, a, consts, grid, block, smem, st, programmatic);
+}
+
 cudaError_t launch_block(int N, int form, const BlockArgs<double> &a, const std::vector<unsigned char> &consts,
                          dim3 grid, dim3 block, size_t smem, cudaStream_t st, bool programmatic) {
     return launch_block_t<double>(N, form, a, consts, grid, block, smem, st, programmatic);

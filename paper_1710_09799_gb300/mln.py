@@ -104,6 +104,7 @@ _SIGS = {
     "mln_kernel_source": (C.c_int, [_P, C.c_char_p, C.c_size_t, C.POINTER(C.c_size_t)]),
     "mln_adjoint": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_int64, C.c_int32,
                               C.POINTER(mln_adjoint_out)]),
+    "mln_set_adjoint_memory": (C.c_int, [C.c_void_p, C.c_int64]),
     "mln_batch_create": (C.c_int, [C.c_int32, _P, C.POINTER(C.c_void_p), C.POINTER(C.c_void_p),
                                    C.POINTER(C.c_void_p), C.POINTER(C.c_void_p), C.c_int64, C.c_void_p,
                                    C.POINTER(C.c_void_p)]),
@@ -468,6 +469,11 @@ class Solver:
 
 
 # ------------------------------------------------------------------ adjoint
+
+def mln_set_adjoint_memory(ctx, n_bytes: int):
+    """Limit of mln_adjoint's recorded sets of all segments at once (0: half the free memory)."""
+    _check(lib().mln_set_adjoint_memory(ctx, n_bytes), ctx)
+
 
 def mln_adjoint(ctx, N: int, n_steps: int, src_ptr: int | None, probe_cell: int, every: int):
     """J and its gradients: (J, dJ/dsrc (n_steps), dJ/dmu params (N*N), dJ/dG (N^2 x N^2 complex))."""

@@ -25,11 +25,12 @@ def _built():
     build()
 
 
-def J_and_grads(p, src, precision="fp64", every=32, mu=None, G=None):
+def J_and_grads(p, src, precision="fp64", every=32, mu=None, G=None, memory=0):
     import torch
     from paper_1710_09799_gb300 import mln
     q = p.with_(mu=p.mu if mu is None else mu, G=p.G if G is None else G)
     s = mln.Solver(params_of(q, precision=precision, form="strang"), E0=q.e_init())
+    mln.mln_set_adjoint_memory(s.ctx, memory)
     t = torch.as_tensor(src, dtype=torch.float64, device="cuda")
     out = mln.mln_adjoint(s.ctx, q.N, len(src), t.data_ptr(), p.meta["probe_cell"], every)
     s.close()
@@ -149,6 +150,32 @@ def test_checkpoint_interval_does_not_change_gradients(small):
     J2, dsrc2, dmu2, dG2 = J_and_grads(p, src, every=7)
     assert abs(J2 - J) <= 1e-12 * J
     assert rel_inf(dsrc2, dsrc) < 1e-10 and rel_inf(dmu2, dmu) < 1e-10 and rel_inf(dG2, dG) < 1e-10
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("every", [7, 32])
+def test_recompute_schedules_give_the_same_bits(small, precision, every):
+    """All segments recomputed side by side (the default, memory permitting)
+    and two segments at a time (a 1-byte limit forces it): the same kernels
+    on the same inputs, so the same bits. 300 steps: 42 segments of 7 and
+    one of 6, or 9 of 32 and one of 12."""
+    p, src, _ = small
+    a = J_and_grads(p, src, precision=precision, every=every)
+    b = J_and_grads(p, src, precision=precision, every=every, memory=1)
+    assert a[0] == b[0]
+    for x, y in zip(a[1:], b[1:]):
+        assert np.array_equal(x, y)
+
+
+def test_adjoint_memory_limit_rejects_negative(small):
+    import torch
+    from paper_1710_09799_gb300 import mln
+    p, _, _ = small
+    s = mln.Solver(params_of(p, precision="fp64", form="strang"), E0=p.e_init())
+    with pytest.raises(mln.MLNError) as ei:
+        mln.mln_set_adjoint_memory(s.ctx, -1)
+    assert ei.value.status == mln.MLN_EINVAL
+    s.close()
 
 
 def test_fp32_adjoint_close_to_fp64(small):
