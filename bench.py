@@ -708,8 +708,12 @@ def _rec_adjoint(out, refs):
         f_fwd = p.n_medium * work[0] + p.n_cells * work[1]
         D, Q = p.D, p.N * (p.N - 1) // 2
         rot = 6 * Q + 10 * (Q - (p.N - 1)) + 8 * (p.N - 1)
-        f_rev = p.n_medium * (20 * D * D + 8 * D * Q + 6 * D + 24 * Q + rot) + p.n_cells * 12
-        flops = (2 * f_fwd + f_rev) * p.n_steps
+        # the method's work: the forward step, and the transposed step with the
+        # gradients' outer products (A dnb, T^T on the 2q plane rows, T on the
+        # plane columns, A yb: 4 D^2 + 8 D q; Dl and T gradients: 4 D^2 + 8 D q;
+        # plane terms and the small vectors), not the recomputation
+        f_rev = p.n_medium * (8 * D * D + 16 * D * Q + 3 * D + 14 * Q + rot) + p.n_cells * 12
+        flops = (f_fwd + f_rev) * p.n_steps
         peak = alu_peak_tflops(prec)
         out[f"adjoint_{prec}"] = {
             "value": p.n_cells * p.n_steps / t_grad, "unit": UNIT + " (forward cell-updates per second of a J + gradient evaluation)",
@@ -718,9 +722,9 @@ def _rec_adjoint(out, refs):
             "timed": "3 evaluations after 3 warm-up (host clock around synchronised calls)",
             "roofline": {"bound": "alu", "achieved": flops / t_grad / 1e12, "peak": peak, "unit": "TFLOP/s",
                          "frac": flops / t_grad / 1e12 / peak, "traffic": None,
-                         "kernel": "whole gradient: forward with checkpoints, recomputation, mln_adjoint_step_rows",
-                         "counted": "forward and recomputation (mln_work_per_step) + the reverse step's dense products "
-                                    "and accumulations"},
+                         "kernel": "whole gradient: forward pass (recording), mln_adjoint_block",
+                         "counted": "the forward step (mln_work_per_step) + the transposed step's products and the "
+                                    "gradients' outer products, once per medium cell and step"},
             "error_vs_oracle": {"J_rel": abs(J - J_orc) / abs(J_orc), "oracle_s": t_orc,
                                 "directional_derivative_vs_central_difference": abs(ad - fd) / max(abs(fd), 1e-300),
                                 "direction": "seeded normal over the 512 free source samples, h = 1e-6 max|src| (FP64 forward)"},

@@ -113,46 +113,26 @@ struct AdjBlockArgs {
 };
 
 // The constant matrices as one lane needs them (its row r and column r of Dl
-// and T): held in registers in FP32; in FP64, whose arithmetic is slow
-// enough that shared-memory reads cost nothing, read from a padded copy in
-// shared memory (rows of D + 1 entries: conflict-free for rows and columns),
-// which leaves the registers to the accumulators.
-template <int N, typename R, bool kRegs>
-struct AdjLaneConsts;
+// and T): read from a padded copy in shared memory (rows of D + 1 entries:
+// conflict-free for rows and columns), which leaves the registers to the
+// accumulators (in FP32 the copy in registers had left the kernel at 126
+// registers a thread and 8 % slower).
 template <int N, typename R>
-struct AdjLaneConsts<N, R, true> {
-    static constexpr int D = Dims<N>::D;
-    R dlr[D], dlc[D], tr[D], tc[D];
-    __device__ __forceinline__ void init(const AdjConsts<N, R> &k, int rr, R *) {
-#pragma unroll
-        for (int j = 0; j < D; ++j) {
-            dlr[j] = k.Dl[rr * D + j];
-            dlc[j] = k.Dl[j * D + rr];
-            tr[j] = k.T[rr * D + j];
-            tc[j] = k.T[j * D + rr];
-        }
-    }
-    __device__ __forceinline__ R dl_row(int j) const { return dlr[j]; }
-    __device__ __forceinline__ R dl_col(int j) const { return dlc[j]; }
-    __device__ __forceinline__ R t_row(int j) const { return tr[j]; }
-    __device__ __forceinline__ R t_col(int j) const { return tc[j]; }
-};
-template <int N, typename R>
-struct AdjLaneConsts<N, R, false> {
-    static constexpr int D = Dims<N>::D, P = D + 1;
+struct AdjLaneConsts {
+    static constexpr int D = Dims<N>::D, P = D + 1, kMats = 2;
     const R *dl, *t;  // shared memory, [D][D + 1] each
     int rr;
-    // block-cooperative: copy Dl and T into the padded layout (needs a barrier after)
+    // block-cooperative: copy the matrices into the padded layout (needs a barrier after)
     __device__ __forceinline__ void init(const AdjConsts<N, R> &k, int r, R *sm) {
         for (int e = threadIdx.x; e < D * D; e += blockDim.x) {
-            sm[(e / D) * P + e % D] = k.Dl[e];
-            sm[D * P + (e / D) * P + e % D] = k.T[e];
+            const int o = (e / D) * P + e % D;
+            sm[o] = k.Dl[e];
+            sm[D * P + o] = k.T[e];
         }
         dl = sm;
         t = sm + D * P;
         rr = r;
     }
-    __device__ __forceinline__ R dl_row(int j) const { return dl[rr * P + j]; }
     __device__ __forceinline__ R dl_col(int j) const { return dl[j * P + rr]; }
     __device__ __forceinline__ R t_row(int j) const { return t[rr * P + j]; }
     __device__ __forceinline__ R t_col(int j) const { return t[j * P + rr]; }
@@ -162,11 +142,12 @@ struct AdjLaneConsts<N, R, false> {
 // (one slot each, written once per step).
 enum AdjSlot { kSlotD, kSlotDz, kSlotY2, kSlotDnb, kSlotY2b, kSlotDzb, kSlotYb, kSlotBr, kAdjSlots };
 
-// Shared memory of the blocked reverse kernel: the padded constants (FP64),
+// Shared memory of the blocked reverse kernel: the padded constants,
 // two field arrays of the block's cells and the exchange slots.
 template <int N, typename R>
 __host__ __device__ constexpr size_t adj_block_smem(int cells) {
-    return (sizeof(R) == 8 ? 2 * Dims<N>::D * (Dims<N>::D + 1) * sizeof(R) : 0) + 2 * static_cast<size_t>(cells) * sizeof(R) +
+    return AdjLaneConsts<N, R>::kMats * Dims<N>::D * (Dims<N>::D + 1) * sizeof(R) +
+           2 * static_cast<size_t>(cells) * sizeof(R) +
            static_cast<size_t>(kAdjSlots) * cells * AdjLanes<N>::value * sizeof(R);
 }
 
@@ -235,12 +216,11 @@ template <int N, typename R>
 __global__ void __launch_bounds__(512) mln_adjoint_block(const __grid_constant__ AdjBlockArgs<R> a,
                                                          const __grid_constant__ AdjConsts<N, R> k) {
     constexpr int D = Dims<N>::D, Q = Dims<N>::Q, LN = AdjLanes<N>::value;
-    constexpr bool kRegs = sizeof(R) == 4;
     using L = AccLayout<N>;
     extern __shared__ __align__(16) unsigned char adj_smem[];
     R *smc = reinterpret_cast<R *>(adj_smem);
     const int cells = blockDim.x / LN;
-    R *sEp = smc + (kRegs ? 0 : 2 * D * (D + 1));  // epre of each cell
+    R *sEp = smc + AdjLaneConsts<N, R>::kMats * D * (D + 1);  // epre of each cell
     R *sHh = sEp + cells;                            // new Hbar of each cell
     R *sVec = sHh + cells;                           // exchange slots, [kAdjSlots][cells][LN]
 
@@ -279,7 +259,7 @@ __global__ void __launch_bounds__(512) mln_adjoint_block(const __grid_constant__
     };
     auto row = [&](int sl, R (&v)[LN]) { adj_row_load<LN>(sVec + (sl * cells + lc) * LN, v); };
 
-    AdjLaneConsts<N, R, kRegs> cm;
+    AdjLaneConsts<N, R> cm;
     cm.init(k, rr, smc);
     const R b_r = k.b[rr], w_r = k.w[rr];
 
@@ -382,17 +362,16 @@ __global__ void __launch_bounds__(512) mln_adjoint_block(const __grid_constant__
         if (!mrow) yv = zv = dnv = R(0);
         const R pbar = (medium && in_e) ? -a.cb * epre : R(0);
         const R dnb = sbar + pbar * w_r;
-        R y2b;  // y2b = dnb + Dl^T dnb
-        {
-            put(kSlotDnb, dnb);
-            row(kSlotDnb, v);
+        R y2b, zb;
+        put(kSlotDnb, dnb);
+        row(kSlotDnb, v);
+        {  // y2b = dnb + Dl^T dnb
             R acc = dnb;
 #pragma unroll
             for (int c = 0; c < D; ++c) acc = fma(cm.dl_col(c), v[c], acc);
             y2b = acc;
         }
-        R zb;  // zb = T^T y2b
-        {
+        {  // zb = T^T y2b
             put(kSlotY2b, y2b);
             row(kSlotY2b, v);
             R acc = cm.t_col(0) * v[0];
@@ -412,21 +391,21 @@ __global__ void __launch_bounds__(512) mln_adjoint_block(const __grid_constant__
             }
         }
         R e_term = R(0);
-        put(kSlotBr, br);
+        stage(kSlotBr, br);
+        stage(kSlotDzb, dzb);
+        __syncwarp();
         row(kSlotBr, v);
 #pragma unroll
         for (int p = 0; p < Q; ++p) e_term = fma(k.theta_dt[p], v[2 * p], e_term);
-        R yb;  // yb = y2b + T dzb
-        {
-            put(kSlotDzb, dzb);
-            row(kSlotDzb, v);
+        row(kSlotDzb, v);
+        R yb, db;
+        {  // yb = y2b + T dzb
             R acc = cm.t_row(0) * v[0];
 #pragma unroll
             for (int c = 1; c < D; ++c) acc = fma(cm.t_row(c), v[c], acc);
             yb = y2b + acc;
         }
-        R db;  // db = yb + Dl^T yb
-        {
+        {  // db = yb + Dl^T yb
             put(kSlotYb, yb);
             row(kSlotYb, v);
             R acc = yb;
