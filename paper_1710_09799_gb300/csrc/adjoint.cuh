@@ -64,6 +64,32 @@ __global__ void __launch_bounds__(256) mln_adjoint_reduce(const double *__restri
     if (threadIdx.x == 0) out[k] = part[0];
 }
 
+// acc_add for NR entries of one cell: every entry read before any is written.
+template <int NR>
+__device__ __forceinline__ void acc_add_rows(double *acc, int64_t n, int64_t i, const int (&idx)[NR],
+                                             const double (&v)[NR]) {
+    double old[NR];
+#pragma unroll
+    for (int e = 0; e < NR; ++e) old[e] = acc[idx[e] * n + i];
+#pragma unroll
+    for (int e = 0; e < NR; ++e) acc[idx[e] * n + i] = old[e] + v[e];
+}
+template <int NR>
+__device__ __forceinline__ void acc_add_rows(double *acc_d, int64_t n, int64_t i, const int (&idx)[NR],
+                                             const float (&v)[NR]) {
+    float2 *acc = reinterpret_cast<float2 *>(acc_d);
+    float2 old[NR];
+#pragma unroll
+    for (int e = 0; e < NR; ++e) old[e] = acc[idx[e] * n + i];
+#pragma unroll
+    for (int e = 0; e < NR; ++e) {  // two-sum, as acc_add
+        const float s = old[e].x + v[e];
+        const float bv = s - old[e].x;
+        const float err = (old[e].x - (s - bv)) + (v[e] - bv);
+        acc[idx[e] * n + i] = make_float2(s, old[e].y + err);
+    }
+}
+
 // The same sum over (hi, lo) pairs (FP32 contexts), in FP64.
 __global__ void __launch_bounds__(256) mln_adjoint_reduce_pairs(const float2 *__restrict__ acc, int64_t n,
                                                                 double *__restrict__ out) {
@@ -136,6 +162,13 @@ struct AdjLaneConsts {
     __device__ __forceinline__ R dl_col(int j) const { return dl[j * P + rr]; }
     __device__ __forceinline__ R t_row(int j) const { return t[rr * P + j]; }
     __device__ __forceinline__ R t_col(int j) const { return t[j * P + rr]; }
+};
+
+// Most threads of a reverse-sweep block: FP32 up to 640 (80 cells of 8 lanes,
+// the register file at ~100 registers a thread), FP64 512.
+template <typename R>
+struct AdjThreads {
+    static constexpr int kMax = sizeof(R) == 4 ? 640 : 512;
 };
 
 // Vectors of a step that the lanes of a cell exchange through shared memory
@@ -213,7 +246,7 @@ __device__ __forceinline__ void adj_row_load(const double *p, double (&v)[LN]) {
 // Ebar itself (the Mur cell is vacuum: Ebar_{n-1} = ch Hbar_{n-2} - kappa m),
 // so reading it needs no third barrier.
 template <int N, typename R>
-__global__ void __launch_bounds__(512) mln_adjoint_block(const __grid_constant__ AdjBlockArgs<R> a,
+__global__ void __launch_bounds__(AdjThreads<R>::kMax) mln_adjoint_block(const __grid_constant__ AdjBlockArgs<R> a,
                                                          const __grid_constant__ AdjConsts<N, R> k) {
     constexpr int D = Dims<N>::D, Q = Dims<N>::Q, LN = AdjLanes<N>::value;
     using L = AccLayout<N>;
@@ -470,12 +503,27 @@ __global__ void __launch_bounds__(512) mln_adjoint_block(const __grid_constant__
         };
         if (mrow) {
             a.Sb[r * a.stride + m] = sbar;
+            // this lane's row entries: all loaded first, then added and stored (one
+            // read-modify-write after another would wait a memory round trip each,
+            // since the compiler cannot tell the entries apart)
+            constexpr int NR = D + 2 * Q + 2;
+            R v[NR];
+            int idx[NR];
 #pragma unroll
-            for (int c = 0; c < D; ++c) add(L::Dl + r * D + c, gDl[c]);
+            for (int c = 0; c < D; ++c) {
+                v[c] = gDl[c];
+                idx[c] = L::Dl + r * D + c;
+            }
 #pragma unroll
-            for (int c = 0; c < 2 * Q; ++c) add(L::T + r * D + c, gT[c]);
-            add(L::b + r, gb);
-            add(L::w + r, gw);
+            for (int c = 0; c < 2 * Q; ++c) {
+                v[D + c] = gT[c];
+                idx[D + c] = L::T + r * D + c;
+            }
+            v[NR - 2] = gb;
+            idx[NR - 2] = L::b + r;
+            v[NR - 1] = gw;
+            idx[NR - 1] = L::w + r;
+            acc_add_rows<NR>(a.acc, n, ii, idx, v);
         }
         if (medium && r == 0) add(L::c, gc);
         if (medium && r < 2 * Q && r % 2 == 0) add(L::th + r / 2, gth);
