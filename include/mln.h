@@ -338,11 +338,14 @@ mln_status mln_load_state(mln_ctx *ctx, const double *d_host, const double *Ez_h
  *               its checkpoint, keeping each step's state, fields and traced
  *               intermediates (a "set", about 3 x the state bytes). When the
  *               sets of all segments (about n_steps + n_steps / every of them)
- *               fit the memory limit (mln_set_adjoint_memory), every segment
- *               is recomputed at once, side by side, after the forward pass;
- *               otherwise two segments' sets are kept and segment s - 1 is
- *               recomputed while the reverse sweep of segment s runs. Both
- *               give the same bits.
+ *               fit the memory limit (mln_set_adjoint_memory), a Strang-form
+ *               context on the register model records them in its forward
+ *               pass (nothing recomputed) and any other context recomputes
+ *               every segment at once, side by side, after its forward pass;
+ *               the backward pass then runs from one CUDA graph captured on
+ *               a stream of the call's own. Otherwise two segments' sets are
+ *               kept and segment s - 1 is recomputed while the reverse sweep
+ *               of segment s runs. All give the same bits.
  *   out->J      the objective.
  *   out->dJ_dsrc  NULL or n_steps doubles: dJ / d(source sample k).
  *   out->dJ_dmu   NULL or N*N doubles: dJ / d mu_ll (l = 0..N-1), then
