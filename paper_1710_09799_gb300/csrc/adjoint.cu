@@ -85,8 +85,9 @@ mln_status adjoint_t(mln_ctx *c, int64_t n_steps, const double *src, int64_t pro
     const int64_t n = c->p.n_cells;
     const size_t sb = c->state_bytes, fb = c->field_bytes;
     // a set: state, E, H, then the intermediates of the step from it
-    // (2 D + 2 q rows of `stride`, see StrangTraceCell)
-    const size_t ib = static_cast<size_t>(2 * mln::Dims<N>::D + 2 * mln::Dims<N>::Q) * c->stride * sizeof(R);
+    // (2 D + 2 q rows of `stride`, 2 q more in FP64: see StrangTraceCell)
+    const size_t ib = static_cast<size_t>(2 * mln::Dims<N>::D + (sizeof(R) == 8 ? 4 : 2) * mln::Dims<N>::Q) *
+                      c->stride * sizeof(R);
     const size_t off_I = (sb + 2 * fb + 255) / 256 * 256;
     const size_t set_bytes = (off_I + ib + 255) / 256 * 256;
     const int64_t nseg = (n_steps + every - 1) / every;

@@ -213,9 +213,10 @@ __device__ __forceinline__ void adj_row_load(const double *p, double (&v)[LN]) {
 // AdjLanes lanes of a cell each own one row r < D of every vector and of
 // every product and read the other components of a product's input from
 // the cell's row of an exchange slot in shared memory (each vector stored
-// once, read back whole). The step's forward values d', z and d'' come from
-// the recomputation's trace (StrangTraceCell) and d^{n+1/2} from the next
-// recorded state, so only the transposed products run here; each lane also owns row r of the
+// once, read back whole). The step's forward values d', z, d'' (and in FP64
+// the plane terms) come from the recomputation's trace (StrangTraceCell) and
+// d^{n+1/2} from the next recorded state, so only the transposed products run here;
+// each lane also owns row r of the
 // outer-product gradients, summed in registers over the launch's steps and
 // added to the cell's accumulator column once at the end (interior cells
 // only: halo cells are the neighbouring tiles' interior).
@@ -329,12 +330,19 @@ __global__ void __launch_bounds__(AdjThreads<R>::kMax) mln_adjoint_block(const _
     R z_nx = zrow ? rec_I(a.j_hi, D + r) : R(0);
     R y2_nx = mrow ? rec_I(a.j_hi, D + 2 * Q + r) : R(0);
     R dn_nx = mrow ? rec_S(a.j_hi + 1)[r * a.stride + m] : R(0);
+    // FP64: this lane's plane (r / 2), its sin phi and cos phi - 1 recorded
+    // too (their evaluation is a quarter of the step's FP64 work); FP32
+    // evaluates them (fewer loads on its latency-bound path: measured faster)
+    constexpr bool kRecPlanes = sizeof(R) == 8;
+    R sn_nx = (kRecPlanes && zrow) ? rec_I(a.j_hi, 2 * D + 2 * Q + r / 2) : R(0);
+    R c1_nx = (kRecPlanes && zrow) ? rec_I(a.j_hi, 2 * D + 3 * Q + r / 2) : R(0);
     __syncthreads();  // padded constants in place
 
     for (int s = 0; s < a.nsteps; ++s) {
         const int j = a.j_hi - s;
         const R *E1 = rec_E(j + 1);
         const R e = e_nx, d = d_nx, e1_rec = e1_nx, y = y_nx, z = z_nx, y2 = y2_nx, dn = dn_nx;
+        R snp = sn_nx, c1p = c1_nx;
         if (s + 1 < a.nsteps) {
             e_nx = loaded ? rec_E(j - 1)[ii] : R(0);
             d_nx = mrow ? rec_S(j - 1)[r * a.stride + m] : R(0);
@@ -343,6 +351,10 @@ __global__ void __launch_bounds__(AdjThreads<R>::kMax) mln_adjoint_block(const _
             z_nx = zrow ? rec_I(j - 1, D + r) : R(0);
             y2_nx = mrow ? rec_I(j - 1, D + 2 * Q + r) : R(0);
             dn_nx = d;  // d^{j} is the dn of step j - 1
+            if constexpr (kRecPlanes) {
+                sn_nx = zrow ? rec_I(j - 1, 2 * D + 2 * Q + r / 2) : R(0);
+                c1_nx = zrow ? rec_I(j - 1, 2 * D + 3 * Q + r / 2) : R(0);
+            }
         }
         // adjoint of E^{n+1} with the objective's term; the source's adjoint
         R ebn = ebar;
@@ -373,16 +385,19 @@ __global__ void __launch_bounds__(AdjThreads<R>::kMax) mln_adjoint_block(const _
 
         // the medium: the step's forward values (recorded), then its reverse
         R v[LN];
-        R sn[Q], c1[Q];
-        plane_terms<N>(k.psi_dt, e, sn, c1);
-        // this lane's plane terms, selected in registers (no indexed array)
-        R c1p = c1[0], snp = sn[0];
+        if constexpr (!kRecPlanes) {
+            R sn[Q], c1[Q];
+            plane_terms<N>(k.psi_dt, e, sn, c1);
+            // this lane's plane terms, selected in registers (no indexed array)
+            c1p = c1[0];
+            snp = sn[0];
 #pragma unroll
-        for (int q = 1; q < Q; ++q)
-            if (rr / 2 == q) {
-                c1p = c1[q];
-                snp = sn[q];
-            }
+            for (int q = 1; q < Q; ++q)
+                if (rr / 2 == q) {
+                    c1p = c1[q];
+                    snp = sn[q];
+                }
+        }
         const R z_pair = __shfl_xor_sync(full, z, 1, LN);
         R dz = R(0);  // (R - I) z
         if (r < 2 * Q) dz = (r % 2 == 0) ? fma(c1p, z, snp * z_pair) : fma(c1p, z, -(snp * z_pair));

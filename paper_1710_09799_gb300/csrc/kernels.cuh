@@ -207,9 +207,8 @@ __device__ __forceinline__ void plane_terms(const R *psi_dt, R e, R (&s)[Dims<N>
 // [[0, theta], [-theta, 0]] of T^T U T over E dt; the null space of U (the
 // last N - 1 coordinates) does not change.
 template <int N, typename R>
-__device__ __forceinline__ void rotation_increment(R (&z)[Dims<N>::D], const R *psi_dt, R e) {
-    R s[Dims<N>::Q], c1[Dims<N>::Q];
-    plane_terms<N>(psi_dt, e, s, c1);
+__device__ __forceinline__ void rotation_apply(R (&z)[Dims<N>::D], const R (&s)[Dims<N>::Q],
+                                               const R (&c1)[Dims<N>::Q]) {
 #pragma unroll
     for (int k = 0; k < Dims<N>::Q; ++k) {
         const R x = z[2 * k], y = z[2 * k + 1];
@@ -218,6 +217,12 @@ __device__ __forceinline__ void rotation_increment(R (&z)[Dims<N>::D], const R *
     }
 #pragma unroll
     for (int i = 2 * Dims<N>::Q; i < Dims<N>::D; ++i) z[i] = R(0);
+}
+template <int N, typename R>
+__device__ __forceinline__ void rotation_increment(R (&z)[Dims<N>::D], const R *psi_dt, R e) {
+    R s[Dims<N>::Q], c1[Dims<N>::Q];
+    plane_terms<N>(psi_dt, e, s, c1);
+    rotation_apply<N>(z, s, c1);
 }
 
 // y = x + (A x + b) with A row-major D x D held in the constant bank.
@@ -443,7 +448,8 @@ struct CellTraces<C, mln_void_t<decltype(C::kTrace)>> {
 // The Strang step of RegisterCell<N, R, StrangConsts> (same operations, same
 // bits) that also writes the step's intermediates for the reverse sweep of
 // the adjoint: rows 0..D-1 d' = A0 d + b, rows D..D+2q-1 the plane rows of
-// z = T^T d', rows D+2q..2D+2q-1 d'' = d' + T (R - I) z, each row `stride`
+// z = T^T d', rows D+2q..2D+2q-1 d'' = d' + T (R - I) z, then (FP64) q rows
+// of the planes' sin phi_k and q rows of cos phi_k - 1, each row `stride`
 // apart, at the pointer given by trace_to before the step (nullptr: none).
 template <int N, typename R>
 struct StrangTraceCell {
@@ -479,11 +485,20 @@ struct StrangTraceCell {
 #pragma unroll
             for (int i = 0; i < P; ++i) tp[(D + i) * ts + tm] = s[i];
         }
-        rotation_increment<N>(s, k.psi_dt, e);  // (R - I) z
-        matvec_acc<D>(y, k.T, s);               // d'' = d' + T (R - I) z
+        R sn[P / 2], c1[P / 2];
+        plane_terms<N>(k.psi_dt, e, sn, c1);
+        rotation_apply<N>(s, sn, c1);  // (R - I) z, as rotation_increment
+        matvec_acc<D>(y, k.T, s);      // d'' = d' + T (R - I) z
         if (tp) {
 #pragma unroll
             for (int i = 0; i < D; ++i) tp[(D + P + i) * ts + tm] = y[i];
+            if constexpr (sizeof(R) == 8) {
+#pragma unroll
+                for (int i = 0; i < P / 2; ++i) {
+                    tp[(2 * D + P + i) * ts + tm] = sn[i];
+                    tp[(2 * D + P + P / 2 + i) * ts + tm] = c1[i];
+                }
+            }
         }
         affine_inc<D>(s, k.Dl, y, k.b);  // d = A0 d'' + b
         return dot_bias<D>(k.w, s, k.c);
