@@ -62,23 +62,24 @@ FP32_FLOP_PER_CLK_SM = 256
 # An entry is used only while the kernel sources hash to the value recorded
 # with it; after any change to them the traffic is reported as null.
 # dram__bytes_read.sum + dram__bytes_write.sum of one launch (ncu, same launch shape, tile 432),
-# profiles/mln_block_kernel_fp64_sparse_three_level_ring.md
+# profiles/mln_jit_step_fp64_three_level_ring.md (the default run-time compiled
+# kernel)
 MEASURED_TRAFFIC = {
-    ("sparse", "fp64", "three_level_ring", 8): (5276160.0, "ncu, --block-steps 8 --tile 432"),
-    ("sparse", "fp64", "three_level_ring", 12): (5276416.0, "ncu, --block-steps 12 --tile 432"),
-    ("sparse", "fp64", "three_level_ring", 16): (5276160.0, "ncu, --block-steps 16 --tile 432"),
-    ("sparse", "fp64", "three_level_ring", 20): (5276160.0, "ncu, --block-steps 20 --tile 432"),
+    ("jit", "fp64", "three_level_ring", 8): (5274112.0, "ncu, --block-steps 8 --tile 432"),
+    ("jit", "fp64", "three_level_ring", 12): (5274368.0, "ncu, --block-steps 12 --tile 432"),
+    ("jit", "fp64", "three_level_ring", 16): (5274624.0, "ncu, --block-steps 16 --tile 432"),
+    ("jit", "fp64", "three_level_ring", 20): (5274112.0, "ncu, --block-steps 20 --tile 432"),
 }
-# sha256 of the sources the measured kernel (the sparse FP64 step kernel) is
-# compiled from, when the counters were taken: a later change of one of them
-# makes the reported traffic null until it is measured again
-TRAFFIC_SOURCES_SHA = "5a19aee66b6c1fc15fe3f2e533b3e73b2d808852fb05d4c154afb5eb51c54114"
+# sha256 of the sources the measured kernels (the FP64 step kernels) are
+# compiled or generated from, when the counters were taken: a later change of
+# one of them makes the reported traffic null until it is measured again
+TRAFFIC_SOURCES_SHA = "2d73899f3243dad8a323f20f3d2f78955f2192e5af195f86b4d9cd218bbbf0d4"
 
 
 def kernel_sources_sha() -> str:
     import hashlib
     h = hashlib.sha256()
-    for f in ("kernels.cuh", "dispatch.cuh", "kernels_fp64.cu"):
+    for f in ("kernels.cuh", "dispatch.cuh", "kernels_fp64.cu", "jit.cu"):
         h.update(open(os.path.join(ROOT, "paper_1710_09799_gb300", "csrc", f), "rb").read())
     return h.hexdigest()
 

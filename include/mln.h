@@ -85,10 +85,11 @@ enum { MLN_FORM_STRANG = 0, MLN_FORM_MERGED = 1, MLN_FORM_RODRIGUES = 2, MLN_FOR
  * MLN_KERNEL_SPARSE (FP64, merged form only) keeps the vectors in shared
  * memory and multiplies only by the entries of the constant matrices that
  * are not exactly zero; the sums run in the same order, so both give the
- * same result. MLN_KERNEL_AUTO picks SPARSE for FP64 merged, TENSOR for FP32
- * merged or rotated with N = 5 or 6 (the dense case), JIT for the other FP32
- * merged problems when NVRTC is available and for the other rotated-basis
- * problems, REGISTER otherwise. */
+ * same result. MLN_KERNEL_AUTO picks TENSOR for FP32 merged or rotated with
+ * N = 5 or 6 (the dense case); JIT for the other merged FDTD problems (FP64
+ * and FP32) when NVRTC is available and for the other rotated-basis problems;
+ * SPARSE for FP64 merged problems otherwise (without NVRTC, or with the PSTD
+ * field solver); REGISTER otherwise. */
 /* MLN_KERNEL_JIT (merged form) generates, at mln_create, this problem's step
  * as straight-line CUDA with the constants as literals and the exactly-zero
  * entries left out, compiles it for sm_103a at run time (NVRTC) and launches

@@ -9,7 +9,7 @@
   samples, the dipole element, the relaxation strength), J against the
   oracle's J, and one finite difference through the oracle.
 * A soft source on an open grid (the source cell's field passes through).
-* Merged-form contexts (the FP64 default uses the sparse cell model): the
+* Merged-form contexts (sparse, register and run-time compiled cell models): the
   forward pass runs the merged step, the backward pass recomputes in the
   Strang form from checkpoints mapped to d; J and the gradients equal those of
   a Strang-form context up to rounding.
