@@ -609,11 +609,13 @@ def _rec_six_level(out, refs):
 
 def _rec_batched(out, refs):
     """batched devices (256 grids, N in {2, 3, 4}, 1k-64k cells): the smallest
-    grid of each N compared with the oracle after the first 1000 steps"""
+    grid of each N compared with the oracle after the first 1000 steps; the
+    default launch structure (a graph of chunked launches) timed, then the
+    persistent launch on the same batch"""
     import torch
     from paper_1710_09799_gb300 import mln
     for prec, seg, steps in (("fp32", 1000, 3), ("fp64", 100, 3)):
-        total = 1000 + (3 + steps) * seg
+        total = 1000 + (4 + 2 * steps) * seg
         devs = W.batched_devices(n_steps=total)
         pars = [make_params(d, prec, "merged") for d in devs]
         srcs = [d.source_samples(0, total) for d in devs]
@@ -635,18 +637,26 @@ def _rec_batched(out, refs):
             b.step(seg)
         b.sync()
         flush_buf = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
-        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
-        l0 = b.shape[3]
-        torch.cuda.synchronize()
-        with torch.cuda.stream(b.stream):
-            for i in range(steps):
-                flush_buf.fill_(i & 0xFF)
-                evs[i][0].record(b.stream)
-                b.step(seg)
-                evs[i][1].record(b.stream)
-        torch.cuda.synchronize()
-        ms = sum(x.elapsed_time(y) for x, y in evs)
-        launches = b.shape[3] - l0
+
+        def timed():
+            evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+            l0 = b.shape[3]
+            torch.cuda.synchronize()
+            with torch.cuda.stream(b.stream):
+                for i in range(steps):
+                    flush_buf.fill_(i & 0xFF)
+                    evs[i][0].record(b.stream)
+                    b.step(seg)
+                    evs[i][1].record(b.stream)
+            torch.cuda.synchronize()
+            return sum(x.elapsed_time(y) for x, y in evs), b.shape[3] - l0
+
+        ms, launches = timed()
+        b.set_launch("persistent")
+        b.step(seg)  # capture of the persistent call's graph, outside the timed steps
+        b.sync()
+        ms_p, launches_p = timed()
+        b.sync()
         flops = 0.0
         for i, d in enumerate(devs):
             f_med, f_cell, _, _ = mln.mln_work_per_step(mln.mln_batch_context(b.b, i))
@@ -664,6 +674,10 @@ def _rec_batched(out, refs):
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                          "traffic": None, "kernel": "mln_jit_batch (one launch per N per K steps)"},
             "error_vs_oracle": {"after": "1000 steps", "devices": errs, "oracle_s": t_orc},
+            "persistent_launch": {"value": cells * seg * steps / (ms_p / 1e3), "unit": UNIT,
+                                  "ms_per_1000_steps": ms_p / (seg * steps) * 1e3, "gpu_launches": launches_p,
+                                  "note": "the same batch after mln_batch_set_launch(MLN_BATCH_PERSISTENT): one "
+                                          "launch per call and N (mln_jit_batch_persist); not the default"},
         }
 
 
