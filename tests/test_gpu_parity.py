@@ -426,3 +426,27 @@ def test_rotated_form_six_level_costs_fewer_flops_and_agrees_with_merged():
     assert rel_inf(b[0], a[0]) < 1e-11
     assert np.abs(b[2] - a[2]).max() < 1e-11
 
+
+
+@pytest.mark.parametrize("precision,form,maxwell,N,want", [
+    ("fp64", "merged", "fdtd", 3, "jit"),        # the run-time compiled model (NVRTC on the GPU machine)
+    ("fp64", "merged", "pstd", 3, "sparse"),     # PSTD takes the sparse model
+    ("fp64", "strang", "fdtd", 3, "register"),
+    ("fp32", "merged", "fdtd", 3, "jit"),
+    ("fp32", "merged", "fdtd", 6, "tensor"),
+    ("fp32", "rotated", "fdtd", 6, "tensor"),
+    ("fp64", "rotated", "fdtd", 6, "jit"),
+])
+def test_auto_cell_model_choice(precision, form, maxwell, N, want):
+    """MLN_KERNEL_AUTO's choice per precision, form, field solver and N (the
+    models give the same bits where they overlap; the choice is the faster)."""
+    if N == 3:
+        p = W.three_level_ring(n_cells=1024, n_steps=10) if maxwell == "fdtd" else W.three_level_ring_pstd(
+            n_cells=1024, n_steps=10)
+    else:
+        p = W.six_level_pulse(n_cells=600, n_steps=10, t0=15e-15, fwhm=10e-15)
+    s = make_solver(p, precision, form)
+    assert s.kernel_in_use == want
+    s.step(2)
+    s.sync()
+    s.close()
