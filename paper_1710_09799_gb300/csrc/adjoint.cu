@@ -1,17 +1,20 @@
 // mln_adjoint: gradients of a probe-field objective by the discrete adjoint
 // (reverse-time) method with checkpointing and recomputation.
 //
-// Forward: the context's own step (any form and cell model) advances it,
-// saving the state at the start of every segment of `every` steps.
-// Backward: for the segments in reverse order, the segment is recomputed from
-// its checkpoint in the literal Strang form by the fused step kernel with
-// every step's state and intermediates recorded (all kept; a checkpoint of another
-// form is first mapped to the adjoint vector d, which these forms share up to
-// rounding: the merged and rotated forms hold an affine image of d), then the
-// reverse step kernel runs from the segment's last step to its first,
-// carrying the adjoint of (E, H, d) and accumulating the gradients of the
-// step's constants. The host then maps those to the dipole operator and the
-// relaxation superoperator (exact Frechet derivatives, see adjoint_chain).
+// The reverse sweep reads, for every step, a recorded "set": the step's
+// state, fields and the intermediates of its medium step, written by the
+// tracing kernel (the literal Strang step). Where the sets of all segments
+// of `every` steps fit the memory limit, a Strang-form context on the
+// register model records them in its forward pass and any other context
+// recomputes all segments side by side from its checkpoints (mapped to the
+// adjoint vector d, which all forms share up to rounding: the merged and
+// rotated forms hold an affine image of d); the backward pass is then
+// replayed from one CUDA graph. Otherwise segment s - 1 is recomputed while
+// the reverse sweep of segment s runs. The reverse sweep runs from each
+// segment's last step to its first, carrying the adjoint of (E, H, d) and
+// accumulating the gradients of the step's constants; the host maps those
+// to the dipole operator and the relaxation superoperator (exact Frechet
+// derivatives, see adjoint_chain).
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -144,10 +147,11 @@ mln_status adjoint_t(mln_ctx *c, int64_t n_steps, const double *src, int64_t pro
     // Two ways to schedule the recomputation (segments are independent given
     // their checkpoints; a ring of a few thousand cells leaves most of the GPU
     // idle in one segment's launches):
-    // - all at once, when every segment's slot fits in half the free device
-    //   memory: after the forward pass, each launch advances the same steps of
-    //   all full segments side by side (grid y = segment), then the reverse
-    //   sweeps run segment after segment;
+    // - all at once, when every segment's slot fits the memory limit (by
+    //   default half the free device memory): the forward pass records them
+    //   (Strang contexts on the register model), or after it each launch
+    //   advances the same steps of all full segments side by side (grid y =
+    //   segment); then the reverse sweeps run segment after segment;
     // - otherwise two slot buffers: segment s - 1 is recomputed on a second
     //   stream while the reverse sweep of segment s runs; events order the
     //   recompute after the sweep that last used its buffer, and each sweep
