@@ -193,9 +193,9 @@ __device__ __forceinline__ void plane_terms(const R *psi_dt, R e, R (&s)[Dims<N>
             if (b == N - 1) {
                 s[k] = sp[a];
                 c1[k] = cp[a];
-            } else {
-                s[k] = (sp[a] - sp[b]) + fma(sp[a], cp[b], -(cp[a] * sp[b]));
-                c1[k] = (cp[a] + cp[b]) + fma(cp[a], cp[b], sp[a] * sp[b]);
+            } else {  // three operations each: the two products fused onto the sum
+                s[k] = fma(sp[a], cp[b], fma(-cp[a], sp[b], sp[a] - sp[b]));
+                c1[k] = fma(cp[a], cp[b], fma(sp[a], sp[b], cp[a] + cp[b]));
             }
             ++k;
         }
