@@ -356,13 +356,19 @@ mln_status mln_load_state(mln_ctx *ctx, const double *d_host, const double *Ez_h
  *   out->dJ_dG    NULL or (N*N)^2 complex (interleaved): Gamma with
  *               dJ = Re sum_rc conj(Gamma_rc) dG_rc for the relaxation
  *               superoperator of the parameter set (zero rows and columns included).
- * Device memory for checkpoints and adjoints is allocated inside the call and
- * freed before it returns. Synchronises.
+ * Device memory for the checkpoints, the recorded sets and the adjoints is one
+ * workspace that the context keeps after the call and reuses in its next
+ * mln_adjoint call when it is large enough (else it is freed and a larger one
+ * allocated); mln_adjoint_release or mln_destroy frees it. Synchronises.
  *
  * mln_set_adjoint_memory: the most device memory, in bytes, that mln_adjoint
  * on this context may take for the recorded sets of all segments at once;
- * 0 (the default): half the free device memory at the call. MLN_EINVAL for a
- * negative value.
+ * 0 (the default): half of the free device memory at the call plus the
+ * workspace the context already holds. MLN_EINVAL for a negative value.
+ *
+ * mln_adjoint_release: wait for the context's stream, then free the adjoint
+ * workspace it holds (nothing to do if it holds none). MLN_EINVAL for NULL,
+ * MLN_ECUDA if the wait or the free fails.
  */
 typedef struct mln_adjoint_out {
     double J;
@@ -371,6 +377,7 @@ typedef struct mln_adjoint_out {
     double *dJ_dG;
 } mln_adjoint_out;
 mln_status mln_set_adjoint_memory(mln_ctx *ctx, int64_t bytes);
+mln_status mln_adjoint_release(mln_ctx *ctx);
 mln_status mln_adjoint(mln_ctx *ctx, int64_t n_steps, const double *src, int64_t probe_cell, int32_t every,
                        mln_adjoint_out *out);
 

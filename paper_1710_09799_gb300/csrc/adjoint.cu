@@ -176,10 +176,22 @@ mln_status adjoint_t(mln_ctx *c, int64_t n_steps, const double *src, int64_t pro
     {
         size_t free_b = 0, total_b = 0;
         if (nfull <= 65535 && cudaMemGetInfo(&free_b, &total_b) == cudaSuccess) {
-            const double limit = c->adj_mem > 0 ? static_cast<double>(c->adj_mem) : 0.5 * static_cast<double>(free_b);
+            // the workspace this context already holds counts as free
+            const double avail = static_cast<double>(free_b) + static_cast<double>(c->adj_buf_bytes);
+            const double limit = c->adj_mem > 0 ? static_cast<double>(c->adj_mem) : 0.5 * avail;
             all_at_once = static_cast<double>(nseg) * static_cast<double>(slot_bytes) <= limit;
         }
     }
+    // the workspace's parts: offsets of the slots, the adjoint sets, the
+    // accumulators, their sums and dJ/dsrc from its base (the checkpoints)
+    auto up256 = [](size_t b) { return (b + 255) / 256 * 256; };
+    size_t ws_off[5];
+    ws_off[0] = up256(static_cast<size_t>(nseg) * set_bytes);
+    ws_off[1] = ws_off[0] + up256(static_cast<size_t>(all_at_once ? nseg : 2) * slot_bytes);
+    ws_off[2] = ws_off[1] + up256(2 * set_bytes);
+    ws_off[3] = ws_off[2] + up256(static_cast<size_t>(L::size) * n * sizeof(double));
+    ws_off[4] = ws_off[3] + up256(static_cast<size_t>(L::size) * sizeof(double));
+    const size_t ws_need = ws_off[4] + (src ? up256(static_cast<size_t>(n_steps) * sizeof(double)) : 0);
     auto slot_of = [&](int64_t sg) { return all_at_once ? slots + sg * slot_bytes : slot_buf[sg & 1]; };
     // A Strang-form context whose step is the register model (the tracing
     // kernel's arithmetic) and whose segments all fit: its forward pass can
@@ -242,8 +254,23 @@ mln_status adjoint_t(mln_ctx *c, int64_t n_steps, const double *src, int64_t pro
         return e;
     };
 
-    MLN_ACK(c, cudaMalloc(&ckpt, nseg * set_bytes));
-    MLN_ACK(c, cudaMalloc(&slots, (all_at_once ? nseg : 2) * slot_bytes));
+    // One workspace, kept by the context for its next call (an optimisation
+    // loop evaluates the gradient again and again; allocating and freeing
+    // 5-13 GB took 4-8 ms a call): checkpoints | slots | adjoint sets |
+    // accumulators | their sums | dJ/dsrc, each on a 256-byte boundary.
+    if (c->adj_buf_bytes < ws_need) {
+        cudaFree(c->adj_buf);  // synchronises with the device first
+        c->adj_buf = nullptr;
+        c->adj_buf_bytes = 0;
+        MLN_ACK(c, cudaMalloc(&c->adj_buf, ws_need));
+        c->adj_buf_bytes = ws_need;
+    }
+    ckpt = c->adj_buf;
+    slots = ckpt + ws_off[0];
+    adj = ckpt + ws_off[1];
+    acc = reinterpret_cast<double *>(ckpt + ws_off[2]);
+    accsum = reinterpret_cast<double *>(ckpt + ws_off[3]);
+    dsrc = src ? reinterpret_cast<double *>(ckpt + ws_off[4]) : nullptr;
     slot_buf[0] = slots;
     slot_buf[1] = slots + slot_bytes;
     MLN_ACK(c, cudaStreamCreateWithFlags(&rs, cudaStreamNonBlocking));
@@ -252,10 +279,6 @@ mln_status adjoint_t(mln_ctx *c, int64_t n_steps, const double *src, int64_t pro
         MLN_ACK(c, cudaEventCreateWithFlags(&ev_rec[b], cudaEventDisableTiming));
         MLN_ACK(c, cudaEventCreateWithFlags(&ev_rev[b], cudaEventDisableTiming));
     }
-    MLN_ACK(c, cudaMalloc(&adj, 2 * set_bytes));
-    MLN_ACK(c, cudaMalloc(&acc, L::size * n * sizeof(double)));
-    MLN_ACK(c, cudaMalloc(&accsum, L::size * sizeof(double)));
-    if (src) MLN_ACK(c, cudaMalloc(&dsrc, n_steps * sizeof(double)));
 
     if (!traced_forward) {
         // forward with checkpoints, the context's own step on its stream
@@ -398,12 +421,6 @@ done:
     }
     if (graph_exec) cudaGraphExecDestroy(graph_exec);
     if (graph) cudaGraphDestroy(graph);
-    cudaFree(ckpt);
-    cudaFree(slots);
-    cudaFree(adj);
-    cudaFree(acc);
-    cudaFree(accsum);
-    cudaFree(dsrc);
     return st;
 }
 
@@ -414,6 +431,21 @@ extern "C" {
 mln_status mln_set_adjoint_memory(mln_ctx *c, int64_t bytes) {
     if (!c || bytes < 0) return MLN_EINVAL;
     c->adj_mem = bytes;
+    return MLN_OK;
+}
+
+mln_status mln_adjoint_release(mln_ctx *c) {
+    if (!c) return MLN_EINVAL;
+    if (c->adj_buf) {
+        cudaError_t e = cudaStreamSynchronize(c->stream);
+        if (e == cudaSuccess) e = cudaFree(c->adj_buf);
+        c->adj_buf = nullptr;
+        c->adj_buf_bytes = 0;
+        if (e != cudaSuccess) {
+            c->err = std::string("adjoint workspace release: ") + cudaGetErrorString(e);
+            return MLN_ECUDA;
+        }
+    }
     return MLN_OK;
 }
 

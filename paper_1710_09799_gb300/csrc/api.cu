@@ -561,6 +561,7 @@ void mln_destroy(mln_ctx *c) {
     cudaFree(c->scratch);
     cudaFree(c->prog);
     cudaFree(c->tc_img);
+    cudaFree(c->adj_buf);
     mln::pstd_free(c);
     delete c;
 }

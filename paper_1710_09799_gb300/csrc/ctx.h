@@ -32,6 +32,8 @@ struct mln_ctx {
     int tc = 0;                        // tensor-core cell model: 0 none, MLN_KERNEL_TENSOR(_SMEM)
     bool tcr = false;                  // ... for the rotated basis (MLN_FORM_ROTATED)
     int64_t adj_mem = 0;               // mln_adjoint's limit for the recorded segments (0: half the free memory)
+    unsigned char *adj_buf = nullptr;  // mln_adjoint's device workspace, kept between calls
+    size_t adj_buf_bytes = 0;
     int sms = 152;                     // SMs of the context's device
     void *tc_img = nullptr;            // its B-operand image (device)
     std::vector<unsigned char> tc_scal;  // and scalar constants

@@ -105,6 +105,7 @@ _SIGS = {
     "mln_adjoint": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_int64, C.c_int32,
                               C.POINTER(mln_adjoint_out)]),
     "mln_set_adjoint_memory": (C.c_int, [C.c_void_p, C.c_int64]),
+    "mln_adjoint_release": (C.c_int, [C.c_void_p]),
     "mln_batch_create": (C.c_int, [C.c_int32, _P, C.POINTER(C.c_void_p), C.POINTER(C.c_void_p),
                                    C.POINTER(C.c_void_p), C.POINTER(C.c_void_p), C.c_int64, C.c_void_p,
                                    C.POINTER(C.c_void_p)]),
@@ -471,8 +472,14 @@ class Solver:
 # ------------------------------------------------------------------ adjoint
 
 def mln_set_adjoint_memory(ctx, n_bytes: int):
-    """Limit of mln_adjoint's recorded sets of all segments at once (0: half the free memory)."""
+    """Limit of mln_adjoint's recorded sets of all segments at once (0: half of
+    the free memory plus the workspace the context holds)."""
     _check(lib().mln_set_adjoint_memory(ctx, n_bytes), ctx)
+
+
+def mln_adjoint_release(ctx):
+    """Free the adjoint workspace the context keeps between mln_adjoint calls."""
+    _check(lib().mln_adjoint_release(ctx), ctx)
 
 
 def mln_adjoint(ctx, N: int, n_steps: int, src_ptr: int | None, probe_cell: int, every: int):

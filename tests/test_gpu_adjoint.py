@@ -178,6 +178,38 @@ def test_adjoint_memory_limit_rejects_negative(small):
     s.close()
 
 
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_workspace_kept_between_calls(small, precision):
+    """The context keeps its adjoint workspace between calls: from the same
+    initial state (reloaded) a second call gives the bits of a fresh context;
+    a longer run grows the workspace; after mln_adjoint_release the next call
+    allocates again, with the same bits."""
+    import torch
+    from paper_1710_09799_gb300 import mln
+    p, src, _ = small
+    fresh = J_and_grads(p, src, precision=precision)
+    src2 = np.concatenate([src, np.zeros(100)])
+    fresh2 = J_and_grads(p, src2, precision=precision)
+    s = mln.Solver(params_of(p, precision=precision, form="strang"), E0=p.e_init())
+    s0 = s.save()
+    t = torch.as_tensor(src, dtype=torch.float64, device="cuda")
+    t2 = torch.as_tensor(src2, dtype=torch.float64, device="cuda")
+
+    def call(tt):
+        s.load(*s0)
+        return mln.mln_adjoint(s.ctx, p.N, tt.numel(), tt.data_ptr(), p.meta["probe_cell"], 32)
+
+    runs = [(call(t), fresh), (call(t), fresh), (call(t2), fresh2), (call(t), fresh)]
+    mln.mln_adjoint_release(s.ctx)
+    mln.mln_adjoint_release(s.ctx)  # nothing held: no-op
+    runs.append((call(t), fresh))
+    s.close()
+    for got, want in runs:
+        assert got[0] == want[0]
+        for x, y in zip(got[1:], want[1:]):
+            assert np.array_equal(x, y)
+
+
 def test_fp32_adjoint_close_to_fp64(small):
     p, src, (J, dsrc, dmu, dG) = small
     J3, dsrc3, dmu3, dG3 = J_and_grads(p, src, precision="fp32")
