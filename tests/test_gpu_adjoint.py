@@ -152,6 +152,28 @@ def test_checkpoint_interval_does_not_change_gradients(small):
     assert rel_inf(dsrc2, dsrc) < 1e-10 and rel_inf(dmu2, dmu) < 1e-10 and rel_inf(dG2, dG) < 1e-10
 
 
+@pytest.mark.parametrize("n_steps,every", [(1, 1), (2, 1), (5, 1), (5, 2), (13, 5)])
+def test_short_runs_and_one_step_segments(orc, n_steps, every):
+    """Runs shorter than one reverse launch, segments of one step, the probe on
+    the source cell next to the ring's wrap: J against the oracle, the
+    gradients equal to those of a single segment, dJ/dsrc against central
+    differences."""
+    p = W.adjoint_ring(n_cells=512, n_steps=n_steps, n_src=n_steps, amplitude=3e7)
+    p.meta["probe_cell"] = 0
+    src = p.source_samples(0, n_steps)
+    J, dsrc, dmu, dG = J_and_grads(p, src, every=every)
+    _, probe = orc.run(p, n_steps=n_steps, probe_cell=0)
+    Jo = p.dt * np.sum(probe ** 2)
+    assert Jo > 0 and abs(J - Jo) < 1e-10 * Jo, (J, Jo)
+    J1, dsrc1, dmu1, dG1 = J_and_grads(p, src, every=10 ** 6)
+    assert abs(J1 - J) <= 1e-12 * J
+    assert rel_inf(dsrc1, dsrc) < 1e-10 and rel_inf(dmu1, dmu) < 1e-10 and rel_inf(dG1, dG) < 1e-10
+    d = np.random.default_rng(n_steps).normal(size=n_steps)
+    h = 1e-6 * np.abs(src).max()
+    fd = (J_only(p, src + h * d) - J_only(p, src - h * d)) / (2 * h)
+    assert abs(fd - dsrc @ d) < 1e-6 * abs(dsrc @ d), (fd, dsrc @ d)
+
+
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
 @pytest.mark.parametrize("every", [7, 32])
 def test_recompute_schedules_give_the_same_bits(small, precision, every):
