@@ -61,19 +61,21 @@ FP32_FLOP_PER_CLK_SM = 256
 # (profiles/*.md), keyed by (cell model, precision, workload, steps per launch).
 # An entry is used only while the kernel sources hash to the value recorded
 # with it; after any change to them the traffic is reported as null.
-# dram__bytes_read.sum + dram__bytes_write.sum of one launch (ncu, same launch shape, tile 432),
-# profiles/mln_jit_step_fp64_three_level_ring.md (the default run-time compiled
-# kernel)
+# dram__bytes_read.sum + dram__bytes_write.sum of one launch (ncu, the launch
+# shape given), profiles/mln_jit_step_fp64_three_level_ring.md (the default
+# run-time compiled kernel) and profiles/mln_jit_step_df32_three_level_ring.md
+# (its double-float variant)
 MEASURED_TRAFFIC = {
-    ("jit", "fp64", "three_level_ring", 8): (5274368.0, "ncu, --block-steps 8 --tile 432"),
-    ("jit", "fp64", "three_level_ring", 12): (5273856.0, "ncu, --block-steps 12 --tile 432"),
-    ("jit", "fp64", "three_level_ring", 16): (5274368.0, "ncu, --block-steps 16 --tile 432"),
-    ("jit", "fp64", "three_level_ring", 20): (5274112.0, "ncu, --block-steps 20 --tile 432"),
+    ("jit", "fp64", "three_level_ring", 8): (5273856.0, "ncu, --block-steps 8 --tile 432"),
+    ("jit", "fp64", "three_level_ring", 12): (5274112.0, "ncu, --block-steps 12 --tile 432"),
+    ("jit", "fp64", "three_level_ring", 16): (5274112.0, "ncu, --block-steps 16 --tile 432"),
+    ("jit", "fp64", "three_level_ring", 20): (5274368.0, "ncu, --block-steps 20 --tile 432"),
+    ("df32", "fp64", "three_level_ring", 10): (5295104.0, "ncu, --kernel df32 --block-steps 10 --tile 108"),
 }
-# sha256 of the sources the measured kernels (the FP64 step kernels) are
+# sha256 of the sources the measured kernels (the FP64 and double-float step kernels) are
 # compiled or generated from, when the counters were taken: a later change of
 # one of them makes the reported traffic null until it is measured again
-TRAFFIC_SOURCES_SHA = "5ae4e9ab0ab61ffc13f39161755e96938160013c1ce89a71a5403b83ebd8b4fa"
+TRAFFIC_SOURCES_SHA = "6998ef592cd59b7d4da0d1303f8b537effc7aa3f9c776f0d146041ec9ee6e14a"
 
 
 def kernel_sources_sha() -> str:
@@ -286,19 +288,19 @@ def make_params(p, precision, form, block_steps=0, tile_cells=0, kernel="auto"):
 
 def fp32_error_vs_oracle(ref, n_cells=4096, n_steps=2000):
     """The error the FP32 rates come with: E_z (relative, infinity norm) and
-    populations (absolute) of the FP32 and FP64 paths (merged form) against the
-    FP64 oracle's result `ref` for a 4096-cell ring with the parameters of the
-    benchmark ring, after 2000 steps."""
+    populations (absolute) of the FP32, FP64 and double-float paths (merged
+    form) against the FP64 oracle's result `ref` for a 4096-cell ring with the
+    parameters of the benchmark ring, after 2000 steps."""
     from paper_1710_09799_gb300 import mln
     q = W.three_level_ring(n_cells=n_cells, n_steps=n_steps)
     out = {"case": f"three-level ring, {n_cells} cells x {n_steps} steps, merged form, against the FP64 oracle"}
-    for prec in ("fp32", "fp64"):
-        s = mln.Solver(make_params(q, prec, "merged"), E0=q.e_init())
+    for key, prec, kern in (("fp32", "fp32", "auto"), ("fp64", "fp64", "auto"), ("df32", "fp64", "df32")):
+        s = mln.Solver(make_params(q, prec, "merged", kernel=kern), E0=q.e_init())
         s.step(n_steps)
         s.sync()
         E, pops = s.fields()[0], s.populations()
         s.close()
-        out[prec] = _oracle_error(E, pops, ref)
+        out[key] = _oracle_error(E, pops, ref)
     return out
 
 
@@ -891,7 +893,7 @@ def main():
     ap.add_argument("--seg", type=int, default=1000, help="time steps per benchmark step")
     ap.add_argument("--block-steps", type=int, default=0, help="0: autotuned")
     ap.add_argument("--tile", type=int, default=0)
-    ap.add_argument("--kernel", default="auto", choices=["auto", "register", "sparse", "jit", "tensor"])
+    ap.add_argument("--kernel", default="auto", choices=["auto", "register", "sparse", "jit", "tensor", "df32"])
     ap.add_argument("--workload", default="three_level_ring", choices=sorted(WORKLOADS))
     ap.add_argument("--quick", action="store_true", help="skip variants, e2e and the CPU baseline")
     ap.add_argument("--batch-launch", default="default", choices=["default", "chunks", "persistent"],
@@ -933,7 +935,9 @@ def main():
     flops_per_step = p.n_medium * f_med + p.n_cells * f_cell
     achieved = flops_per_step * (args.seg * args.steps / max(launches, 1)) / per_launch_s / 1e12
     peak = alu_peak_tflops(args.precision)
-    kname = "mln_jit_step" if main_run["kernel"] == "jit" else f"mln_block_kernel ({main_run['kernel']} cell model)"
+    kname = ("mln_jit_step" if main_run["kernel"] == "jit" else
+             "mln_jit_step (double-float cell update)" if main_run["kernel"] == "df32" else
+             f"mln_block_kernel ({main_run['kernel']} cell model)")
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "kernel": kname,
                 "frac": achieved / peak,
@@ -945,6 +949,18 @@ def main():
     clk = main_run["clocks"] or {}
     if clk.get("sm_mhz"):
         roofline["frac_at_measured_clock"] = achieved / alu_peak_tflops(args.precision, clk["sm_mhz"])
+    if main_run["kernel"] == "df32":
+        # the pairs run on the FP32 pipe: the method's (FP64-equivalent) flops
+        # against the FP32 ALU peak, and their ratio to the FP64 peak beside it
+        p32 = alu_peak_tflops("fp32")
+        roofline.update({"peak": p32, "frac": achieved / p32, "frac_of_fp64_peak": achieved / peak,
+                         "peak_source": f"derived: {SMS} SMs x {FP32_FLOP_PER_CLK_SM} flop/clk x {SM_MAX_MHZ:.0f} MHz "
+                                        "(FP32: the double-float pairs run on the FP32 pipe)",
+                         "note": "achieved counts the method's flops; a pair operation costs 6 to 12 FP32 "
+                                 "instructions (ncu: 1378 FP32 thread instructions per computed cell-step, "
+                                 "issue 71 % active, FMA pipe 66 %)"})
+        if clk.get("sm_mhz"):
+            roofline["frac_at_measured_clock"] = achieved / alu_peak_tflops("fp32", clk["sm_mhz"])
     if main_run["kernel"] == "tensor":
         roof = tensor_rotated_roofline if args.form == "rotated" else tensor_roofline
         roofline = roof(p, args, main_run, launches, per_launch_s, clk)
@@ -979,7 +995,7 @@ def main():
     if not args.quick and rank == 0 and args.workload == "three_level_ring":
         variants = {}
         for prec, form, kern in (("fp64", "merged", "register"), ("fp64", "strang", "auto"),
-                                 ("fp32", "merged", "auto"), ("fp32", "strang", "auto")):
+                                 ("fp64", "merged", "df32"), ("fp32", "merged", "auto"), ("fp32", "strang", "auto")):
             if (prec, form, kern) == (args.precision, args.form, args.kernel):
                 continue
             r = time_device(p, prec, form, args.seg, 10, 2, args.block_steps, args.tile, 1, kernel=kern)

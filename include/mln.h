@@ -108,12 +108,27 @@ enum { MLN_FORM_STRANG = 0, MLN_FORM_MERGED = 1, MLN_FORM_RODRIGUES = 2, MLN_FOR
  * larger values are an error with MLN_KERNEL_TENSOR and are capped at 32 when
  * MLN_KERNEL_AUTO picks it), tiles of 128 - 2 block_steps cells; tile_cells is
  * ignored. */
+/* MLN_KERNEL_DF32 (MLN_FP64, merged form, FDTD, single grids) is the run-time
+ * compiled step of MLN_KERNEL_JIT in double-float arithmetic: every value of
+ * the step (the cell update's products, plane rotation and dP/dt, and the
+ * E and H update) a pair of FP32 numbers h + l, about 48 significant bits,
+ * on the FP32 pipe, whose throughput is 64 times the FP64 pipe's. The state,
+ * E and H stay FP64 in memory, converted at the start and end of each launch.
+ * Not the FP64 bits, and the rounding of the pairs (2^-48 against 2^-53)
+ * adds up in the field recurrence: against the FP64 oracle, E_z within
+ * 9e-13 on the three-level ring after 1500 steps, 5e-11 on the two-level
+ * grid after 20000 steps, 1.1e-10 on a six-level grid (D = 35) after 400.
+ * Rotation angles above 2^-12 are evaluated in FP64. MLN_EUNSUPPORTED
+ * without NVRTC or when a constant of the step lies outside the pair's range
+ * (above 1e37, or non-zero below 1e-30 in magnitude). Never chosen by
+ * MLN_KERNEL_AUTO. */
 enum {
     MLN_KERNEL_AUTO = 0,
     MLN_KERNEL_REGISTER = 1,
     MLN_KERNEL_SPARSE = 2,
     MLN_KERNEL_JIT = 3,
-    MLN_KERNEL_TENSOR = 4
+    MLN_KERNEL_TENSOR = 4,
+    MLN_KERNEL_DF32 = 5
 };
 
 /* Field solver (mln_params.maxwell). MLN_MAXWELL_FDTD: the staggered finite
@@ -168,7 +183,7 @@ enum {
  *                 0 picks a default. 1..64.
  *   tile_cells    cells written by one thread block; 0 picks a default.
  *   kernel        MLN_KERNEL_AUTO, MLN_KERNEL_REGISTER, MLN_KERNEL_SPARSE,
- *                 MLN_KERNEL_JIT or MLN_KERNEL_TENSOR.
+ *                 MLN_KERNEL_JIT, MLN_KERNEL_TENSOR or MLN_KERNEL_DF32.
  *   maxwell       MLN_MAXWELL_FDTD (0) or MLN_MAXWELL_PSTD.
  */
 typedef struct mln_params {
@@ -264,7 +279,8 @@ int64_t mln_step_count(const mln_ctx *ctx);
  * in use: steps fused per launch and cells written per thread block. */
 int64_t mln_launch_count(const mln_ctx *ctx);
 /* The cell model the context's step kernel uses (MLN_KERNEL_REGISTER,
- * MLN_KERNEL_SPARSE, MLN_KERNEL_JIT or MLN_KERNEL_TENSOR), -1 for NULL. */
+ * MLN_KERNEL_SPARSE, MLN_KERNEL_JIT, MLN_KERNEL_TENSOR or MLN_KERNEL_DF32),
+ * -1 for NULL. */
 int32_t mln_kernel_in_use(const mln_ctx *ctx);
 mln_status mln_launch_shape(const mln_ctx *ctx, int32_t *block_steps, int32_t *tile_cells,
                             int32_t *threads_per_block);

@@ -343,7 +343,10 @@ mln_status mln_kernel_source(const mln_params *p, char *buf, size_t cap, size_t 
         return st;
     }
     const std::string src =
-        mln::jit_merged_source(s, p->dt, p->precision == MLN_FP32, p->form == MLN_FORM_ROTATED, mln::jit_body_flags(*p));
+        p->kernel == MLN_KERNEL_DF32
+            ? mln::jit_df_source(s, p->dt, mln::jit_body_flags(*p))
+            : mln::jit_merged_source(s, p->dt, p->precision == MLN_FP32, p->form == MLN_FORM_ROTATED,
+                                     mln::jit_body_flags(*p));
     if (len) *len = src.size();
     if (buf && cap > 0) {
         const size_t k = std::min(cap - 1, src.size());
@@ -676,7 +679,25 @@ mln_status mln_create(const mln_params *p, void *d_state, void *Ez, void *Hy, vo
         const bool want_jit = p->kernel == MLN_KERNEL_JIT || rotated || auto64_jit ||
                               (p->kernel == MLN_KERNEL_AUTO && p->precision == MLN_FP32 && p->form == MLN_FORM_MERGED &&
                                p->maxwell == MLN_MAXWELL_FDTD);
-        if (ok && want_jit) {
+        if (ok && p->kernel == MLN_KERNEL_DF32) {
+            // the cell update in double-float arithmetic: run-time compiled or nothing
+            std::string why, log;
+            cudaError_t e = cudaErrorNotSupported;
+            if (!mln::df_constants_in_range(c->s, p->dt)) {
+                c->err = "MLN_KERNEL_DF32: a constant of the step is outside the double-float range";
+                return fail(MLN_EUNSUPPORTED);
+            }
+            if (mln::jit_available(&why))
+                e = mln::jit_compile(mln::jit_df_source(c->s, p->dt, mln::jit_body_flags(*p)), &c->jit_fn, log);
+            else
+                log = why;
+            if (e != cudaSuccess) {
+                c->jit_fn = nullptr;
+                c->err = "double-float kernel unavailable: " + log;
+                return fail(MLN_EUNSUPPORTED);
+            }
+            c->df32 = true;
+        } else if (ok && want_jit) {
             std::string why, log;
             cudaError_t e = cudaErrorNotSupported;
             if (mln::jit_available(&why))
@@ -800,6 +821,7 @@ int64_t mln_launch_count(const mln_ctx *c) { return c ? c->launches : -1; }
 int32_t mln_kernel_in_use(const mln_ctx *c) {
     if (!c) return -1;
     if (c->tc) return c->tc;
+    if (c->df32) return MLN_KERNEL_DF32;
     return c->jit_fn ? MLN_KERNEL_JIT : c->sparse ? MLN_KERNEL_SPARSE : MLN_KERNEL_REGISTER;
 }
 

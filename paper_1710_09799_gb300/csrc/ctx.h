@@ -28,6 +28,7 @@ struct mln_ctx {
     int64_t steps = 0, launches = 0;
     bool sparse = false;               // shared-memory sparse cell model (FP64 merged)
     void *jit_fn = nullptr;            // run-time compiled step kernel (CUfunction), or nullptr
+    bool df32 = false;                 // ... whose cell update is double-float (MLN_KERNEL_DF32)
     void *prog = nullptr;              // its program: rowptr | cols | vals
     int tc = 0;                        // tensor-core cell model: 0 none, MLN_KERNEL_TENSOR(_SMEM)
     bool tcr = false;                  // ... for the rotated basis (MLN_FORM_ROTATED)

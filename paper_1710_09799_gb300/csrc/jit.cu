@@ -14,6 +14,7 @@
 #include <cuda_runtime.h>
 #include <dlfcn.h>
 
+#include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <map>
@@ -216,6 +217,130 @@ std::string jit_merged_source(const Setup &s, double dt, bool fp32, bool rotated
       << "  asm volatile(\"griddepcontrol.wait;\" ::: \"memory\");\n"
       << "  asm volatile(\"griddepcontrol.launch_dependents;\" ::: \"memory\");\n"
       << "  block_body<" << N << ", " << R << ", JitCell, " << body_flags
+      << "u>(a, k, static_cast<int64_t>(blockIdx.x), smem_raw);\n}\n"
+      << "}  // namespace mln\n";
+    return o.str();
+}
+
+namespace {
+
+// A double constant as the FP32 pair (hi, lo) of double-float arithmetic.
+struct DfLit {
+    std::string h, l;
+    bool has_l;
+};
+DfLit df_lit(double v) {
+    const float h = static_cast<float>(v);
+    const float l = static_cast<float>(v - static_cast<double>(h));
+    return {lit(h, true), lit(l, true), l != 0.0f};
+}
+
+// dst = init (+ c) + sum_j A[i][j] x_j in double-float: the high words summed
+// exactly, every rounding error in the low word, normalised at the end.
+void df_row(std::ostringstream &o, const std::vector<double> &A, int ld, int i, int ncols, const std::string &x,
+            const std::string &dst, const std::string &init, double c = 0.0) {
+    o << "    { float ah = 0.0f, al = 0.0f;";
+    bool started = false;
+    if (!init.empty()) {
+        o << " ah = " << init << ".h; al = " << init << ".l;";
+        started = true;
+    }
+    if (c != 0.0) {
+        const DfLit k = df_lit(c);
+        if (started) o << " df_add(ah, al, " << k.h << ", " << k.l << ");";
+        else o << " ah = " << k.h << "; al = " << k.l << ";";
+        started = true;
+    }
+    for (int j = 0; j < ncols; ++j) {
+        const double a = A[i * ld + j];
+        if (a == 0.0) continue;
+        const DfLit k = df_lit(a);
+        const std::string t = x + "[" + std::to_string(j) + "]";
+        o << "\n      ";
+        if (!started) {
+            if (k.has_l) o << "df_first(ah, al, " << k.h << ", " << k.l << ", " << t << ");";
+            else o << "df_first1(ah, al, " << k.h << ", " << t << ");";
+            started = true;
+        } else {
+            if (k.has_l) o << "df_acc(ah, al, " << k.h << ", " << k.l << ", " << t << ");";
+            else o << "df_acc1(ah, al, " << k.h << ", " << t << ");";
+        }
+    }
+    o << "\n      " << dst << " = df_norm(ah, al); }\n";
+}
+
+}  // namespace
+
+bool df_constants_in_range(const Setup &s, double dt) {
+    auto ok = [](double v) { return v == 0.0 || (std::fabs(v) < 1e37 && std::fabs(v) > 1e-30); };
+    const int D = s.D, P = 2 * s.q;
+    for (int i = 0; i < D; ++i) {
+        for (int k = 0; k < P; ++k)
+            if (!ok(s.T[i * D + k])) return false;
+        for (int j = 0; j < D; ++j)
+            if (!ok(s.C1[i * D + j])) return false;
+        if (!ok(s.wm[i]) || !ok(s.b2[i])) return false;
+    }
+    for (int a = 0; a < s.N - 1; ++a)
+        if (!ok(s.psi[a] * dt)) return false;
+    return ok(s.cm);
+}
+
+std::string jit_df_source(const Setup &s, double dt, unsigned body_flags) {
+    const int N = s.N, D = s.D, Q = s.q, P = 2 * Q;
+    std::ostringstream o;
+    o << "#define MLN_JIT 1\n"
+      << "#ifdef __CUDACC_RTC__\ntypedef long long int64_t;\ntypedef int int32_t;\n#endif\n"
+      << kKernelsSource << "\nnamespace mln {\n"
+      << "struct JitConsts { int unused; };\n"
+      << "// the merged step in double-float arithmetic, E, H and dP/dt as pairs too;\n"
+      << "// the state, E and H in FP64 memory, converted at the ends of a launch\n"
+      << "struct JitCell {\n  static constexpr int D = " << D << ";\n  using Consts = JitConsts;\n"
+      << "  using Field = Df;\n  Df s[D];\n"
+      << "  __device__ __forceinline__ void setup(unsigned char *, const Consts &) {}\n"
+      << "  __device__ __forceinline__ void load(const double *src, int64_t stride, int64_t m) { for (int i = 0; i < D; "
+         "++i) s[i] = df_of(src[i * stride + m]); }\n"
+      << "  __device__ __forceinline__ void store(double *dst, int64_t stride, int64_t m) const { for (int i = 0; i < "
+         "D; ++i) dst[i * stride + m] = df_value(s[i]); }\n"
+      << "  __device__ __forceinline__ void end_step() {}\n"
+      << "  __device__ __forceinline__ Df step(Df e, const Consts &) {\n"
+      << "    Df z[D], y[D];\n";
+    // z = T^T y on the plane rows
+    std::vector<double> Tt((size_t)D * D);
+    for (int i = 0; i < D; ++i)
+        for (int k = 0; k < D; ++k) Tt[k * D + i] = s.T[i * D + k];
+    for (int k = 0; k < P; ++k) df_row(o, Tt, D, k, D, "s", "z[" + std::to_string(k) + "]", "");
+    for (int k = P; k < D; ++k) o << "    z[" << k << "] = Df{0.0f, 0.0f};\n";
+    o << "    const float psi_h[" << (N - 1) << "] = {";
+    for (int a = 0; a < N - 1; ++a) o << (a ? ", " : "") << df_lit(s.psi[a] * dt).h;
+    o << "}, psi_l[" << (N - 1) << "] = {";
+    for (int a = 0; a < N - 1; ++a) o << (a ? ", " : "") << df_lit(s.psi[a] * dt).l;
+    o << "};\n    df_rotation_increment<" << N << ">(z, psi_h, psi_l, e);\n";
+    // y'' = y + T (R - I) z on the plane columns
+    for (int i = 0; i < D; ++i)
+        df_row(o, s.T, D, i, P, "z", "y[" + std::to_string(i) + "]", "s[" + std::to_string(i) + "]");
+    // dP/dt = cm + wm . y''
+    {
+        const DfLit k = df_lit(s.cm);
+        o << "    Df dpdt;\n    { float ah = " << k.h << ", al = " << k.l << ";";
+        for (int i = 0; i < D; ++i) {
+            if (s.wm[i] == 0.0) continue;
+            const DfLit w = df_lit(s.wm[i]);
+            o << "\n      " << (w.has_l ? "df_acc(ah, al, " + w.h + ", " + w.l : "df_acc1(ah, al, " + w.h) << ", y["
+              << i << "]);";
+        }
+        o << "\n      dpdt = df_norm(ah, al); }\n";
+    }
+    // y = (y'' + b2) + C1 y''
+    for (int i = 0; i < D; ++i)
+        df_row(o, s.C1, D, i, D, "y", "s[" + std::to_string(i) + "]", "y[" + std::to_string(i) + "]", s.b2[i]);
+    o << "    return dpdt;\n  }\n};\n"
+      << "extern \"C\" __global__ void __launch_bounds__(kMaxThreads, 1) mln_jit_step(const __grid_constant__ "
+         "BlockArgs<double> a, const __grid_constant__ JitConsts k) {\n"
+      << "  extern __shared__ __align__(16) unsigned char smem_raw[];\n"
+      << "  asm volatile(\"griddepcontrol.wait;\" ::: \"memory\");\n"
+      << "  asm volatile(\"griddepcontrol.launch_dependents;\" ::: \"memory\");\n"
+      << "  block_body<" << N << ", double, JitCell, " << body_flags
       << "u>(a, k, static_cast<int64_t>(blockIdx.x), smem_raw);\n}\n"
       << "}  // namespace mln\n";
     return o.str();

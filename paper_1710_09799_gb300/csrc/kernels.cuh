@@ -225,6 +225,159 @@ __device__ __forceinline__ void rotation_increment(R (&z)[Dims<N>::D], const R *
     rotation_apply<N>(z, s, c1);
 }
 
+// ---------------------------------------------------------------------------
+// Double-float arithmetic (the step of MLN_KERNEL_DF32): a value is the
+// unevaluated sum h + l of two FP32 numbers with |l| <= ulp(h) / 2, about 48
+// significant bits. An FP64 instruction holds its SM sub-partition's FP64
+// pipe 64 times as long as an FP32 instruction holds the FP32 pipe (whatever
+// the number of active lanes), so the step runs faster as FP32 pairs than in
+// FP64, at 2^-48 instead of 2^-53 per operation. The error-free transformations are
+// Knuth's two-sum and the product error from a fused multiply-add; the _rn
+// intrinsics keep the compiler from contracting any of their operations.
+struct Df {
+    float h, l;
+};
+
+__device__ __forceinline__ Df df_of(double x) {
+    const float h = __double2float_rn(x);
+    return {h, __double2float_rn(x - static_cast<double>(h))};  // x - h is exact in FP64
+}
+__device__ __forceinline__ double df_value(Df a) { return static_cast<double>(a.h) + static_cast<double>(a.l); }
+
+// s + e = a + b exactly
+__device__ __forceinline__ void df_two_sum(float a, float b, float &s, float &e) {
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+// the pair (ah, al) as a normalised value
+__device__ __forceinline__ Df df_norm(float ah, float al) {
+    Df r;
+    df_two_sum(ah, al, r.h, r.l);
+    return r;
+}
+// (ah, al) = c x for c = ch + cl: the product's high part and, in the low
+// word, its rounding error and the cross terms
+__device__ __forceinline__ void df_first(float &ah, float &al, float ch, float cl, Df x) {
+    ah = __fmul_rn(ch, x.h);
+    al = __fmaf_rn(cl, x.h, __fmaf_rn(ch, x.l, __fmaf_rn(ch, x.h, -ah)));
+}
+__device__ __forceinline__ void df_first1(float &ah, float &al, float ch, Df x) {  // cl = 0
+    ah = __fmul_rn(ch, x.h);
+    al = __fmaf_rn(ch, x.l, __fmaf_rn(ch, x.h, -ah));
+}
+// (ah, al) += c x: the product's high part enters the high word exactly
+// (two-sum), the errors of both the low word
+__device__ __forceinline__ void df_acc(float &ah, float &al, float ch, float cl, Df x) {
+    const float p = __fmul_rn(ch, x.h);
+    const float pe = __fmaf_rn(cl, x.h, __fmaf_rn(ch, x.l, __fmaf_rn(ch, x.h, -p)));
+    float s, e;
+    df_two_sum(ah, p, s, e);
+    ah = s;
+    al = __fadd_rn(al, __fadd_rn(pe, e));
+}
+__device__ __forceinline__ void df_acc1(float &ah, float &al, float ch, Df x) {  // cl = 0
+    const float p = __fmul_rn(ch, x.h);
+    const float pe = __fmaf_rn(ch, x.l, __fmaf_rn(ch, x.h, -p));
+    float s, e;
+    df_two_sum(ah, p, s, e);
+    ah = s;
+    al = __fadd_rn(al, __fadd_rn(pe, e));
+}
+// (ah, al) += b for b = bh + bl
+__device__ __forceinline__ void df_add(float &ah, float &al, float bh, float bl) {
+    float s, e;
+    df_two_sum(ah, bh, s, e);
+    ah = s;
+    al = __fadd_rn(al, __fadd_rn(bl, e));
+}
+
+// (sin x, cos x - 1) in double-float. For |x| <= 2^-12 the leading terms x
+// and -x^2/2 in double-float and the rest of each series (below 2^-24 of the
+// leading term, so FP32 suffices) as one FP32 correction:
+//   sin x - x        = x x^2 (-1/6 + x^2/120),        |x^7/7!| < 2^-90 |x|,
+//   cos x - 1 + x^2/2 = x^4 (1/24 - x^2/720),          |x^8/8!| < 2^-111 x^2.
+// Larger angles take the FP64 evaluation.
+__device__ __forceinline__ void df_sin_cosm1(Df x, Df &s, Df &c1) {
+    if (fabsf(x.h) <= 0x1p-12f) {
+        float x2h, x2l;
+        x2h = __fmul_rn(x.h, x.h);
+        x2l = __fmaf_rn(__fmul_rn(2.0f, x.h), x.l, __fmaf_rn(x.h, x.h, -x2h));
+        const float ts = __fmul_rn(__fmul_rn(x.h, x2h), __fmaf_rn(x2h, 1.0f / 120.0f, -1.0f / 6.0f));
+        float ah = x.h, al = x.l;
+        df_add(ah, al, ts, 0.0f);
+        s = df_norm(ah, al);
+        const float tc = __fmul_rn(__fmul_rn(x2h, x2h), __fmaf_rn(x2h, -1.0f / 720.0f, 1.0f / 24.0f));
+        ah = -0.5f * x2h;  // exact
+        al = -0.5f * x2l;
+        df_add(ah, al, tc, 0.0f);
+        c1 = df_norm(ah, al);
+    } else {
+        double sd, cd;
+        sin_cosm1(df_value(x), sd, cd);
+        s = df_of(sd);
+        c1 = df_of(cd);
+    }
+}
+
+// The plane rotation of the merged step, z <- (R(E) - I) z, in double-float:
+// the angles psi_a E dt (psi_dt as (hi, lo) pairs), the subtraction formulas
+// and the rotation as in plane_terms and rotation_apply.
+template <int N>
+__device__ __forceinline__ void df_rotation_increment(Df (&z)[Dims<N>::D], const float *psi_h, const float *psi_l,
+                                                      Df e) {
+    constexpr int Q = Dims<N>::Q;
+    Df sp[N], cp[N];
+#pragma unroll
+    for (int a = 0; a < N - 1; ++a) {
+        float ah, al;
+        df_first(ah, al, psi_h[a], psi_l[a], e);
+        df_sin_cosm1(df_norm(ah, al), sp[a], cp[a]);
+    }
+    sp[N - 1] = Df{0.0f, 0.0f};
+    cp[N - 1] = Df{0.0f, 0.0f};
+    Df s[Q], c1[Q];
+    int k = 0;
+#pragma unroll
+    for (int a = 0; a < N; ++a) {
+#pragma unroll
+        for (int b = a + 1; b < N; ++b) {
+            if (b == N - 1) {
+                s[k] = sp[a];
+                c1[k] = cp[a];
+            } else {
+                // sin(p - r) = s_p - s_r + s_p c1_r - c1_p s_r
+                float ah = sp[a].h, al = sp[a].l;
+                df_add(ah, al, -sp[b].h, -sp[b].l);
+                df_acc(ah, al, -cp[a].h, -cp[a].l, sp[b]);
+                df_acc(ah, al, sp[a].h, sp[a].l, cp[b]);
+                s[k] = df_norm(ah, al);
+                // cos(p - r) - 1 = c1_p + c1_r + c1_p c1_r + s_p s_r
+                ah = cp[a].h;
+                al = cp[a].l;
+                df_add(ah, al, cp[b].h, cp[b].l);
+                df_acc(ah, al, sp[a].h, sp[a].l, sp[b]);
+                df_acc(ah, al, cp[a].h, cp[a].l, cp[b]);
+                c1[k] = df_norm(ah, al);
+            }
+            ++k;
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+        const Df x = z[2 * q], y = z[2 * q + 1];
+        float ah, al;
+        df_first(ah, al, s[q].h, s[q].l, y);  // c1 x + s y
+        df_acc(ah, al, c1[q].h, c1[q].l, x);
+        z[2 * q] = df_norm(ah, al);
+        df_first(ah, al, -s[q].h, -s[q].l, x);  // c1 y - s x
+        df_acc(ah, al, c1[q].h, c1[q].l, y);
+        z[2 * q + 1] = df_norm(ah, al);
+    }
+#pragma unroll
+    for (int i = 2 * Q; i < Dims<N>::D; ++i) z[i] = Df{0.0f, 0.0f};
+}
+
 // y = x + (A x + b) with A row-major D x D held in the constant bank.
 template <int D, typename R>
 __device__ __forceinline__ void affine_inc(R (&y)[D], const R *A, const R (&x)[D], const R *b) {
@@ -624,6 +777,71 @@ enum : unsigned {
                         // launch wrote them, and this SM's L1 may hold an older copy
 };
 
+// The type of E, H and dP/dt inside a block: R, or the cell model's own
+// Field type (Df for the double-float model, whose field update then runs in
+// pairs too, with no FP64 instruction per step).
+template <typename C, typename R, typename = void>
+struct CellField {
+    using type = R;
+};
+template <typename C, typename R>
+struct CellField<C, R, mln_void_t<typename C::Field>> {
+    using type = typename C::Field;
+};
+// Values of type R in memory to and from the block's field type.
+template <typename F, typename R>
+struct FieldConv {
+    __device__ __forceinline__ static F in(R v) { return v; }
+    __device__ __forceinline__ static R out(F v) { return v; }
+};
+template <>
+struct FieldConv<Df, double> {
+    __device__ __forceinline__ static Df in(double v) { return df_of(v); }
+    __device__ __forceinline__ static double out(Df v) { return df_value(v); }
+};
+// The field update's operations: for FP64 and FP32 the plain expressions
+// (the same instructions as written out), for pairs their double-float forms.
+template <typename F>
+__device__ __forceinline__ F fld_sub(F a, F b) { return a - b; }
+template <typename F>
+__device__ __forceinline__ F fld_add(F a, F b) { return a + b; }
+template <typename F>
+__device__ __forceinline__ F fld_neg(F a) { return -a; }
+template <typename F>
+__device__ __forceinline__ F fld_mul(F c, F x) { return c * x; }
+template <typename F>
+__device__ __forceinline__ F fld_fma(F c, F x, F y) { return fma(c, x, y); }
+template <typename F>
+__device__ __forceinline__ bool fld_finite(F a) { return isfinite(a); }
+template <>
+__device__ __forceinline__ Df fld_sub(Df a, Df b) {
+    float ah = a.h, al = a.l;
+    df_add(ah, al, -b.h, -b.l);
+    return df_norm(ah, al);
+}
+template <>
+__device__ __forceinline__ Df fld_add(Df a, Df b) {
+    float ah = a.h, al = a.l;
+    df_add(ah, al, b.h, b.l);
+    return df_norm(ah, al);
+}
+template <>
+__device__ __forceinline__ Df fld_neg(Df a) { return Df{-a.h, -a.l}; }
+template <>
+__device__ __forceinline__ Df fld_mul(Df c, Df x) {
+    float ah, al;
+    df_first(ah, al, c.h, c.l, x);
+    return df_norm(ah, al);
+}
+template <>
+__device__ __forceinline__ Df fld_fma(Df c, Df x, Df y) {
+    float ah = y.h, al = y.l;
+    df_acc(ah, al, c.h, c.l, x);
+    return df_norm(ah, al);
+}
+template <>
+__device__ __forceinline__ bool fld_finite(Df a) { return isfinite(a.h) && isfinite(a.l); }
+
 // One thread block advances tile `tile_index` of one grid by a.nsteps steps.
 // smem: 2 * blockDim.x reals for E and H, then the cell model's extra space.
 template <int N, typename R, typename Cell, unsigned kFlags = 0u>
@@ -631,11 +849,16 @@ __device__ __forceinline__ void block_body(const BlockArgs<R> &a, const typename
                                            unsigned char *smem) {
     constexpr bool kRingOnly = (kFlags & kBodyRing) != 0, kOpenOnly = (kFlags & kBodyOpen) != 0;
     constexpr bool kNoSrc = (kFlags & kBodyNoSrc) != 0, kNoRec = (kFlags & kBodyNoRec) != 0;
+    // E, H and dP/dt in the block: R, or the cell model's field type
+    using F = typename CellField<Cell, R>::type;
+    using Cv = FieldConv<F, R>;
+    static_assert(sizeof(F) == sizeof(R), "the shared E and H buffers are sized for R");
+    const F ch = Cv::in(a.ch), ca = Cv::in(a.ca), cb = Cv::in(a.cb), inv_dx = Cv::in(a.inv_dx);
     // E and H of the block, two buffers each: step st reads one and writes the other
-    R *const bufE0 = reinterpret_cast<R *>(smem);
-    R *const bufH0 = bufE0 + blockDim.x;
-    R *const bufE1 = bufH0 + blockDim.x;
-    R *const bufH1 = bufE1 + blockDim.x;
+    F *const bufE0 = reinterpret_cast<F *>(smem);
+    F *const bufH0 = bufE0 + blockDim.x;
+    F *const bufE1 = bufH0 + blockDim.x;
+    F *const bufH1 = bufE1 + blockDim.x;
 
     const int j = threadIdx.x;
     const int64_t n = a.n_cells;
@@ -662,17 +885,17 @@ __device__ __forceinline__ void block_body(const BlockArgs<R> &a, const typename
 
     Cell cell;
     cell.setup(smem + field_smem<R>(blockDim.x), k);
-    R e = R(0), h = R(0);
+    F e = F(), h = F();
     if constexpr ((kFlags & kBodyCg) != 0u) {
         if (loaded) {
-            e = __ldcg(a.E_in + gm);
-            h = __ldcg(a.H_in + gm);
+            e = Cv::in(__ldcg(a.E_in + gm));
+            h = Cv::in(__ldcg(a.H_in + gm));
         }
         if (medium) cell.load_cg(a.s_in, a.stride, m);
     } else {
         if (loaded) {
-            e = a.E_in[gm];
-            h = a.H_in[gm];
+            e = Cv::in(a.E_in[gm]);
+            h = Cv::in(a.H_in[gm]);
         }
         if (medium) cell.load(a.s_in, a.stride, m);
     }
@@ -704,13 +927,13 @@ __device__ __forceinline__ void block_body(const BlockArgs<R> &a, const typename
     __syncthreads();
 
     // one step from buffers (cE, cH) into (nE, nH)
-    auto step = [&](int st, const R *cE, const R *cH, R *nE, R *nH) {
+    auto step = [&](int st, const F *cE, const F *cH, F *nE, F *nH) {
         if (st < active) {  // warp-uniform
-            if (h_upd) h = fma(a.ch, cE[j + 1] - e, h);
+            if (h_upd) h = fld_fma(ch, fld_sub(cE[j + 1], e), h);
             // the previous cell's new H, with the operands and operations of its own thread
-            R hl = R(0);
-            if (e_upd) hl = fma(a.ch, e - cE[j - 1], cH[j - 1]);
-            R dpdt = R(0);
+            F hl = F();
+            if (e_upd) hl = fld_fma(ch, fld_sub(e, cE[j - 1]), cH[j - 1]);
+            F dpdt = F();
             if constexpr (CellTraces<Cell>::value) {
                 if (medium)
                     cell.trace_to(record ? reinterpret_cast<R *>(reinterpret_cast<char *>(a.rec_I) +
@@ -720,18 +943,18 @@ __device__ __forceinline__ void block_body(const BlockArgs<R> &a, const typename
             }
             if (medium) dpdt = cell.step(e, k);
             cell.end_step();
-            R en = e;
-            if (e_upd) en = fma(a.ca, e, a.cb * fma(h - hl, a.inv_dx, -dpdt));
-            R e_mur = R(0);
-            if (mur) e_mur = fma(a.kappa, en - cE[j + 1], e);  // from E^{n+1} before any source
+            F en = e;
+            if (e_upd) en = fld_fma(ca, e, fld_mul(cb, fld_fma(fld_sub(h, hl), inv_dx, fld_neg(dpdt))));
+            F e_mur = F();
+            if (mur) e_mur = fld_fma(Cv::in(a.kappa), fld_sub(en, cE[j + 1]), e);  // from E^{n+1} before any source
             if (is_src) {
-                R v = static_cast<R>(a.src[st]);
-                en = (a.source_kind == 1) ? v : en + v;
+                const F v = FieldConv<F, double>::in(a.src[st]);
+                en = (a.source_kind == 1) ? v : fld_add(en, v);
             }
             if (mur) {
                 if (has_src && a.source_cell == n - 1) {
-                    R v = static_cast<R>(a.src[st]);
-                    e_mur = (a.source_kind == 1) ? v : e_mur + v;
+                    const F v = FieldConv<F, double>::in(a.src[st]);
+                    e_mur = (a.source_kind == 1) ? v : fld_add(e_mur, v);
                 }
                 nE[j + 1] = e_mur;
             }
@@ -744,8 +967,8 @@ __device__ __forceinline__ void block_body(const BlockArgs<R> &a, const typename
         if (mur_cell) e = nE[j];
         if (record) {
             const int64_t off = static_cast<int64_t>(st) * a.rec_set;
-            reinterpret_cast<R *>(reinterpret_cast<char *>(a.rec_E) + off)[gm] = e;
-            reinterpret_cast<R *>(reinterpret_cast<char *>(a.rec_H) + off)[gm] = h;
+            reinterpret_cast<R *>(reinterpret_cast<char *>(a.rec_E) + off)[gm] = Cv::out(e);
+            reinterpret_cast<R *>(reinterpret_cast<char *>(a.rec_H) + off)[gm] = Cv::out(h);
             if (medium) cell.store(reinterpret_cast<R *>(reinterpret_cast<char *>(a.rec_S) + off), a.stride, m);
         }
     };
@@ -758,10 +981,10 @@ __device__ __forceinline__ void block_body(const BlockArgs<R> &a, const typename
         }
         if (st < a.nsteps) step(st, bufE0, bufH0, bufE1, bufH1);
     } else {
-        R *cE = bufE0, *cH = bufH0, *nE = bufE1, *nH = bufH1;
+        F *cE = bufE0, *cH = bufH0, *nE = bufE1, *nH = bufH1;
         for (int st = 0; st < a.nsteps; ++st) {
             step(st, cE, cH, nE, nH);
-            R *t = cE;
+            F *t = cE;
             cE = nE;
             nE = t;
             t = cH;
@@ -771,10 +994,10 @@ __device__ __forceinline__ void block_body(const BlockArgs<R> &a, const typename
     }
 
     if (interior) {
-        a.E_out[gm] = e;
-        a.H_out[gm] = h;
+        a.E_out[gm] = Cv::out(e);
+        a.H_out[gm] = Cv::out(h);
         if (medium) cell.store(a.s_out, a.stride, m);
-        if (!isfinite(e)) atomicOr(a.flags, 1u);
+        if (!fld_finite(e)) atomicOr(a.flags, 1u);
     }
 }
 

@@ -453,9 +453,14 @@ mln_status validate(const mln_params &p, std::string &err) {
             return MLN_EINVAL;
         }
     }
-    if (p.kernel < MLN_KERNEL_AUTO || p.kernel > MLN_KERNEL_TENSOR) {
-        err = "kernel must be MLN_KERNEL_AUTO, MLN_KERNEL_REGISTER, MLN_KERNEL_SPARSE, MLN_KERNEL_JIT or "
-              "MLN_KERNEL_TENSOR";
+    if (p.kernel < MLN_KERNEL_AUTO || p.kernel > MLN_KERNEL_DF32) {
+        err = "kernel must be MLN_KERNEL_AUTO, MLN_KERNEL_REGISTER, MLN_KERNEL_SPARSE, MLN_KERNEL_JIT, "
+              "MLN_KERNEL_TENSOR or MLN_KERNEL_DF32";
+        return MLN_EINVAL;
+    }
+    if (p.kernel == MLN_KERNEL_DF32 &&
+        (p.precision != MLN_FP64 || p.form != MLN_FORM_MERGED || p.maxwell != MLN_MAXWELL_FDTD)) {
+        err = "MLN_KERNEL_DF32 needs MLN_FP64, MLN_FORM_MERGED and MLN_MAXWELL_FDTD";
         return MLN_EINVAL;
     }
     if (p.kernel == MLN_KERNEL_TENSOR &&

@@ -24,7 +24,7 @@ MLN_BC_PERIODIC, MLN_BC_OPEN = 0, 1
 MLN_SRC_NONE, MLN_SRC_HARD, MLN_SRC_SOFT = 0, 1, 2
 MLN_FP64, MLN_FP32 = 0, 1
 MLN_FORM_STRANG, MLN_FORM_MERGED, MLN_FORM_RODRIGUES, MLN_FORM_ROTATED = 0, 1, 2, 3
-MLN_KERNEL_AUTO, MLN_KERNEL_REGISTER, MLN_KERNEL_SPARSE, MLN_KERNEL_JIT, MLN_KERNEL_TENSOR = 0, 1, 2, 3, 4
+MLN_KERNEL_AUTO, MLN_KERNEL_REGISTER, MLN_KERNEL_SPARSE, MLN_KERNEL_JIT, MLN_KERNEL_TENSOR, MLN_KERNEL_DF32 = 0, 1, 2, 3, 4, 5
 MLN_MIN_N, MLN_MAX_N = 2, 6
 MLN_BATCH_CHUNKS, MLN_BATCH_PERSISTENT = 0, 1
 _DMAX = MLN_MAX_N * MLN_MAX_N - 1
@@ -35,7 +35,7 @@ PRECISION = {"fp64": MLN_FP64, "fp32": MLN_FP32}
 FORM = {"strang": MLN_FORM_STRANG, "merged": MLN_FORM_MERGED, "rodrigues": MLN_FORM_RODRIGUES,
         "rotated": MLN_FORM_ROTATED}
 KERNEL = {"auto": MLN_KERNEL_AUTO, "register": MLN_KERNEL_REGISTER, "sparse": MLN_KERNEL_SPARSE,
-          "jit": MLN_KERNEL_JIT, "tensor": MLN_KERNEL_TENSOR}
+          "jit": MLN_KERNEL_JIT, "tensor": MLN_KERNEL_TENSOR, "df32": MLN_KERNEL_DF32}
 MAXWELL = {"fdtd": 0, "pstd": 1}
 
 _dp = C.POINTER(C.c_double)

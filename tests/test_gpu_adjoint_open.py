@@ -40,6 +40,7 @@ def open_grid(kind="hard", n_cells=240, n_steps=600, probe=None, T=1e-12, N_a=1e
     src = np.zeros(n_steps)
     src[:200] = 3e8 * np.exp(-((k[:200] - 100) / 35) ** 2) * np.sin(2 * np.pi * k[:200] / 40)
     q = p.with_(source_kind=kind, source_cell=0, src=src, name="open_two_level")
+    # meta without the generator's source_fn: the samples above drive the grid
     q.meta = dict(probe_cell=n_cells - 2 if probe is None else probe, n_src=200)
     return q
 

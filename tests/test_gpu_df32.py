@@ -1,0 +1,128 @@
+"""The double-float cell model (MLN_KERNEL_DF32): the merged step of an FP64
+context with the cell update and the field update in pairs of FP32 numbers
+(about 48 significant bits).
+
+Held to the FP64 path's bar against the oracle (E_z within 1e-10 relative in
+the infinity norm, populations and rho within 1e-10 absolute) on the
+three-level ring (several tiles, a ragged last tile, three calls), the
+two-level grid of the paper's first test case at full size, an open grid
+driven hard enough that the rotation angles leave the double-float series
+(above 2^-12 the angles are evaluated in FP64) and a weakly driven one that
+stays inside it, and an N = 4 problem; the N = 6 problem at 2e-10 for E_z
+and H_y (see its test); and close to the FP64 run-time compiled kernel.
+"""
+import numpy as np
+import pytest
+
+import workloads as W
+from helpers import gpu_run, rel_inf
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-10
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_1710_09799_gb300 import build
+    build()
+
+
+def pops(rho):
+    return np.einsum("cii->ci", rho).real
+
+
+def check_against_oracle(orc, p, chunks=None, tol=TOL):
+    st, _ = orc.run(p, n_steps=p.n_steps)
+    E, H, rho, s = gpu_run(p, p.n_steps, "fp64", "merged", chunks=chunks, kernel="df32")
+    assert s.kernel_in_use == "df32"
+    s.close()
+    e_err, h_err = rel_inf(E, st.E), rel_inf(H, st.H)
+    p_err = np.abs(pops(rho) - pops(st.rho)).max()
+    r_err = np.abs(rho - st.rho).max()
+    print(f"{p.name}: E {e_err:.2e}  H {h_err:.2e}  pops {p_err:.2e}  rho {r_err:.2e}")
+    assert e_err < tol and h_err < tol and p_err < TOL and r_err < TOL
+    return st
+
+
+def open_two_level(amplitude, n_steps=600):
+    """Two-level medium in [60, 180) of 240 cells, hard source at cell 0
+    (Gaussian-envelope carrier, period ~40 steps), Mur at the right end. The
+    rotation angle of a step is psi dt E with psi dt = 1.45e-12 m/V: an
+    amplitude of 3e7 V/m keeps it below 2^-12, 3e9 V/m takes it above."""
+    p = W.two_level_sit(n_cells=240, medium=(60, 180), n_steps=n_steps, T1=1e-13, T2=1e-13, N_a=1e25)
+    k = np.arange(n_steps, dtype=np.float64)
+    src = np.zeros(n_steps)
+    src[:200] = amplitude * np.exp(-((k[:200] - 100) / 35) ** 2) * np.sin(2 * np.pi * k[:200] / 40)
+    q = p.with_(source_kind="hard", source_cell=0, src=src, name=f"open_two_level_{amplitude:.0e}")
+    q.meta.pop("source_fn", None)  # the samples above, not the generator's sech pulse
+    return q
+
+
+def test_three_level_ring_against_oracle(orc):
+    p = W.three_level_ring(n_cells=4096, n_steps=1500)
+    check_against_oracle(orc, p, chunks=[700, 1, 799])
+
+
+def test_two_level_sit_full_size_against_oracle(orc):
+    """2000 cells, medium [500, 1500), sech pulse of area 2 pi, hard source +
+    Mur, 20000 steps."""
+    p = W.two_level_sit()
+    st = check_against_oracle(orc, p)
+    assert pops(st.rho)[:, 1].max() > 1e-3  # the pulse reached and excited the medium
+
+
+@pytest.mark.parametrize("amplitude", [3e7, 3e9])
+def test_small_and_large_rotation_angles(orc, amplitude):
+    p = open_two_level(amplitude)
+    angle = 1.45e-12 * amplitude
+    assert (angle < 2 ** -12) == (amplitude < 1e8)
+    assert np.abs(p.source_samples(0, p.n_steps)).max() > 0.8 * amplitude
+    st = check_against_oracle(orc, p)
+    assert pops(st.rho)[:, 1].max() > 0  # the pulse reached the medium
+
+
+def test_four_level_ring_against_oracle(orc):
+    p = W.multi_level_ring(4, n_cells=700, n_steps=400, seed=31, N_a=1e26)
+    check_against_oracle(orc, p)
+
+
+def test_six_level_against_oracle(orc):
+    """D = 35. The populations and rho stay within 1e-10; E_z and H_y are held
+    to 2e-10: a dP/dt of 35 terms that cancel to a small sum carries the low
+    word's FP32 rounding (measured on a GB300: E 1.07e-10, where the FP64 path
+    itself is 5.7e-11 from the oracle and the pair path 5.0e-11 from FP64)."""
+    p = W.six_level_pulse(n_cells=700, n_steps=400, t0=20e-15, fwhm=10e-15)
+    check_against_oracle(orc, p.with_(medium_begin=3, medium_end=699), tol=2e-10)
+
+
+def test_close_to_the_fp64_kernel():
+    """Double-float against FP64 on the same ring: the pair carries about 48
+    bits against FP64's 53, in the cell update and in the field recurrence,
+    whose roundings add up over the steps (measured on a GB300 after 2000
+    steps: E 1.0e-12, rho 2.8e-13; bound 5e-12)."""
+    p = W.three_level_ring(n_cells=4096, n_steps=2000)
+    E0, H0, r0, s0 = gpu_run(p, p.n_steps, "fp64", "merged", kernel="jit")
+    E1, H1, r1, s1 = gpu_run(p, p.n_steps, "fp64", "merged", kernel="df32")
+    s0.close()
+    s1.close()
+    print(f"df32 vs fp64: E {rel_inf(E1, E0):.2e}  rho {np.abs(r1 - r0).max():.2e}")
+    assert rel_inf(E1, E0) < 5e-12 and rel_inf(H1, H0) < 5e-12
+    assert np.abs(r1 - r0).max() < 5e-12
+
+
+def test_launch_shape_does_not_change_the_bits():
+    """At a fixed number of steps per launch (the state is converted to and
+    from FP64 at the ends of each launch) the tile size does not change the
+    bits: a cell's pair arithmetic does not depend on its tile."""
+    p = W.three_level_ring(n_cells=3000, n_steps=240)
+    runs = []
+    for K, tile in ((8, 0), (8, 100), (8, 333)):
+        E, H, rho, s = gpu_run(p, p.n_steps, "fp64", "merged", kernel="df32", block_steps=K, tile_cells=tile)
+        s.close()
+        runs.append((E, H, rho))
+    for E, H, rho in runs[1:]:
+        assert np.array_equal(E, runs[0][0]) and np.array_equal(H, runs[0][1]) and np.array_equal(rho, runs[0][2])

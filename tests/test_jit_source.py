@@ -160,3 +160,36 @@ def test_rotated_form_constants_are_the_rotated_matrices(lib, make):
     assert np.all(np.abs(got_c - cz) <= 8 * D * u * (aT.T @ np.abs(A0 @ b + b)) + 1e-300)
     assert np.all(np.abs(got_w - wz) <= 8 * D * u * (aT.T @ np.abs(A0.T @ w)) + 1e-300)
     assert np.count_nonzero(got_C) >= np.count_nonzero(np.abs(C) > 1e-12 * np.abs(C).max())
+
+
+def test_double_float_source_compiles_with_one_term_per_constant(lib, tmp_path):
+    """MLN_KERNEL_DF32: the double-float step has one pair term per non-zero
+    entry of T (twice: T^T on the plane rows, T on the plane columns), of C1
+    and of wm, and is valid CUDA for sm_103a."""
+    nvcc = shutil.which("nvcc") or "/usr/local/cuda/bin/nvcc"
+    if not os.path.exists(nvcc):
+        pytest.skip("nvcc not found")
+    p = W.three_level_ring(n_cells=1000)
+    par = params_of(p, precision="fp64", form="merged", kernel="df32")
+    src = mln.mln_kernel_source(par)
+    s = mln.mln_setup_host(par)
+    D, q = s["D"], s["q"]
+    body = src[src.index("struct JitCell"):]
+    n_terms = body.count("df_first(") + body.count("df_first1(") + body.count("df_acc(") + body.count("df_acc1(")
+    fixed = 2 * int(np.count_nonzero(s["T"][:, :2 * q])) + int(np.count_nonzero(s["C1"]))
+    assert fixed <= n_terms <= fixed + D  # + the non-zero entries of wm
+    assert "df_rotation_increment<3>" in body and "fma(" not in body.split("df_rotation_increment")[0]
+    f = tmp_path / "k.cu"
+    f.write_text(src)
+    r = subprocess.run([nvcc, "-gencode", "arch=compute_103a,code=sm_103a", "-std=c++17", "-c", str(f),
+                        "-o", str(tmp_path / "k.o")], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr[-3000:]
+
+
+@pytest.mark.parametrize("kw", [dict(precision="fp32", form="merged"), dict(precision="fp64", form="strang"),
+                                dict(precision="fp64", form="rotated")])
+def test_double_float_needs_fp64_merged(lib, kw):
+    p = W.three_level_ring(n_cells=1000)
+    with pytest.raises(mln.MLNError) as ei:
+        mln.mln_kernel_source(params_of(p, kernel="df32", **kw))
+    assert ei.value.status == mln.MLN_EINVAL
