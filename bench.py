@@ -936,7 +936,7 @@ def main():
     achieved = flops_per_step * (args.seg * args.steps / max(launches, 1)) / per_launch_s / 1e12
     peak = alu_peak_tflops(args.precision)
     kname = ("mln_jit_step" if main_run["kernel"] == "jit" else
-             "mln_jit_step (double-float cell update)" if main_run["kernel"] == "df32" else
+             "mln_jit_step (double-float pairs)" if main_run["kernel"] == "df32" else
              f"mln_block_kernel ({main_run['kernel']} cell model)")
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "kernel": kname,
