@@ -853,7 +853,7 @@ def run_batched(args, ws, rank, local):
     smi_index = int(vis.split(",")[local]) if vis and vis.split(",")[local].isdigit() else local
     prec = args.precision
     r = time_batch(prec, args.seg, args.steps, args.warmup, ClockSampler(smi_index),
-                   kernel=args.kernel if args.kernel in ("register", "jit") else "auto",
+                   kernel=args.kernel if args.kernel in ("register", "jit", "df32") else "auto",
                    launch=None if args.batch_launch == "default" else args.batch_launch)
     total_s = max_over_ranks(ws, r["ms"]) / 1e3
     value = ws * r["cells"] * args.seg * args.steps / total_s
@@ -874,6 +874,11 @@ def run_batched(args, ws, rank, local):
                      "kernel": "mln_jit_batch" if "jit" in r["kernels"].values() else "mln_batch_kernel"},
         "gpu_launches": r["launches"], "clocks": r["clocks"],
     }
+    if "df32" in r["kernels"].values():
+        # double-float pairs run on the FP32 pipe (as the single-grid line)
+        p32 = alu_peak_tflops("fp32")
+        line["roofline"].update({"kernel": "mln_jit_batch (double-float pairs)", "peak": p32,
+                                 "frac": achieved / p32, "frac_of_fp64_peak": achieved / peak})
     if rank == 0:
         print(json.dumps(line), flush=True)
     return 0

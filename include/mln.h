@@ -108,8 +108,9 @@ enum { MLN_FORM_STRANG = 0, MLN_FORM_MERGED = 1, MLN_FORM_RODRIGUES = 2, MLN_FOR
  * larger values are an error with MLN_KERNEL_TENSOR and are capped at 32 when
  * MLN_KERNEL_AUTO picks it), tiles of 128 - 2 block_steps cells; tile_cells is
  * ignored. */
-/* MLN_KERNEL_DF32 (MLN_FP64, merged form, FDTD, single grids) is the run-time
- * compiled step of MLN_KERNEL_JIT in double-float arithmetic: every value of
+/* MLN_KERNEL_DF32 (MLN_FP64, merged form, FDTD) is the run-time
+ * compiled step of MLN_KERNEL_JIT in double-float arithmetic (also for the
+ * grids of a batch, mln_batch_create): every value of
  * the step (the cell update's products, plane rotation and dP/dt, and the
  * E and H update) a pair of FP32 numbers h + l, about 48 significant bits,
  * on the FP32 pipe, whose throughput is 64 times the FP64 pipe's. The state,
@@ -405,7 +406,9 @@ mln_status mln_adjoint(mln_ctx *ctx, int64_t n_steps, const double *src, int64_t
  * call are captured into a CUDA graph and replayed as one graph launch.
  *
  * mln_batch_create: count grids, params[i] as for mln_create with one common
- * precision, form MLN_FORM_MERGED, N <= 4 and kernel AUTO, REGISTER or JIT;
+ * precision, form MLN_FORM_MERGED, N <= 4 and kernel AUTO, REGISTER or JIT,
+ * or MLN_KERNEL_DF32 with MLN_FP64 for every grid (the batch kernels in
+ * double-float pairs, each grid's constants staged as pairs);
  * d_state[i], Ez[i], Hy[i] caller-owned device buffers as for mln_create;
  * src NULL or count device pointers to src_len source samples per grid
  * (sample k applies to the batch's step k; NULL entries for grids without a
@@ -432,8 +435,9 @@ mln_status mln_adjoint(mln_ctx *ctx, int64_t n_steps, const double *src, int64_t
  * staged in shared memory and, when they fit, held in registers; the default
  * when NVRTC is available and no grid asks for MLN_KERNEL_REGISTER) or
  * MLN_KERNEL_REGISTER (dense products, padded constants in shared memory);
- * -1 if the batch has no grid with N levels. Both give the register model's
- * bits.
+ * both give the register model's bits; or MLN_KERNEL_DF32 for a batch of
+ * double-float grids (the bits of those grids stepped alone at the same
+ * steps per launch); -1 if the batch has no grid with N levels.
  * mln_batch_kernel_source: host only; the CUDA source that the batch with
  * these params would compile for its N-level grids (as mln_kernel_source).
  * mln_batch_set_launch: the launch structure of later mln_batch_step calls.

@@ -150,6 +150,7 @@ struct mln_batch {
     void *jit[mln::kBatchMaxN + 1] = {};
     void *jitp[mln::kBatchMaxN + 1] = {};  // the persistent kernel of the same module
     mln::BatchPattern pat[mln::kBatchMaxN + 1];
+    bool df32 = false;                  // FP64 grids stepped in double-float pairs (MLN_KERNEL_DF32)
     int mode = MLN_BATCH_CHUNKS;
     int wait_limit = 1 << 22;           // polls of a persistent block's wait (about 0.4 s at 100 ns each)
     void *d_work = nullptr;             // persistent: one work counter per N
@@ -244,7 +245,7 @@ mln_status build_tables(mln_batch *b) {
         g.source_kind = c->p.source_kind;
         std::vector<unsigned char> padded;
         if (b->jit[c->p.N]) {
-            mln::batch_pack(b->pat[c->p.N], c->s, c->p.dt, sizeof(R) == 4, padded);
+            mln::batch_pack(b->pat[c->p.N], c->s, c->p.dt, sizeof(R) == 4, padded, b->df32);
         } else if (!pad_consts<R>(c->p.N, c->consts, padded)) {
             b->err = "batch: no padded constants for this N";
             return MLN_EUNSUPPORTED;
@@ -457,13 +458,16 @@ mln_status mln_batch_create(int32_t count, const mln_params *params, void *const
         mln::create_error() = "invalid batch arguments";
         return MLN_EINVAL;
     }
+    const bool df32 = params[0].kernel == MLN_KERNEL_DF32;
     for (int32_t i = 0; i < count; ++i) {
         const mln_params &p = params[i];
         if (p.precision != params[0].precision || p.form != MLN_FORM_MERGED || p.N > mln::kBatchMaxN ||
             p.maxwell != MLN_MAXWELL_FDTD ||
-            (p.kernel != MLN_KERNEL_AUTO && p.kernel != MLN_KERNEL_REGISTER && p.kernel != MLN_KERNEL_JIT)) {
+            (df32 ? (p.kernel != MLN_KERNEL_DF32 || p.precision != MLN_FP64)
+                  : (p.kernel != MLN_KERNEL_AUTO && p.kernel != MLN_KERNEL_REGISTER && p.kernel != MLN_KERNEL_JIT))) {
             mln::create_error() = "batch grids need one precision, MLN_FORM_MERGED, MLN_MAXWELL_FDTD, N <= 4 and kernel AUTO, "
-                                  "REGISTER or JIT (grid " + std::to_string(i) + ")";
+                                  "REGISTER or JIT, or MLN_KERNEL_DF32 with MLN_FP64 for every grid (grid " +
+                                  std::to_string(i) + ")";
             return MLN_EINVAL;
         }
         if (p.source_kind != MLN_SRC_NONE && src_len > 0 && (!src || !src[i])) {
@@ -474,6 +478,7 @@ mln_status mln_batch_create(int32_t count, const mln_params *params, void *const
     mln_batch *b = new (std::nothrow) mln_batch();
     if (!b) return MLN_ENOMEM;
     b->precision = params[0].precision;
+    b->df32 = df32;
     b->user = static_cast<cudaStream_t>(stream);
     b->src_len = src_len;
     if (cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) != cudaSuccess ||
@@ -500,11 +505,19 @@ mln_status mln_batch_create(int32_t count, const mln_params *params, void *const
     // Cell model per N: the run-time compiled kernel over the union sparsity
     // pattern of that N's grids unless a grid asks for the register model
     // (MLN_KERNEL_REGISTER); MLN_KERNEL_JIT makes its absence an error.
-    bool want_jit = true, need_jit = false;
+    bool want_jit = true, need_jit = df32;
     for (int32_t i = 0; i < count; ++i) {
         want_jit = want_jit && params[i].kernel != MLN_KERNEL_REGISTER;
         need_jit = need_jit || params[i].kernel == MLN_KERNEL_JIT;
     }
+    if (df32)
+        for (int32_t i = 0; i < count; ++i)
+            if (!mln::df_constants_in_range(b->ctx[i]->s, params[i].dt)) {
+                mln::create_error() = "grid " + std::to_string(i) +
+                                      ": MLN_KERNEL_DF32: a constant of the step is outside the double-float range";
+                mln_batch_destroy(b);
+                return MLN_EUNSUPPORTED;
+            }
     std::string why;
     if (want_jit && mln::jit_available(&why)) {
         const bool fp32 = b->precision == MLN_FP32;
@@ -512,7 +525,7 @@ mln_status mln_batch_create(int32_t count, const mln_params *params, void *const
         for (int N = 2; N <= mln::kBatchMaxN; ++N) {
             if (b->pat[N].N == 0) continue;
             std::string log;
-            const std::string src_n = mln::jit_batch_source(b->pat[N], fp32);
+            const std::string src_n = mln::jit_batch_source(b->pat[N], fp32, df32);
             if (mln::jit_compile(src_n, &b->jit[N], log, "mln_jit_batch") != cudaSuccess ||
                 mln::jit_compile(src_n, &b->jitp[N], log, "mln_jit_batch_persist") != cudaSuccess) {
                 b->jit[N] = b->jitp[N] = nullptr;
@@ -523,7 +536,8 @@ mln_status mln_batch_create(int32_t count, const mln_params *params, void *const
     if (need_jit) {
         for (mln_ctx *c : b->ctx)
             if (!b->jit[c->p.N]) {
-                mln::create_error() = "run-time compiled batch kernel unavailable: " + why;
+                mln::create_error() = std::string(df32 ? "double-float" : "run-time compiled") +
+                                      " batch kernel unavailable: " + why;
                 mln_batch_destroy(b);
                 return MLN_EUNSUPPORTED;
             }
@@ -659,6 +673,7 @@ const char *mln_batch_error(const mln_batch *b) { return b ? b->err.c_str() : ""
 
 int32_t mln_batch_kernel_in_use(const mln_batch *b, int32_t N) {
     if (!b || N < 2 || N > mln::kBatchMaxN || b->item_cnt[N] == 0) return -1;
+    if (b->jit[N] && b->df32) return MLN_KERNEL_DF32;
     return b->jit[N] ? MLN_KERNEL_JIT : MLN_KERNEL_REGISTER;
 }
 
@@ -686,7 +701,7 @@ mln_status mln_batch_kernel_source(int32_t count, const mln_params *params, int3
         mln::create_error() = "no grid with this N";
         return MLN_EINVAL;
     }
-    const std::string src = mln::jit_batch_source(pat, fp32);
+    const std::string src = mln::jit_batch_source(pat, fp32, params[0].kernel == MLN_KERNEL_DF32);
     if (len) *len = src.size();
     if (buf && cap > 0) {
         const size_t k = std::min(cap - 1, src.size());

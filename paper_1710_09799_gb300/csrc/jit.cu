@@ -391,10 +391,15 @@ int batch_consts_count(const BatchPattern &pat) {
     return n;
 }
 
-void batch_pack(const BatchPattern &pat, const Setup &s, double dt, bool fp32, std::vector<unsigned char> &out) {
+void batch_pack(const BatchPattern &pat, const Setup &s, double dt, bool fp32, std::vector<unsigned char> &out,
+                bool df) {
     out.clear();
     batch_walk(pat, &s, dt, [&](double x) {
-        if (fp32) {
+        if (df) {  // the (hi, lo) FP32 pair of the double
+            const float f[2] = {static_cast<float>(x), static_cast<float>(x - static_cast<double>(static_cast<float>(x)))};
+            const unsigned char *b = reinterpret_cast<const unsigned char *>(f);
+            out.insert(out.end(), b, b + 8);
+        } else if (fp32) {
             const float f = static_cast<float>(x);
             const unsigned char *b = reinterpret_cast<const unsigned char *>(&f);
             out.insert(out.end(), b, b + 4);
@@ -406,7 +411,10 @@ void batch_pack(const BatchPattern &pat, const Setup &s, double dt, bool fp32, s
     out.resize((out.size() + 15) / 16 * 16, 0);
 }
 
-std::string jit_batch_source(const BatchPattern &pat, bool fp32) {
+std::string jit_batch_df_source(const BatchPattern &pat);
+
+std::string jit_batch_source(const BatchPattern &pat, bool fp32, bool df) {
+    if (df) return jit_batch_df_source(pat);
     const int N = pat.N, D = N * N - 1, P = N * (N - 1);
     const char *R = fp32 ? "float" : "double";
     const int nc = batch_consts_count(pat);
@@ -508,6 +516,121 @@ std::string jit_batch_source(const BatchPattern &pat, bool fp32) {
          "BatchPersist p) {\n"
       << "  extern __shared__ __align__(16) unsigned char smem_raw[];\n"
       << "  batch_persistent<" << N << ", " << R << ", JitBatchCell, " << (pat.flags == ~0u ? 0u : pat.flags)
+      << "u>(grids, items, consts, halo, tile, step_offset, p, smem_raw);\n}\n"
+      << "}  // namespace mln\n";
+    return o.str();
+}
+
+// The batched step of the FP64 grids of one N in double-float pairs (the
+// step of jit_df_source with each grid's constants as (hi, lo) pairs staged
+// by batch_pack, over the union pattern: a term whose constant is zero for a
+// grid leaves that grid's pair sums unchanged).
+std::string jit_batch_df_source(const BatchPattern &pat) {
+    const int N = pat.N, D = N * N - 1, P = N * (N - 1);
+    const int nc = batch_consts_count(pat);
+    const bool regs = 2 * nc <= 176;  // pairs in registers, as FP64 words
+    const int ncp = (nc * 8 + 15) / 16 * 16 / 8;
+    std::vector<int> iT(static_cast<size_t>(D) * P, -1), iW(D, -1), iB(D, -1), iC(static_cast<size_t>(D) * D, -1);
+    std::vector<int> iPsi(N - 1);
+    int idx = 0, iCm = -1;
+    for (int i = 0; i < D; ++i)
+        for (int p = 0; p < P; ++p)
+            if (pat.t[i * P + p] || pat.tt[p * D + i]) iT[i * P + p] = idx++;
+    for (int a = 0; a < N - 1; ++a) iPsi[a] = idx++;
+    iCm = idx++;
+    for (int i = 0; i < D; ++i)
+        if (pat.wm[i]) iW[i] = idx++;
+    for (int i = 0; i < D; ++i) {
+        iB[i] = idx++;
+        for (int j = 0; j < D; ++j)
+            if (pat.c1[i * D + j]) iC[i * D + j] = idx++;
+    }
+    auto C = [&](int k) { return std::string(regs ? "c[" : "k.c[") + std::to_string(k) + "]"; };
+    // dst = init (+ b) + sum of the pattern's terms, normalised once
+    auto row = [&](std::ostringstream &o, const std::string &dst, const std::string &init, int ib,
+                   const std::vector<std::pair<int, std::string>> &terms) {
+        o << "    { float ah = 0.0f, al = 0.0f;";
+        bool started = false;
+        if (!init.empty()) {
+            o << " ah = " << init << ".h; al = " << init << ".l;";
+            started = true;
+        }
+        if (ib >= 0) {
+            o << (started ? " df_add(ah, al, " + C(ib) + ".h, " + C(ib) + ".l);"
+                          : " ah = " + C(ib) + ".h; al = " + C(ib) + ".l;");
+            started = true;
+        }
+        for (const auto &t : terms) {
+            o << "\n      " << (started ? "df_acc" : "df_first") << "(ah, al, " << C(t.first) << ".h, " << C(t.first)
+              << ".l, " << t.second << ");";
+            started = true;
+        }
+        o << "\n      " << dst << " = df_norm(ah, al); }\n";
+    };
+    std::ostringstream o;
+    o << "#define MLN_JIT 1\n"
+      << "#ifdef __CUDACC_RTC__\ntypedef long long int64_t;\ntypedef int int32_t;\ntypedef unsigned int uint32_t;\n#endif\n"
+      << kKernelsSource << "\nnamespace mln {\n"
+      << "struct JitBatchConsts { Df c[" << ncp << "]; };\n"
+      << "struct JitBatchCell {\n  static constexpr int D = " << D << ";\n  using Consts = JitBatchConsts;\n"
+      << "  using Field = Df;\n  Df s[D];\n";
+    if (regs) o << "  Df c[" << nc << "];\n";
+    o << "  __device__ __forceinline__ void setup(unsigned char *, const Consts &k) {";
+    if (regs) o << " for (int i = 0; i < " << nc << "; ++i) c[i] = k.c[i];";
+    o << " }\n"
+      << "  __device__ __forceinline__ void load(const double *src, int64_t stride, int64_t m) { for (int i = 0; i < D; "
+         "++i) s[i] = df_of(src[i * stride + m]); }\n"
+      << "  __device__ __forceinline__ void load_cg(const double *src, int64_t stride, int64_t m) { for (int i = 0; i < "
+         "D; ++i) s[i] = df_of(__ldcg(src + i * stride + m)); }\n"
+      << "  __device__ __forceinline__ void store(double *dst, int64_t stride, int64_t m) const { for (int i = 0; i < "
+         "D; ++i) dst[i * stride + m] = df_value(s[i]); }\n"
+      << "  __device__ __forceinline__ void end_step() {}\n"
+      << "  __device__ __forceinline__ Df step(Df e, const Consts &k) {\n"
+      << "    Df z[D], y[D];\n";
+    for (int k = 0; k < P; ++k) {
+        std::vector<std::pair<int, std::string>> t;
+        for (int i = 0; i < D; ++i)
+            if (pat.tt[k * D + i]) t.push_back({iT[i * P + k], "s[" + std::to_string(i) + "]"});
+        row(o, "z[" + std::to_string(k) + "]", "", -1, t);
+    }
+    for (int k = P; k < D; ++k) o << "    z[" << k << "] = Df{0.0f, 0.0f};\n";
+    o << "    const float psi_h[" << (N - 1) << "] = {";
+    for (int a = 0; a < N - 1; ++a) o << (a ? ", " : "") << C(iPsi[a]) << ".h";
+    o << "}, psi_l[" << (N - 1) << "] = {";
+    for (int a = 0; a < N - 1; ++a) o << (a ? ", " : "") << C(iPsi[a]) << ".l";
+    o << "};\n    df_rotation_increment<" << N << ">(z, psi_h, psi_l, e);\n";
+    for (int i = 0; i < D; ++i) {
+        std::vector<std::pair<int, std::string>> t;
+        for (int p = 0; p < P; ++p)
+            if (pat.t[i * P + p]) t.push_back({iT[i * P + p], "z[" + std::to_string(p) + "]"});
+        row(o, "y[" + std::to_string(i) + "]", "s[" + std::to_string(i) + "]", -1, t);
+    }
+    {
+        std::vector<std::pair<int, std::string>> t;
+        for (int i = 0; i < D; ++i)
+            if (pat.wm[i]) t.push_back({iW[i], "y[" + std::to_string(i) + "]"});
+        o << "    Df dpdt;\n";
+        row(o, "dpdt", "", iCm, t);
+    }
+    for (int i = 0; i < D; ++i) {
+        std::vector<std::pair<int, std::string>> t;
+        for (int j = 0; j < D; ++j)
+            if (pat.c1[i * D + j]) t.push_back({iC[i * D + j], "y[" + std::to_string(j) + "]"});
+        row(o, "s[" + std::to_string(i) + "]", "y[" + std::to_string(i) + "]", iB[i], t);
+    }
+    const unsigned flags = pat.flags == ~0u ? 0u : pat.flags;
+    o << "    return dpdt;\n  }\n};\n"
+      << "extern \"C\" __global__ void __launch_bounds__(kBatchThreads, 1) mln_jit_batch(const BatchGrid<double> *grids, "
+         "const BatchItem *items, const unsigned char *consts, int parity, int nsteps, int halo, int tile, "
+         "int64_t step_offset) {\n"
+      << "  extern __shared__ __align__(16) unsigned char smem_raw[];\n"
+      << "  batch_body<" << N << ", double, JitBatchCell, " << flags
+      << "u>(grids, items, consts, parity, nsteps, halo, tile, step_offset, smem_raw);\n}\n"
+      << "extern \"C\" __global__ void __launch_bounds__(kBatchThreads, 1) mln_jit_batch_persist(const BatchGrid<double> "
+         "*grids, const BatchItem *items, const unsigned char *consts, int halo, int tile, int64_t step_offset, "
+         "BatchPersist p) {\n"
+      << "  extern __shared__ __align__(16) unsigned char smem_raw[];\n"
+      << "  batch_persistent<" << N << ", double, JitBatchCell, " << flags
       << "u>(grids, items, consts, halo, tile, step_offset, p, smem_raw);\n}\n"
       << "}  // namespace mln\n";
     return o.str();

@@ -47,12 +47,15 @@ void batch_pattern_add(BatchPattern &pat, const Setup &s, const mln_params &p, b
 // Number of constants of one grid in the pattern's compacted order.
 int batch_consts_count(const BatchPattern &pat);
 // One grid's constants in that order (precision's reals, padded to 16 bytes).
-void batch_pack(const BatchPattern &pat, const Setup &s, double dt, bool fp32, std::vector<unsigned char> &out);
+// df: each constant as the (hi, lo) FP32 pair of double-float arithmetic (8 bytes).
+void batch_pack(const BatchPattern &pat, const Setup &s, double dt, bool fp32, std::vector<unsigned char> &out,
+                bool df = false);
 // Source of the batched step kernel for the pattern's N (kernel mln_jit_batch):
 // the products over the pattern's entries only, same order as the register
 // model; each grid's constants are staged in shared memory and, when they
 // fit, held in registers for the launch.
-std::string jit_batch_source(const BatchPattern &pat, bool fp32);
+// df: the FP64 grids' step in double-float pairs (MLN_KERNEL_DF32), constants as pairs.
+std::string jit_batch_source(const BatchPattern &pat, bool fp32, bool df = false);
 cudaError_t jit_launch_batch(void *fn, const void *grids, const void *items, const void *consts, int parity,
                              int nsteps, int halo, int tile, int64_t step_offset, unsigned nblocks, unsigned threads,
                              size_t smem, cudaStream_t st);

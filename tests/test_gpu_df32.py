@@ -15,7 +15,7 @@ import numpy as np
 import pytest
 
 import workloads as W
-from helpers import gpu_run, rel_inf
+from helpers import gpu_run, make_solver, params_of, rel_inf, src_tensor
 
 pytestmark = pytest.mark.gpu
 
@@ -126,3 +126,39 @@ def test_launch_shape_does_not_change_the_bits():
         runs.append((E, H, rho))
     for E, H, rho in runs[1:]:
         assert np.array_equal(E, runs[0][0]) and np.array_equal(H, runs[0][1]) and np.array_equal(rho, runs[0][2])
+
+
+def test_batch_of_double_float_grids(orc):
+    """A batch of MLN_KERNEL_DF32 grids (N = 2, 3, 4, the batch kernels over
+    the union pattern with the constants staged as pairs) gives the bits of
+    each grid stepped alone in pairs at the same steps per launch (16, the
+    batch's default; the calls split alike), and stays within 1e-10 of the
+    oracle."""
+    from paper_1710_09799_gb300 import mln
+    devs = W.batched_devices(count=7, n_steps=260, seed=3, min_cells=100, max_cells=3000)
+    assert {p.N for p in devs} == {2, 3, 4}
+    pars = [params_of(p, precision="fp64", form="merged", kernel="df32") for p in devs]
+    srcs = [p.source_samples(0, 260) for p in devs]
+    has = any(x is not None for x in srcs)
+    b = mln.Batch(pars, [p.e_init() for p in devs], srcs if has else None, 260 if has else 0)
+    for N in (2, 3, 4):
+        assert b.kernel_in_use(N) == "df32"
+    assert b.shape[0] == 16
+    b.step(256)
+    b.step(4)
+    b.sync()
+    for i, p in enumerate(devs):
+        s = make_solver(p, "fp64", "merged", kernel="df32", block_steps=16)
+        s.step(256, src_tensor(p, 0, 256))
+        s.step(4, src_tensor(p, 256, 4))
+        s.sync()
+        E0, H0 = s.fields()
+        r0 = s.rho()
+        s.close()
+        E1, H1 = b.fields(i)
+        assert np.array_equal(E0, E1) and np.array_equal(H0, H1), (i, p.name)
+        assert np.array_equal(r0, b.rho(i)), (i, p.name)
+        if i < 2:
+            ref, _ = orc.run(p.with_(n_steps=260), n_steps=260)
+            assert rel_inf(E1, ref.E) < TOL and np.abs(b.rho(i) - ref.rho).max() < TOL, (i, p.name)
+    b.close()

@@ -193,3 +193,23 @@ def test_double_float_needs_fp64_merged(lib, kw):
     with pytest.raises(mln.MLNError) as ei:
         mln.mln_kernel_source(params_of(p, kernel="df32", **kw))
     assert ei.value.status == mln.MLN_EINVAL
+
+
+@pytest.mark.parametrize("N", [2, 3, 4])
+def test_double_float_batch_source_compiles(lib, tmp_path, N):
+    """The batch kernels of MLN_KERNEL_DF32 grids: pair constants, pair cell
+    and field update, valid CUDA for sm_103a."""
+    nvcc = shutil.which("nvcc") or "/usr/local/cuda/bin/nvcc"
+    if not os.path.exists(nvcc):
+        pytest.skip("nvcc not found")
+    devs = W.batched_devices(count=12, n_steps=10)
+    pars = [params_of(d, precision="fp64", form="merged", kernel="df32") for d in devs]
+    if not any(d.N == N for d in devs):
+        pytest.skip(f"no {N}-level grid in the sample")
+    src = mln.mln_batch_kernel_source(pars, N)
+    assert "using Field = Df;" in src and "Df c[" in src and "df_rotation_increment<%d>" % N in src
+    f = tmp_path / "b.cu"
+    f.write_text(src)
+    r = subprocess.run([nvcc, "-gencode", "arch=compute_103a,code=sm_103a", "-std=c++17", "-c", str(f),
+                        "-o", str(tmp_path / "b.o")], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr[-3000:]
