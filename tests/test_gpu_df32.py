@@ -162,3 +162,24 @@ def test_batch_of_double_float_grids(orc):
             ref, _ = orc.run(p.with_(n_steps=260), n_steps=260)
             assert rel_inf(E1, ref.E) < TOL and np.abs(b.rho(i) - ref.rho).max() < TOL, (i, p.name)
     b.close()
+
+
+def test_full_size_ring_in_the_benchmark_shape(orc):
+    """The full 65536-cell ring in pairs, in the launch shape the benchmark
+    times (autotuned), over calls that split the launches unevenly; cells
+    sampled across tiles are recomputed by the oracle from their light cones."""
+    p = W.three_level_ring()
+    s = make_solver(p, "fp64", "merged", kernel="df32")
+    s.autotune(2)
+    K, tile, _ = s.launch_shape
+    s.step(137)
+    s.step(63)
+    s.sync()
+    E, H = s.fields()
+    rho = s.rho()
+    s.close()
+    for c in (0, tile - 1, tile, 30000, 65535):
+        e, h, r = orc.run_window(p, c, 200)
+        assert abs(E[c] - e) <= TOL * np.abs(E).max(), (K, tile, c)
+        assert abs(H[c] - h) <= TOL * np.abs(H).max(), (K, tile, c)
+        assert np.abs(rho[c] - r).max() < TOL, (K, tile, c)
