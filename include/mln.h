@@ -76,7 +76,8 @@ enum { MLN_FP64 = 0, MLN_FP32 = 1 };
  * the six-level model: 2750 against 6919 flops per cell update), more where
  * T is sparse and C is not (the three-level ring: 199 against 179). Same
  * result up to rounding. Runs on the run-time compiled kernel
- * (MLN_KERNEL_JIT) or, in FP32 with N = 5 or 6, on the tensor cores
+ * (MLN_KERNEL_JIT; in FP64 also in double-float pairs, MLN_KERNEL_DF32) or,
+ * in FP32 with N = 5 or 6, on the tensor cores
  * (MLN_KERNEL_TENSOR, which MLN_KERNEL_AUTO picks there), with the FDTD field
  * solver, single grids (no batches, adjoint or allocation-free step). */
 enum { MLN_FORM_STRANG = 0, MLN_FORM_MERGED = 1, MLN_FORM_RODRIGUES = 2, MLN_FORM_ROTATED = 3 };
@@ -108,7 +109,7 @@ enum { MLN_FORM_STRANG = 0, MLN_FORM_MERGED = 1, MLN_FORM_RODRIGUES = 2, MLN_FOR
  * larger values are an error with MLN_KERNEL_TENSOR and are capped at 32 when
  * MLN_KERNEL_AUTO picks it), tiles of 128 - 2 block_steps cells; tile_cells is
  * ignored. */
-/* MLN_KERNEL_DF32 (MLN_FP64, merged form, FDTD) is the run-time
+/* MLN_KERNEL_DF32 (MLN_FP64, merged form or rotated basis, FDTD) is the run-time
  * compiled step of MLN_KERNEL_JIT in double-float arithmetic (also for the
  * grids of a batch, mln_batch_create): every value of
  * the step (the cell update's products, plane rotation and dP/dt, and the
@@ -118,7 +119,8 @@ enum { MLN_FORM_STRANG = 0, MLN_FORM_MERGED = 1, MLN_FORM_RODRIGUES = 2, MLN_FOR
  * Not the FP64 bits, and the rounding of the pairs (2^-48 against 2^-53)
  * adds up in the field recurrence: against the FP64 oracle, E_z within
  * 9e-13 on the three-level ring after 1500 steps, 5e-11 on the two-level
- * grid after 20000 steps, 1.1e-10 on a six-level grid (D = 35) after 400.
+ * grid after 20000 steps, on a six-level grid (D = 35) after 400 1.1e-10
+ * (merged form) and 5e-11 (rotated basis, blocks of at most 256 threads).
  * Rotation angles above 2^-12 are evaluated in FP64. MLN_EUNSUPPORTED
  * without NVRTC or when a constant of the step lies outside the pair's range
  * (above 1e37, or non-zero below 1e-30 in magnitude). Never chosen by

@@ -344,7 +344,7 @@ mln_status mln_kernel_source(const mln_params *p, char *buf, size_t cap, size_t 
     }
     const std::string src =
         p->kernel == MLN_KERNEL_DF32
-            ? mln::jit_df_source(s, p->dt, mln::jit_body_flags(*p))
+            ? mln::jit_df_source(s, p->dt, mln::jit_body_flags(*p), p->form == MLN_FORM_ROTATED)
             : mln::jit_merged_source(s, p->dt, p->precision == MLN_FP32, p->form == MLN_FORM_ROTATED,
                                      mln::jit_body_flags(*p));
     if (len) *len = src.size();
@@ -680,15 +680,16 @@ mln_status mln_create(const mln_params *p, void *d_state, void *Ez, void *Hy, vo
                               (p->kernel == MLN_KERNEL_AUTO && p->precision == MLN_FP32 && p->form == MLN_FORM_MERGED &&
                                p->maxwell == MLN_MAXWELL_FDTD);
         if (ok && p->kernel == MLN_KERNEL_DF32) {
-            // the cell update in double-float arithmetic: run-time compiled or nothing
+            // the step in double-float arithmetic: run-time compiled or nothing
             std::string why, log;
             cudaError_t e = cudaErrorNotSupported;
-            if (!mln::df_constants_in_range(c->s, p->dt)) {
+            if (!mln::df_constants_in_range(c->s, p->dt, rotated)) {
                 c->err = "MLN_KERNEL_DF32: a constant of the step is outside the double-float range";
                 return fail(MLN_EUNSUPPORTED);
             }
             if (mln::jit_available(&why))
-                e = mln::jit_compile(mln::jit_df_source(c->s, p->dt, mln::jit_body_flags(*p)), &c->jit_fn, log);
+                e = mln::jit_compile(mln::jit_df_source(c->s, p->dt, mln::jit_body_flags(*p), rotated), &c->jit_fn,
+                                     log);
             else
                 log = why;
             if (e != cudaSuccess) {
@@ -697,6 +698,7 @@ mln_status mln_create(const mln_params *p, void *d_state, void *Ez, void *Hy, vo
                 return fail(MLN_EUNSUPPORTED);
             }
             c->df32 = true;
+            c->max_threads = mln::df_threads(c->s.D, rotated);
         } else if (ok && want_jit) {
             std::string why, log;
             cudaError_t e = cudaErrorNotSupported;

@@ -271,23 +271,28 @@ void df_row(std::ostringstream &o, const std::vector<double> &A, int ld, int i, 
 
 }  // namespace
 
-bool df_constants_in_range(const Setup &s, double dt) {
+int df_threads(int D, bool rotated) { return rotated && D > 15 ? 256 : kMaxThreads; }
+
+bool df_constants_in_range(const Setup &s, double dt, bool rotated) {
     auto ok = [](double v) { return v == 0.0 || (std::fabs(v) < 1e37 && std::fabs(v) > 1e-30); };
     const int D = s.D, P = 2 * s.q;
+    const std::vector<double> &Cm = rotated ? s.C1z : s.C1, &wv = rotated ? s.wz : s.wm, &bv = rotated ? s.cz : s.b2;
     for (int i = 0; i < D; ++i) {
-        for (int k = 0; k < P; ++k)
-            if (!ok(s.T[i * D + k])) return false;
+        if (!rotated)
+            for (int k = 0; k < P; ++k)
+                if (!ok(s.T[i * D + k])) return false;
         for (int j = 0; j < D; ++j)
-            if (!ok(s.C1[i * D + j])) return false;
-        if (!ok(s.wm[i]) || !ok(s.b2[i])) return false;
+            if (!ok(Cm[i * D + j])) return false;
+        if (!ok(wv[i]) || !ok(bv[i])) return false;
     }
     for (int a = 0; a < s.N - 1; ++a)
         if (!ok(s.psi[a] * dt)) return false;
     return ok(s.cm);
 }
 
-std::string jit_df_source(const Setup &s, double dt, unsigned body_flags) {
+std::string jit_df_source(const Setup &s, double dt, unsigned body_flags, bool rotated) {
     const int N = s.N, D = s.D, Q = s.q, P = 2 * Q;
+    const std::vector<double> &Cm = rotated ? s.C1z : s.C1, &wv = rotated ? s.wz : s.wm, &bv = rotated ? s.cz : s.b2;
     std::ostringstream o;
     o << "#define MLN_JIT 1\n"
       << "#ifdef __CUDACC_RTC__\ntypedef long long int64_t;\ntypedef int int32_t;\n#endif\n"
@@ -305,37 +310,50 @@ std::string jit_df_source(const Setup &s, double dt, unsigned body_flags) {
       << "  __device__ __forceinline__ void end_step() {}\n"
       << "  __device__ __forceinline__ Df step(Df e, const Consts &) {\n"
       << "    Df z[D], y[D];\n";
-    // z = T^T y on the plane rows
+    // z = T^T y on the plane rows; in the rotated form the state already is z
     std::vector<double> Tt((size_t)D * D);
     for (int i = 0; i < D; ++i)
         for (int k = 0; k < D; ++k) Tt[k * D + i] = s.T[i * D + k];
-    for (int k = 0; k < P; ++k) df_row(o, Tt, D, k, D, "s", "z[" + std::to_string(k) + "]", "");
+    for (int k = 0; k < P; ++k) {
+        if (rotated) o << "    z[" << k << "] = s[" << k << "];\n";
+        else df_row(o, Tt, D, k, D, "s", "z[" + std::to_string(k) + "]", "");
+    }
     for (int k = P; k < D; ++k) o << "    z[" << k << "] = Df{0.0f, 0.0f};\n";
     o << "    const float psi_h[" << (N - 1) << "] = {";
     for (int a = 0; a < N - 1; ++a) o << (a ? ", " : "") << df_lit(s.psi[a] * dt).h;
     o << "}, psi_l[" << (N - 1) << "] = {";
     for (int a = 0; a < N - 1; ++a) o << (a ? ", " : "") << df_lit(s.psi[a] * dt).l;
     o << "};\n    df_rotation_increment<" << N << ">(z, psi_h, psi_l, e);\n";
-    // y'' = y + T (R - I) z on the plane columns
-    for (int i = 0; i < D; ++i)
-        df_row(o, s.T, D, i, P, "z", "y[" + std::to_string(i) + "]", "s[" + std::to_string(i) + "]");
-    // dP/dt = cm + wm . y''
+    // y'' = y + T (R - I) z on the plane columns; rotated: z'' = z + (R - I) z
+    // on the plane pairs, the rest unchanged
+    for (int i = 0; i < D; ++i) {
+        const std::string si = "s[" + std::to_string(i) + "]", yi = "y[" + std::to_string(i) + "]";
+        if (!rotated)
+            df_row(o, s.T, D, i, P, "z", yi, si);
+        else if (i < P)
+            o << "    { float ah = " << si << ".h, al = " << si << ".l; df_add(ah, al, z[" << i << "].h, z[" << i
+              << "].l); " << yi << " = df_norm(ah, al); }\n";
+        else
+            o << "    " << yi << " = " << si << ";\n";
+    }
+    // dP/dt = cm + wm . y'' (rotated: wz . z'')
     {
         const DfLit k = df_lit(s.cm);
         o << "    Df dpdt;\n    { float ah = " << k.h << ", al = " << k.l << ";";
         for (int i = 0; i < D; ++i) {
-            if (s.wm[i] == 0.0) continue;
-            const DfLit w = df_lit(s.wm[i]);
+            if (wv[i] == 0.0) continue;
+            const DfLit w = df_lit(wv[i]);
             o << "\n      " << (w.has_l ? "df_acc(ah, al, " + w.h + ", " + w.l : "df_acc1(ah, al, " + w.h) << ", y["
               << i << "]);";
         }
         o << "\n      dpdt = df_norm(ah, al); }\n";
     }
-    // y = (y'' + b2) + C1 y''
+    // y = (y'' + b2) + C1 y'' (rotated: z = (z'' + c') + C1z z'')
     for (int i = 0; i < D; ++i)
-        df_row(o, s.C1, D, i, D, "y", "s[" + std::to_string(i) + "]", "y[" + std::to_string(i) + "]", s.b2[i]);
+        df_row(o, Cm, D, i, D, "y", "s[" + std::to_string(i) + "]", "y[" + std::to_string(i) + "]", bv[i]);
     o << "    return dpdt;\n  }\n};\n"
-      << "extern \"C\" __global__ void __launch_bounds__(kMaxThreads, 1) mln_jit_step(const __grid_constant__ "
+      << "extern \"C\" __global__ void __launch_bounds__(" << (df_threads(D, rotated) == kMaxThreads ? "kMaxThreads" : "256")
+      << ", 1) mln_jit_step(const __grid_constant__ "
          "BlockArgs<double> a, const __grid_constant__ JitConsts k) {\n"
       << "  extern __shared__ __align__(16) unsigned char smem_raw[];\n"
       << "  asm volatile(\"griddepcontrol.wait;\" ::: \"memory\");\n"

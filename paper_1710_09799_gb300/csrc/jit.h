@@ -15,12 +15,15 @@ namespace mln {
 // exact zeros left out), kernel name mln_jit_step.
 // rotated: the state is z = T^T y (MLN_FORM_ROTATED), else y (MLN_FORM_MERGED)
 std::string jit_merged_source(const Setup &s, double dt, bool fp32, bool rotated = false, unsigned body_flags = 0u);
-// The same step (merged form, FP64 context) with the cell update in
-// double-float arithmetic (MLN_KERNEL_DF32); kernel name mln_jit_step.
-std::string jit_df_source(const Setup &s, double dt, unsigned body_flags = 0u);
+// The same step (merged or rotated form, FP64 context) in double-float
+// arithmetic (MLN_KERNEL_DF32); kernel name mln_jit_step.
+std::string jit_df_source(const Setup &s, double dt, unsigned body_flags = 0u, bool rotated = false);
+// Threads per block that kernel is compiled for: 256 for the dense rotated
+// form (D > 15: its pair vectors need up to 255 registers), else kMaxThreads.
+int df_threads(int D, bool rotated);
 // Whether every constant of that kernel is an FP32 pair without overflow and
 // with a normal low word (zero, or 1e-30 < |v| < 1e37).
-bool df_constants_in_range(const Setup &s, double dt);
+bool df_constants_in_range(const Setup &s, double dt, bool rotated = false);
 // Flags of the fused step's block body (kBody* of kernels.cuh) for a problem:
 // its boundary, whether it has a source; the compiled kernels never record.
 unsigned jit_body_flags(const mln_params &p);

@@ -389,10 +389,11 @@ mln_status validate(const mln_params &p, std::string &err) {
         return MLN_EINVAL;
     }
     if (p.form == MLN_FORM_ROTATED &&
-        ((p.kernel != MLN_KERNEL_AUTO && p.kernel != MLN_KERNEL_JIT && p.kernel != MLN_KERNEL_TENSOR) ||
+        ((p.kernel != MLN_KERNEL_AUTO && p.kernel != MLN_KERNEL_JIT && p.kernel != MLN_KERNEL_TENSOR &&
+          p.kernel != MLN_KERNEL_DF32) ||
          p.maxwell != MLN_MAXWELL_FDTD)) {
-        err = "MLN_FORM_ROTATED runs on the run-time compiled or the tensor-core kernel (MLN_KERNEL_AUTO, "
-              "MLN_KERNEL_JIT or MLN_KERNEL_TENSOR) with MLN_MAXWELL_FDTD";
+        err = "MLN_FORM_ROTATED runs on the run-time compiled, double-float or tensor-core kernel (MLN_KERNEL_AUTO, "
+              "MLN_KERNEL_JIT, MLN_KERNEL_DF32 or MLN_KERNEL_TENSOR) with MLN_MAXWELL_FDTD";
         return MLN_EINVAL;
     }
     if (p.form == MLN_FORM_RODRIGUES && p.N > 4) {
@@ -458,9 +459,10 @@ mln_status validate(const mln_params &p, std::string &err) {
               "MLN_KERNEL_TENSOR or MLN_KERNEL_DF32";
         return MLN_EINVAL;
     }
-    if (p.kernel == MLN_KERNEL_DF32 &&
-        (p.precision != MLN_FP64 || p.form != MLN_FORM_MERGED || p.maxwell != MLN_MAXWELL_FDTD)) {
-        err = "MLN_KERNEL_DF32 needs MLN_FP64, MLN_FORM_MERGED and MLN_MAXWELL_FDTD";
+    if (p.kernel == MLN_KERNEL_DF32 && (p.precision != MLN_FP64 ||
+                                        (p.form != MLN_FORM_MERGED && p.form != MLN_FORM_ROTATED) ||
+                                        p.maxwell != MLN_MAXWELL_FDTD)) {
+        err = "MLN_KERNEL_DF32 needs MLN_FP64, MLN_FORM_MERGED or MLN_FORM_ROTATED, and MLN_MAXWELL_FDTD";
         return MLN_EINVAL;
     }
     if (p.kernel == MLN_KERNEL_TENSOR &&

@@ -8,8 +8,9 @@ three-level ring (several tiles, a ragged last tile, three calls), the
 two-level grid of the paper's first test case at full size, an open grid
 driven hard enough that the rotation angles leave the double-float series
 (above 2^-12 the angles are evaluated in FP64) and a weakly driven one that
-stays inside it, and an N = 4 problem; the N = 6 problem at 2e-10 for E_z
-and H_y (see its test); and close to the FP64 run-time compiled kernel.
+stays inside it, and an N = 4 problem; the N = 6 problem (merged form and
+rotated basis) at 2e-10 for E_z and H_y (see its test); and close to the FP64
+run-time compiled kernels.
 """
 import numpy as np
 import pytest
@@ -35,9 +36,9 @@ def pops(rho):
     return np.einsum("cii->ci", rho).real
 
 
-def check_against_oracle(orc, p, chunks=None, tol=TOL):
+def check_against_oracle(orc, p, chunks=None, tol=TOL, form="merged"):
     st, _ = orc.run(p, n_steps=p.n_steps)
-    E, H, rho, s = gpu_run(p, p.n_steps, "fp64", "merged", chunks=chunks, kernel="df32")
+    E, H, rho, s = gpu_run(p, p.n_steps, "fp64", form, chunks=chunks, kernel="df32")
     assert s.kernel_in_use == "df32"
     s.close()
     e_err, h_err = rel_inf(E, st.E), rel_inf(H, st.H)
@@ -90,13 +91,30 @@ def test_four_level_ring_against_oracle(orc):
     check_against_oracle(orc, p)
 
 
-def test_six_level_against_oracle(orc):
-    """D = 35. The populations and rho stay within 1e-10; E_z and H_y are held
-    to 2e-10: a dP/dt of 35 terms that cancel to a small sum carries the low
-    word's FP32 rounding (measured on a GB300: E 1.07e-10, where the FP64 path
-    itself is 5.7e-11 from the oracle and the pair path 5.0e-11 from FP64)."""
+@pytest.mark.parametrize("form", ["merged", "rotated"])
+def test_six_level_against_oracle(orc, form):
+    """D = 35, in the merged form and in the rotated basis (one dense pair
+    product a step, 256-thread blocks). The populations and rho stay within
+    1e-10; E_z and H_y are held to 2e-10: a dP/dt of 35 terms that cancel to
+    a small sum carries the low word's FP32 rounding (measured on a GB300,
+    merged form: E 1.07e-10, where the FP64 path itself is 5.7e-11 from the
+    oracle and the pair path 5.0e-11 from FP64)."""
     p = W.six_level_pulse(n_cells=700, n_steps=400, t0=20e-15, fwhm=10e-15)
-    check_against_oracle(orc, p.with_(medium_begin=3, medium_end=699), tol=2e-10)
+    check_against_oracle(orc, p.with_(medium_begin=3, medium_end=699), tol=2e-10, form=form)
+
+
+def test_rotated_close_to_the_fp64_kernel():
+    """The six-level step in the rotated basis in pairs against the FP64
+    rotated kernel, 4096 cells x 300 steps."""
+    p = W.six_level_pulse(n_cells=4096, n_steps=300, t0=20e-15, fwhm=10e-15)
+    E0, H0, r0, s0 = gpu_run(p, p.n_steps, "fp64", "rotated", kernel="jit")
+    E1, H1, r1, s1 = gpu_run(p, p.n_steps, "fp64", "rotated", kernel="df32")
+    assert s1.kernel_in_use == "df32" and s1.launch_shape[2] <= 256
+    s0.close()
+    s1.close()
+    print(f"df32 vs fp64, rotated: E {rel_inf(E1, E0):.2e}  rho {np.abs(r1 - r0).max():.2e}")
+    assert rel_inf(E1, E0) < 2e-10 and rel_inf(H1, H0) < 2e-10
+    assert np.abs(r1 - r0).max() < 1e-10
 
 
 def test_close_to_the_fp64_kernel():

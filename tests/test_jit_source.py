@@ -187,8 +187,8 @@ def test_double_float_source_compiles_with_one_term_per_constant(lib, tmp_path):
 
 
 @pytest.mark.parametrize("kw", [dict(precision="fp32", form="merged"), dict(precision="fp64", form="strang"),
-                                dict(precision="fp64", form="rotated")])
-def test_double_float_needs_fp64_merged(lib, kw):
+                                dict(precision="fp64", form="rodrigues"), dict(precision="fp32", form="rotated")])
+def test_double_float_needs_fp64_merged_or_rotated(lib, kw):
     p = W.three_level_ring(n_cells=1000)
     with pytest.raises(mln.MLNError) as ei:
         mln.mln_kernel_source(params_of(p, kernel="df32", **kw))
@@ -212,4 +212,24 @@ def test_double_float_batch_source_compiles(lib, tmp_path, N):
     f.write_text(src)
     r = subprocess.run([nvcc, "-gencode", "arch=compute_103a,code=sm_103a", "-std=c++17", "-c", str(f),
                         "-o", str(tmp_path / "b.o")], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr[-3000:]
+
+
+def test_double_float_rotated_source_compiles(lib, tmp_path):
+    """MLN_KERNEL_DF32 in the rotated basis (the dense six-level model): one
+    pair term per non-zero entry of C1z and wz, blocks of at most 256
+    threads, valid CUDA for sm_103a."""
+    nvcc = shutil.which("nvcc") or "/usr/local/cuda/bin/nvcc"
+    if not os.path.exists(nvcc):
+        pytest.skip("nvcc not found")
+    p = W.six_level_pulse(n_cells=600, n_steps=10)
+    src = mln.mln_kernel_source(params_of(p, precision="fp64", form="rotated", kernel="df32"))
+    body = src[src.index("struct JitCell"):]
+    assert "__launch_bounds__(256, 1)" in body and "df_rotation_increment<6>" in body
+    n_terms = body.count("df_first(") + body.count("df_first1(") + body.count("df_acc(") + body.count("df_acc1(")
+    assert 35 * 35 // 2 < n_terms <= 35 * 35 + 35
+    f = tmp_path / "k.cu"
+    f.write_text(src)
+    r = subprocess.run([nvcc, "-gencode", "arch=compute_103a,code=sm_103a", "-std=c++17", "-c", str(f),
+                        "-o", str(tmp_path / "k.o")], capture_output=True, text=True)
     assert r.returncode == 0, r.stderr[-3000:]
