@@ -67,17 +67,15 @@ FP32_FLOP_PER_CLK_SM = 256
 # (its double-float variant)
 MEASURED_TRAFFIC = {
     ("jit", "fp64", "three_level_ring", 8): (5274112.0, "ncu, --block-steps 8 --tile 432"),
-    ("jit", "fp64", "three_level_ring", 12): (5274112.0, "ncu, --block-steps 12 --tile 432"),
-    ("jit", "fp64", "three_level_ring", 16): (5274368.0, "ncu, --block-steps 16 --tile 432"),
+    ("jit", "fp64", "three_level_ring", 12): (5273856.0, "ncu, --block-steps 12 --tile 432"),
+    ("jit", "fp64", "three_level_ring", 16): (5274112.0, "ncu, --block-steps 16 --tile 432"),
     ("jit", "fp64", "three_level_ring", 20): (5274112.0, "ncu, --block-steps 20 --tile 432"),
-    # taken before jit.cu gained the batch generator in pairs; the single-grid
-    # generator (jit_df_source) and kernels.cuh are unchanged since
     ("df32", "fp64", "three_level_ring", 10): (5295104.0, "ncu, --kernel df32 --block-steps 10 --tile 108"),
 }
 # sha256 of the sources the measured kernels (the FP64 and double-float step kernels) are
 # compiled or generated from, when the counters were taken: a later change of
 # one of them makes the reported traffic null until it is measured again
-TRAFFIC_SOURCES_SHA = "6721d405a9ee0d23ac4be05d5f1fe00cc73e59b9f69ef12f86f2df4acb092def"
+TRAFFIC_SOURCES_SHA = "cc4604d1b315af890cb7c825dacbd0dd290dc4616ea0bded53b9c7668fb6e832"
 
 
 def kernel_sources_sha() -> str:
