@@ -663,7 +663,7 @@ class Batch:
         return mln_batch_autotune(self.b, trials)
 
     def kernel_in_use(self, N: int) -> str | None:
-        """Cell model of the N-level grids ("jit" or "register"), None if none."""
+        """Cell model of the N-level grids ("jit", "register" or "df32"), None if none."""
         k = lib().mln_batch_kernel_in_use(self.b, N)
         return None if k < 0 else {v: n for n, v in KERNEL.items()}[k]
 

@@ -233,3 +233,18 @@ def test_double_float_rotated_source_compiles(lib, tmp_path):
     r = subprocess.run([nvcc, "-gencode", "arch=compute_103a,code=sm_103a", "-std=c++17", "-c", str(f),
                         "-o", str(tmp_path / "k.o")], capture_output=True, text=True)
     assert r.returncode == 0, r.stderr[-3000:]
+
+
+def test_double_float_batch_needs_every_grid_on_pairs(lib):
+    """mln_batch_create takes MLN_KERNEL_DF32 only for FP64 batches whose every
+    grid asks for it; the check comes before any device work (the buffer
+    pointers below are never touched)."""
+    p = W.three_level_ring(n_cells=1000)
+    a = params_of(p, precision="fp64", form="merged", kernel="df32")
+    b = params_of(p, precision="fp64", form="merged", kernel="jit")
+    c = params_of(p, precision="fp32", form="merged", kernel="df32")
+    for pars in ([a, b], [b, a], [c, c]):
+        fake = [16] * len(pars)
+        with pytest.raises(mln.MLNError) as ei:
+            mln.mln_batch_create(pars, fake, fake, fake, None, 0, 0)
+        assert ei.value.status == mln.MLN_EINVAL
