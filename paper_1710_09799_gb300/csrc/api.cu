@@ -342,6 +342,10 @@ mln_status mln_kernel_source(const mln_params *p, char *buf, size_t cap, size_t 
         mln::create_error() = err;
         return st;
     }
+    if (p->kernel == MLN_KERNEL_DF32 && !mln::df_constants_in_range(s, p->dt, p->form == MLN_FORM_ROTATED)) {
+        mln::create_error() = "MLN_KERNEL_DF32: a constant of the step is outside the double-float range";
+        return MLN_EUNSUPPORTED;
+    }
     const std::string src =
         p->kernel == MLN_KERNEL_DF32
             ? mln::jit_df_source(s, p->dt, mln::jit_body_flags(*p), p->form == MLN_FORM_ROTATED)

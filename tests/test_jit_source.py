@@ -248,3 +248,13 @@ def test_double_float_batch_needs_every_grid_on_pairs(lib):
         with pytest.raises(mln.MLNError) as ei:
             mln.mln_batch_create(pars, fake, fake, fake, None, 0, 0)
         assert ei.value.status == mln.MLN_EINVAL
+
+
+def test_double_float_rejects_constants_outside_the_pair_range(lib):
+    """A density that makes the dP/dt coefficients exceed the FP32 range of a
+    pair's high word: MLN_EUNSUPPORTED, for the source as for mln_create."""
+    p = W.three_level_ring(n_cells=1000)
+    mln.mln_kernel_source(params_of(p, precision="fp64", form="merged", kernel="df32"))
+    with pytest.raises(mln.MLNError) as ei:
+        mln.mln_kernel_source(params_of(p.with_(N_a=1e60), precision="fp64", form="merged", kernel="df32"))
+    assert ei.value.status == mln.MLN_EUNSUPPORTED
